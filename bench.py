@@ -1,0 +1,257 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 sphere-GMRF sampler on its headline workload.
+
+Workload (default): 1024 x 2048 equiangular grid, C_l = 1/((l(l+1)+20^2)(l(l+1)+50^2))
+(p = 2), 64 realisations per step, FP64 tables, FP32 recursion + FFT, anchors every 32
+rings.  A step is one smerf_sample call: the anchor kernel and the segment kernel that
+synthesises and writes every ring.  Metric: sphere grid points per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the oracle (the FP64 CPU
+restatement of the method) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+KAPPA = [20.0, 50.0]
+AMP = 1.0
+N_THETA, N_PHI, N_REAL, ANCHOR, SEED = 1024, 2048, 64, 32, 1
+WORKLOAD = ("1024x2048 equiangular grid, C_l=1/((l(l+1)+20^2)(l(l+1)+50^2)) (p=2), 64 realisations, "
+            "FP64 tables, FP32 recursion+FFT")
+METRIC = "sphere grid points/s"
+FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample_step(n_real=1, seed=SEED):
+    """The oracle on a bounded sample of the workload: the start ring (k0) of n_real
+    realisations, including the oracle's own covariance construction for that ring."""
+    import oracle
+    order = oracle.conditioning_order(N_THETA, ANCHOR)
+    t0 = time.perf_counter()
+    oracle.sample(KAPPA, AMP, N_THETA, N_PHI, seed, n_real, H=ANCHOR, rings=order[:1])
+    return time.perf_counter() - t0, n_real * N_PHI
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    dts = []
+    for i in range(args.warmup + args.steps):
+        dt, pts = oracle_sample_step()
+        if i >= args.warmup:
+            dts.append(dt)
+    ms = 1e3 * sum(dts) / len(dts)
+    value = pts / (ms / 1e3)
+    sample = "start ring (k0=512) of 1 realisation of the workload per step (2048 points), oracle incl. its covariance sums"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_theta": N_THETA, "n_phi": N_PHI},
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gb300(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1709_10314_gb300 import SMERF_TABLES_FP64, Plan
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    plan = Plan(KAPPA, AMP, N_THETA, N_PHI, flags=SMERF_TABLES_FP64, anchor_spacing=ANCHOR)
+    info = plan.info()
+    out = torch.empty((N_REAL, N_THETA, N_PHI), dtype=torch.float32, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    seed0 = SEED + rank * N_REAL * (args.warmup + args.steps + 8)
+
+    for w in range(args.warmup):
+        plan.sample(seed0 + w * N_REAL, N_REAL, out)
+        flush.fill_(float(w))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    e0 = [ev() for _ in range(args.steps)]
+    e1 = [ev() for _ in range(args.steps)]
+    s0 = [ev() for _ in range(args.steps)]
+    s1 = [ev() for _ in range(args.steps)]
+    clk = Clocks(local_rank)
+    clk.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    for i in range(args.steps):
+        e0[i].record()
+        plan.sample_timed(seed0 + (args.warmup + i) * N_REAL, N_REAL, out, s0[i], s1[i])
+        e1[i].record()
+        flush.fill_(float(i))  # L2 flush between timed steps (outside the step events)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    step_ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / args.steps
+    seg_ms = sum(a.elapsed_time(b) for a, b in zip(s0, s1)) / args.steps
+    if world > 1:
+        t = torch.tensor([step_ms, seg_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms, seg_ms = float(t[0]), float(t[1])
+    points = N_REAL * N_THETA * N_PHI
+    value = world * points / (step_ms / 1e3)
+
+    # roofline of the segment kernel: algorithmic bytes = field written once + tables read once
+    out_bytes = points * 4
+    alg_bytes = out_bytes + info["table_bytes"]
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes / (seg_ms / 1e3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "segment_kernel_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("traffic_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # end to end through the C ABI with a host buffer (device->host copy inside)
+    host = torch.empty((N_REAL, N_THETA, N_PHI), dtype=torch.float32, pin_memory=True)
+    plan.sample_host(seed0, N_REAL, host)
+    ne = 3
+    t0 = time.perf_counter()
+    for i in range(ne):
+        plan.sample_host(seed0 + i * N_REAL, N_REAL, host)
+    e2e_s = (time.perf_counter() - t0) / ne
+    e2e_val = world * points / e2e_s
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        dt, pts = oracle_sample_step(n_real=4)
+        cpu = {"value": pts / dt, "unit": "points/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": "start ring (k0=512) of realisations 1-4 of the workload (4 x 2048 points), "
+                         "the oracle's spectral-sum covariance, Cholesky, Philox noise and naive DFT"}
+    line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_theta": N_THETA, "n_phi": N_PHI, "realisations_per_gpu": N_REAL,
+                       "anchor_spacing": ANCHOR, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed between timed steps (256 MiB write outside the step events)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "segment_kernel", "kernel_ms": seg_ms, "algorithmic_bytes": alg_bytes},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "points/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": out_bytes},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+            "setup_ms": info["setup_ms"], "table_bytes": info["table_bytes"]}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_gb300(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

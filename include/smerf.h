@@ -1,0 +1,173 @@
+/*
+ * smerf.h -- C ABI of the GB300 sampler for isotropic Gaussian Markov random fields on
+ * the sphere (Creasey & Lang, "Fast generation of isotropic Gaussian random fields on the
+ * sphere", arXiv 1709.10314).
+ *
+ * Field model.  Angular power spectrum C_l = A / prod_{i<p} (l(l+1) + kappa_i^2)
+ * (Eq. (Cl) with kappa-hat_i = kappa_i^2, times an amplitude A).  The field T on an
+ * equiangular grid of n_theta rings theta_k = pi (k + 1/2) / n_theta (k = 0 north) and
+ * n_phi longitudes phi_j = 2 pi j / n_phi is the sum of azimuthal modes
+ * g_m, m = 0..n_phi/2 (Sec. 2), each a Gaussian Markov process in z = cos(theta) whose
+ * p-dimensional state (the U-basis "derivatives", Eq. (Jmatrix_more_efficient)) is
+ * sampled ring by ring outward from the equator (Eqs. (state_space), (state_initial),
+ * Alg. 2) and synthesised per ring by a real inverse DFT with prefactor 1:
+ *     T(theta_k, phi_j) = g_0 + 2 sum_{0<m<n_phi/2} Re(g_m e^{i m phi_j}) + Re(g_{n_phi/2}) (-1)^j.
+ *
+ * Conventions shared by every entry point
+ *  - All calls return an int status (SMERF_OK or a negative SMERF_E* code); none aborts,
+ *    exits or throws.  Asynchronous calls report launch errors only; kernel faults surface
+ *    at the caller's next synchronisation.
+ *  - Device pointers are plain CUDA device addresses of the current device; `stream` is a
+ *    cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Output layout: out[r][k][j], r = realisation, k = ring (north to south), j = longitude,
+ *    row-major and dense; float, or double for plans made with SMERF_RECUR_FP64.
+ *  - Realisation r of a call draws Philox4x32-10 noise under the 64-bit key seed + r;
+ *    call c of ring k uses counter (c, k, 0, 0) (Salmon et al., SC'11).
+ */
+#ifndef SMERF_H
+#define SMERF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct smerf_plan smerf_plan;
+
+/* status codes */
+#define SMERF_OK 0
+#define SMERF_EINVAL (-1)      /* bad argument (p, kappa, sizes, pointers, flags)              */
+#define SMERF_EILLCOND (-2)    /* kappa_i^2 closer than 1e-6 relative: partial fractions cancel */
+#define SMERF_ENOMEM (-3)      /* device or host allocation failed                              */
+#define SMERF_ECUDA (-4)       /* a CUDA runtime call or kernel launch failed                    */
+#define SMERF_EUNSUPPORTED (-5) /* valid but not built (e.g. p > 2, n_phi not a power of two)   */
+
+/* plan flags */
+#define SMERF_RECUR_FP64 0x1u    /* recursion, FFT and output in FP64 (default FP32, float out)   */
+#define SMERF_TABLES_FP64 0x2u   /* store the step tables in FP64 (default: recursion precision)  */
+#define SMERF_TABLES_FP32 0x4u   /* store the step tables in FP32 (default: recursion precision)  */
+#define SMERF_ORDER_PAPER 0x8u   /* no anchor rings: every ring conditions on its inner neighbour
+                                    only, exactly Alg. 2's order (less parallelism)              */
+
+/*
+ * smerf_plan_create_ex -- build the conditional-covariance tables for one grid and spectrum
+ * (Alg. 1 and its equator-symmetric layout, Sec. 4; Sec. 3 "efficient covariance
+ * computation").  Synchronous: returns after the FP64 set-up kernels finished.
+ *
+ *   kappa[p]       p distinct values kappa_i > 0 (host pointer, read during the call)
+ *   p              number of spectrum factors, 1 <= p <= 2 (state dimension p per real chain)
+ *   A              amplitude > 0
+ *   n_theta        rings, 2 <= n_theta <= 65536
+ *   n_phi          longitudes, a power of two, 8 <= n_phi <= 32768
+ *   flags          SMERF_* plan flags
+ *   anchor_spacing H: every H-th ring of each chain is sampled first (an "anchor"); the
+ *                  rings between two anchors are then sampled conditionally on both ends,
+ *                  independently of other segments.  0 selects the default (32), and any
+ *                  H >= n_theta (or SMERF_ORDER_PAPER) means no anchors.  The anchor order
+ *                  changes the map from noise to field, not the field's law.
+ *   out_plan       receives the plan (host pointer to a pointer)
+ *
+ * The plan owns its device tables; it is immutable after creation and may be used by
+ * concurrent smerf_sample calls on different streams.  Errors: SMERF_EINVAL,
+ * SMERF_EILLCOND, SMERF_ENOMEM, SMERF_ECUDA, SMERF_EUNSUPPORTED; *out_plan is NULL then.
+ */
+int smerf_plan_create_ex(const double* kappa, int p, double A, int n_theta, int n_phi,
+                         unsigned flags, int anchor_spacing, smerf_plan** out_plan);
+
+/* smerf_plan_create -- smerf_plan_create_ex with the default anchor spacing. */
+int smerf_plan_create(const double* kappa, int p, double A, int n_theta, int n_phi,
+                      unsigned flags, smerf_plan** out_plan);
+
+/* smerf_plan_destroy -- frees the plan and its device memory.  The caller must have
+ * synchronised every stream that still uses it.  NULL is accepted. */
+int smerf_plan_destroy(smerf_plan* plan);
+
+/*
+ * smerf_sample -- draw n_samples realisations into caller-owned device memory
+ * (Alg. 2: start state at the equator ring, Markov recursion outward along both chains,
+ * per-ring real DFT).  Asynchronous on `stream`.
+ *
+ *   plan       a plan from smerf_plan_create*
+ *   seed       Philox key of realisation 0; realisation r uses seed + r
+ *   n_samples  >= 0 (0 is a no-op)
+ *   out        device pointer to n_samples * n_theta * n_phi floats (doubles with
+ *              SMERF_RECUR_FP64), 16-byte aligned
+ *   stream     cudaStream_t as void*
+ *
+ * Scratch (the anchor states, 2 * n_samples * (anchors + 1) * 2p * n_phi/2 values) is
+ * taken from the stream-ordered allocator and released on the same stream.
+ */
+int smerf_sample(const smerf_plan* plan, uint64_t seed, int n_samples, void* out, void* stream);
+
+/*
+ * smerf_sample_timed -- smerf_sample that also records two caller-owned CUDA events
+ * (cudaEvent_t as void*, may be NULL) on `stream` immediately before and after the
+ * segment kernel, the kernel that synthesises and writes the field.  For measuring that
+ * kernel's duration on the stream it runs on; otherwise identical to smerf_sample.
+ */
+int smerf_sample_timed(const smerf_plan* plan, uint64_t seed, int n_samples, void* out, void* stream,
+                       void* event_before_segments, void* event_after_segments);
+
+/*
+ * smerf_sample_host -- smerf_sample into HOST memory: allocates device output on the stream,
+ * samples, copies to `host_out` (n_samples * n_theta * n_phi elements) and synchronises the
+ * stream before returning.  For callers without device buffers; includes the copies.
+ */
+int smerf_sample_host(const smerf_plan* plan, uint64_t seed, int n_samples, void* host_out,
+                      void* stream);
+
+/*
+ * smerf_sample_batched -- n_req independent requests (plans may differ in grid, spectrum
+ * and precision) issued back to back on one stream; request i behaves exactly like
+ * smerf_sample(plans[i], seeds[i], n_samples[i], outs[i], stream).  Host arrays of length
+ * n_req; outs[i] are device pointers.
+ */
+int smerf_sample_batched(const smerf_plan* const* plans, const uint64_t* seeds,
+                         const int* n_samples, void* const* outs, int n_req, void* stream);
+
+/* Plan description, filled by smerf_plan_info. */
+typedef struct smerf_plan_info_t {
+    int p, n_theta, n_phi, n_modes;       /* n_modes = n_phi/2 + 1                              */
+    int start_ring;                        /* k0 = n_theta/2                                     */
+    int chain_len[2];                      /* rings after the start ring: [0] north, [1] south   */
+    int anchor_spacing;                    /* effective H (0 = none)                             */
+    int n_anchors[2];                      /* anchors per chain                                  */
+    int n_segments;                        /* independent segments over both chains             */
+    unsigned flags;
+    size_t table_bytes;                    /* device bytes of step + coarse + start tables      */
+    size_t scratch_bytes_per_sample;       /* anchor-state scratch per realisation              */
+    double setup_ms;                       /* wall time of the set-up kernels                   */
+} smerf_plan_info_t;
+
+int smerf_plan_info(const smerf_plan* plan, smerf_plan_info_t* info);
+
+/*
+ * smerf_plan_copy_tables -- copy one table block to host memory as FP64, for inspection.
+ *   which = 0: start factor B_eq, [p(p+1)/2][n_modes]       (chain ignored)
+ *   which = 1: step tables of chain c at position pos (1..chain_len[c]),
+ *              [2p^2 + p(p+1)/2][n_modes]: A (p x p), C (p x p), B (lower, row-major)
+ *   which = 2: coarse (anchor) tables of chain c, anchor pos (1..n_anchors[c]),
+ *              [p^2 + p(p+1)/2][n_modes]: A, B
+ * Chain 1 (south) tables act on the mirrored state S x, S = diag((-1)^q).  B factors of
+ * modes m >= 1 carry the 1/sqrt(2) of the Re and Im chains.  host_out holds
+ * rows * n_modes doubles.  Synchronous.
+ */
+int smerf_plan_copy_tables(const smerf_plan* plan, int which, int chain, int pos, double* host_out);
+
+/* Test hooks (device noise, bit-exact against any Philox4x32-10 implementation).
+ * smerf_philox_uint32: out[4*c + i] = word i of call c = 0..ncalls-1 of ring `ring` under
+ *   key64 (device pointer, 4*ncalls uint32).
+ * smerf_ring_normals: the first n normals of that ring, Box-Muller of words (0,1), (2,3),
+ *   in FP32 (fp64 = 0, float out) or FP64 (fp64 = 1, double out).  Asynchronous. */
+int smerf_philox_uint32(uint64_t key64, uint32_t ring, int64_t ncalls, uint32_t* out, void* stream);
+int smerf_ring_normals(uint64_t key64, uint32_t ring, int64_t n, int fp64, void* out, void* stream);
+
+/* Human-readable name of a status code. */
+const char* smerf_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMERF_H */

@@ -1,0 +1,325 @@
+// smerf_api.cu -- the C ABI of the GB300 sphere-GMRF sampler (declared in include/smerf.h).
+// Validation, plan layout (chains, anchors, segments), scratch management and the
+// noise test hooks.  No entry point aborts, exits or throws.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "smerf_internal.cuh"
+
+int smerf_launch_sample_ff(const smerf_plan*, uint64_t, int, void*, void*, cudaStream_t, cudaEvent_t, cudaEvent_t);
+int smerf_launch_sample_fd(const smerf_plan*, uint64_t, int, void*, void*, cudaStream_t, cudaEvent_t, cudaEvent_t);
+int smerf_launch_sample_dd(const smerf_plan*, uint64_t, int, void*, void*, cudaStream_t, cudaEvent_t, cudaEvent_t);
+int smerf_launch_sample_df(const smerf_plan*, uint64_t, int, void*, void*, cudaStream_t, cudaEvent_t, cudaEvent_t);
+
+using namespace smerf;
+
+namespace {
+
+void free_plan_memory(smerf_plan* pl)
+{
+    if (!pl) return;
+    cudaFree(pl->beq);
+    for (int c = 0; c < 2; ++c) {
+        cudaFree(pl->steps[c]);
+        cudaFree(pl->coarse[c]);
+    }
+    cudaFree(pl->tw);
+    cudaFree(pl->pre);
+    cudaFree(pl->segs_dev);
+    free(pl->segs_host);
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+__global__ void philox_kernel(uint64_t key64, uint32_t ring, int64_t ncalls, uint32_t* out)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ncalls) return;
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)j, ring, 0u, 0u), PhiloxKey{(uint32_t)key64, (uint32_t)(key64 >> 32)});
+    out[4 * j + 0] = w.x;
+    out[4 * j + 1] = w.y;
+    out[4 * j + 2] = w.z;
+    out[4 * j + 3] = w.w;
+}
+
+template <class Real>
+__global__ void normals_kernel(uint64_t key64, uint32_t ring, int64_t n, Real* out)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (4 * j >= n) return;
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)j, ring, 0u, 0u), PhiloxKey{(uint32_t)key64, (uint32_t)(key64 >> 32)});
+    Real v[4];
+    box_muller(w.x, w.y, v[0], v[1]);
+    box_muller(w.z, w.w, v[2], v[3]);
+    for (int i = 0; i < 4 && 4 * j + i < n; ++i) out[4 * j + i] = v[i];
+}
+
+}  // namespace
+
+size_t smerf_scratch_bytes(const smerf_plan* pl, int n_samples)
+{
+    const int na = pl->chain[0].n_anchors > pl->chain[1].n_anchors ? pl->chain[0].n_anchors : pl->chain[1].n_anchors;
+    const size_t rs = pl->recur64 ? 8 : 4;
+    return (size_t)2 * n_samples * (na + 1) * 2 * pl->p * (size_t)(pl->n_phi / 2) * rs;
+}
+
+int smerf_launch_sample(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch, cudaStream_t st,
+                        cudaEvent_t ev0, cudaEvent_t ev1)
+{
+    if (pl->recur64) return pl->tab64 ? smerf_launch_sample_dd(pl, seed, n, out, scratch, st, ev0, ev1)
+                                      : smerf_launch_sample_df(pl, seed, n, out, scratch, st, ev0, ev1);
+    return pl->tab64 ? smerf_launch_sample_fd(pl, seed, n, out, scratch, st, ev0, ev1)
+                     : smerf_launch_sample_ff(pl, seed, n, out, scratch, st, ev0, ev1);
+}
+
+int smerf_launch_philox(uint64_t key64, uint32_t ring, int64_t ncalls, uint32_t* out, cudaStream_t s)
+{
+    if (ncalls <= 0) return SMERF_OK;
+    philox_kernel<<<(unsigned)((ncalls + 255) / 256), 256, 0, s>>>(key64, ring, ncalls, out);
+    return cudaGetLastError() == cudaSuccess ? SMERF_OK : SMERF_ECUDA;
+}
+
+int smerf_launch_normals(uint64_t key64, uint32_t ring, int64_t n, int fp64, void* out, cudaStream_t s)
+{
+    if (n <= 0) return SMERF_OK;
+    const int64_t calls = (n + 3) / 4;
+    if (fp64) normals_kernel<double><<<(unsigned)((calls + 255) / 256), 256, 0, s>>>(key64, ring, n, (double*)out);
+    else normals_kernel<float><<<(unsigned)((calls + 255) / 256), 256, 0, s>>>(key64, ring, n, (float*)out);
+    return cudaGetLastError() == cudaSuccess ? SMERF_OK : SMERF_ECUDA;
+}
+
+extern "C" {
+
+const char* smerf_status_string(int status)
+{
+    switch (status) {
+        case SMERF_OK: return "ok";
+        case SMERF_EINVAL: return "invalid argument";
+        case SMERF_EILLCOND: return "kappa values too close (ill-conditioned partial fractions)";
+        case SMERF_ENOMEM: return "out of memory";
+        case SMERF_ECUDA: return "CUDA error";
+        case SMERF_EUNSUPPORTED: return "unsupported configuration";
+        default: return "unknown status";
+    }
+}
+
+int smerf_plan_create_ex(const double* kappa, int p, double A, int n_theta, int n_phi,
+                         unsigned flags, int anchor_spacing, smerf_plan** out_plan)
+{
+    if (!out_plan) return SMERF_EINVAL;
+    *out_plan = nullptr;
+    if (!kappa || p < 1 || p > 3) return SMERF_EINVAL;
+    if (!(A > 0.0) || !isfinite(A)) return SMERF_EINVAL;
+    if (n_theta < 2 || n_theta > 65536) return SMERF_EINVAL;
+    if (n_phi < 2 || (n_phi & 1)) return SMERF_EINVAL;
+    if ((flags & ~0xFu) != 0) return SMERF_EINVAL;
+    if ((flags & SMERF_TABLES_FP64) && (flags & SMERF_TABLES_FP32)) return SMERF_EINVAL;
+    if (anchor_spacing < 0) return SMERF_EINVAL;
+    for (int i = 0; i < p; ++i)
+        if (!(kappa[i] > 0.0) || !isfinite(kappa[i])) return SMERF_EINVAL;
+    for (int i = 0; i < p; ++i)
+        for (int j = i + 1; j < p; ++j) {
+            const double a = kappa[i] * kappa[i], b = kappa[j] * kappa[j];
+            if (fabs(a - b) < 1e-6 * fmax(a, b)) return SMERF_EILLCOND;
+        }
+    if (p > kMaxP) return SMERF_EUNSUPPORTED;
+    if (!is_pow2(n_phi) || n_phi < 8 || n_phi > 32768) return SMERF_EUNSUPPORTED;
+
+    smerf_plan* pl = new (std::nothrow) smerf_plan;
+    if (!pl) return SMERF_ENOMEM;
+    memset(pl, 0, sizeof(*pl));
+    pl->p = p;
+    for (int i = 0; i < p; ++i) pl->kappa[i] = kappa[i];
+    pl->A = A;
+    pl->n_theta = n_theta;
+    pl->n_phi = n_phi;
+    pl->n_slots = n_phi / 2;
+    pl->n_modes = n_phi / 2 + 1;
+    pl->n_modes_pad = ((pl->n_modes + 31) / 32) * 32;
+    pl->k0 = n_theta / 2;
+    pl->flags = flags;
+    pl->recur64 = (flags & SMERF_RECUR_FP64) != 0;
+    pl->tab64 = (flags & SMERF_TABLES_FP64) ? true : ((flags & SMERF_TABLES_FP32) ? false : pl->recur64);
+    int H = anchor_spacing == 0 ? kDefaultAnchor : anchor_spacing;
+    if ((flags & SMERF_ORDER_PAPER) || H >= n_theta) H = 0;
+    pl->H = H;
+    pl->chain[0].len = pl->k0;
+    pl->chain[1].len = n_theta - 1 - pl->k0;
+    for (int c = 0; c < 2; ++c) pl->chain[c].n_anchors = H > 0 ? pl->chain[c].len / H : 0;
+    cudaGetDevice(&pl->dev);
+
+    std::vector<Segment> segs;
+    for (int c = 0; c < 2; ++c) {
+        const int len = pl->chain[c].len;
+        const int nseg = H > 0 ? pl->chain[c].n_anchors + 1 : 1;
+        for (int j = 0; j < nseg; ++j) {
+            Segment s;
+            s.chain = c;
+            s.p0 = H > 0 ? j * H : 0;
+            const bool right = H > 0 && s.p0 + H <= len;
+            s.p1 = right ? s.p0 + H : len + 1;
+            s.left = j;
+            s.right = right ? j + 1 : -1;
+            if (c == 1 && s.p0 == 0 && s.p1 == 1) continue;  // nothing to write: k0 belongs to the north
+            segs.push_back(s);
+        }
+    }
+    pl->n_segments = (int)segs.size();
+    pl->segs_host = (Segment*)malloc(sizeof(Segment) * segs.size());
+    if (!pl->segs_host) { delete pl; return SMERF_ENOMEM; }
+    memcpy(pl->segs_host, segs.data(), sizeof(Segment) * segs.size());
+    int rc = SMERF_OK;
+    if (cudaMalloc(&pl->segs_dev, sizeof(Segment) * segs.size()) != cudaSuccess) rc = SMERF_ENOMEM;
+    else if (cudaMemcpy(pl->segs_dev, segs.data(), sizeof(Segment) * segs.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = SMERF_ECUDA;
+    if (rc == SMERF_OK) rc = smerf_setup_tables(pl);
+    if (rc != SMERF_OK) {
+        free_plan_memory(pl);
+        delete pl;
+        return rc;
+    }
+    *out_plan = pl;
+    return SMERF_OK;
+}
+
+int smerf_plan_create(const double* kappa, int p, double A, int n_theta, int n_phi, unsigned flags,
+                      smerf_plan** out_plan)
+{
+    return smerf_plan_create_ex(kappa, p, A, n_theta, n_phi, flags, 0, out_plan);
+}
+
+int smerf_plan_destroy(smerf_plan* plan)
+{
+    if (!plan) return SMERF_OK;
+    free_plan_memory(plan);
+    delete plan;
+    return SMERF_OK;
+}
+
+int smerf_sample(const smerf_plan* plan, uint64_t seed, int n_samples, void* out, void* stream)
+{
+    return smerf_sample_timed(plan, seed, n_samples, out, stream, nullptr, nullptr);
+}
+
+int smerf_sample_timed(const smerf_plan* plan, uint64_t seed, int n_samples, void* out, void* stream,
+                       void* event_before_segments, void* event_after_segments)
+{
+    if (!plan || n_samples < 0 || n_samples > 65535) return SMERF_EINVAL;
+    if (n_samples == 0) return SMERF_OK;
+    if (!out || ((uintptr_t)out & 15u)) return SMERF_EINVAL;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != plan->dev) return SMERF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    void* scratch = nullptr;
+    const size_t sb = smerf_scratch_bytes(plan, n_samples);
+    cudaError_t e = cudaMallocAsync(&scratch, sb, st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? SMERF_ENOMEM : SMERF_ECUDA;
+    const int rc = smerf_launch_sample(plan, seed, n_samples, out, scratch, st, (cudaEvent_t)event_before_segments,
+                                       (cudaEvent_t)event_after_segments);
+    cudaFreeAsync(scratch, st);
+    return rc;
+}
+
+int smerf_sample_host(const smerf_plan* plan, uint64_t seed, int n_samples, void* host_out, void* stream)
+{
+    if (!plan || n_samples < 0 || (n_samples > 0 && !host_out)) return SMERF_EINVAL;
+    if (n_samples == 0) return SMERF_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)n_samples * plan->n_theta * plan->n_phi * (plan->recur64 ? 8 : 4);
+    void* dout = nullptr;
+    cudaError_t e = cudaMallocAsync(&dout, bytes, st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? SMERF_ENOMEM : SMERF_ECUDA;
+    int rc = smerf_sample(plan, seed, n_samples, dout, stream);
+    if (rc == SMERF_OK && cudaMemcpyAsync(host_out, dout, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = SMERF_ECUDA;
+    cudaFreeAsync(dout, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == SMERF_OK) rc = SMERF_ECUDA;
+    return rc;
+}
+
+int smerf_sample_batched(const smerf_plan* const* plans, const uint64_t* seeds, const int* n_samples,
+                         void* const* outs, int n_req, void* stream)
+{
+    if (n_req < 0 || (n_req > 0 && (!plans || !seeds || !n_samples || !outs))) return SMERF_EINVAL;
+    for (int i = 0; i < n_req; ++i) {
+        const int rc = smerf_sample(plans[i], seeds[i], n_samples[i], outs[i], stream);
+        if (rc != SMERF_OK) return rc;
+    }
+    return SMERF_OK;
+}
+
+int smerf_plan_info(const smerf_plan* plan, smerf_plan_info_t* info)
+{
+    if (!plan || !info) return SMERF_EINVAL;
+    memset(info, 0, sizeof(*info));
+    info->p = plan->p;
+    info->n_theta = plan->n_theta;
+    info->n_phi = plan->n_phi;
+    info->n_modes = plan->n_modes;
+    info->start_ring = plan->k0;
+    for (int c = 0; c < 2; ++c) {
+        info->chain_len[c] = plan->chain[c].len;
+        info->n_anchors[c] = plan->chain[c].n_anchors;
+    }
+    info->anchor_spacing = plan->H;
+    info->n_segments = plan->n_segments;
+    info->flags = plan->flags;
+    info->table_bytes = plan->table_bytes;
+    info->scratch_bytes_per_sample = smerf_scratch_bytes(plan, 1);
+    info->setup_ms = plan->setup_ms;
+    return SMERF_OK;
+}
+
+int smerf_plan_copy_tables(const smerf_plan* plan, int which, int chain, int pos, double* host_out)
+{
+    if (!plan || !host_out || chain < 0 || chain > 1) return SMERF_EINVAL;
+    const int M = plan->p;
+    const size_t mp = plan->n_modes_pad;
+    const size_t es = plan->tab64 ? 8 : 4;
+    const unsigned char* base;
+    int rows;
+    if (which == 0) {
+        base = (const unsigned char*)plan->beq;
+        rows = tri(M);
+    } else if (which == 1) {
+        if (pos < 1 || pos > plan->chain[chain].len) return SMERF_EINVAL;
+        rows = step_elems(M);
+        base = (const unsigned char*)plan->steps[chain] + (size_t)pos * rows * mp * es;
+    } else if (which == 2) {
+        if (pos < 1 || pos > plan->chain[chain].n_anchors) return SMERF_EINVAL;
+        rows = coarse_elems(M);
+        base = (const unsigned char*)plan->coarse[chain] + (size_t)pos * rows * mp * es;
+    } else {
+        return SMERF_EINVAL;
+    }
+    std::vector<unsigned char> tmp((size_t)rows * mp * es);
+    if (cudaMemcpy(tmp.data(), base, tmp.size(), cudaMemcpyDeviceToHost) != cudaSuccess) return SMERF_ECUDA;
+    for (int r = 0; r < rows; ++r)
+        for (int m = 0; m < plan->n_modes; ++m) {
+            const size_t i = (size_t)r * mp + m;
+            host_out[(size_t)r * plan->n_modes + m] = plan->tab64 ? ((const double*)tmp.data())[i]
+                                                                  : (double)((const float*)tmp.data())[i];
+        }
+    return SMERF_OK;
+}
+
+int smerf_philox_uint32(uint64_t key64, uint32_t ring, int64_t ncalls, uint32_t* out, void* stream)
+{
+    if (ncalls < 0 || (ncalls > 0 && !out)) return SMERF_EINVAL;
+    return smerf_launch_philox(key64, ring, ncalls, out, (cudaStream_t)stream);
+}
+
+int smerf_ring_normals(uint64_t key64, uint32_t ring, int64_t n, int fp64, void* out, void* stream)
+{
+    if (n < 0 || (n > 0 && !out)) return SMERF_EINVAL;
+    return smerf_launch_normals(key64, ring, n, fp64, out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

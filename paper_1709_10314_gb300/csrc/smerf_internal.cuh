@@ -1,0 +1,147 @@
+// smerf_internal.cuh -- shared device helpers and the plan structure of the GB300
+// sphere-GMRF sampler (Creasey & Lang, arXiv 1709.10314).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+#include "../../include/smerf.h"
+
+#ifndef SMERF_PI
+#define SMERF_PI 3.14159265358979323846
+#endif
+
+namespace smerf {
+
+constexpr int kMaxP = 2;             // spectrum factors supported by the kernels
+constexpr int kDefaultAnchor = 32;   // default anchor spacing H
+
+// ------------------------------------------------------------------ plan
+struct Chain {
+    int len;          // positions 1..len after the start ring
+    int n_anchors;    // anchors at positions H, 2H, ... <= len
+};
+
+struct Segment {      // one independently sampled run of rings
+    int chain;        // 0 north, 1 south
+    int p0;           // left anchor position (0 = start ring)
+    int p1;           // one past the last position sampled here
+    int left;         // anchor index of p0 (0 = start)
+    int right;        // anchor index of p1 if p1 is an anchor, else -1
+};
+
+}  // namespace smerf
+
+struct smerf_plan {
+    int p;                 // M
+    double kappa[smerf::kMaxP];
+    double A;
+    int n_theta, n_phi, n_modes, n_modes_pad, n_slots;
+    int k0;
+    unsigned flags;
+    int H;                 // effective anchor spacing (0 = none)
+    bool recur64, tab64;
+    smerf::Chain chain[2];
+    int n_segments;
+    smerf::Segment* segs_host;
+    smerf::Segment* segs_dev;
+    // tables (TabT = double if tab64 else float)
+    void* beq;             // [tri][n_modes_pad]
+    void* steps[2];        // [len+1][E][n_modes_pad]
+    void* coarse[2];       // [n_anchors+1][Ec][n_modes_pad] (row 0 unused)
+    // FFT twiddles in the recursion precision: tw[Nc] = e^{2 pi i n / Nc}, pre[Nc] = e^{2 pi i s / n_phi}
+    void* tw;
+    void* pre;
+    size_t table_bytes;
+    double setup_ms;
+    int dev;
+};
+
+namespace smerf {
+
+__host__ __device__ constexpr int tri(int M) { return M * (M + 1) / 2; }
+__host__ __device__ constexpr int step_elems(int M) { return 2 * M * M + tri(M); }
+__host__ __device__ constexpr int coarse_elems(int M) { return M * M + tri(M); }
+
+// units: the slots whose normals fill whole Philox calls.  p = 1: 2 slots per call;
+// p = 2: 1 slot per call.
+__host__ __device__ constexpr int unit_slots(int M) { return M == 1 ? 2 : 1; }
+
+// ----------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11.
+struct PhiloxKey { uint32_t k0, k1; };
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey key)
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t k0 = key.k0, k1 = key.k1;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// ------------------------------------------------------------------ Box-Muller
+// Normals (r cos t, r sin t) with r = sqrt(-2 ln u0), t = 2 pi u1, u = (x + 1/2) 2^-32.
+// FP32: ln u0 from the hardware log2 except when 1 - u0 < 2^-10, where the log2 of a
+// rounded u0 would lose the small radius; there -ln(1 - v) = v + v^2/2 + v^3/3 + O(v^4)
+// with v = (~x + 1/2) 2^-32 exact.
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& n0, float& n1)
+{
+    float r2;
+    const uint32_t na = ~a;
+    if (na < (1u << 22)) {
+        const float v = fmaf((float)na, 0x1p-32f, 0x1p-33f);
+        r2 = 2.0f * v * fmaf(v, fmaf(v, 0.33333334f, 0.5f), 1.0f);
+    } else {
+        const float u = fmaf((float)a, 0x1p-32f, 0x1p-33f);
+        r2 = -1.3862944f * __log2f(u);  // -2 ln 2 * log2(u)
+    }
+    const float r = sqrtf(r2);
+    const float t = fmaf((float)b, 0x1p-32f, 0x1p-33f) * 6.2831855f;
+    float s, c;
+    __sincosf(t, &s, &c);
+    n0 = r * c;
+    n1 = r * s;
+}
+
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double& n0, double& n1)
+{
+    const double u0 = ((double)a + 0.5) * 0x1p-32;
+    const double u1 = ((double)b + 0.5) * 0x1p-32;
+    const double r = sqrt(-2.0 * log(u0));
+    double s, c;
+    sincospi(2.0 * u1, &s, &c);
+    n0 = r * c;
+    n1 = r * s;
+}
+
+// ------------------------------------------------------------------ complex helpers
+template <class R> struct cplx_t;
+template <> struct cplx_t<float> { using type = float2; };
+template <> struct cplx_t<double> { using type = double2; };
+template <class R> using cplx = typename cplx_t<R>::type;
+
+template <class C> __device__ __forceinline__ C cmk(decltype(C::x) a, decltype(C::x) b) { C c; c.x = a; c.y = b; return c; }
+template <class C> __device__ __forceinline__ C cadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y); }
+template <class C> __device__ __forceinline__ C csub(C a, C b) { return cmk<C>(a.x - b.x, a.y - b.y); }
+template <class C> __device__ __forceinline__ C cmul(C a, C b) { return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <class C> __device__ __forceinline__ C cconj(C a) { return cmk<C>(a.x, -a.y); }
+template <class C> __device__ __forceinline__ C cmuli(C a) { return cmk<C>(-a.y, a.x); }  // i * a
+
+}  // namespace smerf
+
+// set-up (smerf_setup.cu) and sampling (smerf_sample.cu) entry points used by smerf_api.cu
+int smerf_setup_tables(smerf_plan* plan);
+int smerf_launch_sample(const smerf_plan* plan, uint64_t seed, int n_samples, void* out,
+                        void* scratch, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
+                        cudaEvent_t ev1 = nullptr);
+size_t smerf_scratch_bytes(const smerf_plan* plan, int n_samples);
+int smerf_launch_philox(uint64_t key64, uint32_t ring, int64_t ncalls, uint32_t* out, cudaStream_t s);
+int smerf_launch_normals(uint64_t key64, uint32_t ring, int64_t n, int fp64, void* out, cudaStream_t s);

@@ -1,0 +1,481 @@
+// smerf_setup.cu -- FP64 set-up of the conditional-covariance tables on the GPU
+// (Alg. 1 of Creasey & Lang, arXiv 1709.10314, with the efficient covariance of Sec. 3).
+//
+// Everything lives in the "northern frame": a chain runs from its start angle toward the
+// north pole (theta decreasing).  The southern chain is the mirror image z -> -z of the
+// northern problem (Sec. 4: "negative values follow by symmetry"); its tables act on the
+// mirrored state S x, S = diag((-1)^q).
+//
+// Notation (Sec. 3).  kappa-hat_i = kappa_i^2 = -l_i (l_i + 1).  For integer order mu,
+//   P^mu_l(z)  = (Q_mu / mu!) t^mu F_mu(x),   P^mu_l(-z) = (Q_mu / mu!) t^-mu F_mu(1-x),
+//   t = tan(theta/2), x = sin^2(theta/2) = (1-z)/2,
+//   Q_mu = prod_{j<mu} (j(j+1) + kappa^2) = (-l)_mu (1+l)_mu,
+//   F_mu(x) = 2F1(-l, l+1; 1+mu; x)          (Eq. (Legendre_hypergeometric)),
+// whose series has positive terms with ratio (n(n+1) + kappa^2) x / ((n+1+mu)(n+1)).
+//
+// U-basis state x_q = U^q_m g_m (Eq. (Jmatrix_more_efficient)), q < p.  The solution
+// matrix regular at the north pole is U(z)_{q,i} = P^{m+q}_{l_i}(z).  Gaussian
+// conditioning (Eqs. (trans_matrix), (innov_matrix)) with the product form of the
+// cross covariance (Eq. (Jmatrix_efficient)) gives, for a northward step z1 -> z2:
+//   A = U(z2) U(z1)^{-1}                                               (transition)
+//   Q = Cov(x(z2) | x(z1)) = (A_amp / 2 pi) int_{z1}^{z2} phi phi^T ds / (1 - s^2),
+//       phi(s) = U(z2) U(s)^{-1} e_{p-1}.
+// The second form follows from the state-space model of the process: its covariance
+// operator is (2 pi D_m)^{-1} (Lemma 2.1 and the orthonormality of sqrt(2 pi) L_lm in
+// dz), D_m has leading coefficient (-1)^p (1-z^2)^p, so only the last U-component is
+// driven, with intensity A_amp / (2 pi (1 - s^2)).  It needs only the regular solution,
+// i.e. 2F1 at x <= 1/2, and has no cancellation when z1 and z2 are close.
+// The start covariance J(z0, z0) uses Eq. (Jmatrix_efficient) directly (both solutions
+// at |z0| ~ 0, where both series converge fast).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <vector>
+
+#include "smerf_internal.cuh"
+
+using namespace smerf;
+
+namespace {
+
+struct Spec {
+    int M;
+    double k2[kMaxP];     // kappa_i^2
+    double b[kMaxP];      // partial-fraction weights (Eq. (C_ell_efficient))
+    double lG0[kMaxP];    // log Gamma(1+l_i) Gamma(-l_i)
+    double A;
+    double kmax;
+    int n_theta, k0, n_modes, n_modes_pad;
+};
+
+// log of 2F1(-l, l+1; 1+mu; x) for kappa^2 = k2 (positive series).
+__device__ double log_hyp(double k2, int mu, double x)
+{
+    double s = 1.0, t = 1.0, e = 0.0;
+    for (int n = 0; n < 1000000; ++n) {
+        const double dn = (double)n;
+        const double ratio = (dn * (dn + 1.0) + k2) * x / ((dn + 1.0 + mu) * (dn + 1.0));
+        t *= ratio;
+        s += t;
+        if (t < 1e-17 * s && ratio < 0.9) break;
+        if (s > 1e250) { s *= 1e-250; t *= 1e-250; e += 575.64627324851142; }
+    }
+    return log(s) + e;
+}
+
+// ring angle of position pos in chain c, in the northern frame
+__device__ __host__ inline double chain_theta(const Spec& sp, int c, int pos)
+{
+    const int k = (c == 0) ? sp.k0 - pos : sp.n_theta - 1 - sp.k0 - pos;
+    return SMERF_PI * ((double)k + 0.5) / (double)sp.n_theta;
+}
+
+// ---------------------------------------------------------------- small matrices
+template <int M> struct Mat { double a[M][M]; };
+
+template <int M> __device__ inline Mat<M> mzero() { Mat<M> r; for (int i = 0; i < M; ++i) for (int j = 0; j < M; ++j) r.a[i][j] = 0.0; return r; }
+template <int M> __device__ inline Mat<M> meye() { Mat<M> r = mzero<M>(); for (int i = 0; i < M; ++i) r.a[i][i] = 1.0; return r; }
+template <int M> __device__ inline Mat<M> mmul(const Mat<M>& x, const Mat<M>& y)
+{
+    Mat<M> r;
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < M; ++k) s += x.a[i][k] * y.a[k][j];
+            r.a[i][j] = s;
+        }
+    return r;
+}
+template <int M> __device__ inline Mat<M> mT(const Mat<M>& x) { Mat<M> r; for (int i = 0; i < M; ++i) for (int j = 0; j < M; ++j) r.a[i][j] = x.a[j][i]; return r; }
+template <int M> __device__ inline Mat<M> madd(const Mat<M>& x, const Mat<M>& y) { Mat<M> r; for (int i = 0; i < M; ++i) for (int j = 0; j < M; ++j) r.a[i][j] = x.a[i][j] + y.a[i][j]; return r; }
+template <int M> __device__ inline Mat<M> msym(const Mat<M>& x) { Mat<M> r; for (int i = 0; i < M; ++i) for (int j = 0; j < M; ++j) r.a[i][j] = 0.5 * (x.a[i][j] + x.a[j][i]); return r; }
+
+// inverse of a general M x M matrix (M <= 2)
+template <int M> __device__ inline Mat<M> minv(const Mat<M>& x);
+template <> __device__ inline Mat<1> minv<1>(const Mat<1>& x) { Mat<1> r; r.a[0][0] = 1.0 / x.a[0][0]; return r; }
+template <> __device__ inline Mat<2> minv<2>(const Mat<2>& x)
+{
+    const double d = x.a[0][0] * x.a[1][1] - x.a[0][1] * x.a[1][0];
+    Mat<2> r;
+    r.a[0][0] = x.a[1][1] / d; r.a[0][1] = -x.a[0][1] / d;
+    r.a[1][0] = -x.a[1][0] / d; r.a[1][1] = x.a[0][0] / d;
+    return r;
+}
+
+// lower Cholesky factor of a symmetric positive semi-definite matrix (0 where it degenerates)
+template <int M> __device__ inline Mat<M> mchol(const Mat<M>& x)
+{
+    Mat<M> L = mzero<M>();
+    for (int j = 0; j < M; ++j) {
+        double d = x.a[j][j];
+        for (int k = 0; k < j; ++k) d -= L.a[j][k] * L.a[j][k];
+        const double ljj = d > 0.0 ? sqrt(d) : 0.0;
+        L.a[j][j] = ljj;
+        for (int i = j + 1; i < M; ++i) {
+            double s = x.a[i][j];
+            for (int k = 0; k < j; ++k) s -= L.a[i][k] * L.a[j][k];
+            L.a[i][j] = ljj > 0.0 ? s / ljj : 0.0;
+        }
+    }
+    return L;
+}
+
+// inverse of a symmetric positive definite matrix through its Cholesky factor
+template <int M> __device__ inline Mat<M> mspd_inv(const Mat<M>& x)
+{
+    if (M == 1) { Mat<M> r; r.a[0][0] = 1.0 / x.a[0][0]; return r; }
+    Mat<M> L = mchol<M>(x);
+    Mat<M> Li = mzero<M>();  // L^{-1}, lower
+    for (int i = 0; i < M; ++i) {
+        Li.a[i][i] = 1.0 / L.a[i][i];
+        for (int j = 0; j < i; ++j) {
+            double s = 0.0;
+            for (int k = j; k < i; ++k) s += L.a[i][k] * Li.a[k][j];
+            Li.a[i][j] = -s / L.a[i][i];
+        }
+    }
+    return mmul<M>(mT<M>(Li), Li);
+}
+
+// H_{q,i}(x) = r_{q,i} F^i_{m+q}(x) exp(-lsc_i); r_{q,i} = prod_{j=m}^{m+q-1} (j(j+1)+kappa_i^2)/(j+1)
+template <int M> __device__ inline Mat<M> hmat(const Spec& sp, int m, double x, const double* lsc)
+{
+    Mat<M> H;
+    for (int i = 0; i < M; ++i) {
+        double r = 1.0;
+        for (int q = 0; q < M; ++q) {
+            if (q > 0) {
+                const double j = (double)(m + q - 1);
+                r *= (j * (j + 1.0) + sp.k2[i]) / (j + 1.0);
+            }
+            H.a[q][i] = r * exp(log_hyp(sp.k2[i], m + q, x) - lsc[i]);
+        }
+    }
+    return H;
+}
+
+__constant__ double kGL8x[8] = {-0.9602898564975363, -0.7966664774136267, -0.5255324099163290, -0.1834346424956498,
+                                 0.1834346424956498,  0.5255324099163290,  0.7966664774136267,  0.9602898564975363};
+__constant__ double kGL8w[8] = {0.1012285362903763, 0.2223810344533745, 0.3137066458778873, 0.3626837833783620,
+                                0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+
+// Transition Phi and conditional covariance Q of every northward step, one thread per
+// (chain, position, mode).  phi/q: [c][pos][m][M*M] doubles (pos 1..len).
+template <int M>
+__global__ void step_kernel(Spec sp, int c, int len, double* phi, double* qout)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pos = blockIdx.y + 1;
+    if (m >= sp.n_modes || pos > len) return;
+    const double th1 = chain_theta(sp, c, pos - 1), th2 = chain_theta(sp, c, pos);
+    const double t1 = tan(0.5 * th1), t2 = tan(0.5 * th2);
+    const double u1 = log(t1), u2 = log(t2);
+    const double s1 = sin(0.5 * th1), s2 = sin(0.5 * th2);
+    const double x1 = s1 * s1, x2 = s2 * s2;
+    double lsc[M];
+    for (int i = 0; i < M; ++i) lsc[i] = log_hyp(sp.k2[i], m, x2);
+    const Mat<M> H2 = hmat<M>(sp, m, x2, lsc);
+    const Mat<M> H1 = hmat<M>(sp, m, x1, lsc);
+    // A = (t2/t1)^m diag(t2^q) H2 H1^{-1} diag(t1^-q)
+    Mat<M> A = mmul<M>(H2, minv<M>(H1));
+    const double g = exp((double)m * (u2 - u1));
+    for (int p = 0; p < M; ++p)
+        for (int q = 0; q < M; ++q) A.a[p][q] *= g * pow(t2, (double)p) / pow(t1, (double)q);
+    // W = diag(t2^(q-M+1)) H2
+    Mat<M> W = H2;
+    for (int p = 0; p < M; ++p)
+        for (int q = 0; q < M; ++q) W.a[p][q] *= pow(t2, (double)(p - M + 1));
+    // Q = A_amp/(2 pi) int_0^{du} e^{-c v} (W h)(W h)^T dv, h = H(x(u2+v))^{-1} e_{M-1}
+    const double cexp = 2.0 * (double)(m + M - 1);
+    const double du = u1 - u2;
+    const double vmax = cexp > 0.0 ? fmin(du, 46.0 / cexp) : du;
+    const double sinmax = th1 > 0.5 * SMERF_PI ? 1.0 : sin(th1);
+    const double rho = cexp + 2.0 * sp.kmax * sinmax + 1.0;
+    int nsub = (int)ceil(0.5 * rho * vmax);
+    nsub = nsub < 1 ? 1 : (nsub > 256 ? 256 : nsub);
+    const double h = vmax / nsub;
+    Mat<M> acc = mzero<M>();
+    for (int j = 0; j < nsub; ++j)
+        for (int n = 0; n < 8; ++n) {
+            const double v = (j + 0.5 * (kGL8x[n] + 1.0)) * h;
+            const double w = 0.5 * h * kGL8w[n] * exp(-cexp * v);
+            const double u = u2 + v;
+            const double x = 1.0 / (1.0 + exp(-2.0 * u));   // sin^2(theta/2), tan(theta/2) = e^u
+            const Mat<M> Hs = hmat<M>(sp, m, x, lsc);
+            const Mat<M> Hi = minv<M>(Hs);
+            double ph[M];
+            for (int p = 0; p < M; ++p) {
+                double s = 0.0;
+                for (int k = 0; k < M; ++k) s += W.a[p][k] * Hi.a[k][M - 1];
+                ph[p] = s;
+            }
+            for (int p = 0; p < M; ++p)
+                for (int q = 0; q < M; ++q) acc.a[p][q] += w * ph[p] * ph[q];
+        }
+    const double f = sp.A / (2.0 * SMERF_PI);
+    const size_t o = (((size_t)pos) * sp.n_modes + m) * (M * M);
+    for (int p = 0; p < M; ++p)
+        for (int q = 0; q < M; ++q) {
+            phi[o + p * M + q] = A.a[p][q];
+            qout[o + p * M + q] = f * acc.a[p][q];
+        }
+}
+
+template <class T>
+__device__ inline void put(void* base, bool is64, size_t idx, double v)
+{
+    if (is64) ((double*)base)[idx] = v;
+    else ((float*)base)[idx] = (float)v;
+}
+
+// Start factor B_eq = chol J(z0, z0) (Eq. (state_initial)), one thread per mode.
+template <int M>
+__global__ void start_kernel(Spec sp, void* beq, bool tab64)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= sp.n_modes) return;
+    const double th0 = SMERF_PI * ((double)sp.k0 + 0.5) / (double)sp.n_theta;
+    const double t0 = tan(0.5 * th0);
+    const double sx = sin(0.5 * th0), cx = cos(0.5 * th0);
+    const double x0 = sx * sx, xb0 = cx * cx;
+    Mat<M> J = mzero<M>();
+    for (int i = 0; i < M; ++i) {
+        const double k2 = sp.k2[i];
+        double lq = 0.0;  // log Q_m / (m!)^2
+        for (int j = 0; j < m; ++j) lq += log((j * (j + 1.0) + k2) / ((j + 1.0) * (j + 1.0)));
+        double lF0[M], lF1[M], r[M];
+        double rr = 1.0;
+        for (int q = 0; q < M; ++q) {
+            if (q > 0) {
+                const double j = (double)(m + q - 1);
+                rr *= (j * (j + 1.0) + k2) / (j + 1.0);
+            }
+            r[q] = rr;
+            lF0[q] = log_hyp(k2, m + q, x0);
+            lF1[q] = log_hyp(k2, m + q, xb0);
+        }
+        const double sb = sp.b[i] > 0.0 ? 1.0 : -1.0;
+        const double lb = log(fabs(sp.b[i])) + sp.lG0[i] - log(4.0 * SMERF_PI) + lq;
+        for (int p = 0; p < M; ++p)
+            for (int q = 0; q < M; ++q) {
+                const double v = exp(lb + lF1[p] + lF0[q]) * r[p] * r[q] * pow(t0, (double)(q - p));
+                J.a[p][q] += sb * ((p & 1) ? -v : v);
+            }
+    }
+    const Mat<M> L = mchol<M>(msym<M>(J));
+    const double sc = m > 0 ? 0.70710678118654752440 : 1.0;
+    int e = 0;
+    for (int p = 0; p < M; ++p)
+        for (int q = 0; q <= p; ++q, ++e)
+            put<double>(beq, tab64, (size_t)e * sp.n_modes_pad + m, L.a[p][q] * sc);
+}
+
+// Bridge, forward and coarse tables of one segment, one thread per (segment, mode).
+// Segment [pa, pb] with right anchor pb: for pa < pos < pb, condition x_pos on x_{pos-1}
+// (prior N(Phi x, Q)) and on x_pb = Psi x_pos + N(0, S) (Psi, S accumulated backward):
+//   P = (Q^{-1} + Psi^T S^{-1} Psi)^{-1},  Abar = P Q^{-1} Phi,  C = P Psi^T S^{-1},  B = chol P.
+// The coarse step pa -> pb is (Psi_pa, chol S_pa).  Without a right anchor the tables are
+// the plain forward step (Phi, 0, chol Q).
+template <int M>
+__global__ void segment_tables_kernel(Spec sp, int c, int len, int H, const double* phi,
+                                      const double* qv, void* steps, void* coarse, bool tab64)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int seg = blockIdx.y;
+    if (m >= sp.n_modes) return;
+    const int E = step_elems(M), Ec = coarse_elems(M);
+    const size_t mp = sp.n_modes_pad;
+    const double sc = m > 0 ? 0.70710678118654752440 : 1.0;
+    const int pa = H > 0 ? seg * H : 0;
+    const int pb = (H > 0 && pa + H <= len) ? pa + H : -1;
+    auto load = [&](const double* base, int pos) {
+        Mat<M> r;
+        const size_t o = (((size_t)pos) * sp.n_modes + m) * (M * M);
+        for (int p = 0; p < M; ++p)
+            for (int q = 0; q < M; ++q) r.a[p][q] = base[o + p * M + q];
+        return r;
+    };
+    auto store_step = [&](int pos, const Mat<M>& A, const Mat<M>& C, const Mat<M>& B) {
+        const size_t base = (size_t)pos * E * mp + m;
+        int e = 0;
+        for (int p = 0; p < M; ++p)
+            for (int q = 0; q < M; ++q, ++e) put<double>(steps, tab64, base + (size_t)e * mp, A.a[p][q]);
+        for (int p = 0; p < M; ++p)
+            for (int q = 0; q < M; ++q, ++e) put<double>(steps, tab64, base + (size_t)e * mp, C.a[p][q]);
+        for (int p = 0; p < M; ++p)
+            for (int q = 0; q <= p; ++q, ++e) put<double>(steps, tab64, base + (size_t)e * mp, B.a[p][q] * sc);
+    };
+    if (pb < 0) {
+        const int end = len;
+        for (int pos = pa + 1; pos <= end; ++pos) {
+            const Mat<M> Ph = load(phi, pos), Q = load(qv, pos);
+            store_step(pos, Ph, mzero<M>(), mchol<M>(msym<M>(Q)));
+        }
+        return;
+    }
+    Mat<M> Psi = meye<M>(), S = mzero<M>();
+    for (int pos = pb; pos > pa; --pos) {
+        const Mat<M> Ph = load(phi, pos), Q = msym<M>(load(qv, pos));
+        if (pos < pb) {
+            const Mat<M> Qi = mspd_inv<M>(Q);
+            const Mat<M> Si = mspd_inv<M>(msym<M>(S));
+            const Mat<M> PsT = mT<M>(Psi);
+            const Mat<M> P = msym<M>(mspd_inv<M>(msym<M>(madd<M>(Qi, mmul<M>(mmul<M>(PsT, Si), Psi)))));
+            const Mat<M> Ab = mmul<M>(mmul<M>(P, Qi), Ph);
+            const Mat<M> C = mmul<M>(mmul<M>(P, PsT), Si);
+            store_step(pos, Ab, C, mchol<M>(P));
+        }
+        // move to pos-1: S_{pos-1} = Psi Q Psi^T + S, Psi_{pos-1} = Psi Phi
+        S = madd<M>(mmul<M>(mmul<M>(Psi, Q), mT<M>(Psi)), S);
+        Psi = mmul<M>(Psi, Ph);
+    }
+    const Mat<M> Bc = mchol<M>(msym<M>(S));
+    const int j = pb / H;
+    const size_t base = (size_t)j * Ec * mp + m;
+    int e = 0;
+    for (int p = 0; p < M; ++p)
+        for (int q = 0; q < M; ++q, ++e) put<double>(coarse, tab64, base + (size_t)e * mp, Psi.a[p][q]);
+    for (int p = 0; p < M; ++p)
+        for (int q = 0; q <= p; ++q, ++e) put<double>(coarse, tab64, base + (size_t)e * mp, Bc.a[p][q] * sc);
+}
+
+template <class R>
+__global__ void twiddle_kernel(int Nc, int n_phi, R* tw, R* pre)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= Nc) return;
+    double s, c;
+    sincospi(2.0 * (double)n / (double)Nc, &s, &c);
+    tw[2 * n] = (R)c;
+    tw[2 * n + 1] = (R)s;
+    sincospi(2.0 * (double)n / (double)n_phi, &s, &c);
+    pre[2 * n] = (R)c;
+    pre[2 * n + 1] = (R)s;
+}
+
+#define CK(x)                                                                     \
+    do {                                                                          \
+        cudaError_t e_ = (x);                                                     \
+        if (e_ != cudaSuccess) {                                                  \
+            fprintf(stderr, "smerf setup: %s at %s:%d\n", cudaGetErrorString(e_), \
+                    __FILE__, __LINE__);                                          \
+            rc = (e_ == cudaErrorMemoryAllocation) ? SMERF_ENOMEM : SMERF_ECUDA;  \
+            goto done;                                                            \
+        }                                                                         \
+    } while (0)
+
+template <int M>
+int setup_impl(smerf_plan* pl)
+{
+    int rc = SMERF_OK;
+    Spec sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.M = M;
+    sp.A = pl->A;
+    sp.kmax = 0.0;
+    for (int i = 0; i < M; ++i) {
+        const double k = pl->kappa[i];
+        sp.k2[i] = k * k;
+        sp.kmax = fmax(sp.kmax, k);
+        double b = pl->A;
+        for (int j = 0; j < M; ++j)
+            if (j != i) b /= pl->kappa[j] * pl->kappa[j] - k * k;
+        sp.b[i] = b;
+        if (k * k > 0.25) {
+            const double nu = sqrt(k * k - 0.25);
+            sp.lG0[i] = log(SMERF_PI) - SMERF_PI * nu - log(0.5 * (1.0 + exp(-2.0 * SMERF_PI * nu)));
+        } else {
+            const double lam = -0.5 + sqrt(0.25 - k * k);
+            sp.lG0[i] = log(-SMERF_PI / sin(SMERF_PI * lam));
+        }
+    }
+    sp.n_theta = pl->n_theta;
+    sp.k0 = pl->k0;
+    sp.n_modes = pl->n_modes;
+    sp.n_modes_pad = pl->n_modes_pad;
+
+    const bool t64 = pl->tab64;
+    const size_t es = t64 ? 8 : 4;
+    const size_t mp = pl->n_modes_pad;
+    double* phi = nullptr;
+    double* qv = nullptr;
+    const int threads = 128;
+    const int gm = (pl->n_modes + threads - 1) / threads;
+    auto t_start = std::chrono::steady_clock::now();
+
+    pl->table_bytes = 0;
+    CK(cudaMalloc(&pl->beq, (size_t)tri(M) * mp * es));
+    CK(cudaMemset(pl->beq, 0, (size_t)tri(M) * mp * es));
+    pl->table_bytes += (size_t)tri(M) * mp * es;
+    for (int c = 0; c < 2; ++c) {
+        const int len = pl->chain[c].len;
+        const size_t sb = (size_t)(len + 1) * step_elems(M) * mp * es;
+        const size_t cb = (size_t)(pl->chain[c].n_anchors + 1) * coarse_elems(M) * mp * es;
+        CK(cudaMalloc(&pl->steps[c], sb > 0 ? sb : 16));
+        CK(cudaMemset(pl->steps[c], 0, sb > 0 ? sb : 16));
+        CK(cudaMalloc(&pl->coarse[c], cb > 0 ? cb : 16));
+        CK(cudaMemset(pl->coarse[c], 0, cb > 0 ? cb : 16));
+        pl->table_bytes += sb + cb;
+    }
+    {
+        const size_t rs = pl->recur64 ? 8 : 4;
+        const int Nc = pl->n_phi / 2;
+        CK(cudaMalloc(&pl->tw, (size_t)2 * Nc * rs));
+        CK(cudaMalloc(&pl->pre, (size_t)2 * Nc * rs));
+        if (pl->recur64)
+            twiddle_kernel<double><<<(Nc + 255) / 256, 256>>>(Nc, pl->n_phi, (double*)pl->tw, (double*)pl->pre);
+        else
+            twiddle_kernel<float><<<(Nc + 255) / 256, 256>>>(Nc, pl->n_phi, (float*)pl->tw, (float*)pl->pre);
+        CK(cudaGetLastError());
+    }
+    start_kernel<M><<<gm, threads>>>(sp, pl->beq, t64);
+    CK(cudaGetLastError());
+    for (int c = 0; c < 2; ++c) {
+        const int len = pl->chain[c].len;
+        if (len == 0) continue;
+        const size_t nb = (size_t)(len + 1) * pl->n_modes * M * M * sizeof(double);
+        CK(cudaMalloc(&phi, nb));
+        CK(cudaMalloc(&qv, nb));
+        // positions in chunks of the grid's y-dimension limit
+        for (int p0 = 0; p0 < len; p0 += 65535) {
+            const int cnt = (len - p0) < 65535 ? (len - p0) : 65535;
+            dim3 grid(gm, cnt);
+            // shift positions by p0 through the chain offset: launch with len and an offset
+            step_kernel<M><<<grid, threads>>>(sp, c, len, phi, qv);
+            CK(cudaGetLastError());
+            if (p0 + cnt < len) { rc = SMERF_EUNSUPPORTED; goto done; }
+        }
+        {
+            const int H = pl->H;
+            const int nseg = H > 0 ? (len / H + 1) : 1;
+            dim3 grid(gm, nseg);
+            segment_tables_kernel<M><<<grid, threads>>>(sp, c, len, H, phi, qv, pl->steps[c],
+                                                         pl->coarse[c], t64);
+            CK(cudaGetLastError());
+        }
+        CK(cudaDeviceSynchronize());
+        cudaFree(phi);
+        cudaFree(qv);
+        phi = qv = nullptr;
+    }
+    CK(cudaDeviceSynchronize());
+    pl->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+done:
+    if (phi) cudaFree(phi);
+    if (qv) cudaFree(qv);
+    return rc;
+}
+
+}  // namespace
+
+int smerf_setup_tables(smerf_plan* pl)
+{
+    switch (pl->p) {
+        case 1: return setup_impl<1>(pl);
+        case 2: return setup_impl<2>(pl);
+        default: return SMERF_EUNSUPPORTED;
+    }
+}

@@ -1,0 +1,208 @@
+"""ctypes binding of the C ABI declared in include/smerf.h (argument marshalling only).
+
+Names follow the C entry points: ``Plan`` wraps smerf_plan_create_ex / smerf_plan_info /
+smerf_plan_copy_tables / smerf_sample / smerf_sample_host / smerf_plan_destroy.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libsmerf.so")
+
+SMERF_RECUR_FP64 = 0x1
+SMERF_TABLES_FP64 = 0x2
+SMERF_TABLES_FP32 = 0x4
+SMERF_ORDER_PAPER = 0x8
+
+
+class SmerfError(RuntimeError):
+    def __init__(self, call, status):
+        self.status = status
+        msg = _lib().smerf_status_string(status).decode() if _LIB is not None else str(status)
+        super().__init__("%s failed: %s (%d)" % (call, msg, status))
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("n_theta", ctypes.c_int), ("n_phi", ctypes.c_int),
+                ("n_modes", ctypes.c_int), ("start_ring", ctypes.c_int),
+                ("chain_len", ctypes.c_int * 2), ("anchor_spacing", ctypes.c_int),
+                ("n_anchors", ctypes.c_int * 2), ("n_segments", ctypes.c_int),
+                ("flags", ctypes.c_uint), ("table_bytes", ctypes.c_size_t),
+                ("scratch_bytes_per_sample", ctypes.c_size_t), ("setup_ms", ctypes.c_double)]
+
+
+_LIB = None
+
+
+def library_path():
+    return _LIBPATH
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(_LIBPATH):
+            raise ImportError("libsmerf.so is not built: run `python -m paper_1709_10314_gb300.build` "
+                              "(there is no CPU fallback)")
+        L = ctypes.CDLL(_LIBPATH)
+        vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+        L.smerf_plan_create_ex.argtypes = [dp, ip, ctypes.c_double, ip, ip, ctypes.c_uint, ip,
+                                           ctypes.POINTER(vp)]
+        L.smerf_plan_create_ex.restype = ip
+        L.smerf_plan_destroy.argtypes = [vp]
+        L.smerf_plan_destroy.restype = ip
+        L.smerf_sample.argtypes = [vp, ctypes.c_uint64, ip, vp, vp]
+        L.smerf_sample.restype = ip
+        L.smerf_sample_timed.argtypes = [vp, ctypes.c_uint64, ip, vp, vp, vp, vp]
+        L.smerf_sample_timed.restype = ip
+        L.smerf_sample_host.argtypes = [vp, ctypes.c_uint64, ip, vp, vp]
+        L.smerf_sample_host.restype = ip
+        L.smerf_sample_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_uint64),
+                                           ctypes.POINTER(ip), ctypes.POINTER(vp), ip, vp]
+        L.smerf_sample_batched.restype = ip
+        L.smerf_plan_info.argtypes = [vp, ctypes.POINTER(_Info)]
+        L.smerf_plan_info.restype = ip
+        L.smerf_plan_copy_tables.argtypes = [vp, ip, ip, ip, dp]
+        L.smerf_plan_copy_tables.restype = ip
+        L.smerf_philox_uint32.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, vp, vp]
+        L.smerf_philox_uint32.restype = ip
+        L.smerf_ring_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ip, vp, vp]
+        L.smerf_ring_normals.restype = ip
+        L.smerf_status_string.argtypes = [ip]
+        L.smerf_status_string.restype = ctypes.c_char_p
+        _LIB = L
+    return _LIB
+
+
+def _check(call, status):
+    if status != 0:
+        raise SmerfError(call, status)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """A sampling plan (device-resident conditional-covariance tables)."""
+
+    def __init__(self, kappa, A=1.0, n_theta=64, n_phi=128, flags=0, anchor_spacing=0):
+        L = _lib()
+        k = np.ascontiguousarray(np.atleast_1d(kappa), dtype=np.float64)
+        h = ctypes.c_void_p()
+        _check("smerf_plan_create_ex",
+               L.smerf_plan_create_ex(k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(k),
+                                      float(A), int(n_theta), int(n_phi), int(flags),
+                                      int(anchor_spacing), ctypes.byref(h)))
+        self._h = h
+        self.kappa = k
+        self.A = float(A)
+        self.n_theta = int(n_theta)
+        self.n_phi = int(n_phi)
+        self.flags = int(flags)
+        self.fp64 = bool(flags & SMERF_RECUR_FP64)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib().smerf_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        inf = _Info()
+        _check("smerf_plan_info", _lib().smerf_plan_info(self._h, ctypes.byref(inf)))
+        return {"p": inf.p, "n_theta": inf.n_theta, "n_phi": inf.n_phi, "n_modes": inf.n_modes,
+                "start_ring": inf.start_ring, "chain_len": list(inf.chain_len),
+                "anchor_spacing": inf.anchor_spacing, "n_anchors": list(inf.n_anchors),
+                "n_segments": inf.n_segments, "flags": inf.flags, "table_bytes": inf.table_bytes,
+                "scratch_bytes_per_sample": inf.scratch_bytes_per_sample, "setup_ms": inf.setup_ms}
+
+    def tables(self, which, chain=0, pos=0):
+        """Copy a table block to host as float64 [rows][n_modes] (see smerf_plan_copy_tables)."""
+        p = len(self.kappa)
+        rows = {0: p * (p + 1) // 2, 1: 2 * p * p + p * (p + 1) // 2, 2: p * p + p * (p + 1) // 2}[which]
+        out = np.zeros((rows, self.n_phi // 2 + 1))
+        _check("smerf_plan_copy_tables",
+               _lib().smerf_plan_copy_tables(self._h, which, chain, pos,
+                                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.fp64 else torch.float32
+
+    def sample(self, seed, n_samples, out=None, stream=None):
+        """Device realisations [n_samples][n_theta][n_phi] (torch tensor on the current device)."""
+        import torch
+        if out is None:
+            out = torch.empty((n_samples, self.n_theta, self.n_phi), dtype=self.dtype, device="cuda")
+        assert out.is_cuda and out.is_contiguous() and out.dtype == self.dtype
+        assert out.numel() >= n_samples * self.n_theta * self.n_phi
+        _check("smerf_sample", _lib().smerf_sample(self._h, ctypes.c_uint64(seed & (2**64 - 1)), int(n_samples),
+                                                    ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def sample_timed(self, seed, n_samples, out, ev_before, ev_after, stream=None):
+        """smerf_sample_timed: records the two torch.cuda.Event objects around the segment kernel."""
+        for ev in (ev_before, ev_after):
+            if not ev.cuda_event:
+                ev.record()  # torch creates the event handle lazily
+        _check("smerf_sample_timed",
+               _lib().smerf_sample_timed(self._h, ctypes.c_uint64(seed & (2**64 - 1)), int(n_samples),
+                                         ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream),
+                                         ctypes.c_void_p(ev_before.cuda_event), ctypes.c_void_p(ev_after.cuda_event)))
+        return out
+
+    def sample_host(self, seed, n_samples, out=None, stream=None):
+        """Realisations into host memory (numpy array or pinned torch CPU tensor)."""
+        dt = np.float64 if self.fp64 else np.float32
+        if out is None:
+            out = np.empty((n_samples, self.n_theta, self.n_phi), dtype=dt)
+        ptr = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
+        _check("smerf_sample_host", _lib().smerf_sample_host(self._h, ctypes.c_uint64(seed & (2**64 - 1)),
+                                                              int(n_samples), ctypes.c_void_p(ptr),
+                                                              _stream_ptr(stream)))
+        return out
+
+
+def sample_batched(plans, seeds, n_samples, outs, stream=None):
+    n = len(plans)
+    P = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+    S = (ctypes.c_uint64 * n)(*[s & (2**64 - 1) for s in seeds])
+    N = (ctypes.c_int * n)(*[int(v) for v in n_samples])
+    O = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    _check("smerf_sample_batched", _lib().smerf_sample_batched(P, S, N, O, n, _stream_ptr(stream)))
+    return outs
+
+
+def philox_uint32(key64, ring, ncalls, stream=None):
+    import torch
+    out = torch.empty(4 * ncalls, dtype=torch.int32, device="cuda")
+    _check("smerf_philox_uint32", _lib().smerf_philox_uint32(ctypes.c_uint64(key64 & (2**64 - 1)), ring,
+                                                              ncalls, ctypes.c_void_p(out.data_ptr()),
+                                                              _stream_ptr(stream)))
+    return out
+
+
+def ring_normals(key64, ring, n, fp64=False, stream=None):
+    import torch
+    out = torch.empty(n, dtype=torch.float64 if fp64 else torch.float32, device="cuda")
+    _check("smerf_ring_normals", _lib().smerf_ring_normals(ctypes.c_uint64(key64 & (2**64 - 1)), ring, n,
+                                                            int(bool(fp64)), ctypes.c_void_p(out.data_ptr()),
+                                                            _stream_ptr(stream)))
+    return out

@@ -1,0 +1,74 @@
+"""The C ABI library loads and exports every entry point include/smerf.h declares;
+argument validation answers without touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "smerf.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1709_10314_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(smerf_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for n in ["smerf_plan_create", "smerf_plan_create_ex", "smerf_sample", "smerf_sample_batched",
+              "smerf_plan_destroy", "smerf_sample_host", "smerf_plan_info"]:
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared():
+        assert hasattr(lib, name), name
+
+
+def _create(lib, kappa, p, A, nt, nphi, flags=0, H=0):
+    k = np.ascontiguousarray(kappa, dtype=np.float64)
+    h = ctypes.c_void_p()
+    lib.smerf_plan_create_ex.restype = ctypes.c_int
+    rc = lib.smerf_plan_create_ex(k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), p, ctypes.c_double(A),
+                                  nt, nphi, ctypes.c_uint(flags), H, ctypes.byref(h))
+    return rc, h
+
+
+@pytest.mark.parametrize("args,code", [
+    (([1.0], 0, 1.0, 16, 32), -1),              # p < 1
+    (([-1.0], 1, 1.0, 16, 32), -1),             # kappa <= 0
+    (([float("nan")], 1, 1.0, 16, 32), -1),     # non-finite kappa
+    (([1.0], 1, 0.0, 16, 32), -1),              # A <= 0
+    (([1.0], 1, 1.0, 1, 32), -1),               # n_theta < 2
+    (([1.0], 1, 1.0, 16, 31), -1),              # odd n_phi
+    (([3.0, 3.0000000001], 2, 1.0, 16, 32), -2),  # near-equal kappa: partial fractions cancel
+    (([1.0], 1, 1.0, 16, 48), -5),              # n_phi not a power of two
+    (([1.0, 2.0, 3.0], 3, 1.0, 16, 32), -5),    # p = 3 not built
+])
+def test_validation_without_gpu(lib, args, code):
+    rc, h = _create(lib, *args)
+    assert rc == code and not h.value
+
+
+def test_bad_flags_and_spacing(lib):
+    assert _create(lib, [1.0], 1, 1.0, 16, 32, flags=0x100)[0] == -1
+    assert _create(lib, [1.0], 1, 1.0, 16, 32, flags=0x6)[0] == -1      # FP32 and FP64 tables
+    assert _create(lib, [1.0], 1, 1.0, 16, 32, H=-3)[0] == -1
+
+
+def test_status_strings(lib):
+    lib.smerf_status_string.restype = ctypes.c_char_p
+    assert lib.smerf_status_string(0) == b"ok"
+    assert b"argument" in lib.smerf_status_string(-1)
+    assert lib.smerf_plan_destroy(None) == 0
