@@ -43,6 +43,7 @@ typedef struct smerf_plan smerf_plan;
 #define SMERF_ENOMEM (-3)      /* device or host allocation failed                              */
 #define SMERF_ECUDA (-4)       /* a CUDA runtime call or kernel launch failed                    */
 #define SMERF_EUNSUPPORTED (-5) /* valid but not built (e.g. p > 2, n_phi not a power of two)   */
+#define SMERF_ESCRATCH (-6)    /* smerf_sample_noalloc: request exceeds its fixed 16 MiB scratch */
 
 /* plan flags */
 #define SMERF_RECUR_FP64 0x1u    /* recursion, FFT and output in FP64 (default FP32, float out)   */
@@ -126,6 +127,27 @@ int smerf_sample_host(const smerf_plan* plan, uint64_t seed, int n_samples, void
  */
 int smerf_sample_batched(const smerf_plan* const* plans, const uint64_t* seeds,
                          const int* n_samples, void* const* outs, int n_req, void* stream);
+
+/*
+ * smerf_sample_noalloc -- smerf_sample without any device allocation.  The paper has no
+ * counterpart; this exists for callers that cannot let a library allocate device memory
+ * (work captured once into a CUDA graph and replayed, hosts whose device memory is carved
+ * out up front, frameworks that own all device memory through their own pool).
+ *
+ * Same arguments, output and noise as smerf_sample; `out` is still caller-owned device
+ * memory.  The anchor-state scratch is a fixed 16 MiB array inside the library's device
+ * image (present on every GPU that loads the library until the process exits).  A request
+ * needs 2 * n_samples * (anchors + 1) * 2p * (n_phi/2) * (4 or 8 with SMERF_RECUR_FP64)
+ * bytes of it (smerf_plan_info: scratch_bytes_per_sample * n_samples); larger requests
+ * return SMERF_ESCRATCH and launch nothing.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's contents: two calls
+ * whose kernels overlap on the GPU (different streams, no ordering between them) race on
+ * it, so serialise them.  Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+int smerf_sample_noalloc(const smerf_plan* plan, uint64_t seed, int n_samples, void* out, void* stream);
 
 /* Plan description, filled by smerf_plan_info. */
 typedef struct smerf_plan_info_t {

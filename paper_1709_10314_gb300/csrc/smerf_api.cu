@@ -105,6 +105,7 @@ const char* smerf_status_string(int status)
         case SMERF_ENOMEM: return "out of memory";
         case SMERF_ECUDA: return "CUDA error";
         case SMERF_EUNSUPPORTED: return "unsupported configuration";
+        case SMERF_ESCRATCH: return "request exceeds the fixed scratch of smerf_sample_noalloc";
         default: return "unknown status";
     }
 }

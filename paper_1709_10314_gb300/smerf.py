@@ -57,6 +57,8 @@ def _lib():
         L.smerf_sample.restype = ip
         L.smerf_sample_timed.argtypes = [vp, ctypes.c_uint64, ip, vp, vp, vp, vp]
         L.smerf_sample_timed.restype = ip
+        L.smerf_sample_noalloc.argtypes = [vp, ctypes.c_uint64, ip, vp, vp]
+        L.smerf_sample_noalloc.restype = ip
         L.smerf_sample_host.argtypes = [vp, ctypes.c_uint64, ip, vp, vp]
         L.smerf_sample_host.restype = ip
         L.smerf_sample_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_uint64),
@@ -155,6 +157,16 @@ class Plan:
         assert out.numel() >= n_samples * self.n_theta * self.n_phi
         _check("smerf_sample", _lib().smerf_sample(self._h, ctypes.c_uint64(seed & (2**64 - 1)), int(n_samples),
                                                     ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def sample_noalloc(self, seed, n_samples, out, stream=None):
+        """smerf_sample_noalloc: like sample() but the library allocates nothing (its scratch
+        is a fixed 16 MiB device array; larger requests raise SmerfError SMERF_ESCRATCH)."""
+        assert out.is_cuda and out.is_contiguous() and out.dtype == self.dtype
+        assert out.numel() >= n_samples * self.n_theta * self.n_phi
+        _check("smerf_sample_noalloc",
+               _lib().smerf_sample_noalloc(self._h, ctypes.c_uint64(seed & (2**64 - 1)), int(n_samples),
+                                           ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out
 
     def sample_timed(self, seed, n_samples, out, ev_before, ev_after, stream=None):
