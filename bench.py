@@ -124,7 +124,8 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_theta": N_THETA, "n_phi": N_PHI},
+            "config": {"workload": WORKLOAD if args.tables == "fp64" else WORKLOAD.replace("FP64 tables", "FP32 tables"),
+                       "n_theta": N_THETA, "n_phi": N_PHI},
             "cpu_baseline": {"value": value, "unit": "points/s", "cores": cpu_cores(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -138,7 +139,9 @@ def run_gb300(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    plan = Plan(KAPPA, AMP, N_THETA, N_PHI, flags=SMERF_TABLES_FP64, anchor_spacing=ANCHOR)
+    from paper_1709_10314_gb300 import SMERF_TABLES_FP32
+    tflag = SMERF_TABLES_FP32 if args.tables == "fp32" else SMERF_TABLES_FP64
+    plan = Plan(KAPPA, AMP, N_THETA, N_PHI, flags=tflag, anchor_spacing=ANCHOR)
     info = plan.info()
     out = torch.empty((N_REAL, N_THETA, N_PHI), dtype=torch.float32, device=dev)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -213,7 +216,8 @@ def run_gb300(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_theta": N_THETA, "n_phi": N_PHI, "realisations_per_gpu": N_REAL,
+            "config": {"workload": WORKLOAD if args.tables == "fp64" else WORKLOAD.replace("FP64 tables", "FP32 tables"),
+                       "n_theta": N_THETA, "n_phi": N_PHI, "realisations_per_gpu": N_REAL,
                        "anchor_spacing": ANCHOR, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between timed steps (256 MiB write outside the step events)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -235,6 +239,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tables", default="fp64", choices=["fp64", "fp32"],
+                    help="table storage precision (the workload specifies fp64)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -50,7 +50,7 @@ struct smerf_plan {
     void* beq;             // [tri][n_modes_pad]
     void* steps[2];        // [len+1][E][n_modes_pad]
     void* coarse[2];       // [n_anchors+1][Ec][n_modes_pad] (row 0 unused)
-    // FFT twiddles in the recursion precision: tw[Nc] = e^{2 pi i n / Nc}, pre[Nc] = e^{2 pi i s / n_phi}
+    // FFT tables in the recursion precision: per-pass twiddles, pre[Nc] = e^{2 pi i s / n_phi}
     void* tw;
     void* pre;
     size_t table_bytes;
@@ -103,7 +103,7 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& n0, fl
         const float u = fmaf((float)a, 0x1p-32f, 0x1p-33f);
         r2 = -1.3862944f * __log2f(u);  // -2 ln 2 * log2(u)
     }
-    const float r = sqrtf(r2);
+    const float r = r2 * rsqrtf(r2);  // r2 > 0: u0 < 1 and v > 0
     const float t = fmaf((float)b, 0x1p-32f, 0x1p-33f) * 6.2831855f;
     float s, c;
     __sincosf(t, &s, &c);

@@ -29,14 +29,15 @@ struct SampleParams {
     const void* steps[2];
     const void* coarse[2];
     const void* beq;
-    const void* tw;   // complex twiddles e^{2 pi i n / Nc}, n < Nc
+    const void* tw;   // per-pass complex twiddle tables (see pass_radix)
     const void* pre;  // complex e^{2 pi i s / n_phi}, s < Nc
     void* anc;        // anchor states [c][r][j][2M][n_slots]
     void* out;
     uint64_t seed;
     int n_samples, n_theta, n_phi, Nc, n_units, n_modes_pad, k0, H, na_max;
     int n_anchors[2];
-    int xr_smem;      // 1: right-anchor states staged in shared memory
+    int pingpong;     // 1: two FFT buffers + right anchors on chip; 0: one buffer, in place
+    int lgNc;
 };
 
 template <int M> constexpr int kG = unit_slots(M);
@@ -53,6 +54,21 @@ __device__ __forceinline__ void unit_normals(uint64_t key64, uint32_t call, uint
 
 template <class Real, class TabT>
 __device__ __forceinline__ Real tabld(const TabT* p) { return (Real)__ldg(p); }
+
+// FP64 table value -> FP32 with integer instructions only (GB300 runs FP64 conversions on
+// its narrow FP64 pipe).  Truncates the mantissa; values below the FP32 normal range
+// become 0 (tables hold no values above it).
+template <>
+__device__ __forceinline__ float tabld<float, double>(const double* p)
+{
+    const double v = __ldg(p);
+    const uint32_t hi = (uint32_t)(__double_as_longlong(v) >> 32);
+    const uint32_t lo = (uint32_t)__double_as_longlong(v);
+    const uint32_t e11 = (hi >> 20) & 0x7FFu;
+    uint32_t t = __funnelshift_l(lo, hi, 3) - (128u << 23);
+    t = (t & 0x7FFFFFFFu) | (hi & 0x80000000u);
+    return e11 > 896u ? __uint_as_float(t) : 0.0f;
+}
 
 // anchor scratch offset: [c][r][j][f][slot], f = part * M + q
 template <int M>
@@ -182,84 +198,173 @@ __device__ __forceinline__ void dft(C* v)
     else dft8(v);
 }
 
-// One radix-RP Stockham pass over R rings of Nc points, in place through registers
-// (every thread reads all its inputs before the barrier, writes after it).
-template <class C, int RP, int BPT>
-__device__ __forceinline__ void stockham_pass(C* buf, int R, int Nc, int Ns, const C* __restrict__ tw)
+// Z_s of the C2R packing (s < Nc): Z_0 = (X_0 + X_Nc) + i (X_0 - X_Nc) from slot 0 = (X_0, X_Nc);
+// Z_s = (X_s + conj X_{Nc-s}) + i e^{2 pi i s / n_phi} (X_s - conj X_{Nc-s}).  The Nc-point
+// inverse FFT of Z gives z_n = x_{2n} + i x_{2n+1}.
+template <class C>
+__device__ __forceinline__ C c2r_pack(const C* X, int s, int Nc, const C* pre)
 {
-    const int nb = Nc / RP;
-    const int total = R * nb;
-    const int nt = blockDim.x, tid = threadIdx.x;
-    const int tstride = Nc / (Ns * RP);
+    if (s == 0) {
+        const C x = X[0];
+        return cmk<C>(x.x + x.y, x.x - x.y);
+    }
+    const C a = X[s], b = cconj(X[Nc - s]);
+    return cadd(cadd(a, b), cmuli(cmul(pre[s], csub(a, b))));
+}
+
+// Pass plan of the Nc-point FFT: radix 4 while at least 4 points remain per group, then
+// radix 2.  Pass p with Ns > 1 reads its twiddles e^{2 pi i i kk / (Ns RP)} from
+// twp[off + (i-1) Ns + kk] (laid out so that neighbouring butterflies read neighbouring
+// entries); the tables are built with the plan (smerf_setup.cu, pass_twiddle_kernel).
+__host__ __device__ inline int pass_radix(int lgNc, int Ns) { return (1 << lgNc) / Ns >= 4 ? 4 : 2; }
+
+// One radix-RP Stockham pass over R rings of Nc points, src -> dst (distinct shared
+// buffers), or, for the last pass, straight to the rings' rows in global memory (gout[r]).
+// The first pass (Ns = 1) has unit twiddles and applies the C2R packing as it loads.
+template <class C, int RP, bool FIRST, bool LAST>
+__device__ __forceinline__ void fft_pass(const C* __restrict__ src, C* __restrict__ dst, int R, int lgNc,
+                                         int Ns, const C* __restrict__ twp, const C* __restrict__ pre,
+                                         C* const* gout)
+{
+    const int Nc = 1 << lgNc;
+    constexpr int LR = RP == 4 ? 2 : 1;
+    const int lgnb = lgNc - LR;
+    const int nb = 1 << lgnb;
+    const int total = R << lgnb;
+    for (int b = threadIdx.x; b < total; b += blockDim.x) {
+        const int r = b >> lgnb, j = b & (nb - 1);
+        const C* S = src + (r << lgNc);
+        C v[RP];
+        int kk = 0;
+        if (FIRST) {
+#pragma unroll
+            for (int i = 0; i < RP; ++i) v[i] = c2r_pack(S, j + i * nb, Nc, pre);
+        } else {
+            kk = j & (Ns - 1);
+#pragma unroll
+            for (int i = 0; i < RP; ++i) v[i] = S[j + i * nb];
+#pragma unroll
+            for (int i = 1; i < RP; ++i) v[i] = cmul(v[i], __ldg(twp + (i - 1) * Ns + kk));
+        }
+        dft<C, RP>(v);
+        const int idx = ((j - kk) << LR) + kk;
+        if (LAST) {
+            C* D = gout[r] + idx;
+#pragma unroll
+            for (int a = 0; a < RP; ++a) __stcs(D + a * Ns, v[a]);
+        } else {
+            C* D = dst + (r << lgNc) + idx;
+#pragma unroll
+            for (int a = 0; a < RP; ++a) D[a * Ns] = v[a];
+        }
+    }
+}
+
+template <class C>
+__device__ __forceinline__ C c2r_pack_g(const C* X, int s, int Nc, const C* pre) { return c2r_pack(X, s, Nc, pre); }
+
+// In-place variant: every thread reads all its butterflies before a barrier and writes after
+// it (BPT butterflies per thread at most).
+template <class C, int RP, int BPT, bool FIRST>
+__device__ __forceinline__ void fft_pass_inplace(C* buf, int R, int lgNc, int Ns, const C* twp, const C* pre)
+{
+    const int Nc = 1 << lgNc;
+    const int lgnb = lgNc - (RP == 4 ? 2 : 1);
+    const int nb = 1 << lgnb;
+    const int total = R << lgnb;
     C v[BPT][RP];
 #pragma unroll
     for (int k = 0; k < BPT; ++k) {
-        const int b = tid + k * nt;
+        const int b = threadIdx.x + k * blockDim.x;
         if (b < total) {
-            const int r = b / nb, j = b - r * nb;
-            const C* base = buf + (size_t)r * Nc;
+            const int r = b >> lgnb, j = b & (nb - 1);
+            const C* S = buf + ((size_t)r << lgNc);
 #pragma unroll
-            for (int i = 0; i < RP; ++i) v[k][i] = base[j + i * nb];
+            for (int i = 0; i < RP; ++i) v[k][i] = FIRST ? c2r_pack(S, j + i * nb, Nc, pre) : S[j + i * nb];
         }
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < BPT; ++k) {
-        const int b = tid + k * nt;
+        const int b = threadIdx.x + k * blockDim.x;
         if (b < total) {
-            const int r = b / nb, j = b - r * nb;
-            const int kk = j % Ns;
+            const int r = b >> lgnb, j = b & (nb - 1);
+            const int kk = FIRST ? 0 : (j & (Ns - 1));
+            if (!FIRST) {
 #pragma unroll
-            for (int i = 1; i < RP; ++i) v[k][i] = cmul(v[k][i], tw[i * kk * tstride]);
+                for (int i = 1; i < RP; ++i) v[k][i] = cmul(v[k][i], __ldg(twp + (i - 1) * Ns + kk));
+            }
             dft<C, RP>(v[k]);
-            C* base = buf + (size_t)r * Nc;
-            const int idx = (j / Ns) * Ns * RP + kk;
+            C* D = buf + ((size_t)r << lgNc) + (j - kk) * RP + kk;
 #pragma unroll
-            for (int a = 0; a < RP; ++a) base[idx + a * Ns] = v[k][a];
+            for (int a = 0; a < RP; ++a) D[a * Ns] = v[k][a];
         }
     }
     __syncthreads();
 }
 
-// Real inverse DFT of R rings (prefactor 1): buf[r] holds the packed coefficients
-// (slot 0 = (X_0, X_{Nc}), slot s = X_s); on return it holds the ring's n_phi reals
-// in natural order, viewed as Nc complex (x_{2n}, x_{2n+1}).
 template <class C, int EPT>
-__device__ void c2r_rings(C* buf, int R, int Nc, const C* __restrict__ tw, const C* __restrict__ pre)
+__device__ __forceinline__ void c2r_rings_inplace(C* buf, int R, int lgNc, const C* twp, const C* pre)
 {
-    const int nt = blockDim.x, tid = threadIdx.x;
-    const int half = Nc / 2 + 1;
-    for (int idx = tid; idx < R * half; idx += nt) {
-        const int r = idx / half, s = idx - r * half;
-        C* b = buf + (size_t)r * Nc;
-        if (s == 0) {
-            const C x = b[0];
-            b[0] = cmk<C>(x.x + x.y, x.x - x.y);
-        } else {
-            const int s2 = Nc - s;
-            const C a = b[s], bb = b[s2];
-            const C Zs = cadd(cadd(a, cconj(bb)), cmuli(cmul(pre[s], csub(a, cconj(bb)))));
-            if (s2 != s) {
-                const C Z2 = cadd(cadd(bb, cconj(a)), cmuli(cmul(pre[s2], csub(bb, cconj(a)))));
-                b[s2] = Z2;
-            }
-            b[s] = Zs;
-        }
-    }
-    __syncthreads();
-    int Ns = 1;
+    const int Nc = 1 << lgNc;
+    int Ns = 1, off = 0;
+    bool first = true;
     while (Ns < Nc) {
-        const int rem = Nc / Ns;
-        if (rem >= 8) {
-            stockham_pass<C, 8, (EPT + 7) / 8>(buf, R, Nc, Ns, tw);
-            Ns *= 8;
-        } else if (rem == 4) {
-            stockham_pass<C, 4, (EPT + 3) / 4>(buf, R, Nc, Ns, tw);
-            Ns *= 4;
+        const int RP = pass_radix(lgNc, Ns);
+        if (RP == 4) {
+            if (first) fft_pass_inplace<C, 4, (EPT + 3) / 4, true>(buf, R, lgNc, Ns, twp + off, pre);
+            else fft_pass_inplace<C, 4, (EPT + 3) / 4, false>(buf, R, lgNc, Ns, twp + off, pre);
         } else {
-            stockham_pass<C, 2, (EPT + 1) / 2>(buf, R, Nc, Ns, tw);
-            Ns *= 2;
+            if (first) fft_pass_inplace<C, 2, (EPT + 1) / 2, true>(buf, R, lgNc, Ns, twp + off, pre);
+            else fft_pass_inplace<C, 2, (EPT + 1) / 2, false>(buf, R, lgNc, Ns, twp + off, pre);
         }
+        if (!first) off += (RP - 1) * Ns;
+        Ns *= RP;
+        first = false;
+    }
+}
+
+// Real inverse DFT (prefactor 1) of R rings straight into their output rows gout[r]:
+// buf0 holds the packed coefficients (slot 0 = (X_0, X_Nc), slot s = X_s); buf1 is the
+// second ping-pong buffer.  The last pass writes global memory (rows of n_phi reals viewed
+// as Nc complex (x_{2n}, x_{2n+1})).  One barrier per shared-memory pass; on return both
+// buffers may be reused after the caller's next barrier.
+template <class C>
+__device__ __forceinline__ void c2r_rings_to_global(C* buf0, C* buf1, int R, int lgNc, const C* twp,
+                                                    const C* pre, C* const* gout)
+{
+    const int Nc = 1 << lgNc;
+    C* src = buf0;
+    C* dst = buf1;
+    int Ns = 1, off = 0;
+    bool first = true;
+    while (Ns < Nc) {
+        const int RP = pass_radix(lgNc, Ns);
+        const bool last = Ns * RP == Nc;
+        if (RP == 4) {
+            if (first) {
+                if (last) fft_pass<C, 4, true, true>(src, dst, R, lgNc, Ns, twp + off, pre, gout);
+                else fft_pass<C, 4, true, false>(src, dst, R, lgNc, Ns, twp + off, pre, gout);
+            } else {
+                if (last) fft_pass<C, 4, false, true>(src, dst, R, lgNc, Ns, twp + off, pre, gout);
+                else fft_pass<C, 4, false, false>(src, dst, R, lgNc, Ns, twp + off, pre, gout);
+            }
+        } else {
+            if (first) {
+                if (last) fft_pass<C, 2, true, true>(src, dst, R, lgNc, Ns, twp + off, pre, gout);
+                else fft_pass<C, 2, true, false>(src, dst, R, lgNc, Ns, twp + off, pre, gout);
+            } else {
+                if (last) fft_pass<C, 2, false, true>(src, dst, R, lgNc, Ns, twp + off, pre, gout);
+                else fft_pass<C, 2, false, false>(src, dst, R, lgNc, Ns, twp + off, pre, gout);
+            }
+        }
+        if (!first) off += (RP - 1) * Ns;
+        Ns *= RP;
+        first = false;
+        if (!last) __syncthreads();
+        C* t = src;
+        src = dst;
+        dst = t;
     }
 }
 
@@ -282,15 +387,38 @@ __device__ __forceinline__ void store_ring<double>(double* dst, const double2* s
     for (int j = tid; j < Nc; j += nt) __stcs(d2 + j, src[j]);
 }
 
-template <class Real, class TabT, int M, int UPT, int RMAX>
-__global__ void __launch_bounds__(512) segment_kernel(SampleParams P)
+// x <- A x + C x_right + B xi for one real chain (tables t = [A | C | B], B lower); x_right
+// is read at xr[q * Nc] (null when the segment has no right anchor).
+template <class Real, int M>
+__device__ __forceinline__ void step_state(const Real* t, Real (&x)[M], const Real (&xi)[M], const Real* xr, int Nc)
+{
+    Real xn[M];
+#pragma unroll
+    for (int p = 0; p < M; ++p) {
+        Real acc = 0;
+#pragma unroll
+        for (int q = 0; q < M; ++q) acc = fma(t[p * M + q], x[q], acc);
+        if (xr) {
+#pragma unroll
+            for (int q = 0; q < M; ++q) acc = fma(t[M * M + p * M + q], xr[(size_t)q * Nc], acc);
+        }
+        int e = 2 * M * M + p * (p + 1) / 2;
+#pragma unroll
+        for (int q = 0; q <= p; ++q, ++e) acc = fma(t[e], xi[q], acc);
+        xn[p] = acc;
+    }
+#pragma unroll
+    for (int q = 0; q < M; ++q) x[q] = xn[q];
+}
+
+template <class Real, class TabT, int M, int UPT, int RMAX, bool INPLACE>
+__global__ void __launch_bounds__(1024) segment_kernel(SampleParams P)
 {
     using C = cplx<Real>;
     constexpr int G = kG<M>;
     constexpr int E = step_elems(M);
-    constexpr int EPT = RMAX * UPT * G;   // complex FFT points per thread
+    constexpr int EPT = RMAX * UPT * G;   // complex FFT points per thread (in-place mode)
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
 
     const Segment sg = P.segs[blockIdx.x];
     const int r0 = blockIdx.y * RMAX;
@@ -299,16 +427,28 @@ __global__ void __launch_bounds__(512) segment_kernel(SampleParams P)
     const int nt = blockDim.x, tid = threadIdx.x;
     const int Nc = P.Nc;
     const size_t mp = P.n_modes_pad;
-    Real* xR = reinterpret_cast<Real*>(buf + (size_t)RMAX * Nc);
     const Real* anc = (const Real*)P.anc;
     const bool has_right = sg.right >= 0;
-    // right-anchor states: staged in shared memory when the launch reserved room for
-    // them (xr_smem), read from the scratch otherwise; same [f][slot] layout per r
-    const Real* xrb[RMAX];
+
+    // shared memory: FFT buffer(s), then (ping-pong mode) the right-anchor states
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + (size_t)RMAX * Nc;
+    Real* xRs = reinterpret_cast<Real*>(buf0 + (size_t)RMAX * Nc * (INPLACE ? 1 : 2));
+    const C* twp = (const C*)P.tw;
+    const C* pre = (const C*)P.pre;
+    // right-anchor states: shared memory in ping-pong mode, the scratch itself in place mode;
+    // layout [f][slot] per realisation in both
+    const Real* xrg[RMAX];
 #pragma unroll
     for (int r = 0; r < RMAX; ++r)
-        xrb[r] = P.xr_smem ? xR + (size_t)r * 2 * M * Nc
-                           : anc + aoff<M>(P, c, min(r0 + r, P.n_samples - 1), has_right ? sg.right : 0, 0, 0);
+        xrg[r] = anc + aoff<M>(P, c, min(r0 + r, P.n_samples - 1), has_right ? sg.right : 0, 0, 0);
+    if (!INPLACE && has_right) {
+        const int per = 2 * M * Nc;
+        for (int idx = tid; idx < R * per; idx += nt) {
+            const int r = idx / per, rest = idx - r * per;
+            xRs[idx] = anc[aoff<M>(P, c, r0 + r, sg.right, 0, 0) + rest];
+        }
+    }
 
     Real x[UPT][RMAX][G][2][M];
 #pragma unroll
@@ -326,19 +466,9 @@ __global__ void __launch_bounds__(512) segment_kernel(SampleParams P)
                                                   ? anc[aoff<M>(P, c, r0 + r, sg.left, part * M + q, G * u + g)]
                                                   : (Real)0;
     }
-    if (has_right && P.xr_smem) {
-        const int per = 2 * M * Nc;
-        for (int idx = tid; idx < R * per; idx += nt) {
-            const int r = idx / per, rest = idx - r * per;
-            const int f = rest / Nc, slot = rest - f * Nc;
-            xR[idx] = anc[aoff<M>(P, c, r0 + r, sg.right, f, slot)];
-        }
-    }
     __syncthreads();
 
     const TabT* steps = (const TabT*)P.steps[c];
-    const C* tw = (const C*)P.tw;
-    const C* pre = (const C*)P.pre;
     for (int pos = sg.p0; pos < sg.p1; ++pos) {
         const int ring = c == 0 ? P.k0 - pos : P.k0 + pos;
         if (pos > sg.p0) {
@@ -347,58 +477,41 @@ __global__ void __launch_bounds__(512) segment_kernel(SampleParams P)
             for (int i = 0; i < UPT; ++i) {
                 const int u = tid + i * nt;
                 if (u >= P.n_units) continue;
-                // tables of the unit's slots: [g][0] mode s, [g][1] the Im chain's mode
-                // (s, or the Nyquist mode Nc for slot 0)
-                Real ta[G][2][E];
+                // tables of the unit's slots (mode = slot); slot 0's second chain is the
+                // Nyquist mode, stepped on a separate path that only unit 0 takes
+                Real ta[G][E];
 #pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    const int s = G * u + g;
+                for (int g = 0; g < G; ++g)
 #pragma unroll
-                    for (int e = 0; e < E; ++e) ta[g][0][e] = tabld<Real, TabT>(tb + (size_t)e * mp + s);
-                    const int m1 = (s == 0) ? Nc : s;
-                    if (s == 0) {
-#pragma unroll
-                        for (int e = 0; e < E; ++e) ta[g][1][e] = tabld<Real, TabT>(tb + (size_t)e * mp + m1);
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < E; ++e) ta[g][1][e] = ta[g][0][e];
-                    }
-                }
+                    for (int e = 0; e < E; ++e) ta[g][e] = tabld<Real, TabT>(tb + (size_t)e * mp + G * u + g);
 #pragma unroll
                 for (int r = 0; r < RMAX; ++r) {
                     if (r >= R) continue;
                     Real nr[4];
                     unit_normals<Real>(P.seed + (uint64_t)(r0 + r), (uint32_t)u, (uint32_t)ring, nr);
 #pragma unroll
-                    for (int g = 0; g < G; ++g)
+                    for (int g = 0; g < G; ++g) {
+                        const int s = G * u + g;
 #pragma unroll
                         for (int part = 0; part < 2; ++part) {
-                            const Real* t = ta[g][part];
-                            Real xi[M], xn[M];
+                            Real xi[M];
 #pragma unroll
                             for (int q = 0; q < M; ++q) {
                                 const Real v = nr[g * 2 * M + part * M + q];
                                 xi[q] = (c == 1 && (q & 1)) ? -v : v;
                             }
-                            const int s = G * u + g;
+                            const Real* xr = INPLACE ? xrg[r] + (size_t)part * M * Nc + s
+                                                     : xRs + ((size_t)r * 2 * M + part * M) * Nc + s;
+                            if (part == 1 && s == 0) {
+                                Real tn[E];
 #pragma unroll
-                            for (int p = 0; p < M; ++p) {
-                                Real acc = 0;
-#pragma unroll
-                                for (int q = 0; q < M; ++q) acc = fma(t[p * M + q], x[i][r][g][part][q], acc);
-                                if (has_right) {
-#pragma unroll
-                                    for (int q = 0; q < M; ++q)
-                                        acc = fma(t[M * M + p * M + q], xrb[r][(size_t)(part * M + q) * Nc + s], acc);
-                                }
-                                int e = 2 * M * M + p * (p + 1) / 2;
-#pragma unroll
-                                for (int q = 0; q <= p; ++q, ++e) acc = fma(t[e], xi[q], acc);
-                                xn[p] = acc;
+                                for (int e = 0; e < E; ++e) tn[e] = tabld<Real, TabT>(tb + (size_t)e * mp + Nc);
+                                step_state<Real, M>(tn, x[i][r][g][part], xi, has_right ? xr : nullptr, Nc);
+                            } else {
+                                step_state<Real, M>(ta[g], x[i][r][g][part], xi, has_right ? xr : nullptr, Nc);
                             }
-#pragma unroll
-                            for (int q = 0; q < M; ++q) x[i][r][g][part][q] = xn[q];
                         }
+                    }
                 }
             }
         }
@@ -412,26 +525,34 @@ __global__ void __launch_bounds__(512) segment_kernel(SampleParams P)
                 if (r >= R) continue;
 #pragma unroll
                 for (int g = 0; g < G; ++g)
-                    buf[(size_t)r * Nc + G * u + g] = cmk<C>(x[i][r][g][0][0], x[i][r][g][1][0]);
+                    buf0[(size_t)r * Nc + G * u + g] = cmk<C>(x[i][r][g][0][0], x[i][r][g][1][0]);
             }
         }
         __syncthreads();
-        c2r_rings<C, EPT>(buf, R, Nc, tw, pre);
-        if (!(c == 1 && pos == 0)) {
-            for (int r = 0; r < R; ++r) {
-                Real* dst = (Real*)P.out + ((size_t)(r0 + r) * P.n_theta + ring) * (size_t)P.n_phi;
-                store_ring<Real>(dst, buf + (size_t)r * Nc, Nc, tid, nt);
+        if (!(c == 1 && pos == 0)) {  // the start ring is written by the northern chain
+            if (INPLACE) {
+                c2r_rings_inplace<C, EPT>(buf0, R, P.lgNc, twp, pre);
+                for (int r = 0; r < R; ++r) {
+                    Real* dst = (Real*)P.out + ((size_t)(r0 + r) * P.n_theta + ring) * (size_t)P.n_phi;
+                    store_ring<Real>(dst, buf0 + (size_t)r * Nc, Nc, tid, nt);
+                }
+            } else {
+                C* gout[RMAX];
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r)
+                    gout[r] = (C*)((Real*)P.out + ((size_t)min(r0 + r, P.n_samples - 1) * P.n_theta + ring) * (size_t)P.n_phi);
+                c2r_rings_to_global<C>(buf0, buf1, R, P.lgNc, twp, pre, gout);
             }
         }
-        __syncthreads();
+        __syncthreads();  // buffers are rewritten by the next ring
     }
 }
 
 // ------------------------------------------------------------------ launch
-template <class Real, class TabT, int M, int UPT, int RMAX>
+template <class Real, class TabT, int M, int UPT, int RMAX, bool INPLACE = false>
 int launch_segments(const SampleParams& P, int n_segments, int nt, size_t smem, cudaStream_t st)
 {
-    auto kern = segment_kernel<Real, TabT, M, UPT, RMAX>;
+    auto kern = segment_kernel<Real, TabT, M, UPT, RMAX, INPLACE>;
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return SMERF_ECUDA;
@@ -441,14 +562,12 @@ int launch_segments(const SampleParams& P, int n_segments, int nt, size_t smem, 
     return cudaGetLastError() == cudaSuccess ? SMERF_OK : SMERF_ECUDA;
 }
 
-constexpr int kMaxThreads = 512;
-constexpr size_t kMaxSmem = 227 * 1024;
-
-// (units per thread, realisations per CTA) pairs that are built: FP32 recursion keeps
-// four realisations per CTA while the state fits in registers, FP64 one.
+// (units per thread, realisations per CTA) pairs that are built: four realisations per CTA
+// share each table load while the state fits in 64 registers, fewer for wide grids;
+// FP64 recursion keeps one.
 template <class Real> constexpr int rmax_for(int upt)
 {
-    return sizeof(Real) == 8 ? 1 : (upt <= 4 ? 4 : (upt == 8 ? 2 : 1));
+    return sizeof(Real) == 8 ? 1 : (upt == 1 ? 4 : (upt == 2 ? 2 : 1));
 }
 
 template <class Real, class TabT, int M>
@@ -457,39 +576,44 @@ int dispatch_upt(const SampleParams& P, int n_segments, int upt, int nt, size_t 
     switch (upt) {
         case 1: return launch_segments<Real, TabT, M, 1, rmax_for<Real>(1)>(P, n_segments, nt, smem, st);
         case 2: return launch_segments<Real, TabT, M, 2, rmax_for<Real>(2)>(P, n_segments, nt, smem, st);
-        case 4: return launch_segments<Real, TabT, M, 4, rmax_for<Real>(4)>(P, n_segments, nt, smem, st);
-        case 8: return launch_segments<Real, TabT, M, 8, rmax_for<Real>(8)>(P, n_segments, nt, smem, st);
-        case 16: return launch_segments<Real, TabT, M, 16, rmax_for<Real>(16)>(P, n_segments, nt, smem, st);
+        case 4:
+            return P.pingpong ? launch_segments<Real, TabT, M, 4, rmax_for<Real>(4)>(P, n_segments, nt, smem, st)
+                              : launch_segments<Real, TabT, M, 4, rmax_for<Real>(4), true>(P, n_segments, nt, smem, st);
+        case 8:
+            return P.pingpong ? launch_segments<Real, TabT, M, 8, rmax_for<Real>(8)>(P, n_segments, nt, smem, st)
+                              : launch_segments<Real, TabT, M, 8, rmax_for<Real>(8), true>(P, n_segments, nt, smem, st);
         default: return SMERF_EUNSUPPORTED;
     }
 }
 
+constexpr int kMaxThreads = 1024;
+constexpr size_t kMaxSmem = 227 * 1024;
+
 // Launch configuration of the segment kernel for a plan: units per thread, threads,
-// realisations per CTA and shared memory.
-struct SegConfig { int upt, nt, rmax; size_t smem; int xr_smem; };
+// realisations per CTA and the optional shared-memory parts.
+struct SegConfig { int upt, nt, rmax; size_t smem; int pingpong; };
 
 template <class Real>
-inline SegConfig seg_config(const smerf_plan* pl, int n_samples)
+inline SegConfig seg_config(const smerf_plan* pl)
 {
     SegConfig cfg{};
     const int M = pl->p;
     const int n_units = pl->n_slots / unit_slots(M);
     int upt = 1;
-    while (upt < 16 && (n_units + upt - 1) / upt > kMaxThreads) upt *= 2;
+    while (upt < 8 && (n_units + upt - 1) / upt > kMaxThreads) upt *= 2;
     int nt = (n_units + upt - 1) / upt;
     nt = ((nt + 31) / 32) * 32;
     if (nt < 64) nt = 64;
-    (void)n_samples;
     const int rmax = rmax_for<Real>(upt);
     const int Nc = pl->n_phi / 2;
-    const size_t cs = 2 * sizeof(Real);
-    const size_t fft = (size_t)rmax * Nc * cs;
-    const size_t xr = (size_t)rmax * 2 * M * Nc * sizeof(Real);
+    const size_t one = (size_t)rmax * Nc * 2 * sizeof(Real);
+    const size_t xr = pl->H > 0 ? (size_t)rmax * 2 * M * Nc * sizeof(Real) : 0;
     cfg.upt = upt;
     cfg.nt = nt;
     cfg.rmax = rmax;
-    cfg.xr_smem = (pl->H > 0 && fft + xr <= kMaxSmem) ? 1 : 0;
-    cfg.smem = fft + (cfg.xr_smem ? xr : 0);
+    // ping-pong: two FFT buffers and the right-anchor states on chip; otherwise one buffer
+    cfg.pingpong = (2 * one + xr <= kMaxSmem) ? 1 : 0;
+    cfg.smem = cfg.pingpong ? 2 * one + xr : one;
     return cfg;
 }
 
@@ -520,9 +644,14 @@ int launch_sample_t(const smerf_plan* pl, uint64_t seed, int n, void* out, void*
     P.n_anchors[0] = pl->chain[0].n_anchors;
     P.n_anchors[1] = pl->chain[1].n_anchors;
     P.na_max = P.n_anchors[0] > P.n_anchors[1] ? P.n_anchors[0] : P.n_anchors[1];
-    const SegConfig cfg = seg_config<Real>(pl, n);
+    const SegConfig cfg = seg_config<Real>(pl);
     if (cfg.smem > kMaxSmem) return SMERF_EUNSUPPORTED;  // one ring per realisation must fit on chip
-    P.xr_smem = cfg.xr_smem;
+    if ((pl->n_slots / unit_slots(pl->p) + cfg.upt - 1) / cfg.upt > kMaxThreads) return SMERF_EUNSUPPORTED;
+    if (!cfg.pingpong && cfg.upt < 4) return SMERF_EUNSUPPORTED;
+    P.pingpong = cfg.pingpong;
+    int lg = 0;
+    while ((1 << lg) < P.Nc) ++lg;
+    P.lgNc = lg;
     {
         dim3 ga((P.n_units + 127) / 128, n, 2);
         if (pl->p == 1) anchor_kernel<Real, TabT, 1><<<ga, 128, 0, st>>>(P);

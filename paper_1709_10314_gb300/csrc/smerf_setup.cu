@@ -342,18 +342,37 @@ __global__ void segment_tables_kernel(Spec sp, int c, int len, int H, const doub
         for (int q = 0; q <= p; ++q, ++e) put<double>(coarse, tab64, base + (size_t)e * mp, Bc.a[p][q] * sc);
 }
 
+// FFT tables, in FP64 on the host then rounded to the recursion precision:
+//   pre[s] = e^{2 pi i s / n_phi}, s < Nc (C2R packing), and for every radix-RP pass with
+//   Ns > 1 (pass plan: radix 4 while Nc/Ns >= 4, then 2) the block
+//   tw[off + (i-1) Ns + kk] = e^{2 pi i i kk / (Ns RP)}, i = 1..RP-1, kk < Ns.
 template <class R>
-__global__ void twiddle_kernel(int Nc, int n_phi, R* tw, R* pre)
+static int upload_fft_tables(int n_phi, void** tw, void** pre)
 {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= Nc) return;
-    double s, c;
-    sincospi(2.0 * (double)n / (double)Nc, &s, &c);
-    tw[2 * n] = (R)c;
-    tw[2 * n + 1] = (R)s;
-    sincospi(2.0 * (double)n / (double)n_phi, &s, &c);
-    pre[2 * n] = (R)c;
-    pre[2 * n + 1] = (R)s;
+    const int Nc = n_phi / 2;
+    std::vector<R> p(2 * (size_t)Nc), t;
+    for (int s = 0; s < Nc; ++s) {
+        p[2 * s] = (R)cos(2.0 * SMERF_PI * s / n_phi);
+        p[2 * s + 1] = (R)sin(2.0 * SMERF_PI * s / n_phi);
+    }
+    int Ns = 1;
+    while (Ns < Nc) {
+        const int RP = (Nc / Ns >= 4) ? 4 : 2;
+        if (Ns > 1)
+            for (int i = 1; i < RP; ++i)
+                for (int kk = 0; kk < Ns; ++kk) {
+                    const double a = 2.0 * SMERF_PI * (double)i * kk / ((double)Ns * RP);
+                    t.push_back((R)cos(a));
+                    t.push_back((R)sin(a));
+                }
+        Ns *= RP;
+    }
+    if (t.empty()) t.assign(2, (R)0);
+    if (cudaMalloc(tw, t.size() * sizeof(R)) != cudaSuccess) return SMERF_ENOMEM;
+    if (cudaMalloc(pre, p.size() * sizeof(R)) != cudaSuccess) return SMERF_ENOMEM;
+    if (cudaMemcpy(*tw, t.data(), t.size() * sizeof(R), cudaMemcpyHostToDevice) != cudaSuccess) return SMERF_ECUDA;
+    if (cudaMemcpy(*pre, p.data(), p.size() * sizeof(R), cudaMemcpyHostToDevice) != cudaSuccess) return SMERF_ECUDA;
+    return SMERF_OK;
 }
 
 #define CK(x)                                                                     \
@@ -420,17 +439,9 @@ int setup_impl(smerf_plan* pl)
         CK(cudaMemset(pl->coarse[c], 0, cb > 0 ? cb : 16));
         pl->table_bytes += sb + cb;
     }
-    {
-        const size_t rs = pl->recur64 ? 8 : 4;
-        const int Nc = pl->n_phi / 2;
-        CK(cudaMalloc(&pl->tw, (size_t)2 * Nc * rs));
-        CK(cudaMalloc(&pl->pre, (size_t)2 * Nc * rs));
-        if (pl->recur64)
-            twiddle_kernel<double><<<(Nc + 255) / 256, 256>>>(Nc, pl->n_phi, (double*)pl->tw, (double*)pl->pre);
-        else
-            twiddle_kernel<float><<<(Nc + 255) / 256, 256>>>(Nc, pl->n_phi, (float*)pl->tw, (float*)pl->pre);
-        CK(cudaGetLastError());
-    }
+    rc = pl->recur64 ? upload_fft_tables<double>(pl->n_phi, &pl->tw, &pl->pre)
+                     : upload_fft_tables<float>(pl->n_phi, &pl->tw, &pl->pre);
+    if (rc != SMERF_OK) goto done;
     start_kernel<M><<<gm, threads>>>(sp, pl->beq, t64);
     CK(cudaGetLastError());
     for (int c = 0; c < 2; ++c) {
