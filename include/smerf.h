@@ -172,8 +172,10 @@ int smerf_plan_info(const smerf_plan* plan, smerf_plan_info_t* info);
  *              [2p^2 + p(p+1)/2][n_modes]: A (p x p), C (p x p), B (lower, row-major)
  *   which = 2: coarse (anchor) tables of chain c, anchor pos (1..n_anchors[c]),
  *              [p^2 + p(p+1)/2][n_modes]: A, B
- * Chain 1 (south) tables act on the mirrored state S x, S = diag((-1)^q).  B factors of
- * modes m >= 1 carry the 1/sqrt(2) of the Re and Im chains.  host_out holds
+ * Chain 1 (south) tables act on the mirrored state S x, S = diag((-1)^q), and their B
+ * factors have S folded into the columns (the chain is driven by S xi).  B factors of
+ * modes m >= 1 carry the 1/sqrt(2) of the Re and Im chains.  FP64 tables hold no entry
+ * of magnitude below 2^-120 (smaller values are stored as +-2^-120).  host_out holds
  * rows * n_modes doubles.  Synchronous.
  */
 int smerf_plan_copy_tables(const smerf_plan* plan, int which, int chain, int pos, double* host_out);

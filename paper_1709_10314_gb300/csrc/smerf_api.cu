@@ -286,13 +286,15 @@ int smerf_plan_copy_tables(const smerf_plan* plan, int which, int chain, int pos
     const size_t es = plan->tab64 ? 8 : 4;
     const unsigned char* base;
     int rows;
+    bool mode_major = false;
     if (which == 0) {
         base = (const unsigned char*)plan->beq;
         rows = tri(M);
     } else if (which == 1) {
         if (pos < 1 || pos > plan->chain[chain].len) return SMERF_EINVAL;
         rows = step_elems(M);
-        base = (const unsigned char*)plan->steps[chain] + (size_t)pos * rows * mp * es;
+        mode_major = true;
+        base = (const unsigned char*)plan->steps[chain] + (size_t)pos * step_row(M) * mp * es;
     } else if (which == 2) {
         if (pos < 1 || pos > plan->chain[chain].n_anchors) return SMERF_EINVAL;
         rows = coarse_elems(M);
@@ -300,11 +302,11 @@ int smerf_plan_copy_tables(const smerf_plan* plan, int which, int chain, int pos
     } else {
         return SMERF_EINVAL;
     }
-    std::vector<unsigned char> tmp((size_t)rows * mp * es);
+    std::vector<unsigned char> tmp((size_t)(mode_major ? step_row(M) : rows) * mp * es);
     if (cudaMemcpy(tmp.data(), base, tmp.size(), cudaMemcpyDeviceToHost) != cudaSuccess) return SMERF_ECUDA;
     for (int r = 0; r < rows; ++r)
         for (int m = 0; m < plan->n_modes; ++m) {
-            const size_t i = (size_t)r * mp + m;
+            const size_t i = mode_major ? (size_t)m * step_row(M) + r : (size_t)r * mp + m;
             host_out[(size_t)r * plan->n_modes + m] = plan->tab64 ? ((const double*)tmp.data())[i]
                                                                   : (double)((const float*)tmp.data())[i];
         }

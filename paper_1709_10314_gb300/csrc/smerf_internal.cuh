@@ -48,7 +48,7 @@ struct smerf_plan {
     smerf::Segment* segs_dev;
     // tables (TabT = double if tab64 else float)
     void* beq;             // [tri][n_modes_pad]
-    void* steps[2];        // [len+1][E][n_modes_pad]
+    void* steps[2];        // [len+1][n_modes_pad][step_row]
     void* coarse[2];       // [n_anchors+1][Ec][n_modes_pad] (row 0 unused)
     // FFT tables in the recursion precision: per-pass twiddles, pre[Nc] = e^{2 pi i s / n_phi}
     void* tw;
@@ -62,6 +62,9 @@ namespace smerf {
 
 __host__ __device__ constexpr int tri(int M) { return M * (M + 1) / 2; }
 __host__ __device__ constexpr int step_elems(int M) { return 2 * M * M + tri(M); }
+// step tables are stored mode-major, one row of step_row(M) values (padded to 16 bytes in
+// FP32 and 32 bytes in FP64) per (ring, mode)
+__host__ __device__ constexpr int step_row(int M) { return (step_elems(M) + 3) & ~3; }
 __host__ __device__ constexpr int coarse_elems(int M) { return M * M + tri(M); }
 
 // units: the slots whose normals fill whole Philox calls.  p = 1: 2 slots per call;
@@ -80,9 +83,9 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey key)
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         if (r > 0) { k0 += W0; k1 += W1; }
-        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
-        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        const uint64_t p0 = (uint64_t)M0 * c.x;  // one 32x32->64 multiply each
+        const uint64_t p1 = (uint64_t)M1 * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
     }
     return c;
 }

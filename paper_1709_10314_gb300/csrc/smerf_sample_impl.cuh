@@ -53,28 +53,55 @@ __device__ __forceinline__ void unit_normals(uint64_t key64, uint32_t call, uint
 }
 
 template <class Real, class TabT>
-__device__ __forceinline__ Real tabld(const TabT* p) { return (Real)__ldg(p); }
+__device__ __forceinline__ Real tabcvt(TabT v) { return (Real)v; }
+template <class Real, class TabT>
+__device__ __forceinline__ Real tabld(const TabT* p) { return tabcvt<Real, TabT>(__ldg(p)); }
 
-// FP64 table value -> FP32 with integer instructions only (GB300 runs FP64 conversions on
-// its narrow FP64 pipe).  Truncates the mantissa; values below the FP32 normal range
-// become 0 (tables hold no values above it).
+// FP64 table value -> FP32 with three integer instructions (GB300 runs FP64 conversions on
+// its narrow FP64 pipe): shift the exponent and top mantissa bits into place, rebias the
+// exponent by 896, restore the sign.  Truncates the mantissa.  Valid because FP64 tables
+// hold no magnitude below 2^-120 (set-up clamps them) and none above the FP32 range.
 template <>
-__device__ __forceinline__ float tabld<float, double>(const double* p)
+__device__ __forceinline__ float tabcvt<float, double>(double v)
 {
-    const double v = __ldg(p);
     const uint32_t hi = (uint32_t)(__double_as_longlong(v) >> 32);
     const uint32_t lo = (uint32_t)__double_as_longlong(v);
-    const uint32_t e11 = (hi >> 20) & 0x7FFu;
-    uint32_t t = __funnelshift_l(lo, hi, 3) - (128u << 23);
-    t = (t & 0x7FFFFFFFu) | (hi & 0x80000000u);
-    return e11 > 896u ? __uint_as_float(t) : 0.0f;
+    const uint32_t t = __funnelshift_l(lo, hi, 3) - (128u << 23);
+    return __uint_as_float((t & 0x7FFFFFFFu) | (hi & 0x80000000u));
 }
 
-// anchor scratch offset: [c][r][j][f][slot], f = part * M + q
+// anchor scratch offset: [c][r][j][slot][f], f = part * M + q (a unit's 2p x unit_slots
+// values, four in both built cases, are contiguous)
 template <int M>
 __device__ __forceinline__ size_t aoff(const SampleParams& P, int c, int r, int j, int f, int slot)
 {
-    return ((((size_t)c * P.n_samples + r) * (P.na_max + 1) + j) * (2 * M) + f) * (size_t)P.Nc + slot;
+    return ((((size_t)c * P.n_samples + r) * (P.na_max + 1) + j) * (size_t)P.Nc + slot) * (2 * M) + f;
+}
+
+// four consecutive values (16 bytes in FP32, 32 in FP64) as one or two vector accesses
+template <class Real> struct Vec4;
+template <> struct Vec4<float> {
+    static __device__ __forceinline__ void ld(const float* p, float (&v)[4]) { const float4 a = *reinterpret_cast<const float4*>(p); v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; }
+    static __device__ __forceinline__ void ldg(const float* p, float (&v)[4]) { const float4 a = __ldg(reinterpret_cast<const float4*>(p)); v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; }
+    static __device__ __forceinline__ void st(float* p, const float (&v)[4]) { *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]); }
+};
+template <> struct Vec4<double> {
+    static __device__ __forceinline__ void ld(const double* p, double (&v)[4]) { const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1]; v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; }
+    static __device__ __forceinline__ void ldg(const double* p, double (&v)[4]) { const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1); v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; }
+    static __device__ __forceinline__ void st(double* p, const double (&v)[4]) { reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]); reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]); }
+};
+
+// one step-table row (step_row(M) values, 16-byte aligned) converted to the recursion precision
+template <class Real, class TabT, int ROW>
+__device__ __forceinline__ void load_row(const TabT* p, Real (&t)[ROW])
+{
+#pragma unroll
+    for (int k = 0; k < ROW; k += 4) {
+        TabT v[4];
+        Vec4<TabT>::ldg(p + k, v);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) t[k + i] = tabcvt<Real, TabT>(v[i]);
+    }
 }
 
 // ------------------------------------------------------------------ anchors
@@ -111,12 +138,16 @@ __global__ void __launch_bounds__(128) anchor_kernel(SampleParams P)
                 x[g][part][p] = (c == 1 && (p & 1)) ? -acc : acc;
             }
         }
+    {
+        Real v[4];
 #pragma unroll
-    for (int g = 0; g < G; ++g)
+        for (int g = 0; g < G; ++g)
 #pragma unroll
-        for (int part = 0; part < 2; ++part)
+            for (int part = 0; part < 2; ++part)
 #pragma unroll
-            for (int q = 0; q < M; ++q) anc[aoff<M>(P, c, r, 0, part * M + q, G * u + g)] = x[g][part][q];
+                for (int q = 0; q < M; ++q) v[g * 2 * M + part * M + q] = x[g][part][q];
+        Vec4<Real>::st(anc + aoff<M>(P, c, r, 0, 0, G * u), v);
+    }
     const TabT* cs = (const TabT*)P.coarse[c];
     for (int j = 1; j <= P.n_anchors[c]; ++j) {
         const int pos = j * P.H;
@@ -131,10 +162,7 @@ __global__ void __launch_bounds__(128) anchor_kernel(SampleParams P)
                 const int mode = (part == 1 && s == 0) ? P.Nc : s;
                 Real xi[M], xn[M];
 #pragma unroll
-                for (int q = 0; q < M; ++q) {
-                    const Real v = nr[g * 2 * M + part * M + q];
-                    xi[q] = (c == 1 && (q & 1)) ? -v : v;
-                }
+                for (int q = 0; q < M; ++q) xi[q] = nr[g * 2 * M + part * M + q];
 #pragma unroll
                 for (int p = 0; p < M; ++p) {
                     Real acc = 0;
@@ -148,12 +176,14 @@ __global__ void __launch_bounds__(128) anchor_kernel(SampleParams P)
 #pragma unroll
                 for (int q = 0; q < M; ++q) x[g][part][q] = xn[q];
             }
+        Real v[4];
 #pragma unroll
         for (int g = 0; g < G; ++g)
 #pragma unroll
             for (int part = 0; part < 2; ++part)
 #pragma unroll
-                for (int q = 0; q < M; ++q) anc[aoff<M>(P, c, r, j, part * M + q, G * u + g)] = x[g][part][q];
+                for (int q = 0; q < M; ++q) v[g * 2 * M + part * M + q] = x[g][part][q];
+        Vec4<Real>::st(anc + aoff<M>(P, c, r, j, 0, G * u), v);
     }
     (void)T;
 }
@@ -368,6 +398,99 @@ __device__ __forceinline__ void c2r_rings_to_global(C* buf0, C* buf1, int R, int
     }
 }
 
+// Fixed-size variant of c2r_rings_to_global: the pass plan, strides and twiddle offsets
+// are compile-time constants (log2 Nc = LGNC).
+template <class C, int LGNC, int LGNS, bool FIRST>
+__device__ __forceinline__ void fft_pass_fixed(const C* __restrict__ src, C* __restrict__ dst, int R,
+                                               const C* __restrict__ twp, const C* __restrict__ pre,
+                                               C* const* gout)
+{
+    constexpr int Nc = 1 << LGNC, Ns = 1 << LGNS;
+    constexpr int RP = (Nc / Ns >= 4) ? 4 : 2, LR = RP == 4 ? 2 : 1;
+    constexpr bool LAST = Ns * RP == Nc;
+    constexpr int LGNB = LGNC - LR, nb = 1 << LGNB;
+    const int total = R << LGNB;
+    for (int b = threadIdx.x; b < total; b += blockDim.x) {
+        const int r = b >> LGNB, j = b & (nb - 1);
+        const C* S = src + (r << LGNC);
+        C v[RP];
+        int kk = 0;
+        if (FIRST) {
+            // element 0 is slot j: j = 0 holds (X_0, X_Nc); the others are never slot 0
+            {
+                const C a = S[j], bb = cconj(S[(Nc - j) & (Nc - 1)]);
+                const C g = cadd(cadd(a, bb), cmuli(cmul(__ldg(pre + j), csub(a, bb))));
+                const C z0 = cmk<C>(a.x + a.y, a.x - a.y);
+                v[0] = j == 0 ? z0 : g;
+            }
+#pragma unroll
+            for (int i = 1; i < RP; ++i) {
+                const int sidx = j + i * nb;
+                const C a = S[sidx], bb = cconj(S[Nc - sidx]);
+                v[i] = cadd(cadd(a, bb), cmuli(cmul(__ldg(pre + sidx), csub(a, bb))));
+            }
+        } else {
+            kk = j & (Ns - 1);
+#pragma unroll
+            for (int i = 0; i < RP; ++i) v[i] = S[j + i * nb];
+#pragma unroll
+            for (int i = 1; i < RP; ++i) v[i] = cmul(v[i], __ldg(twp + (i - 1) * Ns + kk));
+        }
+        dft<C, RP>(v);
+        const int idx = ((j - kk) << LR) + kk;
+        if (LAST) {
+            C* D = gout[r] + idx;
+#pragma unroll
+            for (int a = 0; a < RP; ++a) __stcs(D + a * Ns, v[a]);
+        } else {
+            C* D = dst + (r << LGNC) + idx;
+#pragma unroll
+            for (int a = 0; a < RP; ++a) D[a * Ns] = v[a];
+        }
+    }
+}
+
+template <class C, int LGNC, int LGNS = 0, int OFF = 0, bool FIRST = true>
+__device__ __forceinline__ void c2r_fixed(C* src, C* dst, int R, const C* twp, const C* pre, C* const* gout)
+{
+    constexpr int Nc = 1 << LGNC, Ns = 1 << LGNS;
+    constexpr int RP = (Nc / Ns >= 4) ? 4 : 2, LR = RP == 4 ? 2 : 1;
+    fft_pass_fixed<C, LGNC, LGNS, FIRST>(src, dst, R, twp + OFF, pre, gout);
+    if constexpr (Ns * RP < Nc) {
+        __syncthreads();
+        c2r_fixed<C, LGNC, LGNS + LR, OFF + (FIRST ? 0 : (RP - 1) * Ns), false>(dst, src, R, twp, pre, gout);
+    }
+}
+
+// Sizes with a fixed-size FFT for each units-per-thread width; others use the general one.
+template <class C, int UPT>
+__device__ __forceinline__ void c2r_dispatch(int lgNc, C* b0, C* b1, int R, const C* twp, const C* pre, C* const* gout)
+{
+    if (UPT == 1) {
+        switch (lgNc) {
+            case 7: c2r_fixed<C, 7>(b0, b1, R, twp, pre, gout); return;
+            case 8: c2r_fixed<C, 8>(b0, b1, R, twp, pre, gout); return;
+            case 9: c2r_fixed<C, 9>(b0, b1, R, twp, pre, gout); return;
+            case 10: c2r_fixed<C, 10>(b0, b1, R, twp, pre, gout); return;
+            case 11: c2r_fixed<C, 11>(b0, b1, R, twp, pre, gout); return;
+            default: break;
+        }
+    } else if (UPT == 2) {
+        switch (lgNc) {
+            case 11: c2r_fixed<C, 11>(b0, b1, R, twp, pre, gout); return;
+            case 12: c2r_fixed<C, 12>(b0, b1, R, twp, pre, gout); return;
+            default: break;
+        }
+    } else if (UPT == 4) {
+        switch (lgNc) {
+            case 12: c2r_fixed<C, 12>(b0, b1, R, twp, pre, gout); return;
+            case 13: c2r_fixed<C, 13>(b0, b1, R, twp, pre, gout); return;
+            default: break;
+        }
+    }
+    c2r_rings_to_global<C>(b0, b1, R, lgNc, twp, pre, gout);
+}
+
 // ------------------------------------------------------------------ segments
 template <class Real>
 __device__ __forceinline__ void store_ring(Real* dst, const cplx<Real>* src, int Nc, int tid, int nt);
@@ -387,10 +510,9 @@ __device__ __forceinline__ void store_ring<double>(double* dst, const double2* s
     for (int j = tid; j < Nc; j += nt) __stcs(d2 + j, src[j]);
 }
 
-// x <- A x + C x_right + B xi for one real chain (tables t = [A | C | B], B lower); x_right
-// is read at xr[q * Nc] (null when the segment has no right anchor).
-template <class Real, int M>
-__device__ __forceinline__ void step_state(const Real* t, Real (&x)[M], const Real (&xi)[M], const Real* xr, int Nc)
+// x <- A x + C x_right + B xi for one real chain (tables t = [A | C | B], B lower).
+template <class Real, int M, bool RIGHT>
+__device__ __forceinline__ void step_state(const Real* t, Real (&x)[M], const Real* xi, const Real* xr)
 {
     Real xn[M];
 #pragma unroll
@@ -398,9 +520,9 @@ __device__ __forceinline__ void step_state(const Real* t, Real (&x)[M], const Re
         Real acc = 0;
 #pragma unroll
         for (int q = 0; q < M; ++q) acc = fma(t[p * M + q], x[q], acc);
-        if (xr) {
+        if (RIGHT) {
 #pragma unroll
-            for (int q = 0; q < M; ++q) acc = fma(t[M * M + p * M + q], xr[(size_t)q * Nc], acc);
+            for (int q = 0; q < M; ++q) acc = fma(t[M * M + p * M + q], xr[q], acc);
         }
         int e = 2 * M * M + p * (p + 1) / 2;
 #pragma unroll
@@ -411,14 +533,42 @@ __device__ __forceinline__ void step_state(const Real* t, Real (&x)[M], const Re
     for (int q = 0; q < M; ++q) x[q] = xn[q];
 }
 
+// Philox4x32-10 with precomputed round keys rk[i] = (k0 + i W0, k1 + i W1), i < 10
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const uint2* rk)
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint2 k = rk[r];
+        const uint64_t p0 = (uint64_t)M0 * c.x;
+        const uint64_t p1 = (uint64_t)M1 * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.x, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k.y, (uint32_t)p0);
+    }
+    return c;
+}
+
+template <class Real>
+__device__ __forceinline__ void unit_normals_rk(const uint2* rk, uint32_t call, uint32_t ring, Real (&n)[4])
+{
+    const uint4 w = philox_rk(make_uint4(call, ring, 0u, 0u), rk);
+    box_muller(w.x, w.y, n[0], n[1]);
+    box_muller(w.z, w.w, n[2], n[3]);
+}
+
+// Every ring of one segment of one chain for RMAX realisations.  Per ring: the recursion
+// for the thread's units (state in registers, tables read once per unit and shared by the
+// realisations), the coefficients into shared memory, the C2R FFT, the ring to HBM.
 template <class Real, class TabT, int M, int UPT, int RMAX, bool INPLACE>
 __global__ void __launch_bounds__(1024) segment_kernel(SampleParams P)
 {
     using C = cplx<Real>;
     constexpr int G = kG<M>;
-    constexpr int E = step_elems(M);
+    constexpr int ROW = step_row(M);
     constexpr int EPT = RMAX * UPT * G;   // complex FFT points per thread (in-place mode)
+    static_assert(2 * M * G == 4, "a unit holds four state values");
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint2 rk[RMAX][10];     // Philox round keys of the CTA's realisations
+    __shared__ Real nyq[RMAX * M];     // Nyquist chain state per realisation (thread 0)
 
     const Segment sg = P.segs[blockIdx.x];
     const int r0 = blockIdx.y * RMAX;
@@ -426,6 +576,7 @@ __global__ void __launch_bounds__(1024) segment_kernel(SampleParams P)
     const int c = sg.chain;
     const int nt = blockDim.x, tid = threadIdx.x;
     const int Nc = P.Nc;
+    const int n_units = P.n_units;
     const size_t mp = P.n_modes_pad;
     const Real* anc = (const Real*)P.anc;
     const bool has_right = sg.right >= 0;
@@ -436,35 +587,41 @@ __global__ void __launch_bounds__(1024) segment_kernel(SampleParams P)
     Real* xRs = reinterpret_cast<Real*>(buf0 + (size_t)RMAX * Nc * (INPLACE ? 1 : 2));
     const C* twp = (const C*)P.tw;
     const C* pre = (const C*)P.pre;
+    if (tid < RMAX * 10) {
+        const int r = tid / 10, i = tid % 10;
+        const uint64_t key = P.seed + (uint64_t)(r0 + r);
+        rk[r][i] = make_uint2((uint32_t)key + (uint32_t)i * 0x9E3779B9u, (uint32_t)(key >> 32) + (uint32_t)i * 0xBB67AE85u);
+    }
+    if (tid < R * M) nyq[tid] = anc[aoff<M>(P, c, r0 + tid / M, sg.left, M + tid % M, 0)];
     // right-anchor states: shared memory in ping-pong mode, the scratch itself in place mode;
-    // layout [f][slot] per realisation in both
+    // layout [slot][2M] per realisation in both
     const Real* xrg[RMAX];
 #pragma unroll
     for (int r = 0; r < RMAX; ++r)
         xrg[r] = anc + aoff<M>(P, c, min(r0 + r, P.n_samples - 1), has_right ? sg.right : 0, 0, 0);
     if (!INPLACE && has_right) {
         const int per = 2 * M * Nc;
-        for (int idx = tid; idx < R * per; idx += nt) {
+        for (int idx = 4 * tid; idx < R * per; idx += 4 * nt) {
             const int r = idx / per, rest = idx - r * per;
-            xRs[idx] = anc[aoff<M>(P, c, r0 + r, sg.right, 0, 0) + rest];
+            Real v[4];
+            Vec4<Real>::ldg(xrg[r] + rest, v);
+            Vec4<Real>::st(xRs + idx, v);
         }
     }
 
-    Real x[UPT][RMAX][G][2][M];
+    Real x[UPT][RMAX][4];  // per unit: [g][part][q] flattened (g * 2M + part * M + q)
 #pragma unroll
     for (int i = 0; i < UPT; ++i) {
         const int u = tid + i * nt;
 #pragma unroll
-        for (int r = 0; r < RMAX; ++r)
+        for (int r = 0; r < RMAX; ++r) {
+            if (u < n_units && r < R) {
+                Vec4<Real>::ldg(anc + aoff<M>(P, c, r0 + r, sg.left, 0, G * u), x[i][r]);
+            } else {
 #pragma unroll
-            for (int g = 0; g < G; ++g)
-#pragma unroll
-                for (int part = 0; part < 2; ++part)
-#pragma unroll
-                    for (int q = 0; q < M; ++q)
-                        x[i][r][g][part][q] = (u < P.n_units && r < R)
-                                                  ? anc[aoff<M>(P, c, r0 + r, sg.left, part * M + q, G * u + g)]
-                                                  : (Real)0;
+                for (int k = 0; k < 4; ++k) x[i][r][k] = 0;
+            }
+        }
     }
     __syncthreads();
 
@@ -472,60 +629,76 @@ __global__ void __launch_bounds__(1024) segment_kernel(SampleParams P)
     for (int pos = sg.p0; pos < sg.p1; ++pos) {
         const int ring = c == 0 ? P.k0 - pos : P.k0 + pos;
         if (pos > sg.p0) {
-            const TabT* tb = steps + (size_t)pos * E * mp;
+            const TabT* tb = steps + (size_t)pos * mp * ROW;
 #pragma unroll
             for (int i = 0; i < UPT; ++i) {
                 const int u = tid + i * nt;
-                if (u >= P.n_units) continue;
-                // tables of the unit's slots (mode = slot); slot 0's second chain is the
-                // Nyquist mode, stepped on a separate path that only unit 0 takes
-                Real ta[G][E];
+                if (u >= n_units) continue;
+                // tables of the unit's slots (mode = slot).  Slot 0's second chain (the
+                // Nyquist mode) is stepped here with mode 0's tables and discarded; thread 0
+                // steps the real Nyquist chain separately below.
+                Real ta[G][ROW];
 #pragma unroll
-                for (int g = 0; g < G; ++g)
-#pragma unroll
-                    for (int e = 0; e < E; ++e) ta[g][e] = tabld<Real, TabT>(tb + (size_t)e * mp + G * u + g);
+                for (int g = 0; g < G; ++g) load_row<Real, TabT, ROW>(tb + (size_t)(G * u + g) * ROW, ta[g]);
 #pragma unroll
                 for (int r = 0; r < RMAX; ++r) {
                     if (r >= R) continue;
                     Real nr[4];
-                    unit_normals<Real>(P.seed + (uint64_t)(r0 + r), (uint32_t)u, (uint32_t)ring, nr);
+                    unit_normals_rk<Real>(rk[r], (uint32_t)u, (uint32_t)ring, nr);
+                    if (has_right) {
+                        Real xr[4];
+                        if (INPLACE) Vec4<Real>::ldg(xrg[r] + (size_t)G * u * 2 * M, xr);
+                        else Vec4<Real>::ld(xRs + ((size_t)r * Nc + G * u) * 2 * M, xr);
 #pragma unroll
-                    for (int g = 0; g < G; ++g) {
-                        const int s = G * u + g;
+                        for (int g = 0; g < G; ++g)
 #pragma unroll
-                        for (int part = 0; part < 2; ++part) {
-                            Real xi[M];
-#pragma unroll
-                            for (int q = 0; q < M; ++q) {
-                                const Real v = nr[g * 2 * M + part * M + q];
-                                xi[q] = (c == 1 && (q & 1)) ? -v : v;
+                            for (int part = 0; part < 2; ++part) {
+                                Real* xs = &x[i][r][g * 2 * M + part * M];
+                                step_state<Real, M, true>(ta[g], *reinterpret_cast<Real(*)[M]>(xs),
+                                                          nr + g * 2 * M + part * M, xr + g * 2 * M + part * M);
                             }
-                            const Real* xr = INPLACE ? xrg[r] + (size_t)part * M * Nc + s
-                                                     : xRs + ((size_t)r * 2 * M + part * M) * Nc + s;
-                            if (part == 1 && s == 0) {
-                                Real tn[E];
+                    } else {
 #pragma unroll
-                                for (int e = 0; e < E; ++e) tn[e] = tabld<Real, TabT>(tb + (size_t)e * mp + Nc);
-                                step_state<Real, M>(tn, x[i][r][g][part], xi, has_right ? xr : nullptr, Nc);
-                            } else {
-                                step_state<Real, M>(ta[g], x[i][r][g][part], xi, has_right ? xr : nullptr, Nc);
+                        for (int g = 0; g < G; ++g)
+#pragma unroll
+                            for (int part = 0; part < 2; ++part) {
+                                Real* xs = &x[i][r][g * 2 * M + part * M];
+                                step_state<Real, M, false>(ta[g], *reinterpret_cast<Real(*)[M]>(xs),
+                                                           nr + g * 2 * M + part * M, nullptr);
                             }
-                        }
                     }
                 }
             }
+            if (tid == 0) {  // the Nyquist chain (normals [M, 2M) of unit 0)
+                Real tn[ROW];
+                load_row<Real, TabT, ROW>(tb + (size_t)Nc * ROW, tn);
+                for (int r = 0; r < R; ++r) {
+                    Real nr[4], xs[M], xr[M];
+                    unit_normals_rk<Real>(rk[r], 0u, (uint32_t)ring, nr);
+#pragma unroll
+                    for (int q = 0; q < M; ++q) {
+                        xs[q] = nyq[r * M + q];
+                        xr[q] = has_right ? (INPLACE ? xrg[r][M + q] : xRs[(size_t)r * Nc * 2 * M + M + q]) : (Real)0;
+                    }
+                    if (has_right) step_state<Real, M, true>(tn, xs, nr + M, xr);
+                    else step_state<Real, M, false>(tn, xs, nr + M, nullptr);
+#pragma unroll
+                    for (int q = 0; q < M; ++q) nyq[r * M + q] = xs[q];
+                }
+            }
         }
-        // coefficients of this ring into shared memory
+        // coefficients of this ring into shared memory (slot 0's imaginary part = Nyquist)
 #pragma unroll
         for (int i = 0; i < UPT; ++i) {
             const int u = tid + i * nt;
-            if (u >= P.n_units) continue;
+            if (u >= n_units) continue;
 #pragma unroll
             for (int r = 0; r < RMAX; ++r) {
                 if (r >= R) continue;
 #pragma unroll
                 for (int g = 0; g < G; ++g)
-                    buf0[(size_t)r * Nc + G * u + g] = cmk<C>(x[i][r][g][0][0], x[i][r][g][1][0]);
+                    buf0[(size_t)r * Nc + G * u + g] =
+                        cmk<C>(x[i][r][g * 2 * M], (u == 0 && g == 0) ? nyq[r * M] : x[i][r][g * 2 * M + M]);
             }
         }
         __syncthreads();
@@ -541,7 +714,7 @@ __global__ void __launch_bounds__(1024) segment_kernel(SampleParams P)
 #pragma unroll
                 for (int r = 0; r < RMAX; ++r)
                     gout[r] = (C*)((Real*)P.out + ((size_t)min(r0 + r, P.n_samples - 1) * P.n_theta + ring) * (size_t)P.n_phi);
-                c2r_rings_to_global<C>(buf0, buf1, R, P.lgNc, twp, pre, gout);
+                c2r_dispatch<C, UPT>(P.lgNc, buf0, buf1, R, twp, pre, gout);
             }
         }
         __syncthreads();  // buffers are rewritten by the next ring
@@ -587,7 +760,7 @@ int dispatch_upt(const SampleParams& P, int n_segments, int upt, int nt, size_t 
 }
 
 constexpr int kMaxThreads = 1024;
-constexpr size_t kMaxSmem = 227 * 1024;
+constexpr size_t kMaxSmem = 226 * 1024;  // leaves room for the static shared arrays
 
 // Launch configuration of the segment kernel for a plan: units per thread, threads,
 // realisations per CTA and the optional shared-memory parts.

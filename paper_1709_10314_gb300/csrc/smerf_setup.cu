@@ -224,11 +224,18 @@ __global__ void step_kernel(Spec sp, int c, int len, double* phi, double* qout)
         }
 }
 
+// Table store.  FP64 tables keep every entry at magnitude >= 2^-120 (zeros and smaller
+// values become +-2^-120, a change far below any effect on the field): FP32-recursion
+// kernels then convert them to FP32 with three integer instructions and no range check.
 template <class T>
 __device__ inline void put(void* base, bool is64, size_t idx, double v)
 {
-    if (is64) ((double*)base)[idx] = v;
-    else ((float*)base)[idx] = (float)v;
+    if (is64) {
+        const double tiny = 0x1p-120;
+        ((double*)base)[idx] = fabs(v) < tiny ? (v < 0.0 ? -tiny : tiny) : v;
+    } else {
+        ((float*)base)[idx] = (float)v;
+    }
 }
 
 // Start factor B_eq = chol J(z0, z0) (Eq. (state_initial)), one thread per mode.
@@ -286,9 +293,12 @@ __global__ void segment_tables_kernel(Spec sp, int c, int len, int H, const doub
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int seg = blockIdx.y;
     if (m >= sp.n_modes) return;
-    const int E = step_elems(M), Ec = coarse_elems(M);
+    const int Ec = coarse_elems(M);
     const size_t mp = sp.n_modes_pad;
     const double sc = m > 0 ? 0.70710678118654752440 : 1.0;
+    // the southern chain runs in the mirrored state S x and is driven by S xi; its B
+    // factors are stored with S folded into their columns so that the kernels use xi as is
+    auto colsign = [&](int q) { return (c == 1 && (q & 1)) ? -1.0 : 1.0; };
     const int pa = H > 0 ? seg * H : 0;
     const int pb = (H > 0 && pa + H <= len) ? pa + H : -1;
     auto load = [&](const double* base, int pos) {
@@ -299,14 +309,15 @@ __global__ void segment_tables_kernel(Spec sp, int c, int len, int H, const doub
         return r;
     };
     auto store_step = [&](int pos, const Mat<M>& A, const Mat<M>& C, const Mat<M>& B) {
-        const size_t base = (size_t)pos * E * mp + m;
+        const size_t base = ((size_t)pos * mp + m) * step_row(M);
         int e = 0;
         for (int p = 0; p < M; ++p)
-            for (int q = 0; q < M; ++q, ++e) put<double>(steps, tab64, base + (size_t)e * mp, A.a[p][q]);
+            for (int q = 0; q < M; ++q, ++e) put<double>(steps, tab64, base + e, A.a[p][q]);
         for (int p = 0; p < M; ++p)
-            for (int q = 0; q < M; ++q, ++e) put<double>(steps, tab64, base + (size_t)e * mp, C.a[p][q]);
+            for (int q = 0; q < M; ++q, ++e) put<double>(steps, tab64, base + e, C.a[p][q]);
         for (int p = 0; p < M; ++p)
-            for (int q = 0; q <= p; ++q, ++e) put<double>(steps, tab64, base + (size_t)e * mp, B.a[p][q] * sc);
+            for (int q = 0; q <= p; ++q, ++e) put<double>(steps, tab64, base + e, B.a[p][q] * sc * colsign(q));
+        for (; e < step_row(M); ++e) put<double>(steps, tab64, base + e, 0.0);
     };
     if (pb < 0) {
         const int end = len;
@@ -339,7 +350,7 @@ __global__ void segment_tables_kernel(Spec sp, int c, int len, int H, const doub
     for (int p = 0; p < M; ++p)
         for (int q = 0; q < M; ++q, ++e) put<double>(coarse, tab64, base + (size_t)e * mp, Psi.a[p][q]);
     for (int p = 0; p < M; ++p)
-        for (int q = 0; q <= p; ++q, ++e) put<double>(coarse, tab64, base + (size_t)e * mp, Bc.a[p][q] * sc);
+        for (int q = 0; q <= p; ++q, ++e) put<double>(coarse, tab64, base + (size_t)e * mp, Bc.a[p][q] * sc * colsign(q));
 }
 
 // FFT tables, in FP64 on the host then rounded to the recursion precision:
@@ -431,7 +442,7 @@ int setup_impl(smerf_plan* pl)
     pl->table_bytes += (size_t)tri(M) * mp * es;
     for (int c = 0; c < 2; ++c) {
         const int len = pl->chain[c].len;
-        const size_t sb = (size_t)(len + 1) * step_elems(M) * mp * es;
+        const size_t sb = (size_t)(len + 1) * step_row(M) * mp * es;
         const size_t cb = (size_t)(pl->chain[c].n_anchors + 1) * coarse_elems(M) * mp * es;
         CK(cudaMalloc(&pl->steps[c], sb > 0 ? sb : 16));
         CK(cudaMemset(pl->steps[c], 0, sb > 0 ? sb : 16));
