@@ -25,7 +25,7 @@ sys.path.insert(0, ROOT)
 
 KAPPA = [20.0, 50.0]
 AMP = 1.0
-N_THETA, N_PHI, N_REAL, ANCHOR, SEED = 1024, 2048, 64, 32, 1
+N_THETA, N_PHI, N_REAL, ANCHOR, SEED = 1024, 2048, 64, 16, 1
 WORKLOAD = ("1024x2048 equiangular grid, C_l=1/((l(l+1)+20^2)(l(l+1)+50^2)) (p=2), 64 realisations, "
             "FP64 tables, FP32 recursion+FFT")
 METRIC = "sphere grid points/s"

@@ -65,7 +65,7 @@ typedef struct smerf_plan smerf_plan;
  *   flags          SMERF_* plan flags
  *   anchor_spacing H: every H-th ring of each chain is sampled first (an "anchor"); the
  *                  rings between two anchors are then sampled conditionally on both ends,
- *                  independently of other segments.  0 selects the default (32), and any
+ *                  independently of other segments.  0 selects the default (16), and any
  *                  H >= n_theta (or SMERF_ORDER_PAPER) means no anchors.  The anchor order
  *                  changes the map from noise to field, not the field's law.
  *   out_plan       receives the plan (host pointer to a pointer)

@@ -15,7 +15,7 @@
 namespace smerf {
 
 constexpr int kMaxP = 2;             // spectrum factors supported by the kernels
-constexpr int kDefaultAnchor = 32;   // default anchor spacing H
+constexpr int kDefaultAnchor = 16;   // default anchor spacing H
 
 // ------------------------------------------------------------------ plan
 struct Chain {

@@ -37,6 +37,7 @@ struct SampleParams {
     int n_samples, n_theta, n_phi, Nc, n_units, n_modes_pad, k0, H, na_max;
     int n_anchors[2];
     int pingpong;     // 1: two FFT buffers + right anchors on chip; 0: one buffer, in place
+    int np;           // warp-specialised kernel: producer threads
     int lgNc;
 };
 
@@ -570,8 +571,8 @@ __global__ void __launch_bounds__(1024) segment_kernel(SampleParams P)
     __shared__ uint2 rk[RMAX][10];     // Philox round keys of the CTA's realisations
     __shared__ Real nyq[RMAX * M];     // Nyquist chain state per realisation (thread 0)
 
-    const Segment sg = P.segs[blockIdx.x];
-    const int r0 = blockIdx.y * RMAX;
+    const Segment sg = P.segs[blockIdx.y];
+    const int r0 = blockIdx.x * RMAX;
     const int R = min(RMAX, P.n_samples - r0);
     const int c = sg.chain;
     const int nt = blockDim.x, tid = threadIdx.x;
@@ -703,7 +704,7 @@ __global__ void __launch_bounds__(1024) segment_kernel(SampleParams P)
         }
         __syncthreads();
         if (!(c == 1 && pos == 0)) {  // the start ring is written by the northern chain
-            if (INPLACE) {
+            if constexpr (INPLACE) {
                 c2r_rings_inplace<C, EPT>(buf0, R, P.lgNc, twp, pre);
                 for (int r = 0; r < R; ++r) {
                     Real* dst = (Real*)P.out + ((size_t)(r0 + r) * P.n_theta + ring) * (size_t)P.n_phi;
@@ -721,50 +722,387 @@ __global__ void __launch_bounds__(1024) segment_kernel(SampleParams P)
     }
 }
 
-// ------------------------------------------------------------------ launch
-template <class Real, class TabT, int M, int UPT, int RMAX, bool INPLACE = false>
-int launch_segments(const SampleParams& P, int n_segments, int nt, size_t smem, cudaStream_t st)
+// ------------------------------------------------------------------ warp-specialised
+// Named hardware barriers (bar.sync waits, bar.arrive does not); counts are thread counts,
+// multiples of 32, and every participating thread executes the same sequence.
+__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void bar_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+constexpr int kBarFull = 1;   // + buffer index: coefficients of a ring are ready
+constexpr int kBarEmpty = 3;  // + buffer index: the FFT group is done with a buffer
+constexpr int kBarFft = 5;    // FFT group internal
+
+// FFT group version of the fixed-size pass: threads ftid < nf of the group, group barrier
+// between passes.
+template <class C, int LGNC, int LGNS, bool FIRST>
+__device__ __forceinline__ void grp_pass(const C* __restrict__ src, C* __restrict__ dst, int R,
+                                         const C* __restrict__ twp, const C* __restrict__ pre, C* const* gout,
+                                         int ftid, int nf)
 {
-    auto kern = segment_kernel<Real, TabT, M, UPT, RMAX, INPLACE>;
-    if (smem > 48 * 1024) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return SMERF_ECUDA;
+    constexpr int Nc = 1 << LGNC, Ns = 1 << LGNS;
+    constexpr int RP = (Nc / Ns >= 4) ? 4 : 2, LR = RP == 4 ? 2 : 1;
+    constexpr bool LAST = Ns * RP == Nc;
+    constexpr int LGNB = LGNC - LR, nb = 1 << LGNB;
+    const int total = R << LGNB;
+#pragma unroll 4
+    for (int b = ftid; b < total; b += nf) {
+        const int r = b >> LGNB, j = b & (nb - 1);
+        const C* S = src + (r << LGNC);
+        C v[RP];
+        int kk = 0;
+        if (FIRST) {
+            {
+                const C a = S[j], bb = cconj(S[(Nc - j) & (Nc - 1)]);
+                const C g = cadd(cadd(a, bb), cmuli(cmul(__ldg(pre + j), csub(a, bb))));
+                const C z0 = cmk<C>(a.x + a.y, a.x - a.y);
+                v[0] = j == 0 ? z0 : g;
+            }
+#pragma unroll
+            for (int i = 1; i < RP; ++i) {
+                const int sidx = j + i * nb;
+                const C a = S[sidx], bb = cconj(S[Nc - sidx]);
+                v[i] = cadd(cadd(a, bb), cmuli(cmul(__ldg(pre + sidx), csub(a, bb))));
+            }
+        } else {
+            kk = j & (Ns - 1);
+#pragma unroll
+            for (int i = 0; i < RP; ++i) v[i] = S[j + i * nb];
+#pragma unroll
+            for (int i = 1; i < RP; ++i) v[i] = cmul(v[i], __ldg(twp + (i - 1) * Ns + kk));
+        }
+        dft<C, RP>(v);
+        const int idx = ((j - kk) << LR) + kk;
+        if (LAST) {
+            C* D = gout[r] + idx;
+#pragma unroll
+            for (int a = 0; a < RP; ++a) __stcs(D + a * Ns, v[a]);
+        } else {
+            C* D = dst + (r << LGNC) + idx;
+#pragma unroll
+            for (int a = 0; a < RP; ++a) D[a * Ns] = v[a];
+        }
     }
-    dim3 grid(n_segments, (P.n_samples + RMAX - 1) / RMAX);
+}
+
+template <class C, int LGNC, int LGNS = 0, int OFF = 0, bool FIRST = true>
+__device__ __forceinline__ void grp_c2r_fixed(C* src, C* dst, int R, const C* twp, const C* pre, C* const* gout,
+                                              int ftid, int nf)
+{
+    constexpr int Nc = 1 << LGNC, Ns = 1 << LGNS;
+    constexpr int RP = (Nc / Ns >= 4) ? 4 : 2, LR = RP == 4 ? 2 : 1;
+    grp_pass<C, LGNC, LGNS, FIRST>(src, dst, R, twp + OFF, pre, gout, ftid, nf);
+    if constexpr (Ns * RP < Nc) {
+        bar_sync(kBarFft, nf);
+        grp_c2r_fixed<C, LGNC, LGNS + LR, OFF + (FIRST ? 0 : (RP - 1) * Ns), false>(dst, src, R, twp, pre, gout,
+                                                                                   ftid, nf);
+    }
+}
+
+// general size (runtime log2 Nc)
+template <class C, int RP, bool FIRST, bool LAST>
+__device__ __forceinline__ void grp_pass_rt(const C* __restrict__ src, C* __restrict__ dst, int R, int lgNc, int Ns,
+                                            const C* __restrict__ twp, const C* __restrict__ pre, C* const* gout,
+                                            int ftid, int nf)
+{
+    const int Nc = 1 << lgNc;
+    constexpr int LR = RP == 4 ? 2 : 1;
+    const int lgnb = lgNc - LR;
+    const int nb = 1 << lgnb;
+    const int total = R << lgnb;
+    for (int b = ftid; b < total; b += nf) {
+        const int r = b >> lgnb, j = b & (nb - 1);
+        const C* S = src + (r << lgNc);
+        C v[RP];
+        int kk = 0;
+        if (FIRST) {
+#pragma unroll
+            for (int i = 0; i < RP; ++i) v[i] = c2r_pack(S, j + i * nb, Nc, pre);
+        } else {
+            kk = j & (Ns - 1);
+#pragma unroll
+            for (int i = 0; i < RP; ++i) v[i] = S[j + i * nb];
+#pragma unroll
+            for (int i = 1; i < RP; ++i) v[i] = cmul(v[i], __ldg(twp + (i - 1) * Ns + kk));
+        }
+        dft<C, RP>(v);
+        const int idx = ((j - kk) << LR) + kk;
+        if (LAST) {
+            C* D = gout[r] + idx;
+#pragma unroll
+            for (int a = 0; a < RP; ++a) __stcs(D + a * Ns, v[a]);
+        } else {
+            C* D = dst + (r << lgNc) + idx;
+#pragma unroll
+            for (int a = 0; a < RP; ++a) D[a * Ns] = v[a];
+        }
+    }
+}
+
+template <class C>
+__device__ __forceinline__ void grp_c2r_rt(C* buf0, C* buf1, int R, int lgNc, const C* twp, const C* pre,
+                                           C* const* gout, int ftid, int nf)
+{
+    const int Nc = 1 << lgNc;
+    C* src = buf0;
+    C* dst = buf1;
+    int Ns = 1, off = 0;
+    bool first = true;
+    while (Ns < Nc) {
+        const int RP = pass_radix(lgNc, Ns);
+        const bool last = Ns * RP == Nc;
+        if (RP == 4) {
+            if (first) {
+                if (last) grp_pass_rt<C, 4, true, true>(src, dst, R, lgNc, Ns, twp + off, pre, gout, ftid, nf);
+                else grp_pass_rt<C, 4, true, false>(src, dst, R, lgNc, Ns, twp + off, pre, gout, ftid, nf);
+            } else {
+                if (last) grp_pass_rt<C, 4, false, true>(src, dst, R, lgNc, Ns, twp + off, pre, gout, ftid, nf);
+                else grp_pass_rt<C, 4, false, false>(src, dst, R, lgNc, Ns, twp + off, pre, gout, ftid, nf);
+            }
+        } else {
+            if (first) {
+                if (last) grp_pass_rt<C, 2, true, true>(src, dst, R, lgNc, Ns, twp + off, pre, gout, ftid, nf);
+                else grp_pass_rt<C, 2, true, false>(src, dst, R, lgNc, Ns, twp + off, pre, gout, ftid, nf);
+            } else {
+                if (last) grp_pass_rt<C, 2, false, true>(src, dst, R, lgNc, Ns, twp + off, pre, gout, ftid, nf);
+                else grp_pass_rt<C, 2, false, false>(src, dst, R, lgNc, Ns, twp + off, pre, gout, ftid, nf);
+            }
+        }
+        if (!first) off += (RP - 1) * Ns;
+        Ns *= RP;
+        first = false;
+        if (!last) bar_sync(kBarFft, nf);
+        C* t = src;
+        src = dst;
+        dst = t;
+    }
+}
+
+template <class C, bool FIXED>
+__device__ __forceinline__ void grp_c2r(int lgNc, C* b0, C* b1, int R, const C* twp, const C* pre, C* const* gout,
+                                        int ftid, int nf)
+{
+    if (FIXED) {
+        switch (lgNc) {
+            case 2: grp_c2r_fixed<C, 2>(b0, b1, R, twp, pre, gout, ftid, nf); return;
+            case 3: grp_c2r_fixed<C, 3>(b0, b1, R, twp, pre, gout, ftid, nf); return;
+            case 4: grp_c2r_fixed<C, 4>(b0, b1, R, twp, pre, gout, ftid, nf); return;
+            case 5: grp_c2r_fixed<C, 5>(b0, b1, R, twp, pre, gout, ftid, nf); return;
+            case 6: grp_c2r_fixed<C, 6>(b0, b1, R, twp, pre, gout, ftid, nf); return;
+            case 7: grp_c2r_fixed<C, 7>(b0, b1, R, twp, pre, gout, ftid, nf); return;
+            case 8: grp_c2r_fixed<C, 8>(b0, b1, R, twp, pre, gout, ftid, nf); return;
+            case 9: grp_c2r_fixed<C, 9>(b0, b1, R, twp, pre, gout, ftid, nf); return;
+            case 10: grp_c2r_fixed<C, 10>(b0, b1, R, twp, pre, gout, ftid, nf); return;
+            case 11: grp_c2r_fixed<C, 11>(b0, b1, R, twp, pre, gout, ftid, nf); return;
+            case 12: grp_c2r_fixed<C, 12>(b0, b1, R, twp, pre, gout, ftid, nf); return;
+            default: break;
+        }
+    }
+    grp_c2r_rt<C>(b0, b1, R, lgNc, twp, pre, gout, ftid, nf);
+}
+
+// Warp-specialised segment kernel.  Threads [0, NP) are the producer group: the recursion of
+// ring k (state in registers, units tid, tid + NP, ...) into coefficient buffer B[k & 1].
+// Threads [NP, NP + NF) are the FFT group: the C2R FFT of ring k from B[k & 1] (with W as
+// the second ping-pong buffer), last pass straight to HBM.  Handoff per ring:
+//   producer: (k >= 2: sync EMPTY[k&1]) produce; arrive FULL[k&1]; after the last ring it
+//             syncs the two outstanding EMPTY barriers
+//   FFT:      sync FULL[k&1]; FFT; arrive EMPTY[k&1]
+// Every FULL/EMPTY barrier counts NP + NF threads; the FFT passes use a group barrier.
+template <class Real, class TabT, int M, int UPT, int RMAX>
+__global__ void __launch_bounds__(768) segment_ws_kernel(SampleParams P)
+{
+    using C = cplx<Real>;
+    constexpr int G = kG<M>;
+    constexpr int ROW = step_row(M);
+    static_assert(2 * M * G == 4, "a unit holds four state values");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint2 rk[RMAX][10];
+    __shared__ Real nyq[RMAX * M];
+
+    const Segment sg = P.segs[blockIdx.y];
+    const int r0 = blockIdx.x * RMAX;
+    const int R = min(RMAX, P.n_samples - r0);
+    const int c = sg.chain;
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int NP = P.np, NF = nt - P.np;
+    const int Nc = P.Nc;
+    const int n_units = P.n_units;
+    const size_t mp = P.n_modes_pad;
+    const Real* anc = (const Real*)P.anc;
+    const bool has_right = sg.right >= 0;
+    const int nrings = sg.p1 - sg.p0;
+
+    C* bufs = reinterpret_cast<C*>(smem_raw);  // B0, B1, W: RMAX * Nc each
+    C* W = bufs + (size_t)2 * RMAX * Nc;
+    Real* xRs = reinterpret_cast<Real*>(bufs + (size_t)3 * RMAX * Nc);
+    const C* twp = (const C*)P.tw;
+    const C* pre = (const C*)P.pre;
+    if (tid < RMAX * 10) {
+        const int r = tid / 10, i = tid % 10;
+        const uint64_t key = P.seed + (uint64_t)(r0 + r);
+        rk[r][i] = make_uint2((uint32_t)key + (uint32_t)i * 0x9E3779B9u, (uint32_t)(key >> 32) + (uint32_t)i * 0xBB67AE85u);
+    }
+    if (tid < R * M) nyq[tid] = anc[aoff<M>(P, c, r0 + tid / M, sg.left, M + tid % M, 0)];
+    if (has_right) {
+        const int per = 2 * M * Nc;
+        for (int idx = 4 * tid; idx < R * per; idx += 4 * nt) {
+            const int r = idx / per, rest = idx - r * per;
+            Real v[4];
+            Vec4<Real>::ldg(anc + aoff<M>(P, c, r0 + r, sg.right, 0, 0) + rest, v);
+            Vec4<Real>::st(xRs + idx, v);
+        }
+    }
+    __syncthreads();
+
+    if (tid < NP) {
+        // ------------------------------------------------ producer group
+        Real x[UPT][RMAX][4];
+#pragma unroll
+        for (int i = 0; i < UPT; ++i) {
+            const int u = tid + i * NP;
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r) {
+                if (u < n_units && r < R) {
+                    Vec4<Real>::ldg(anc + aoff<M>(P, c, r0 + r, sg.left, 0, G * u), x[i][r]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) x[i][r][k] = 0;
+                }
+            }
+        }
+        const TabT* steps = (const TabT*)P.steps[c];
+        for (int k = 0; k < nrings + 2; ++k) {
+            if (k >= 2) bar_sync(kBarEmpty + (k & 1), nt);
+            if (k >= nrings) continue;
+            const int pos = sg.p0 + k;
+            const int ring = c == 0 ? P.k0 - pos : P.k0 + pos;
+            C* B = bufs + (size_t)(k & 1) * RMAX * Nc;
+            if (k > 0) {
+                const TabT* tb = steps + (size_t)pos * mp * ROW;
+#pragma unroll
+                for (int i = 0; i < UPT; ++i) {
+                    const int u = tid + i * NP;
+                    if (u >= n_units) continue;
+                    Real ta[G][ROW];
+#pragma unroll
+                    for (int g = 0; g < G; ++g) load_row<Real, TabT, ROW>(tb + (size_t)(G * u + g) * ROW, ta[g]);
+#pragma unroll
+                    for (int r = 0; r < RMAX; ++r) {
+                        if (r >= R) continue;
+                        Real nr[4];
+                        unit_normals_rk<Real>(rk[r], (uint32_t)u, (uint32_t)ring, nr);
+                        if (has_right) {
+                            Real xr[4];
+                            Vec4<Real>::ld(xRs + ((size_t)r * Nc + G * u) * 2 * M, xr);
+#pragma unroll
+                            for (int g = 0; g < G; ++g)
+#pragma unroll
+                                for (int part = 0; part < 2; ++part)
+                                    step_state<Real, M, true>(ta[g], *reinterpret_cast<Real(*)[M]>(&x[i][r][g * 2 * M + part * M]),
+                                                              nr + g * 2 * M + part * M, xr + g * 2 * M + part * M);
+                        } else {
+#pragma unroll
+                            for (int g = 0; g < G; ++g)
+#pragma unroll
+                                for (int part = 0; part < 2; ++part)
+                                    step_state<Real, M, false>(ta[g], *reinterpret_cast<Real(*)[M]>(&x[i][r][g * 2 * M + part * M]),
+                                                               nr + g * 2 * M + part * M, nullptr);
+                        }
+                    }
+                }
+                if (tid == 0) {  // the Nyquist chain (normals [M, 2M) of unit 0)
+                    Real tn[ROW];
+                    load_row<Real, TabT, ROW>(tb + (size_t)Nc * ROW, tn);
+                    for (int r = 0; r < R; ++r) {
+                        Real nr[4], xs[M], xr[M];
+                        unit_normals_rk<Real>(rk[r], 0u, (uint32_t)ring, nr);
+#pragma unroll
+                        for (int q = 0; q < M; ++q) {
+                            xs[q] = nyq[r * M + q];
+                            xr[q] = has_right ? xRs[(size_t)r * Nc * 2 * M + M + q] : (Real)0;
+                        }
+                        if (has_right) step_state<Real, M, true>(tn, xs, nr + M, xr);
+                        else step_state<Real, M, false>(tn, xs, nr + M, nullptr);
+#pragma unroll
+                        for (int q = 0; q < M; ++q) nyq[r * M + q] = xs[q];
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < UPT; ++i) {
+                const int u = tid + i * NP;
+                if (u >= n_units) continue;
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r) {
+                    if (r >= R) continue;
+#pragma unroll
+                    for (int g = 0; g < G; ++g)
+                        B[(size_t)r * Nc + G * u + g] =
+                            cmk<C>(x[i][r][g * 2 * M], (u == 0 && g == 0) ? nyq[r * M] : x[i][r][g * 2 * M + M]);
+                }
+            }
+            __threadfence_block();
+            bar_arrive(kBarFull + (k & 1), nt);
+        }
+    } else {
+        // ------------------------------------------------ FFT group
+        const int ftid = tid - NP;
+        for (int k = 0; k < nrings; ++k) {
+            bar_sync(kBarFull + (k & 1), nt);
+            const int pos = sg.p0 + k;
+            const int ring = c == 0 ? P.k0 - pos : P.k0 + pos;
+            C* B = bufs + (size_t)(k & 1) * RMAX * Nc;
+            if (!(c == 1 && pos == 0)) {  // the start ring is written by the northern chain
+                C* gout[RMAX];
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r)
+                    gout[r] = (C*)((Real*)P.out + ((size_t)min(r0 + r, P.n_samples - 1) * P.n_theta + ring) * (size_t)P.n_phi);
+                grp_c2r<C, sizeof(Real) == 4>(P.lgNc, B, W, R, twp, pre, gout, ftid, NF);
+            }
+            bar_arrive(kBarEmpty + (k & 1), nt);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ launch
+constexpr int kMaxThreads = 1024;
+constexpr size_t kMaxSmem = 226 * 1024;  // leaves room for the static shared arrays
+
+template <class Real, class TabT, int M, int UPT, int RMAX>
+int launch_ws(const SampleParams& P, int n_segments, int nt, size_t smem, cudaStream_t st)
+{
+    auto kern = segment_ws_kernel<Real, TabT, M, UPT, RMAX>;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return SMERF_ECUDA;
+    dim3 grid((P.n_samples + RMAX - 1) / RMAX, n_segments);
     kern<<<grid, nt, smem, st>>>(P);
     return cudaGetLastError() == cudaSuccess ? SMERF_OK : SMERF_ECUDA;
 }
 
-// (units per thread, realisations per CTA) pairs that are built: four realisations per CTA
-// share each table load while the state fits in 64 registers, fewer for wide grids;
-// FP64 recursion keeps one.
-template <class Real> constexpr int rmax_for(int upt)
+template <class Real, class TabT, int M, int UPT>
+int launch_inplace(const SampleParams& P, int n_segments, int nt, size_t smem, cudaStream_t st)
 {
-    return sizeof(Real) == 8 ? 1 : (upt == 1 ? 4 : (upt == 2 ? 2 : 1));
+    auto kern = segment_kernel<Real, TabT, M, UPT, 1, true>;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return SMERF_ECUDA;
+    dim3 grid(P.n_samples, n_segments);
+    kern<<<grid, nt, smem, st>>>(P);
+    return cudaGetLastError() == cudaSuccess ? SMERF_OK : SMERF_ECUDA;
 }
 
-template <class Real, class TabT, int M>
-int dispatch_upt(const SampleParams& P, int n_segments, int upt, int nt, size_t smem, cudaStream_t st)
+// Launch configuration of the segment kernels for a plan.  Warp-specialised kernel when its
+// three FFT buffers and the right-anchor states fit on chip: producer threads np = units /
+// upt (<= 512), FFT threads np/2, rmax realisations per CTA (as many as registers and shared
+// memory allow).  Otherwise the in-place kernel (one FFT buffer, anchors read from the
+// scratch, one realisation per CTA, up to 1024 threads).
+struct SegConfig { int ws, upt, nt, np, rmax; size_t smem; };
+
+template <class Real> constexpr int ws_rmax_cap(int upt)
 {
-    switch (upt) {
-        case 1: return launch_segments<Real, TabT, M, 1, rmax_for<Real>(1)>(P, n_segments, nt, smem, st);
-        case 2: return launch_segments<Real, TabT, M, 2, rmax_for<Real>(2)>(P, n_segments, nt, smem, st);
-        case 4:
-            return P.pingpong ? launch_segments<Real, TabT, M, 4, rmax_for<Real>(4)>(P, n_segments, nt, smem, st)
-                              : launch_segments<Real, TabT, M, 4, rmax_for<Real>(4), true>(P, n_segments, nt, smem, st);
-        case 8:
-            return P.pingpong ? launch_segments<Real, TabT, M, 8, rmax_for<Real>(8)>(P, n_segments, nt, smem, st)
-                              : launch_segments<Real, TabT, M, 8, rmax_for<Real>(8), true>(P, n_segments, nt, smem, st);
-        default: return SMERF_EUNSUPPORTED;
-    }
+    return sizeof(Real) == 8 ? 1 : (upt <= 2 ? 4 : (upt == 4 ? 2 : 1));
 }
-
-constexpr int kMaxThreads = 1024;
-constexpr size_t kMaxSmem = 226 * 1024;  // leaves room for the static shared arrays
-
-// Launch configuration of the segment kernel for a plan: units per thread, threads,
-// realisations per CTA and the optional shared-memory parts.
-struct SegConfig { int upt, nt, rmax; size_t smem; int pingpong; };
 
 template <class Real>
 inline SegConfig seg_config(const smerf_plan* pl)
@@ -772,22 +1110,72 @@ inline SegConfig seg_config(const smerf_plan* pl)
     SegConfig cfg{};
     const int M = pl->p;
     const int n_units = pl->n_slots / unit_slots(M);
+    const int Nc = pl->n_phi / 2;
     int upt = 1;
+    while (upt < 8 && (n_units + upt - 1) / upt > 512) upt *= 2;
+    if ((n_units + upt - 1) / upt <= 512) {
+        int np = (n_units + upt - 1) / upt;
+        np = ((np + 31) / 32) * 32;
+        int nf = ((np / 2 + 31) / 32) * 32;
+        if (nf < 32) nf = 32;
+        for (int rmax = ws_rmax_cap<Real>(upt); rmax >= 1; rmax /= 2) {
+            const size_t smem = (size_t)3 * rmax * Nc * 2 * sizeof(Real) +
+                                (pl->H > 0 ? (size_t)rmax * Nc * 2 * M * sizeof(Real) : 0);
+            if (smem <= kMaxSmem) {
+                cfg.ws = 1;
+                cfg.upt = upt;
+                cfg.np = np;
+                cfg.nt = np + nf;
+                cfg.rmax = rmax;
+                cfg.smem = smem;
+                return cfg;
+            }
+        }
+    }
+    upt = 1;
     while (upt < 8 && (n_units + upt - 1) / upt > kMaxThreads) upt *= 2;
+    if (upt < 4) upt = 4;
     int nt = (n_units + upt - 1) / upt;
     nt = ((nt + 31) / 32) * 32;
     if (nt < 64) nt = 64;
-    const int rmax = rmax_for<Real>(upt);
-    const int Nc = pl->n_phi / 2;
-    const size_t one = (size_t)rmax * Nc * 2 * sizeof(Real);
-    const size_t xr = pl->H > 0 ? (size_t)rmax * 2 * M * Nc * sizeof(Real) : 0;
+    cfg.ws = 0;
     cfg.upt = upt;
     cfg.nt = nt;
-    cfg.rmax = rmax;
-    // ping-pong: two FFT buffers and the right-anchor states on chip; otherwise one buffer
-    cfg.pingpong = (2 * one + xr <= kMaxSmem) ? 1 : 0;
-    cfg.smem = cfg.pingpong ? 2 * one + xr : one;
+    cfg.rmax = 1;
+    cfg.smem = (size_t)Nc * 2 * sizeof(Real);
     return cfg;
+}
+
+template <class Real, class TabT, int M>
+int dispatch_segments(const SampleParams& P, int n_segments, const SegConfig& cfg, cudaStream_t st)
+{
+    if (cfg.ws) {
+        if constexpr (sizeof(Real) == 8) {
+            switch (cfg.upt) {
+                case 1: return launch_ws<Real, TabT, M, 1, 1>(P, n_segments, cfg.nt, cfg.smem, st);
+                case 2: return launch_ws<Real, TabT, M, 2, 1>(P, n_segments, cfg.nt, cfg.smem, st);
+                case 4: return launch_ws<Real, TabT, M, 4, 1>(P, n_segments, cfg.nt, cfg.smem, st);
+                case 8: return launch_ws<Real, TabT, M, 8, 1>(P, n_segments, cfg.nt, cfg.smem, st);
+                default: return SMERF_EUNSUPPORTED;
+            }
+        } else {
+        const int key = cfg.upt * 8 + cfg.rmax;
+        switch (key) {
+            case 1 * 8 + 4: return launch_ws<Real, TabT, M, 1, 4>(P, n_segments, cfg.nt, cfg.smem, st);
+            case 2 * 8 + 4: return launch_ws<Real, TabT, M, 2, 4>(P, n_segments, cfg.nt, cfg.smem, st);
+            case 2 * 8 + 2: return launch_ws<Real, TabT, M, 2, 2>(P, n_segments, cfg.nt, cfg.smem, st);
+            case 4 * 8 + 2: return launch_ws<Real, TabT, M, 4, 2>(P, n_segments, cfg.nt, cfg.smem, st);
+            case 4 * 8 + 1: return launch_ws<Real, TabT, M, 4, 1>(P, n_segments, cfg.nt, cfg.smem, st);
+            case 8 * 8 + 1: return launch_ws<Real, TabT, M, 8, 1>(P, n_segments, cfg.nt, cfg.smem, st);
+            default: return SMERF_EUNSUPPORTED;
+        }
+        }
+    }
+    switch (cfg.upt) {
+        case 4: return launch_inplace<Real, TabT, M, 4>(P, n_segments, cfg.nt, cfg.smem, st);
+        case 8: return launch_inplace<Real, TabT, M, 8>(P, n_segments, cfg.nt, cfg.smem, st);
+        default: return SMERF_EUNSUPPORTED;
+    }
 }
 
 template <class Real, class TabT>
@@ -819,9 +1207,10 @@ int launch_sample_t(const smerf_plan* pl, uint64_t seed, int n, void* out, void*
     P.na_max = P.n_anchors[0] > P.n_anchors[1] ? P.n_anchors[0] : P.n_anchors[1];
     const SegConfig cfg = seg_config<Real>(pl);
     if (cfg.smem > kMaxSmem) return SMERF_EUNSUPPORTED;  // one ring per realisation must fit on chip
-    if ((pl->n_slots / unit_slots(pl->p) + cfg.upt - 1) / cfg.upt > kMaxThreads) return SMERF_EUNSUPPORTED;
-    if (!cfg.pingpong && cfg.upt < 4) return SMERF_EUNSUPPORTED;
-    P.pingpong = cfg.pingpong;
+    if (!cfg.ws && (pl->n_slots / unit_slots(pl->p) + cfg.upt - 1) / cfg.upt > kMaxThreads) return SMERF_EUNSUPPORTED;
+    if (pl->n_segments > 65535) return SMERF_EUNSUPPORTED;
+    P.pingpong = cfg.ws;
+    P.np = cfg.np;
     int lg = 0;
     while ((1 << lg) < P.Nc) ++lg;
     P.lgNc = lg;
@@ -832,8 +1221,8 @@ int launch_sample_t(const smerf_plan* pl, uint64_t seed, int n, void* out, void*
         if (cudaGetLastError() != cudaSuccess) return SMERF_ECUDA;
     }
     if (ev0 && cudaEventRecord(ev0, st) != cudaSuccess) return SMERF_ECUDA;
-    const int rc = pl->p == 1 ? dispatch_upt<Real, TabT, 1>(P, pl->n_segments, cfg.upt, cfg.nt, cfg.smem, st)
-                              : dispatch_upt<Real, TabT, 2>(P, pl->n_segments, cfg.upt, cfg.nt, cfg.smem, st);
+    const int rc = pl->p == 1 ? dispatch_segments<Real, TabT, 1>(P, pl->n_segments, cfg, st)
+                              : dispatch_segments<Real, TabT, 2>(P, pl->n_segments, cfg, st);
     if (rc == SMERF_OK && ev1 && cudaEventRecord(ev1, st) != cudaSuccess) return SMERF_ECUDA;
     return rc;
 }
