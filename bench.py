@@ -93,6 +93,17 @@ class Clocks:
         return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def csrc_digest():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    base = os.path.join(ROOT, "paper_1709_10314_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(base, "*.cu")) + glob.glob(os.path.join(base, "*.cuh"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def oracle_sample_step(n_real=1, seed=SEED):
     """The oracle on a bounded sample of the workload: the start ring (k0) of n_real
     realisations, including the oracle's own covariance construction for that ring."""
@@ -187,11 +198,15 @@ def run_gb300(args, rank, world, local_rank):
     alg_bytes = out_bytes + info["table_bytes"]
     peak, peak_kind = _peaks()
     achieved = alg_bytes / (seg_ms / 1e3) / 1e9
+    # DRAM traffic of one segment-kernel launch from the committed ncu record, only while the
+    # kernel sources still hash to what was profiled (null otherwise)
     traffic = None
     prof = os.path.join(ROOT, "profiles", "segment_kernel_traffic.json")
-    if os.path.exists(prof):
+    if os.path.exists(prof) and args.tables == "fp64":
         try:
-            traffic = json.load(open(prof)).get("traffic_bytes_per_launch")
+            rec = json.load(open(prof))
+            if rec.get("csrc_sha256_16") == csrc_digest():
+                traffic = rec.get("traffic_bytes_per_launch")
         except Exception:
             traffic = None
 
