@@ -146,29 +146,95 @@ def run_reference(args, rank, world):
 def run_gb300(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
-    from paper_1709_10314_gb300 import SMERF_TABLES_FP64, Plan
+    from paper_1709_10314_gb300 import Batch, Plan
+    from paper_1709_10314_gb300.replicas import max_over_ranks, rank_seed
+    from paper_1709_10314_gb300.workloads import FIXED, flags_for, uneven_requests
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    from paper_1709_10314_gb300 import SMERF_TABLES_FP32
-    tflag = SMERF_TABLES_FP32 if args.tables == "fp32" else SMERF_TABLES_FP64
-    plan = Plan(KAPPA, AMP, N_THETA, N_PHI, flags=tflag, anchor_spacing=ANCHOR)
-    info = plan.info()
-    out = torch.empty((N_REAL, N_THETA, N_PHI), dtype=torch.float32, device=dev)
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    seed0 = SEED + rank * N_REAL * (args.warmup + args.steps + 8)
+    wl = args.workload
+    batch = None
+    if wl == "uneven-256":
+        reqs = uneven_requests()
+        plans = [Plan(r["kappa"], r["A"], r["n_theta"], r["n_phi"], flags=flags_for("fp32", args.tables or "fp32"))
+                 for r in reqs]
+        counts = [r["n"] for r in reqs]
+        base_seeds = [r["seed"] for r in reqs]
+        outs = [torch.empty((n, p.n_theta, p.n_phi), dtype=torch.float32, device=dev) for p, n in zip(plans, counts)]
+        batch = Batch(plans, counts)
+        points = sum(n * p.n_theta * p.n_phi for p, n in zip(plans, counts))
+        table_bytes = sum(p.info()["table_bytes"] for p in plans)
+        out_bytes = points * 4
+        workload = ("uneven batch: 256 requests, n_theta in {128,256,512,1024}, n_phi=2 n_theta, kappa in [5,200], "
+                    "p in {1,2}, 1-8 realisations, FP32 recursion, FP%s tables, one CUDA-graph replay per step"
+                    % ("64" if args.tables == "fp64" else "32"))
+        dtype = "f32"
+        setup_ms = sum(p.info()["setup_ms"] for p in plans)
+        s_cap = torch.cuda.Stream(device=dev)
 
-    for w in range(args.warmup):
-        plan.sample(seed0 + w * N_REAL, N_REAL, out)
-        flush.fill_(float(w))
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+        def set_seeds(step):
+            off = rank_seed(0, rank, 1 << 40) + (step << 20)
+            batch.set([b_ + off for b_ in base_seeds], outs)
+
+        set_seeds(0)
+        with torch.cuda.stream(s_cap):
+            batch.launch(stream=s_cap)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s_cap, capture_error_mode="relaxed"):
+            batch.launch(stream=s_cap)
+        launches = 2 * batch.info()["groups"] + batch.info()["singles"] * 2
+
+        def step(i, ev0=None, ev1=None):
+            torch.cuda.synchronize()
+            set_seeds(i)
+            if ev0 is not None:
+                ev0.record()
+            graph.replay()
+            if ev1 is not None:
+                ev1.record()
+    else:
+        cfg = dict(FIXED[wl])
+        recur = args.recur or cfg["recur"]
+        tables = args.tables or cfg["tables"]
+        from paper_1709_10314_gb300 import SMERF_ORDER_PAPER
+        paper_order = cfg.get("order") == "paper"
+        plan = Plan(cfg["kappa"], cfg["A"], cfg["n_theta"], cfg["n_phi"],
+                    flags=flags_for(recur, tables) | (SMERF_ORDER_PAPER if paper_order else 0),
+                    anchor_spacing=0 if paper_order else ANCHOR)
+        info = plan.info()
+        n = cfg["n"]
+        out = torch.empty((n, cfg["n_theta"], cfg["n_phi"]), dtype=plan.dtype, device=dev)
+        points = n * cfg["n_theta"] * cfg["n_phi"]
+        out_bytes = points * (8 if recur == "fp64" else 4)
+        table_bytes = info["table_bytes"]
+        setup_ms = info["setup_ms"]
+        dtype = "f64" if recur == "fp64" else "f32"
+        workload = "%dx%d equiangular grid, C_l=1/prod(l(l+1)+kappa^2) kappa=%s (p=%d), %d realisations, %s tables, %s recursion+FFT" % (
+            cfg["n_theta"], cfg["n_phi"], "(" + ",".join("%g" % k for k in cfg["kappa"]) + ")", len(cfg["kappa"]), n,
+            tables.upper(), recur.upper())
+        launches = 2
+        seed0 = rank_seed(cfg["seed"], rank, n * (args.warmup + args.steps + 8))
+
+        def step(i, ev0=None, ev1=None):
+            if ev0 is not None:
+                ev0.record()
+            plan.sample_timed(seed0 + i * n, n, out, s0[i], s1[i]) if ev0 is not None else plan.sample(seed0 + i * n, n, out)
+            if ev1 is not None:
+                ev1.record()
+
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     ev = lambda: torch.cuda.Event(enable_timing=True)
     e0 = [ev() for _ in range(args.steps)]
     e1 = [ev() for _ in range(args.steps)]
     s0 = [ev() for _ in range(args.steps)]
     s1 = [ev() for _ in range(args.steps)]
+    for w in range(args.warmup):
+        step(args.steps + w)
+        flush.fill_(float(w))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     clk = Clocks(local_rank)
     clk.start()
     time.sleep(0.3)
@@ -176,33 +242,31 @@ def run_gb300(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     for i in range(args.steps):
-        e0[i].record()
-        plan.sample_timed(seed0 + (args.warmup + i) * N_REAL, N_REAL, out, s0[i], s1[i])
-        e1[i].record()
+        step(i, e0[i], e1[i])
         flush.fill_(float(i))  # L2 flush between timed steps (outside the step events)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clocks = clk.stop()
     step_ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / args.steps
-    seg_ms = sum(a.elapsed_time(b) for a, b in zip(s0, s1)) / args.steps
-    if world > 1:
-        t = torch.tensor([step_ms, seg_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms, seg_ms = float(t[0]), float(t[1])
-    points = N_REAL * N_THETA * N_PHI
+    if batch is None:
+        seg_ms = sum(a.elapsed_time(b) for a, b in zip(s0, s1)) / args.steps
+        kernel = "segment_ws_kernel"
+    else:
+        seg_ms = step_ms  # the graph replay: all groups' anchor + segment launches
+        kernel = "batched graph replay (anchor + segment launches of every group)"
+    step_ms, seg_ms = max_over_ranks([step_ms, seg_ms], device=dev)
     value = world * points / (step_ms / 1e3)
 
     # roofline of the segment kernel: algorithmic bytes = field written once + tables read once
-    out_bytes = points * 4
-    alg_bytes = out_bytes + info["table_bytes"]
+    alg_bytes = out_bytes + table_bytes
     peak, peak_kind = _peaks()
     achieved = alg_bytes / (seg_ms / 1e3) / 1e9
     # DRAM traffic of one segment-kernel launch from the committed ncu record, only while the
     # kernel sources still hash to what was profiled (null otherwise)
     traffic = None
     prof = os.path.join(ROOT, "profiles", "segment_kernel_traffic.json")
-    if os.path.exists(prof) and args.tables == "fp64":
+    if os.path.exists(prof) and wl == "1024x2048-p2" and (args.tables or "fp64") == "fp64" and not args.recur:
         try:
             rec = json.load(open(prof))
             if rec.get("csrc_sha256_16") == csrc_digest():
@@ -211,39 +275,40 @@ def run_gb300(args, rank, world, local_rank):
             traffic = None
 
     # end to end through the C ABI with a host buffer (device->host copy inside)
-    host = torch.empty((N_REAL, N_THETA, N_PHI), dtype=torch.float32, pin_memory=True)
-    plan.sample_host(seed0, N_REAL, host)
-    ne = 3
-    t0 = time.perf_counter()
-    for i in range(ne):
-        plan.sample_host(seed0 + i * N_REAL, N_REAL, host)
-    e2e_s = (time.perf_counter() - t0) / ne
-    e2e_val = world * points / e2e_s
+    e2e = None
+    if batch is None:
+        host = torch.empty(tuple(out.shape), dtype=out.dtype, pin_memory=True)
+        plan.sample_host(seed0, n, host)
+        ne = 3
+        t0 = time.perf_counter()
+        for i in range(ne):
+            plan.sample_host(seed0 + i * n, n, host)
+        e2e_s = (time.perf_counter() - t0) / ne
+        e2e = {"value": world * points / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": out_bytes}
 
     if rank != 0:
         return
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and wl == "1024x2048-p2":
         dt, pts = oracle_sample_step(n_real=4)
         cpu = {"value": pts / dt, "unit": "points/s", "cores": cpu_cores(), "kind": "oracle",
                "sample": "start ring (k0=512) of realisations 1-4 of the workload (4 x 2048 points), "
                          "the oracle's spectral-sum covariance, Cholesky, Philox noise and naive DFT"}
     line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.tables == "fp64" else WORKLOAD.replace("FP64 tables", "FP32 tables"),
-                       "n_theta": N_THETA, "n_phi": N_PHI, "realisations_per_gpu": N_REAL,
-                       "anchor_spacing": ANCHOR, "parallelism": "replicas" if world > 1 else "single",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": workload, "name": wl, "points_per_gpu": points, "anchor_spacing": ANCHOR,
+                       "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between timed steps (256 MiB write outside the step events)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "segment_kernel", "kernel_ms": seg_ms, "algorithmic_bytes": alg_bytes},
+                         "kernel": kernel, "kernel_ms": seg_ms, "algorithmic_bytes": alg_bytes},
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_val, "unit": "points/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": out_bytes},
-            "gpu_launches": 2 * args.steps,
+            "e2e": e2e,
+            "gpu_launches": launches * args.steps,
             "clocks": clocks,
-            "setup_ms": info["setup_ms"], "table_bytes": info["table_bytes"]}
+            "setup_ms": setup_ms, "table_bytes": table_bytes}
     print(json.dumps(line), flush=True)
 
 
@@ -254,8 +319,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--tables", default="fp64", choices=["fp64", "fp32"],
-                    help="table storage precision (the workload specifies fp64)")
+    ap.add_argument("--tables", default=None, choices=["fp64", "fp32"],
+                    help="override the workload's table storage precision")
+    ap.add_argument("--recur", default=None, choices=["fp64", "fp32"],
+                    help="override the workload's recursion precision")
+    ap.add_argument("--workload", default="1024x2048-p2",
+                    choices=["1024x2048-p2", "plain-64x128-p1-fp64", "4096x8192-p1", "16384x32768-p1", "uneven-256"])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

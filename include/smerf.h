@@ -121,12 +121,41 @@ int smerf_sample_host(const smerf_plan* plan, uint64_t seed, int n_samples, void
 
 /*
  * smerf_sample_batched -- n_req independent requests (plans may differ in grid, spectrum
- * and precision) issued back to back on one stream; request i behaves exactly like
- * smerf_sample(plans[i], seeds[i], n_samples[i], outs[i], stream).  Host arrays of length
- * n_req; outs[i] are device pointers.
+ * and precision) in one call; request i produces exactly what
+ * smerf_sample(plans[i], seeds[i], n_samples[i], outs[i], stream) produces.  Requests of
+ * the same kernel shape (precision, p, n_phi, anchored or not) run as one anchor launch and
+ * one segment launch over a device work list.  Host arrays of length n_req; outs[i] are
+ * device pointers.  Builds a temporary smerf_batch and synchronises `stream` before
+ * returning.
  */
 int smerf_sample_batched(const smerf_plan* const* plans, const uint64_t* seeds,
                          const int* n_samples, void* const* outs, int n_req, void* stream);
+
+/*
+ * Reusable batches (for repeated sampling and CUDA graphs).
+ *
+ * smerf_batch_create: groups the requests (plans[i], n_samples[i]) by kernel shape, builds
+ *   the device work lists and allocates all scratch.  Synchronous.  The plans must outlive
+ *   the batch.
+ * smerf_batch_set: stores seeds[i] and device outputs outs[i] (16-byte aligned) in the
+ *   batch's pinned staging memory.  Host-only; the previous launch's copy of the staging
+ *   memory must have completed (synchronise its stream first).
+ * smerf_batch_launch: copies the staging memory to the device and launches every group on
+ *   `stream` (asynchronous).  Capturable into a CUDA graph: a replay re-reads the staging
+ *   memory, so smerf_batch_set between replays changes seeds and outputs.  Requests whose
+ *   shape has no batched kernel (n_phi = 32768 in FP32) are launched individually with the
+ *   seeds and outputs current at capture.
+ * smerf_batch_sample: smerf_batch_set + smerf_batch_launch.
+ * smerf_batch_info: number of batched groups and of individually launched requests.
+ * smerf_batch_destroy: frees the batch; synchronise its streams first.  NULL is accepted.
+ */
+typedef struct smerf_batch smerf_batch;
+int smerf_batch_create(const smerf_plan* const* plans, const int* n_samples, int n_req, smerf_batch** out);
+int smerf_batch_set(smerf_batch* batch, const uint64_t* seeds, void* const* outs);
+int smerf_batch_launch(smerf_batch* batch, void* stream);
+int smerf_batch_sample(smerf_batch* batch, const uint64_t* seeds, void* const* outs, void* stream);
+int smerf_batch_info(const smerf_batch* batch, int* n_groups, int* n_singles);
+int smerf_batch_destroy(smerf_batch* batch);
 
 /*
  * smerf_sample_noalloc -- smerf_sample without any device allocation.  The paper has no

@@ -342,7 +342,7 @@ def sample(kappa, A, n_theta, n_phi, seed, n_samples=1, H=0, K=6, rings=None,
     return res
 
 
-def mode_variances(kappa, A, n_theta, n_phi, K=6, rings=None):
+def mode_variances(kappa, A, n_theta, n_phi, K=6, rings=None, **level_kw):
     """J^m_00(z_k, z_k) = E|g_m(z_k)|^2 for m = 0..n_phi/2 at the given rings
     (Lemma 2.1).  Returns [n_phi/2+1][n_rings]."""
     kappa = np.asarray(kappa, dtype=np.float64)
@@ -352,7 +352,7 @@ def mode_variances(kappa, A, n_theta, n_phi, K=6, rings=None):
     ms = list(range(n_phi // 2 + 1))
     out = np.zeros((len(ms), len(idx)))
     for i, t in enumerate(th):
-        S = cov_modes(ms, kappa, A, np.array([t]), K=K)
+        S = cov_modes(ms, kappa, A, np.array([t]), K=K, **level_kw)
         out[:, i] = S[:, 0, 0]
     return out
 

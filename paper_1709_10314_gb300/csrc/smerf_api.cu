@@ -7,7 +7,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "smerf_internal.cuh"
@@ -61,6 +64,21 @@ __global__ void normals_kernel(uint64_t key64, uint32_t ring, int64_t n, Real* o
 }
 
 }  // namespace
+
+// Largest dynamic shared memory already granted to each (kernel, device): the attribute is
+// set once, so that later launches (e.g. under stream capture) make no attribute calls.
+int smerf_smem_attr_done(const void* kern, int dev, size_t smem, bool record)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> granted;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& g = granted[std::make_pair(kern, dev)];
+    if (record) {
+        if (smem > g) g = smem;
+        return 1;
+    }
+    return smem <= g ? 1 : 0;
+}
 
 size_t smerf_scratch_bytes(const smerf_plan* pl, int n_samples)
 {
@@ -243,17 +261,6 @@ int smerf_sample_host(const smerf_plan* plan, uint64_t seed, int n_samples, void
     cudaFreeAsync(dout, st);
     if (cudaStreamSynchronize(st) != cudaSuccess && rc == SMERF_OK) rc = SMERF_ECUDA;
     return rc;
-}
-
-int smerf_sample_batched(const smerf_plan* const* plans, const uint64_t* seeds, const int* n_samples,
-                         void* const* outs, int n_req, void* stream)
-{
-    if (n_req < 0 || (n_req > 0 && (!plans || !seeds || !n_samples || !outs))) return SMERF_EINVAL;
-    for (int i = 0; i < n_req; ++i) {
-        const int rc = smerf_sample(plans[i], seeds[i], n_samples[i], outs[i], stream);
-        if (rc != SMERF_OK) return rc;
-    }
-    return SMERF_OK;
 }
 
 int smerf_plan_info(const smerf_plan* plan, smerf_plan_info_t* info)

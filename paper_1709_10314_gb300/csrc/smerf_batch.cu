@@ -1,0 +1,245 @@
+// smerf_batch.cu -- batched sampling: many requests (plans of different grids, spectra and
+// precisions) in few launches.  Requests of the same kernel shape (recursion and table
+// precision, p, n_phi, anchored or not) form a group that runs as one anchor launch and one
+// segment launch over a device work list; per-request parameters (tables, seed, output,
+// scratch) are read from a descriptor array in device memory.  The work lists and the
+// scratch are built once per batch, so a launch (descriptor copy + kernels) can be captured
+// into a CUDA graph and replayed with new seeds and outputs.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "smerf_internal.cuh"
+
+using smerf::SampleParams;
+
+namespace {
+
+enum Kind { kFF = 0, kFD = 1, kDD = 2, kDF = 3 };
+
+int kind_of(const smerf_plan* pl) { return pl->recur64 ? (pl->tab64 ? kDD : kDF) : (pl->tab64 ? kFD : kFF); }
+
+int fill_params(int kind, const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch, SampleParams* P,
+                int* batchable, int* rmax)
+{
+    switch (kind) {
+        case kFF: return smerf_fill_params_ff(pl, seed, n, out, scratch, P, batchable, rmax);
+        case kFD: return smerf_fill_params_fd(pl, seed, n, out, scratch, P, batchable, rmax);
+        case kDD: return smerf_fill_params_dd(pl, seed, n, out, scratch, P, batchable, rmax);
+        default: return smerf_fill_params_df(pl, seed, n, out, scratch, P, batchable, rmax);
+    }
+}
+
+int launch_group(int kind, const smerf_plan* rep, const SampleParams* d, const int4* a, int na, const int4* s, int ns,
+                 cudaStream_t st)
+{
+    switch (kind) {
+        case kFF: return smerf_launch_group_ff(rep, d, a, na, s, ns, st);
+        case kFD: return smerf_launch_group_fd(rep, d, a, na, s, ns, st);
+        case kDD: return smerf_launch_group_dd(rep, d, a, na, s, ns, st);
+        default: return smerf_launch_group_df(rep, d, a, na, s, ns, st);
+    }
+}
+
+struct Group {
+    int kind;
+    const smerf_plan* rep;
+    int4* d_anc = nullptr;
+    int n_anc = 0;
+    int4* d_seg = nullptr;
+    int n_seg = 0;
+};
+
+}  // namespace
+
+struct smerf_batch {
+    int n_req = 0;
+    int dev = 0;
+    std::vector<const smerf_plan*> plans;
+    std::vector<int> counts;
+    std::vector<size_t> offs;
+    std::vector<int> singles;  // requests whose shape has no batched kernel (launched one by one)
+    std::vector<Group> groups;
+    void* scratch = nullptr;
+    SampleParams* h_descs = nullptr;  // pinned staging
+    SampleParams* d_descs = nullptr;
+    std::vector<uint64_t> seeds;
+    std::vector<void*> outs;
+};
+
+static void batch_free(smerf_batch* b)
+{
+    if (!b) return;
+    for (auto& g : b->groups) {
+        cudaFree(g.d_anc);
+        cudaFree(g.d_seg);
+    }
+    cudaFree(b->scratch);
+    cudaFree(b->d_descs);
+    cudaFreeHost(b->h_descs);
+    delete b;
+}
+
+extern "C" {
+
+int smerf_batch_create(const smerf_plan* const* plans, const int* n_samples, int n_req, smerf_batch** out)
+{
+    if (!out) return SMERF_EINVAL;
+    *out = nullptr;
+    if (n_req < 0 || (n_req > 0 && (!plans || !n_samples))) return SMERF_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SMERF_ECUDA;
+    for (int i = 0; i < n_req; ++i)
+        if (!plans[i] || n_samples[i] < 0 || n_samples[i] > 65535 || plans[i]->dev != dev) return SMERF_EINVAL;
+    smerf_batch* b = new (std::nothrow) smerf_batch;
+    if (!b) return SMERF_ENOMEM;
+    b->n_req = n_req;
+    b->dev = dev;
+    b->plans.assign(plans, plans + n_req);
+    b->counts.assign(n_samples, n_samples + n_req);
+    b->seeds.assign(n_req, 0);
+    b->outs.assign(n_req, nullptr);
+    size_t total = 0;
+    for (int i = 0; i < n_req; ++i) {
+        b->offs.push_back(total);
+        total += (smerf_scratch_bytes(plans[i], n_samples[i]) + 255) & ~(size_t)255;
+    }
+    int rc = SMERF_OK;
+    if (total && cudaMalloc(&b->scratch, total) != cudaSuccess) rc = SMERF_ENOMEM;
+    if (rc == SMERF_OK && n_req) {
+        if (cudaMallocHost((void**)&b->h_descs, sizeof(SampleParams) * n_req) != cudaSuccess ||
+            cudaMalloc((void**)&b->d_descs, sizeof(SampleParams) * n_req) != cudaSuccess)
+            rc = SMERF_ENOMEM;
+    }
+    // group by kernel shape; build the work lists
+    std::map<std::tuple<int, int, int, int>, int> gidx;
+    std::vector<std::vector<int4>> anc, seg;
+    for (int i = 0; rc == SMERF_OK && i < n_req; ++i) {
+        const smerf_plan* pl = plans[i];
+        const int n = n_samples[i];
+        int batchable = 0, rmax = 1;
+        const int kind = kind_of(pl);
+        rc = fill_params(kind, pl, 0, n, nullptr, (char*)b->scratch + b->offs[i], &b->h_descs[i], &batchable, &rmax);
+        if (rc != SMERF_OK || n == 0) continue;
+        if (!batchable) {
+            b->singles.push_back(i);
+            continue;
+        }
+        const auto key = std::make_tuple(kind, pl->p, pl->n_phi, pl->H > 0 ? 1 : 0);
+        auto it = gidx.find(key);
+        int g;
+        if (it == gidx.end()) {
+            g = (int)b->groups.size();
+            gidx[key] = g;
+            Group gr;
+            gr.kind = kind;
+            gr.rep = pl;
+            b->groups.push_back(gr);
+            anc.emplace_back();
+            seg.emplace_back();
+        } else {
+            g = it->second;
+        }
+        const int n_units = pl->n_slots / smerf::unit_slots(pl->p);
+        for (int c = 0; c < 2; ++c)
+            for (int r = 0; r < n; ++r)
+                for (int ub = 0; ub < (n_units + 127) / 128; ++ub) anc[g].push_back(make_int4(i, ub, r, c));
+        for (int sgi = 0; sgi < pl->n_segments; ++sgi)
+            for (int gr = 0; gr < (n + rmax - 1) / rmax; ++gr) seg[g].push_back(make_int4(i, sgi, gr, 0));
+    }
+    for (size_t g = 0; rc == SMERF_OK && g < b->groups.size(); ++g) {
+        Group& gr = b->groups[g];
+        gr.n_anc = (int)anc[g].size();
+        gr.n_seg = (int)seg[g].size();
+        if (cudaMalloc(&gr.d_anc, sizeof(int4) * gr.n_anc) != cudaSuccess ||
+            cudaMalloc(&gr.d_seg, sizeof(int4) * gr.n_seg) != cudaSuccess) {
+            rc = SMERF_ENOMEM;
+            break;
+        }
+        if (cudaMemcpy(gr.d_anc, anc[g].data(), sizeof(int4) * gr.n_anc, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(gr.d_seg, seg[g].data(), sizeof(int4) * gr.n_seg, cudaMemcpyHostToDevice) != cudaSuccess)
+            rc = SMERF_ECUDA;
+    }
+    if (rc != SMERF_OK) {
+        batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return SMERF_OK;
+}
+
+int smerf_batch_set(smerf_batch* b, const uint64_t* seeds, void* const* outs)
+{
+    if (!b || (b->n_req > 0 && (!seeds || !outs))) return SMERF_EINVAL;
+    for (int i = 0; i < b->n_req; ++i) {
+        if (b->counts[i] > 0 && (!outs[i] || ((uintptr_t)outs[i] & 15u))) return SMERF_EINVAL;
+        b->seeds[i] = seeds[i];
+        b->outs[i] = outs[i];
+        b->h_descs[i].seed = seeds[i];
+        b->h_descs[i].out = outs[i];
+    }
+    return SMERF_OK;
+}
+
+int smerf_batch_launch(smerf_batch* b, void* stream)
+{
+    if (!b) return SMERF_EINVAL;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != b->dev) return SMERF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (b->n_req == 0) return SMERF_OK;
+    if (cudaMemcpyAsync(b->d_descs, b->h_descs, sizeof(SampleParams) * b->n_req, cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return SMERF_ECUDA;
+    for (const Group& g : b->groups) {
+        const int rc = launch_group(g.kind, g.rep, b->d_descs, g.d_anc, g.n_anc, g.d_seg, g.n_seg, st);
+        if (rc != SMERF_OK) return rc;
+    }
+    for (int i : b->singles) {
+        const int rc = smerf_launch_sample(b->plans[i], b->seeds[i], b->counts[i], b->outs[i],
+                                           (char*)b->scratch + b->offs[i], st);
+        if (rc != SMERF_OK) return rc;
+    }
+    return SMERF_OK;
+}
+
+int smerf_batch_sample(smerf_batch* b, const uint64_t* seeds, void* const* outs, void* stream)
+{
+    const int rc = smerf_batch_set(b, seeds, outs);
+    return rc != SMERF_OK ? rc : smerf_batch_launch(b, stream);
+}
+
+int smerf_batch_info(const smerf_batch* b, int* n_groups, int* n_singles)
+{
+    if (!b) return SMERF_EINVAL;
+    if (n_groups) *n_groups = (int)b->groups.size();
+    if (n_singles) *n_singles = (int)b->singles.size();
+    return SMERF_OK;
+}
+
+int smerf_batch_destroy(smerf_batch* b)
+{
+    batch_free(b);
+    return SMERF_OK;
+}
+
+int smerf_sample_batched(const smerf_plan* const* plans, const uint64_t* seeds, const int* n_samples,
+                         void* const* outs, int n_req, void* stream)
+{
+    if (n_req < 0 || (n_req > 0 && (!plans || !seeds || !n_samples || !outs))) return SMERF_EINVAL;
+    if (n_req == 0) return SMERF_OK;
+    smerf_batch* b = nullptr;
+    int rc = smerf_batch_create(plans, n_samples, n_req, &b);
+    if (rc != SMERF_OK) return rc;
+    rc = smerf_batch_sample(b, seeds, outs, stream);
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess && rc == SMERF_OK) rc = SMERF_ECUDA;
+    smerf_batch_destroy(b);
+    return rc;
+}
+
+}  // extern "C"

@@ -67,6 +67,26 @@ __host__ __device__ constexpr int step_elems(int M) { return 2 * M * M + tri(M);
 __host__ __device__ constexpr int step_row(int M) { return (step_elems(M) + 3) & ~3; }
 __host__ __device__ constexpr int coarse_elems(int M) { return M * M + tri(M); }
 
+// Everything a sampling kernel needs about one request (plan tables, grid, seed, output,
+// scratch); passed by value to single-request kernels and through device memory to batched
+// ones.
+struct SampleParams {
+    const Segment* segs;
+    const void* steps[2];
+    const void* coarse[2];
+    const void* beq;
+    const void* tw;   // per-pass complex twiddle tables (see pass_radix)
+    const void* pre;  // complex e^{2 pi i s / n_phi}, s < Nc
+    void* anc;        // anchor states [c][r][j][2M][n_slots]
+    void* out;
+    uint64_t seed;
+    int n_samples, n_theta, n_phi, Nc, n_units, n_modes_pad, k0, H, na_max;
+    int n_anchors[2];
+    int pingpong;     // 1: two FFT buffers + right anchors on chip; 0: one buffer, in place
+    int np;           // warp-specialised kernel: producer threads
+    int lgNc;
+};
+
 // units: the slots whose normals fill whole Philox calls.  p = 1: 2 slots per call;
 // p = 2: 1 slot per call.
 __host__ __device__ constexpr int unit_slots(int M) { return M == 1 ? 2 : 1; }
@@ -146,5 +166,21 @@ int smerf_launch_sample(const smerf_plan* plan, uint64_t seed, int n_samples, vo
                         void* scratch, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
                         cudaEvent_t ev1 = nullptr);
 size_t smerf_scratch_bytes(const smerf_plan* plan, int n_samples);
+// batched launches (smerf_batch.cu): per precision pair XX in {ff, fd, dd, df}
+//   smerf_fill_params_XX: the request's SampleParams and whether it can join a batched group
+//   smerf_launch_group_XX: one anchor and one segment launch over a group's work items
+#define SMERF_DECLARE_GROUP(XX)                                                                   \
+    int smerf_fill_params_##XX(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch, \
+                               smerf::SampleParams* P, int* batchable, int* rmax);                 \
+    int smerf_launch_group_##XX(const smerf_plan* rep, const smerf::SampleParams* d_descs,          \
+                                const int4* anc_items, int n_anc, const int4* seg_items, int n_seg,  \
+                                cudaStream_t st);
+SMERF_DECLARE_GROUP(ff)
+SMERF_DECLARE_GROUP(fd)
+SMERF_DECLARE_GROUP(dd)
+SMERF_DECLARE_GROUP(df)
+
+// dynamic shared-memory attribute bookkeeping (smerf_api.cu)
+int smerf_smem_attr_done(const void* kern, int dev, size_t smem, bool record);
 int smerf_launch_philox(uint64_t key64, uint32_t ring, int64_t ncalls, uint32_t* out, cudaStream_t s);
 int smerf_launch_normals(uint64_t key64, uint32_t ring, int64_t n, int fp64, void* out, cudaStream_t s);

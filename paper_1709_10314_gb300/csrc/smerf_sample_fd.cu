@@ -6,3 +6,15 @@ int smerf_launch_sample_fd(const smerf_plan* pl, uint64_t seed, int n, void* out
 {
     return smerf::launch_sample_t<float, double>(pl, seed, n, out, scratch, st, ev0, ev1);
 }
+
+int smerf_fill_params_fd(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch,
+                         smerf::SampleParams* P, int* batchable, int* rmax)
+{
+    return smerf::fill_params_c<float, double>(pl, seed, n, out, scratch, P, batchable, rmax);
+}
+
+int smerf_launch_group_fd(const smerf_plan* rep, const smerf::SampleParams* d_descs, const int4* anc_items,
+                          int n_anc, const int4* seg_items, int n_seg, cudaStream_t st)
+{
+    return smerf::launch_group_t<float, double>(rep, d_descs, anc_items, n_anc, seg_items, n_seg, st);
+}

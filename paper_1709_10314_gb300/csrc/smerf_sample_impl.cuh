@@ -24,22 +24,6 @@
 
 namespace smerf {
 
-struct SampleParams {
-    const Segment* segs;
-    const void* steps[2];
-    const void* coarse[2];
-    const void* beq;
-    const void* tw;   // per-pass complex twiddle tables (see pass_radix)
-    const void* pre;  // complex e^{2 pi i s / n_phi}, s < Nc
-    void* anc;        // anchor states [c][r][j][2M][n_slots]
-    void* out;
-    uint64_t seed;
-    int n_samples, n_theta, n_phi, Nc, n_units, n_modes_pad, k0, H, na_max;
-    int n_anchors[2];
-    int pingpong;     // 1: two FFT buffers + right anchors on chip; 0: one buffer, in place
-    int np;           // warp-specialised kernel: producer threads
-    int lgNc;
-};
 
 template <int M> constexpr int kG = unit_slots(M);
 
@@ -107,15 +91,12 @@ __device__ __forceinline__ void load_row(const TabT* p, Real (&t)[ROW])
 
 // ------------------------------------------------------------------ anchors
 template <class Real, class TabT, int M>
-__global__ void __launch_bounds__(128) anchor_kernel(SampleParams P)
+__device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r, int c)
 {
     constexpr int G = kG<M>;
     constexpr int T = tri(M);
     constexpr int Ec = coarse_elems(M);
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y;
-    const int c = blockIdx.z;
-    if (u >= P.n_units) return;
+    if (u >= P.n_units || r >= P.n_samples) return;
     const size_t mp = P.n_modes_pad;
     const uint64_t key = P.seed + (uint64_t)r;
     Real* anc = (Real*)P.anc;
@@ -187,6 +168,23 @@ __global__ void __launch_bounds__(128) anchor_kernel(SampleParams P)
         Vec4<Real>::st(anc + aoff<M>(P, c, r, j, 0, G * u), v);
     }
     (void)T;
+}
+
+// one thread per (chain c, realisation r, unit u)
+template <class Real, class TabT, int M>
+__global__ void __launch_bounds__(128) anchor_kernel(SampleParams P)
+{
+    anchor_body<Real, TabT, M>(P, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// batched: item = (request, block of 128 units, realisation, chain)
+template <class Real, class TabT, int M>
+__global__ void __launch_bounds__(128) anchor_batched_kernel(const SampleParams* __restrict__ descs,
+                                                             const int4* __restrict__ items)
+{
+    const int4 it = items[blockIdx.x];
+    const SampleParams P = descs[it.x];
+    anchor_body<Real, TabT, M>(P, it.y * blockDim.x + threadIdx.x, it.z, it.w);
 }
 
 // ------------------------------------------------------------------ FFT
@@ -909,7 +907,7 @@ __device__ __forceinline__ void grp_c2r(int lgNc, C* b0, C* b1, int R, const C* 
 //   FFT:      sync FULL[k&1]; FFT; arrive EMPTY[k&1]
 // Every FULL/EMPTY barrier counts NP + NF threads; the FFT passes use a group barrier.
 template <class Real, class TabT, int M, int UPT, int RMAX>
-__global__ void __launch_bounds__(768) segment_ws_kernel(SampleParams P)
+__device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, int group)
 {
     using C = cplx<Real>;
     constexpr int G = kG<M>;
@@ -919,8 +917,8 @@ __global__ void __launch_bounds__(768) segment_ws_kernel(SampleParams P)
     __shared__ uint2 rk[RMAX][10];
     __shared__ Real nyq[RMAX * M];
 
-    const Segment sg = P.segs[blockIdx.y];
-    const int r0 = blockIdx.x * RMAX;
+    const Segment sg = P.segs[seg_index];
+    const int r0 = group * RMAX;
     const int R = min(RMAX, P.n_samples - r0);
     const int c = sg.chain;
     const int nt = blockDim.x, tid = threadIdx.x;
@@ -1064,7 +1062,38 @@ __global__ void __launch_bounds__(768) segment_ws_kernel(SampleParams P)
     }
 }
 
+template <class Real, class TabT, int M, int UPT, int RMAX>
+__global__ void __launch_bounds__(768) segment_ws_kernel(SampleParams P)
+{
+    ws_body<Real, TabT, M, UPT, RMAX>(P, blockIdx.y, blockIdx.x);
+}
+
+// batched: item = (request, segment, realisation group); all requests of a launch share the
+// kernel shape (precision, p, n_phi, anchors or not) and hence the launch configuration
+template <class Real, class TabT, int M, int UPT, int RMAX>
+__global__ void __launch_bounds__(768) segment_ws_batched_kernel(const SampleParams* __restrict__ descs,
+                                                                 const int4* __restrict__ items)
+{
+    const int4 it = items[blockIdx.x];
+    const SampleParams P = descs[it.x];
+    ws_body<Real, TabT, M, UPT, RMAX>(P, it.y, it.z);
+}
+
 // ------------------------------------------------------------------ launch
+// Raise a kernel's dynamic shared-memory limit to what it needs, once per kernel and size
+// (so that later launches, e.g. under stream capture, make no attribute calls).
+template <class K>
+inline cudaError_t set_smem_attr(K kern, size_t smem)
+{
+    if (smem <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (::smerf_smem_attr_done((const void*)kern, dev, smem, false)) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) ::smerf_smem_attr_done((const void*)kern, dev, smem, true);
+    return e;
+}
+
 constexpr int kMaxThreads = 1024;
 constexpr size_t kMaxSmem = 226 * 1024;  // leaves room for the static shared arrays
 
@@ -1072,9 +1101,7 @@ template <class Real, class TabT, int M, int UPT, int RMAX>
 int launch_ws(const SampleParams& P, int n_segments, int nt, size_t smem, cudaStream_t st)
 {
     auto kern = segment_ws_kernel<Real, TabT, M, UPT, RMAX>;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return SMERF_ECUDA;
+    if (set_smem_attr(kern, smem) != cudaSuccess) return SMERF_ECUDA;
     dim3 grid((P.n_samples + RMAX - 1) / RMAX, n_segments);
     kern<<<grid, nt, smem, st>>>(P);
     return cudaGetLastError() == cudaSuccess ? SMERF_OK : SMERF_ECUDA;
@@ -1084,9 +1111,7 @@ template <class Real, class TabT, int M, int UPT>
 int launch_inplace(const SampleParams& P, int n_segments, int nt, size_t smem, cudaStream_t st)
 {
     auto kern = segment_kernel<Real, TabT, M, UPT, 1, true>;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return SMERF_ECUDA;
+    if (set_smem_attr(kern, smem) != cudaSuccess) return SMERF_ECUDA;
     dim3 grid(P.n_samples, n_segments);
     kern<<<grid, nt, smem, st>>>(P);
     return cudaGetLastError() == cudaSuccess ? SMERF_OK : SMERF_ECUDA;
@@ -1178,11 +1203,10 @@ int dispatch_segments(const SampleParams& P, int n_segments, const SegConfig& cf
     }
 }
 
+// The request's kernel parameters and launch configuration.
 template <class Real, class TabT>
-int launch_sample_t(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch, cudaStream_t st,
-                    cudaEvent_t ev0, cudaEvent_t ev1)
+int fill_params(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch, SampleParams& P, SegConfig& cfg)
 {
-    SampleParams P;
     P.segs = pl->segs_dev;
     P.steps[0] = pl->steps[0];
     P.steps[1] = pl->steps[1];
@@ -1205,7 +1229,7 @@ int launch_sample_t(const smerf_plan* pl, uint64_t seed, int n, void* out, void*
     P.n_anchors[0] = pl->chain[0].n_anchors;
     P.n_anchors[1] = pl->chain[1].n_anchors;
     P.na_max = P.n_anchors[0] > P.n_anchors[1] ? P.n_anchors[0] : P.n_anchors[1];
-    const SegConfig cfg = seg_config<Real>(pl);
+    cfg = seg_config<Real>(pl);
     if (cfg.smem > kMaxSmem) return SMERF_EUNSUPPORTED;  // one ring per realisation must fit on chip
     if (!cfg.ws && (pl->n_slots / unit_slots(pl->p) + cfg.upt - 1) / cfg.upt > kMaxThreads) return SMERF_EUNSUPPORTED;
     if (pl->n_segments > 65535) return SMERF_EUNSUPPORTED;
@@ -1214,6 +1238,17 @@ int launch_sample_t(const smerf_plan* pl, uint64_t seed, int n, void* out, void*
     int lg = 0;
     while ((1 << lg) < P.Nc) ++lg;
     P.lgNc = lg;
+    return SMERF_OK;
+}
+
+template <class Real, class TabT>
+int launch_sample_t(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch, cudaStream_t st,
+                    cudaEvent_t ev0, cudaEvent_t ev1)
+{
+    SampleParams P;
+    SegConfig cfg;
+    int rc = fill_params<Real, TabT>(pl, seed, n, out, scratch, P, cfg);
+    if (rc != SMERF_OK) return rc;
     {
         dim3 ga((P.n_units + 127) / 128, n, 2);
         if (pl->p == 1) anchor_kernel<Real, TabT, 1><<<ga, 128, 0, st>>>(P);
@@ -1221,10 +1256,71 @@ int launch_sample_t(const smerf_plan* pl, uint64_t seed, int n, void* out, void*
         if (cudaGetLastError() != cudaSuccess) return SMERF_ECUDA;
     }
     if (ev0 && cudaEventRecord(ev0, st) != cudaSuccess) return SMERF_ECUDA;
-    const int rc = pl->p == 1 ? dispatch_segments<Real, TabT, 1>(P, pl->n_segments, cfg, st)
-                              : dispatch_segments<Real, TabT, 2>(P, pl->n_segments, cfg, st);
+    rc = pl->p == 1 ? dispatch_segments<Real, TabT, 1>(P, pl->n_segments, cfg, st)
+                    : dispatch_segments<Real, TabT, 2>(P, pl->n_segments, cfg, st);
     if (rc == SMERF_OK && ev1 && cudaEventRecord(ev1, st) != cudaSuccess) return SMERF_ECUDA;
     return rc;
+}
+
+// ---- batched groups: requests of one shape share one anchor and one segment launch
+template <class Real, class TabT, int M, int UPT, int RMAX>
+int launch_ws_batched(const SampleParams* d, const int4* items, int n_items, int nt, size_t smem, cudaStream_t st)
+{
+    auto kern = segment_ws_batched_kernel<Real, TabT, M, UPT, RMAX>;
+    if (set_smem_attr(kern, smem) != cudaSuccess) return SMERF_ECUDA;
+    kern<<<n_items, nt, smem, st>>>(d, items);
+    return cudaGetLastError() == cudaSuccess ? SMERF_OK : SMERF_ECUDA;
+}
+
+template <class Real, class TabT, int M>
+int group_segments(const SegConfig& cfg, const SampleParams* d, const int4* items, int n_items, cudaStream_t st)
+{
+    if constexpr (sizeof(Real) == 8) {
+        switch (cfg.upt) {
+            case 1: return launch_ws_batched<Real, TabT, M, 1, 1>(d, items, n_items, cfg.nt, cfg.smem, st);
+            case 2: return launch_ws_batched<Real, TabT, M, 2, 1>(d, items, n_items, cfg.nt, cfg.smem, st);
+            case 4: return launch_ws_batched<Real, TabT, M, 4, 1>(d, items, n_items, cfg.nt, cfg.smem, st);
+            case 8: return launch_ws_batched<Real, TabT, M, 8, 1>(d, items, n_items, cfg.nt, cfg.smem, st);
+            default: return SMERF_EUNSUPPORTED;
+        }
+    } else {
+        switch (cfg.upt * 8 + cfg.rmax) {
+            case 1 * 8 + 4: return launch_ws_batched<Real, TabT, M, 1, 4>(d, items, n_items, cfg.nt, cfg.smem, st);
+            case 2 * 8 + 4: return launch_ws_batched<Real, TabT, M, 2, 4>(d, items, n_items, cfg.nt, cfg.smem, st);
+            case 2 * 8 + 2: return launch_ws_batched<Real, TabT, M, 2, 2>(d, items, n_items, cfg.nt, cfg.smem, st);
+            case 4 * 8 + 2: return launch_ws_batched<Real, TabT, M, 4, 2>(d, items, n_items, cfg.nt, cfg.smem, st);
+            case 4 * 8 + 1: return launch_ws_batched<Real, TabT, M, 4, 1>(d, items, n_items, cfg.nt, cfg.smem, st);
+            case 8 * 8 + 1: return launch_ws_batched<Real, TabT, M, 8, 1>(d, items, n_items, cfg.nt, cfg.smem, st);
+            default: return SMERF_EUNSUPPORTED;
+        }
+    }
+}
+
+template <class Real, class TabT>
+int fill_params_c(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch, SampleParams* P,
+                  int* batchable, int* rmax)
+{
+    SegConfig cfg;
+    const int rc = fill_params<Real, TabT>(pl, seed, n, out, scratch, *P, cfg);
+    *batchable = rc == SMERF_OK && cfg.ws;
+    *rmax = cfg.rmax;
+    return rc;
+}
+
+template <class Real, class TabT>
+int launch_group_t(const smerf_plan* rep, const SampleParams* d, const int4* anc_items, int n_anc,
+                   const int4* seg_items, int n_seg, cudaStream_t st)
+{
+    const SegConfig cfg = seg_config<Real>(rep);
+    if (!cfg.ws) return SMERF_EUNSUPPORTED;
+    if (n_anc > 0) {
+        if (rep->p == 1) anchor_batched_kernel<Real, TabT, 1><<<n_anc, 128, 0, st>>>(d, anc_items);
+        else anchor_batched_kernel<Real, TabT, 2><<<n_anc, 128, 0, st>>>(d, anc_items);
+        if (cudaGetLastError() != cudaSuccess) return SMERF_ECUDA;
+    }
+    if (n_seg == 0) return SMERF_OK;
+    return rep->p == 1 ? group_segments<Real, TabT, 1>(cfg, d, seg_items, n_seg, st)
+                       : group_segments<Real, TabT, 2>(cfg, d, seg_items, n_seg, st);
 }
 
 }  // namespace smerf

@@ -64,6 +64,18 @@ def _lib():
         L.smerf_sample_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_uint64),
                                            ctypes.POINTER(ip), ctypes.POINTER(vp), ip, vp]
         L.smerf_sample_batched.restype = ip
+        L.smerf_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ip), ip, ctypes.POINTER(vp)]
+        L.smerf_batch_create.restype = ip
+        L.smerf_batch_set.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(vp)]
+        L.smerf_batch_set.restype = ip
+        L.smerf_batch_launch.argtypes = [vp, vp]
+        L.smerf_batch_launch.restype = ip
+        L.smerf_batch_sample.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(vp), vp]
+        L.smerf_batch_sample.restype = ip
+        L.smerf_batch_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip)]
+        L.smerf_batch_info.restype = ip
+        L.smerf_batch_destroy.argtypes = [vp]
+        L.smerf_batch_destroy.restype = ip
         L.smerf_plan_info.argtypes = [vp, ctypes.POINTER(_Info)]
         L.smerf_plan_info.restype = ip
         L.smerf_plan_copy_tables.argtypes = [vp, ip, ip, ip, dp]
@@ -200,6 +212,55 @@ def sample_batched(plans, seeds, n_samples, outs, stream=None):
     O = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
     _check("smerf_sample_batched", _lib().smerf_sample_batched(P, S, N, O, n, _stream_ptr(stream)))
     return outs
+
+
+class Batch:
+    """A reusable batch (smerf_batch_create / _set / _launch / _sample / _info / _destroy)."""
+
+    def __init__(self, plans, n_samples):
+        L = _lib()
+        n = len(plans)
+        self._plans = list(plans)  # keep the plans alive
+        self.n_samples = [int(v) for v in n_samples]
+        P = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+        N = (ctypes.c_int * n)(*self.n_samples)
+        h = ctypes.c_void_p()
+        _check("smerf_batch_create", L.smerf_batch_create(P, N, n, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib().smerf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _arrays(self, seeds, outs):
+        n = len(self._plans)
+        S = (ctypes.c_uint64 * n)(*[s & (2**64 - 1) for s in seeds])
+        O = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+        return S, O
+
+    def set(self, seeds, outs):
+        S, O = self._arrays(seeds, outs)
+        _check("smerf_batch_set", _lib().smerf_batch_set(self._h, S, O))
+
+    def launch(self, stream=None):
+        _check("smerf_batch_launch", _lib().smerf_batch_launch(self._h, _stream_ptr(stream)))
+
+    def sample(self, seeds, outs, stream=None):
+        S, O = self._arrays(seeds, outs)
+        _check("smerf_batch_sample", _lib().smerf_batch_sample(self._h, S, O, _stream_ptr(stream)))
+        return outs
+
+    def info(self):
+        g, s1 = ctypes.c_int(), ctypes.c_int()
+        _check("smerf_batch_info", _lib().smerf_batch_info(self._h, ctypes.byref(g), ctypes.byref(s1)))
+        return {"groups": g.value, "singles": s1.value}
 
 
 def philox_uint32(key64, ring, ncalls, stream=None):

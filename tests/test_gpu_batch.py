@@ -1,0 +1,82 @@
+"""Batched sampling: requests of different grids, spectra, p and precision in grouped
+launches (one anchor and one segment launch per kernel shape) give exactly what
+individual smerf_sample calls give; a batch is reusable and replays under a CUDA graph
+with new seeds."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _plans():
+    from paper_1709_10314_gb300 import SMERF_ORDER_PAPER, SMERF_RECUR_FP64, SMERF_TABLES_FP64, Plan
+    specs = [
+        ([10.0], 32, 64, 0, 8),
+        ([20.0, 50.0], 64, 128, 0, 16),
+        ([5.0], 17, 64, 0, 4),                    # same shape as the first: one group
+        ([3.0, 8.0], 24, 32, SMERF_RECUR_FP64, 4),
+        ([7.0], 40, 256, SMERF_TABLES_FP64, 0),
+        ([9.0, 30.0], 16, 32, SMERF_ORDER_PAPER, 0),
+    ]
+    return [Plan(k, 1.0, nt, nphi, flags=f, anchor_spacing=H) for (k, nt, nphi, f, H) in specs]
+
+
+def _outs(plans, counts):
+    import torch
+    return [torch.full((n, p.n_theta, p.n_phi), float("nan"), dtype=p.dtype, device="cuda")
+            for p, n in zip(plans, counts)]
+
+
+def test_batched_equals_single_calls():
+    import torch
+    from paper_1709_10314_gb300 import sample_batched
+    plans = _plans()
+    counts = [3, 5, 1, 2, 6, 2]
+    seeds = [11, 22, 33, 44, 55, 66]
+    outs = _outs(plans, counts)
+    sample_batched(plans, seeds, counts, outs)
+    torch.cuda.synchronize()
+    for p, s, n, o in zip(plans, seeds, counts, outs):
+        ref = p.sample(s, n)
+        torch.cuda.synchronize()
+        assert torch.equal(o, ref)
+
+
+def test_batch_object_reuse_and_groups():
+    import torch
+    from paper_1709_10314_gb300 import Batch
+    plans = _plans()
+    counts = [2, 2, 2, 1, 3, 1]
+    b = Batch(plans, counts)
+    info = b.info()
+    assert info["groups"] == 5 and info["singles"] == 0   # plans 0 and 2 share a shape
+    for seeds in ([1, 2, 3, 4, 5, 6], [100, 200, 300, 400, 500, 600]):
+        outs = _outs(plans, counts)
+        b.sample(seeds, outs)
+        torch.cuda.synchronize()
+        for p, s, n, o in zip(plans, seeds, counts, outs):
+            assert torch.equal(o, p.sample(s, n))
+
+
+def test_batch_cuda_graph_replay():
+    import torch
+    from paper_1709_10314_gb300 import Batch
+    plans = _plans()[:3]
+    counts = [4, 2, 3]
+    b = Batch(plans, counts)
+    outs = _outs(plans, counts)
+    b.set([1, 2, 3], outs)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.launch(stream=s)   # first launch outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
+        b.launch(stream=s)
+    for seeds in ([7, 8, 9], [70, 80, 90]):
+        torch.cuda.synchronize()
+        b.set(seeds, outs)
+        g.replay()
+        torch.cuda.synchronize()
+        for p, sd, n, o in zip(plans, seeds, counts, outs):
+            assert torch.equal(o, p.sample(sd, n))
