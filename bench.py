@@ -154,6 +154,7 @@ def run_gb300(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     wl = args.workload
     batch = None
+    launch_cfg = None
     if wl == "uneven-256":
         reqs = uneven_requests()
         plans = [Plan(r["kappa"], r["A"], r["n_theta"], r["n_phi"], flags=flags_for("fp32", args.tables or "fp32"))
@@ -204,6 +205,9 @@ def run_gb300(args, rank, world, local_rank):
                     anchor_spacing=0 if paper_order else ANCHOR)
         info = plan.info()
         n = cfg["n"]
+        # launch configuration of the segment kernel: timed candidates (set-up, untimed)
+        ws_kernel = len(plan.launch_candidates()) > 0
+        launch_cfg = list(plan.autotune(n)) if (ws_kernel and not args.no_tune) else None
         out = torch.empty((n, cfg["n_theta"], cfg["n_phi"]), dtype=plan.dtype, device=dev)
         points = n * cfg["n_theta"] * cfg["n_phi"]
         out_bytes = points * (8 if recur == "fp64" else 4)
@@ -251,7 +255,7 @@ def run_gb300(args, rank, world, local_rank):
     step_ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / args.steps
     if batch is None:
         seg_ms = sum(a.elapsed_time(b) for a, b in zip(s0, s1)) / args.steps
-        kernel = "segment_ws_kernel"
+        kernel = "segment_ws_kernel" if ws_kernel else "segment_kernel"
     else:
         seg_ms = step_ms  # the graph replay: all groups' anchor + segment launches
         kernel = "batched graph replay (anchor + segment launches of every group)"
@@ -269,7 +273,7 @@ def run_gb300(args, rank, world, local_rank):
     if os.path.exists(prof) and wl == "1024x2048-p2" and (args.tables or "fp64") == "fp64" and not args.recur:
         try:
             rec = json.load(open(prof))
-            if rec.get("csrc_sha256_16") == csrc_digest():
+            if rec.get("csrc_sha256_16") == csrc_digest() and rec.get("launch") == launch_cfg:
                 traffic = rec.get("traffic_bytes_per_launch")
         except Exception:
             traffic = None
@@ -299,7 +303,7 @@ def run_gb300(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": workload, "name": wl, "points_per_gpu": points, "anchor_spacing": ANCHOR,
-                       "parallelism": "replicas" if world > 1 else "single",
+                       "launch": launch_cfg, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between timed steps (256 MiB write outside the step events)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
@@ -323,6 +327,8 @@ def main():
                     help="override the workload's table storage precision")
     ap.add_argument("--recur", default=None, choices=["fp64", "fp32"],
                     help="override the workload's recursion precision")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the built-in segment-kernel launch configuration (no autotuning)")
     ap.add_argument("--workload", default="1024x2048-p2",
                     choices=["1024x2048-p2", "plain-64x128-p1-fp64", "4096x8192-p1", "16384x32768-p1", "uneven-256"])
     args = ap.parse_args()

@@ -320,6 +320,107 @@ int smerf_plan_copy_tables(const smerf_plan* plan, int which, int chain, int pos
     return SMERF_OK;
 }
 
+static int tune_candidates(const smerf_plan* plan, int* cand, int max_n)
+{
+    return plan->recur64 ? (plan->tab64 ? smerf_tune_candidates_dd(plan, cand, max_n) : smerf_tune_candidates_df(plan, cand, max_n))
+                         : (plan->tab64 ? smerf_tune_candidates_fd(plan, cand, max_n) : smerf_tune_candidates_ff(plan, cand, max_n));
+}
+
+int smerf_plan_launch_candidates(const smerf_plan* plan, int* cand, int max_n)
+{
+    if (!plan || max_n < 0 || (max_n > 0 && !cand)) return SMERF_EINVAL;
+    int tmp[4 * 64];
+    const int n = tune_candidates(plan, tmp, 64);
+    for (int i = 0; i < n && i < max_n; ++i)
+        for (int k = 0; k < 4; ++k) cand[4 * i + k] = tmp[4 * i + k];
+    return n;
+}
+
+int smerf_plan_set_launch(smerf_plan* plan, const int* config)
+{
+    if (!plan) return SMERF_EINVAL;
+    if (!config) {
+        plan->tune.valid = 0;
+        return SMERF_OK;
+    }
+    int cand[4 * 64];
+    const int n = tune_candidates(plan, cand, 64);
+    for (int i = 0; i < n; ++i) {
+        if (cand[4 * i] == config[0] && cand[4 * i + 1] == config[1] && cand[4 * i + 2] == config[2] &&
+            cand[4 * i + 3] == config[3]) {
+            plan->tune.valid = 1;
+            plan->tune.upt = config[0];
+            plan->tune.rmax = config[1];
+            plan->tune.np = config[2];
+            plan->tune.nf = config[3];
+            plan->tune.ms = 0.0f;
+            return SMERF_OK;
+        }
+    }
+    return SMERF_EINVAL;
+}
+
+int smerf_plan_autotune(smerf_plan* plan, int n_samples, void* stream, int* chosen)
+{
+    if (!plan || n_samples < 1 || n_samples > 65535) return SMERF_EINVAL;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != plan->dev) return SMERF_EINVAL;
+    int cand[4 * 64];
+    const int nc = tune_candidates(plan, cand, 64);
+    plan->tune.valid = 0;
+    if (nc == 0) {
+        if (chosen) chosen[0] = chosen[1] = chosen[2] = chosen[3] = 0;
+        return SMERF_OK;  // no warp-specialised configuration: the built-in choice stays
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t ob = (size_t)n_samples * plan->n_theta * plan->n_phi * (plan->recur64 ? 8 : 4);
+    void* out = nullptr;
+    void* scratch = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = SMERF_OK;
+    if (cudaMalloc(&out, ob) != cudaSuccess || cudaMalloc(&scratch, smerf_scratch_bytes(plan, n_samples)) != cudaSuccess)
+        rc = SMERF_ENOMEM;
+    if (rc == SMERF_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = SMERF_ECUDA;
+    float best = 1e30f;
+    int bi = -1;
+    for (int i = 0; rc == SMERF_OK && i < nc; ++i) {
+        plan->tune.valid = 1;
+        plan->tune.upt = cand[4 * i];
+        plan->tune.rmax = cand[4 * i + 1];
+        plan->tune.np = cand[4 * i + 2];
+        plan->tune.nf = cand[4 * i + 3];
+        float tot = 0.0f;
+        for (int it = 0; rc == SMERF_OK && it < 4; ++it) {
+            rc = smerf_launch_sample(plan, 1 + it, n_samples, out, scratch, st, e0, e1);
+            if (rc == SMERF_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = SMERF_ECUDA;
+            float ms = 0.0f;
+            if (rc == SMERF_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = SMERF_ECUDA;
+            if (it > 0) tot += ms;  // first launch is a warm-up
+        }
+        if (rc == SMERF_OK && tot < best) {
+            best = tot;
+            bi = i;
+        }
+    }
+    plan->tune.valid = 0;
+    if (rc == SMERF_OK && bi >= 0) {
+        plan->tune.valid = 1;
+        plan->tune.upt = cand[4 * bi];
+        plan->tune.rmax = cand[4 * bi + 1];
+        plan->tune.np = cand[4 * bi + 2];
+        plan->tune.nf = cand[4 * bi + 3];
+        plan->tune.ms = best / 3.0f;
+        if (chosen)
+            for (int k = 0; k < 4; ++k) chosen[k] = cand[4 * bi + k];
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+    cudaFree(scratch);
+    return rc;
+}
+
 int smerf_philox_uint32(uint64_t key64, uint32_t ring, int64_t ncalls, uint32_t* out, void* stream)
 {
     if (ncalls < 0 || (ncalls > 0 && !out)) return SMERF_EINVAL;

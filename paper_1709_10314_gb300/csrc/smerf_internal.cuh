@@ -56,6 +56,8 @@ struct smerf_plan {
     size_t table_bytes;
     double setup_ms;
     int dev;
+    // launch parameters chosen by smerf_plan_autotune (valid = 0: built-in heuristic)
+    struct { int valid, upt, rmax, np, nf; float ms; } tune;
 };
 
 namespace smerf {
@@ -179,6 +181,14 @@ SMERF_DECLARE_GROUP(ff)
 SMERF_DECLARE_GROUP(fd)
 SMERF_DECLARE_GROUP(dd)
 SMERF_DECLARE_GROUP(df)
+
+// launch-configuration candidates of a plan for the autotuner (per precision pair XX):
+// writes up to max_n (upt, rmax, np, nf) quadruples, returns how many
+#define SMERF_DECLARE_TUNE(XX) int smerf_tune_candidates_##XX(const smerf_plan* pl, int* cand, int max_n);
+SMERF_DECLARE_TUNE(ff)
+SMERF_DECLARE_TUNE(fd)
+SMERF_DECLARE_TUNE(dd)
+SMERF_DECLARE_TUNE(df)
 
 // dynamic shared-memory attribute bookkeeping (smerf_api.cu)
 int smerf_smem_attr_done(const void* kern, int dev, size_t smem, bool record);

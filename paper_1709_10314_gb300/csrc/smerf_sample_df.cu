@@ -18,3 +18,8 @@ int smerf_launch_group_df(const smerf_plan* rep, const smerf::SampleParams* d_de
 {
     return smerf::launch_group_t<double, float>(rep, d_descs, anc_items, n_anc, seg_items, n_seg, st);
 }
+
+int smerf_tune_candidates_df(const smerf_plan* pl, int* cand, int max_n)
+{
+    return smerf::tune_candidates<double>(pl, cand, max_n);
+}

@@ -18,3 +18,8 @@ int smerf_launch_group_ff(const smerf_plan* rep, const smerf::SampleParams* d_de
 {
     return smerf::launch_group_t<float, float>(rep, d_descs, anc_items, n_anc, seg_items, n_seg, st);
 }
+
+int smerf_tune_candidates_ff(const smerf_plan* pl, int* cand, int max_n)
+{
+    return smerf::tune_candidates<float>(pl, cand, max_n);
+}

@@ -1130,12 +1130,71 @@ template <class Real> constexpr int ws_rmax_cap(int upt)
 }
 
 template <class Real>
+inline size_t ws_smem(const smerf_plan* pl, int rmax)
+{
+    const int Nc = pl->n_phi / 2;
+    return (size_t)3 * rmax * Nc * 2 * sizeof(Real) + (pl->H > 0 ? (size_t)rmax * Nc * 2 * pl->p * sizeof(Real) : 0);
+}
+
+// (units per thread, realisations per CTA) pairs with a built warp-specialised kernel
+template <class Real> inline bool ws_built(int upt, int rmax)
+{
+    if (sizeof(Real) == 8) return rmax == 1 && (upt == 1 || upt == 2 || upt == 4 || upt == 8);
+    return (upt == 1 && rmax == 4) || (upt == 2 && (rmax == 4 || rmax == 2)) || (upt == 4 && (rmax == 2 || rmax == 1)) ||
+           (upt == 8 && rmax == 1);
+}
+
+// Every warp-specialised configuration that fits the plan: producer threads np = units / upt
+// (<= 512, multiple of 32), FFT threads nf in {np/2, np, np/4} (np + nf <= 768).
+template <class Real>
+inline int tune_candidates(const smerf_plan* pl, int* cand, int max_n)
+{
+    const int n_units = pl->n_slots / unit_slots(pl->p);
+    int n = 0;
+    const int rm[3] = {4, 2, 1};
+    for (int upt = 1; upt <= 8; upt *= 2) {
+        int np = (n_units + upt - 1) / upt;
+        np = ((np + 31) / 32) * 32;
+        if (np > 512 || (upt > 1 && (n_units + upt / 2 - 1) / (upt / 2) <= 32)) continue;
+        for (int k = 0; k < 3; ++k) {
+            const int rmax = rm[k];
+            if (!ws_built<Real>(upt, rmax) || ws_smem<Real>(pl, rmax) > 226 * 1024) continue;
+            const int div[3] = {2, 1, 4};
+            for (int d = 0; d < 3; ++d) {
+                int nf = ((np / div[d] + 31) / 32) * 32;
+                if (nf < 32) nf = 32;
+                if (np + nf > 768) continue;
+                if (n < max_n) {
+                    cand[4 * n + 0] = upt;
+                    cand[4 * n + 1] = rmax;
+                    cand[4 * n + 2] = np;
+                    cand[4 * n + 3] = nf;
+                }
+                ++n;
+            }
+        }
+    }
+    return n < max_n ? n : max_n;
+}
+
+template <class Real>
 inline SegConfig seg_config(const smerf_plan* pl)
 {
     SegConfig cfg{};
     const int M = pl->p;
     const int n_units = pl->n_slots / unit_slots(M);
     const int Nc = pl->n_phi / 2;
+    if (pl->tune.valid && ws_built<Real>(pl->tune.upt, pl->tune.rmax) &&
+        ws_smem<Real>(pl, pl->tune.rmax) <= 226 * 1024 &&
+        (n_units + pl->tune.upt - 1) / pl->tune.upt <= pl->tune.np && pl->tune.np + pl->tune.nf <= 768) {
+        cfg.ws = 1;
+        cfg.upt = pl->tune.upt;
+        cfg.rmax = pl->tune.rmax;
+        cfg.np = pl->tune.np;
+        cfg.nt = pl->tune.np + pl->tune.nf;
+        cfg.smem = ws_smem<Real>(pl, cfg.rmax);
+        return cfg;
+    }
     int upt = 1;
     while (upt < 8 && (n_units + upt - 1) / upt > 512) upt *= 2;
     if ((n_units + upt - 1) / upt <= 512) {

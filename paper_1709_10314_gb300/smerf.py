@@ -80,6 +80,12 @@ def _lib():
         L.smerf_plan_info.restype = ip
         L.smerf_plan_copy_tables.argtypes = [vp, ip, ip, ip, dp]
         L.smerf_plan_copy_tables.restype = ip
+        L.smerf_plan_autotune.argtypes = [vp, ip, vp, ctypes.POINTER(ip)]
+        L.smerf_plan_autotune.restype = ip
+        L.smerf_plan_launch_candidates.argtypes = [vp, ctypes.POINTER(ip), ip]
+        L.smerf_plan_launch_candidates.restype = ip
+        L.smerf_plan_set_launch.argtypes = [vp, ctypes.POINTER(ip)]
+        L.smerf_plan_set_launch.restype = ip
         L.smerf_philox_uint32.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, vp, vp]
         L.smerf_philox_uint32.restype = ip
         L.smerf_ring_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ip, vp, vp]
@@ -144,6 +150,28 @@ class Plan:
                 "anchor_spacing": inf.anchor_spacing, "n_anchors": list(inf.n_anchors),
                 "n_segments": inf.n_segments, "flags": inf.flags, "table_bytes": inf.table_bytes,
                 "scratch_bytes_per_sample": inf.scratch_bytes_per_sample, "setup_ms": inf.setup_ms}
+
+    def autotune(self, n_samples, stream=None):
+        """smerf_plan_autotune: returns (units/thread, realisations/CTA, producer, FFT threads)."""
+        ch = (ctypes.c_int * 4)()
+        _check("smerf_plan_autotune", _lib().smerf_plan_autotune(self._h, int(n_samples), _stream_ptr(stream), ch))
+        return tuple(ch)
+
+    def launch_candidates(self):
+        """smerf_plan_launch_candidates: list of (units/thread, realisations/CTA, producer, FFT threads)."""
+        buf = (ctypes.c_int * (4 * 64))()
+        n = _lib().smerf_plan_launch_candidates(self._h, buf, 64)
+        if n < 0:
+            _check("smerf_plan_launch_candidates", n)
+        return [tuple(buf[4 * i:4 * i + 4]) for i in range(n)]
+
+    def set_launch(self, config):
+        """smerf_plan_set_launch: fix a launch configuration (None: built-in choice)."""
+        if config is None:
+            ptr = None
+        else:
+            ptr = (ctypes.c_int * 4)(*[int(v) for v in config])
+        _check("smerf_plan_set_launch", _lib().smerf_plan_set_launch(self._h, ptr))
 
     def tables(self, which, chain=0, pos=0):
         """Copy a table block to host as float64 [rows][n_modes] (see smerf_plan_copy_tables)."""
