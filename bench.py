@@ -207,7 +207,11 @@ def run_gb300(args, rank, world, local_rank):
         n = cfg["n"]
         # launch configuration of the segment kernel: timed candidates (set-up, untimed)
         ws_kernel = len(plan.launch_candidates()) > 0
-        launch_cfg = list(plan.autotune(n)) if (ws_kernel and not args.no_tune) else None
+        if args.launch and ws_kernel:
+            launch_cfg = [int(v) for v in args.launch.split(",")]
+            plan.set_launch(launch_cfg)
+        else:
+            launch_cfg = list(plan.autotune(n)) if (ws_kernel and not args.no_tune) else None
         out = torch.empty((n, cfg["n_theta"], cfg["n_phi"]), dtype=plan.dtype, device=dev)
         points = n * cfg["n_theta"] * cfg["n_phi"]
         out_bytes = points * (8 if recur == "fp64" else 4)
@@ -329,6 +333,9 @@ def main():
                     help="override the workload's recursion precision")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the built-in segment-kernel launch configuration (no autotuning)")
+    ap.add_argument("--launch", default=None,
+                    help="fix the segment-kernel launch configuration: units/thread,realisations/CTA,"
+                         "producer threads,FFT threads (one of the plan's candidates)")
     ap.add_argument("--workload", default="1024x2048-p2",
                     choices=["1024x2048-p2", "plain-64x128-p1-fp64", "4096x8192-p1", "16384x32768-p1", "uneven-256"])
     args = ap.parse_args()

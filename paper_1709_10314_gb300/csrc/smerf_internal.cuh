@@ -53,6 +53,8 @@ struct smerf_plan {
     // FFT tables in the recursion precision: per-pass twiddles, pre[Nc] = e^{2 pi i s / n_phi}
     void* tw;
     void* pre;
+    // per-pass twiddles of the high-radix plan (hr_* below), recursion precision
+    void* tw2;
     size_t table_bytes;
     double setup_ms;
     int dev;
@@ -79,6 +81,7 @@ struct SampleParams {
     const void* beq;
     const void* tw;   // per-pass complex twiddle tables (see pass_radix)
     const void* pre;  // complex e^{2 pi i s / n_phi}, s < Nc
+    const void* tw2;  // per-pass complex twiddles of the high-radix plan (hr_off)
     void* anc;        // anchor states [c][r][j][2M][n_slots]
     void* out;
     uint64_t seed;
@@ -88,6 +91,25 @@ struct SampleParams {
     int np;           // warp-specialised kernel: producer threads
     int lgNc;
 };
+
+// High-radix pass plan of the Nc = 2^L point inverse FFT: ceil(L / 4) Stockham passes whose
+// radices 2^bits split L as evenly as possible, largest first (L = 10: 16, 8, 8).  Pass i runs
+// with stride Ns = 2^hr_lgns(L, i); its twiddles e^{2 pi i a kk / (Ns RP)}, a in [1, RP),
+// kk < Ns, sit at tw2[hr_off(L, i) + (a - 1) Ns + kk] (pass 0 has none).
+__host__ __device__ constexpr int hr_passes(int L) { return (L + 3) / 4; }
+__host__ __device__ constexpr int hr_bits(int L, int i) { return L / hr_passes(L) + (i < L % hr_passes(L) ? 1 : 0); }
+__host__ __device__ constexpr int hr_lgns(int L, int i)
+{
+    int s = 0;
+    for (int p = 0; p < i; ++p) s += hr_bits(L, p);
+    return s;
+}
+__host__ __device__ constexpr int hr_off(int L, int i)
+{
+    int o = 0;
+    for (int p = 1; p < i; ++p) o += ((1 << hr_bits(L, p)) - 1) << hr_lgns(L, p);
+    return o;
+}
 
 // units: the slots whose normals fill whole Philox calls.  p = 1: 2 slots per call;
 // p = 2: 1 slot per call.

@@ -22,8 +22,19 @@
 
 #include "smerf_internal.cuh"
 
+// Thread limit of the warp-specialised kernels (producer + FFT threads per CTA); it also
+// bounds their registers per thread (65536 / limit).
+#ifndef SMERF_WS_MAXT
+#define SMERF_WS_MAXT 768
+#endif
+// Realisations per interleaved group of Philox generators in the producer loop.
+#ifndef SMERF_RB
+#define SMERF_RB 1
+#endif
+
 namespace smerf {
 
+constexpr int kWsMaxThreads = SMERF_WS_MAXT;
 
 template <int M> constexpr int kG = unit_slots(M);
 
@@ -130,11 +141,15 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
                 for (int q = 0; q < M; ++q) v[g * 2 * M + part * M + q] = x[g][part][q];
         Vec4<Real>::st(anc + aoff<M>(P, c, r, 0, 0, G * u), v);
     }
+    // anchors: x_j = Phi x_{j-1} + chol(S) xi.  The table values and normals of anchor j + 1
+    // are fetched before the matrix-vector products of anchor j (the loads come from L2 and
+    // do not depend on the state), so consecutive anchors overlap their latencies.
     const TabT* cs = (const TabT*)P.coarse[c];
-    for (int j = 1; j <= P.n_anchors[c]; ++j) {
-        const int pos = j * P.H;
-        const int ring = c == 0 ? P.k0 - pos : P.k0 + pos;
-        unit_normals<Real>(key, (uint32_t)u, (uint32_t)ring, nr);
+    const int na = P.n_anchors[c];
+    TabT tv[G][2][Ec];
+    auto fetch = [&](int j, TabT (&t)[G][2][Ec], Real (&xi)[4]) {
+        const int ring = c == 0 ? P.k0 - j * P.H : P.k0 + j * P.H;
+        unit_normals<Real>(key, (uint32_t)u, (uint32_t)ring, xi);
         const TabT* tb = cs + (size_t)j * Ec * mp;
 #pragma unroll
         for (int g = 0; g < G; ++g)
@@ -142,6 +157,19 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
             for (int part = 0; part < 2; ++part) {
                 const int s = G * u + g;
                 const int mode = (part == 1 && s == 0) ? P.Nc : s;
+#pragma unroll
+                for (int e = 0; e < Ec; ++e) t[g][part][e] = __ldg(tb + (size_t)e * mp + mode);
+            }
+    };
+    if (na >= 1) fetch(1, tv, nr);
+    for (int j = 1; j <= na; ++j) {
+        TabT tn[G][2][Ec];
+        Real nn[4];
+        if (j < na) fetch(j + 1, tn, nn);
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
                 Real xi[M], xn[M];
 #pragma unroll
                 for (int q = 0; q < M; ++q) xi[q] = nr[g * 2 * M + part * M + q];
@@ -149,10 +177,10 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
                 for (int p = 0; p < M; ++p) {
                     Real acc = 0;
 #pragma unroll
-                    for (int q = 0; q < M; ++q) acc += tabld<Real, TabT>(tb + (size_t)(p * M + q) * mp + mode) * x[g][part][q];
+                    for (int q = 0; q < M; ++q) acc += tabcvt<Real, TabT>(tv[g][part][p * M + q]) * x[g][part][q];
                     int e = M * M + p * (p + 1) / 2;
 #pragma unroll
-                    for (int q = 0; q <= p; ++q, ++e) acc += tabld<Real, TabT>(tb + (size_t)e * mp + mode) * xi[q];
+                    for (int q = 0; q <= p; ++q, ++e) acc += tabcvt<Real, TabT>(tv[g][part][e]) * xi[q];
                     xn[p] = acc;
                 }
 #pragma unroll
@@ -166,6 +194,16 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
 #pragma unroll
                 for (int q = 0; q < M; ++q) v[g * 2 * M + part * M + q] = x[g][part][q];
         Vec4<Real>::st(anc + aoff<M>(P, c, r, j, 0, G * u), v);
+        if (j < na) {
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int part = 0; part < 2; ++part)
+#pragma unroll
+                    for (int e = 0; e < Ec; ++e) tv[g][part][e] = tn[g][part][e];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) nr[i] = nn[i];
+        }
     }
     (void)T;
 }
@@ -219,12 +257,46 @@ __device__ __forceinline__ void dft8(C* v)
     v[3] = cadd(e[3], o3);   v[7] = csub(e[3], o3);
 }
 
+// 16 points as 4 x 4: DFT-4 over n1 of x[4 n1 + n2], twiddles w16^(n2 k1), DFT-4 over n2
+template <class C>
+__device__ __forceinline__ void dft16(C* v)
+{
+    using R = decltype(C::x);
+    const R c1 = (R)0.92387953251128675613, s1 = (R)0.38268343236508977173, h = (R)0.70710678118654752440;
+    C y[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        y[n2][0] = v[n2];
+        y[n2][1] = v[4 + n2];
+        y[n2][2] = v[8 + n2];
+        y[n2][3] = v[12 + n2];
+        dft4(y[n2]);
+    }
+    y[1][1] = cmul(y[1][1], cmk<C>(c1, s1));
+    y[1][2] = cmk<C>(h * (y[1][2].x - y[1][2].y), h * (y[1][2].x + y[1][2].y));
+    y[1][3] = cmul(y[1][3], cmk<C>(s1, c1));
+    y[2][1] = cmk<C>(h * (y[2][1].x - y[2][1].y), h * (y[2][1].x + y[2][1].y));
+    y[2][2] = cmuli(y[2][2]);
+    y[2][3] = cmk<C>(-h * (y[2][3].x + y[2][3].y), h * (y[2][3].x - y[2][3].y));
+    y[3][1] = cmul(y[3][1], cmk<C>(s1, c1));
+    y[3][2] = cmk<C>(-h * (y[3][2].x + y[3][2].y), h * (y[3][2].x - y[3][2].y));
+    y[3][3] = cmul(y[3][3], cmk<C>(-c1, -s1));
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        C t[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+        dft4(t);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
+    }
+}
+
 template <class C, int RP>
 __device__ __forceinline__ void dft(C* v)
 {
-    if (RP == 2) dft2(v[0], v[1]);
-    else if (RP == 4) dft4(v);
-    else dft8(v);
+    if constexpr (RP == 2) dft2(v[0], v[1]);
+    else if constexpr (RP == 4) dft4(v);
+    else if constexpr (RP == 8) dft8(v);
+    else dft16(v);
 }
 
 // Z_s of the C2R packing (s < Nc): Z_0 = (X_0 + X_Nc) + i (X_0 - X_Nc) from slot 0 = (X_0, X_Nc);
@@ -546,6 +618,34 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const uint2* rk)
     return c;
 }
 
+// The normals of one Philox call for NB realisations at once (round keys rk[0..NB)): the NB
+// generator chains are independent and run interleaved; the first round's products, which
+// depend on the counter only, are shared.
+template <class Real, int NB>
+__device__ __forceinline__ void unit_normals_multi(const uint2 (*rk)[10], uint32_t call, uint32_t ring, Real (&n)[NB][4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    uint4 c[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) c[b] = make_uint4(call, ring, 0u, 0u);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const uint2 k = rk[b][r];
+            const uint64_t p0 = (uint64_t)M0 * c[b].x;
+            const uint64_t p1 = (uint64_t)M1 * c[b].z;
+            c[b] = make_uint4((uint32_t)(p1 >> 32) ^ c[b].y ^ k.x, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c[b].w ^ k.y,
+                              (uint32_t)p0);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        box_muller(c[b].x, c[b].y, n[b][0], n[b][1]);
+        box_muller(c[b].z, c[b].w, n[b][2], n[b][3]);
+    }
+}
+
 template <class Real>
 __device__ __forceinline__ void unit_normals_rk(const uint2* rk, uint32_t call, uint32_t ring, Real (&n)[4])
 {
@@ -730,72 +830,6 @@ constexpr int kBarFull = 1;   // + buffer index: coefficients of a ring are read
 constexpr int kBarEmpty = 3;  // + buffer index: the FFT group is done with a buffer
 constexpr int kBarFft = 5;    // FFT group internal
 
-// FFT group version of the fixed-size pass: threads ftid < nf of the group, group barrier
-// between passes.
-template <class C, int LGNC, int LGNS, bool FIRST>
-__device__ __forceinline__ void grp_pass(const C* __restrict__ src, C* __restrict__ dst, int R,
-                                         const C* __restrict__ twp, const C* __restrict__ pre, C* const* gout,
-                                         int ftid, int nf)
-{
-    constexpr int Nc = 1 << LGNC, Ns = 1 << LGNS;
-    constexpr int RP = (Nc / Ns >= 4) ? 4 : 2, LR = RP == 4 ? 2 : 1;
-    constexpr bool LAST = Ns * RP == Nc;
-    constexpr int LGNB = LGNC - LR, nb = 1 << LGNB;
-    const int total = R << LGNB;
-#pragma unroll 4
-    for (int b = ftid; b < total; b += nf) {
-        const int r = b >> LGNB, j = b & (nb - 1);
-        const C* S = src + (r << LGNC);
-        C v[RP];
-        int kk = 0;
-        if (FIRST) {
-            {
-                const C a = S[j], bb = cconj(S[(Nc - j) & (Nc - 1)]);
-                const C g = cadd(cadd(a, bb), cmuli(cmul(__ldg(pre + j), csub(a, bb))));
-                const C z0 = cmk<C>(a.x + a.y, a.x - a.y);
-                v[0] = j == 0 ? z0 : g;
-            }
-#pragma unroll
-            for (int i = 1; i < RP; ++i) {
-                const int sidx = j + i * nb;
-                const C a = S[sidx], bb = cconj(S[Nc - sidx]);
-                v[i] = cadd(cadd(a, bb), cmuli(cmul(__ldg(pre + sidx), csub(a, bb))));
-            }
-        } else {
-            kk = j & (Ns - 1);
-#pragma unroll
-            for (int i = 0; i < RP; ++i) v[i] = S[j + i * nb];
-#pragma unroll
-            for (int i = 1; i < RP; ++i) v[i] = cmul(v[i], __ldg(twp + (i - 1) * Ns + kk));
-        }
-        dft<C, RP>(v);
-        const int idx = ((j - kk) << LR) + kk;
-        if (LAST) {
-            C* D = gout[r] + idx;
-#pragma unroll
-            for (int a = 0; a < RP; ++a) __stcs(D + a * Ns, v[a]);
-        } else {
-            C* D = dst + (r << LGNC) + idx;
-#pragma unroll
-            for (int a = 0; a < RP; ++a) D[a * Ns] = v[a];
-        }
-    }
-}
-
-template <class C, int LGNC, int LGNS = 0, int OFF = 0, bool FIRST = true>
-__device__ __forceinline__ void grp_c2r_fixed(C* src, C* dst, int R, const C* twp, const C* pre, C* const* gout,
-                                              int ftid, int nf)
-{
-    constexpr int Nc = 1 << LGNC, Ns = 1 << LGNS;
-    constexpr int RP = (Nc / Ns >= 4) ? 4 : 2, LR = RP == 4 ? 2 : 1;
-    grp_pass<C, LGNC, LGNS, FIRST>(src, dst, R, twp + OFF, pre, gout, ftid, nf);
-    if constexpr (Ns * RP < Nc) {
-        bar_sync(kBarFft, nf);
-        grp_c2r_fixed<C, LGNC, LGNS + LR, OFF + (FIRST ? 0 : (RP - 1) * Ns), false>(dst, src, R, twp, pre, gout,
-                                                                                   ftid, nf);
-    }
-}
-
 // general size (runtime log2 Nc)
 template <class C, int RP, bool FIRST, bool LAST>
 __device__ __forceinline__ void grp_pass_rt(const C* __restrict__ src, C* __restrict__ dst, int R, int lgNc, int Ns,
@@ -875,27 +909,98 @@ __device__ __forceinline__ void grp_c2r_rt(C* buf0, C* buf1, int R, int lgNc, co
     }
 }
 
-template <class C, bool FIXED>
-__device__ __forceinline__ void grp_c2r(int lgNc, C* b0, C* b1, int R, const C* twp, const C* pre, C* const* gout,
+// ---- high-radix plan (hr_passes / hr_bits): passes of radix up to 16 held in registers.
+// Between passes the rings sit in shared memory in an XOR-swizzled order, element e at
+// e ^ ((e >> 4) & 15), so that the strided stores of the early passes and the unit-stride
+// loads of the next pass are both free of bank conflicts.  The coefficient buffer the
+// producer fills (first pass input) is in natural order; the last pass writes HBM.
+__device__ __forceinline__ int hr_swz(int e) { return e ^ ((e >> 4) & 15); }
+
+template <class C, int LGNC, int PASS>
+__device__ __forceinline__ void hr_pass(const C* __restrict__ src, C* __restrict__ dst, int R,
+                                        const C* __restrict__ tw2, const C* __restrict__ pre, C* const* gout,
                                         int ftid, int nf)
 {
-    if (FIXED) {
-        switch (lgNc) {
-            case 2: grp_c2r_fixed<C, 2>(b0, b1, R, twp, pre, gout, ftid, nf); return;
-            case 3: grp_c2r_fixed<C, 3>(b0, b1, R, twp, pre, gout, ftid, nf); return;
-            case 4: grp_c2r_fixed<C, 4>(b0, b1, R, twp, pre, gout, ftid, nf); return;
-            case 5: grp_c2r_fixed<C, 5>(b0, b1, R, twp, pre, gout, ftid, nf); return;
-            case 6: grp_c2r_fixed<C, 6>(b0, b1, R, twp, pre, gout, ftid, nf); return;
-            case 7: grp_c2r_fixed<C, 7>(b0, b1, R, twp, pre, gout, ftid, nf); return;
-            case 8: grp_c2r_fixed<C, 8>(b0, b1, R, twp, pre, gout, ftid, nf); return;
-            case 9: grp_c2r_fixed<C, 9>(b0, b1, R, twp, pre, gout, ftid, nf); return;
-            case 10: grp_c2r_fixed<C, 10>(b0, b1, R, twp, pre, gout, ftid, nf); return;
-            case 11: grp_c2r_fixed<C, 11>(b0, b1, R, twp, pre, gout, ftid, nf); return;
-            case 12: grp_c2r_fixed<C, 12>(b0, b1, R, twp, pre, gout, ftid, nf); return;
-            default: break;
+    constexpr int Nc = 1 << LGNC;
+    constexpr int LR = hr_bits(LGNC, PASS), RP = 1 << LR;
+    constexpr int Ns = 1 << hr_lgns(LGNC, PASS);
+    constexpr bool FIRST = PASS == 0, LAST = PASS == hr_passes(LGNC) - 1;
+    constexpr int LGNB = LGNC - LR, nb = 1 << LGNB;
+    const C* twp = tw2 + hr_off(LGNC, PASS);
+    const int total = R << LGNB;
+    for (int b = ftid; b < total; b += nf) {
+        const int r = b >> LGNB, j = b & (nb - 1);
+        const C* S = src + (r << LGNC);
+        C v[RP];
+        int kk = 0;
+        if constexpr (FIRST) {
+            // C2R packing on load: element i is slot s = j + i nb (slot 0 = (X_0, X_Nc))
+            {
+                const C a = S[j], bb = cconj(S[(Nc - j) & (Nc - 1)]);
+                const C g = cadd(cadd(a, bb), cmuli(cmul(__ldg(pre + j), csub(a, bb))));
+                const C z0 = cmk<C>(a.x + a.y, a.x - a.y);
+                v[0] = j == 0 ? z0 : g;
+            }
+#pragma unroll
+            for (int i = 1; i < RP; ++i) {
+                const int sidx = j + i * nb;
+                const C a = S[sidx], bb = cconj(S[Nc - sidx]);
+                v[i] = cadd(cadd(a, bb), cmuli(cmul(__ldg(pre + sidx), csub(a, bb))));
+            }
+        } else {
+            kk = j & (Ns - 1);
+#pragma unroll
+            for (int i = 0; i < RP; ++i) v[i] = S[hr_swz(j + i * nb)];
+#pragma unroll
+            for (int i = 1; i < RP; ++i) v[i] = cmul(v[i], __ldg(twp + (i - 1) * Ns + kk));
+        }
+        dft<C, RP>(v);
+        const int idx = ((j - kk) << LR) + kk;
+        if constexpr (LAST) {
+            C* D = gout[r] + idx;
+#pragma unroll
+            for (int a = 0; a < RP; ++a) __stcs(D + a * Ns, v[a]);
+        } else {
+            C* D = dst + (r << LGNC);
+#pragma unroll
+            for (int a = 0; a < RP; ++a) D[hr_swz(idx + a * Ns)] = v[a];
         }
     }
-    grp_c2r_rt<C>(b0, b1, R, lgNc, twp, pre, gout, ftid, nf);
+}
+
+template <class C, int LGNC, int PASS = 0>
+__device__ __forceinline__ void hr_c2r_fixed(C* src, C* dst, int R, const C* tw2, const C* pre, C* const* gout,
+                                             int ftid, int nf)
+{
+    hr_pass<C, LGNC, PASS>(src, dst, R, tw2, pre, gout, ftid, nf);
+    if constexpr (PASS + 1 < hr_passes(LGNC)) {
+        bar_sync(kBarFft, nf);
+        hr_c2r_fixed<C, LGNC, PASS + 1>(dst, src, R, tw2, pre, gout, ftid, nf);
+    }
+}
+
+// high-radix fixed-size FFTs for log2 Nc in [LO, HI], the runtime-size radix-4 one otherwise
+template <class C, int LO, int HI>
+__device__ __forceinline__ void hr_c2r(int lgNc, C* b0, C* b1, int R, const C* twp, const C* tw2, const C* pre,
+                                       C* const* gout, int ftid, int nf)
+{
+    if constexpr (LO <= HI) {
+        if (lgNc == LO) {
+            hr_c2r_fixed<C, LO>(b0, b1, R, tw2, pre, gout, ftid, nf);
+            return;
+        }
+        hr_c2r<C, LO + 1, HI>(lgNc, b0, b1, R, twp, tw2, pre, gout, ftid, nf);
+    } else {
+        grp_c2r_rt<C>(b0, b1, R, lgNc, twp, pre, gout, ftid, nf);
+    }
+}
+
+// log2 Nc range the warp-specialised kernel with UPT units per producer thread meets: the
+// launch configurations use UPT only while 16 UPT < units <= 512 UPT (units = Nc / unit_slots)
+__host__ __device__ constexpr int ws_lg_lo(int UPT, int M) { return UPT == 1 ? 2 : (UPT == 2 ? 6 : UPT == 4 ? 7 : 8) + (M == 1); }
+__host__ __device__ constexpr int ws_lg_hi(int UPT, int M)
+{
+    return ((UPT == 1 ? 9 : UPT == 2 ? 10 : UPT == 4 ? 11 : 12) + (M == 1)) < 12 ? ((UPT == 1 ? 9 : UPT == 2 ? 10 : UPT == 4 ? 11 : 12) + (M == 1)) : 12;
 }
 
 // Warp-specialised segment kernel.  Threads [0, NP) are the producer group: the recursion of
@@ -912,10 +1017,10 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
     using C = cplx<Real>;
     constexpr int G = kG<M>;
     constexpr int ROW = step_row(M);
+    constexpr int RB = RMAX < SMERF_RB ? RMAX : SMERF_RB;  // realisations whose noise is drawn together
     static_assert(2 * M * G == 4, "a unit holds four state values");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint2 rk[RMAX][10];
-    __shared__ Real nyq[RMAX * M];
 
     const Segment sg = P.segs[seg_index];
     const int r0 = group * RMAX;
@@ -940,7 +1045,6 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
         const uint64_t key = P.seed + (uint64_t)(r0 + r);
         rk[r][i] = make_uint2((uint32_t)key + (uint32_t)i * 0x9E3779B9u, (uint32_t)(key >> 32) + (uint32_t)i * 0xBB67AE85u);
     }
-    if (tid < R * M) nyq[tid] = anc[aoff<M>(P, c, r0 + tid / M, sg.left, M + tid % M, 0)];
     if (has_right) {
         const int per = 2 * M * Nc;
         for (int idx = 4 * tid; idx < R * per; idx += 4 * nt) {
@@ -985,44 +1089,36 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
 #pragma unroll
                     for (int g = 0; g < G; ++g) load_row<Real, TabT, ROW>(tb + (size_t)(G * u + g) * ROW, ta[g]);
 #pragma unroll
-                    for (int r = 0; r < RMAX; ++r) {
+                    for (int rb = 0; rb < RMAX; rb += RB) {
+                        if (rb >= R) continue;
+                        // normals of realisations rb .. rb + RB - 1 (those past R are not used)
+                        Real nrb[RB][4];
+                        unit_normals_multi<Real, RB>(rk + rb, (uint32_t)u, (uint32_t)ring, nrb);
+#pragma unroll
+                    for (int r = rb; r < rb + RB; ++r) {
                         if (r >= R) continue;
-                        Real nr[4];
-                        unit_normals_rk<Real>(rk[r], (uint32_t)u, (uint32_t)ring, nr);
-                        if (has_right) {
-                            Real xr[4];
-                            Vec4<Real>::ld(xRs + ((size_t)r * Nc + G * u) * 2 * M, xr);
+                        const Real* nr = nrb[r - rb];
+                        Real xr[4];
+                        if (has_right) Vec4<Real>::ld(xRs + ((size_t)r * Nc + G * u) * 2 * M, xr);
 #pragma unroll
-                            for (int g = 0; g < G; ++g)
+                        for (int g = 0; g < G; ++g)
 #pragma unroll
-                                for (int part = 0; part < 2; ++part)
-                                    step_state<Real, M, true>(ta[g], *reinterpret_cast<Real(*)[M]>(&x[i][r][g * 2 * M + part * M]),
-                                                              nr + g * 2 * M + part * M, xr + g * 2 * M + part * M);
-                        } else {
-#pragma unroll
-                            for (int g = 0; g < G; ++g)
-#pragma unroll
-                                for (int part = 0; part < 2; ++part)
-                                    step_state<Real, M, false>(ta[g], *reinterpret_cast<Real(*)[M]>(&x[i][r][g * 2 * M + part * M]),
-                                                               nr + g * 2 * M + part * M, nullptr);
-                        }
+                            for (int part = 0; part < 2; ++part) {
+                                Real(&xs)[M] = *reinterpret_cast<Real(*)[M]>(&x[i][r][g * 2 * M + part * M]);
+                                const Real* xi = nr + g * 2 * M + part * M;
+                                if (g == 0 && part == 1 && u == 0) {
+                                    // slot 0, second part: the Nyquist chain (mode Nc, own table row)
+                                    Real tn[ROW];
+                                    load_row<Real, TabT, ROW>(tb + (size_t)Nc * ROW, tn);
+                                    if (has_right) step_state<Real, M, true>(tn, xs, xi, xr + M);
+                                    else step_state<Real, M, false>(tn, xs, xi, nullptr);
+                                } else if (has_right) {
+                                    step_state<Real, M, true>(ta[g], xs, xi, xr + g * 2 * M + part * M);
+                                } else {
+                                    step_state<Real, M, false>(ta[g], xs, xi, nullptr);
+                                }
+                            }
                     }
-                }
-                if (tid == 0) {  // the Nyquist chain (normals [M, 2M) of unit 0)
-                    Real tn[ROW];
-                    load_row<Real, TabT, ROW>(tb + (size_t)Nc * ROW, tn);
-                    for (int r = 0; r < R; ++r) {
-                        Real nr[4], xs[M], xr[M];
-                        unit_normals_rk<Real>(rk[r], 0u, (uint32_t)ring, nr);
-#pragma unroll
-                        for (int q = 0; q < M; ++q) {
-                            xs[q] = nyq[r * M + q];
-                            xr[q] = has_right ? xRs[(size_t)r * Nc * 2 * M + M + q] : (Real)0;
-                        }
-                        if (has_right) step_state<Real, M, true>(tn, xs, nr + M, xr);
-                        else step_state<Real, M, false>(tn, xs, nr + M, nullptr);
-#pragma unroll
-                        for (int q = 0; q < M; ++q) nyq[r * M + q] = xs[q];
                     }
                 }
             }
@@ -1035,8 +1131,7 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
                     if (r >= R) continue;
 #pragma unroll
                     for (int g = 0; g < G; ++g)
-                        B[(size_t)r * Nc + G * u + g] =
-                            cmk<C>(x[i][r][g * 2 * M], (u == 0 && g == 0) ? nyq[r * M] : x[i][r][g * 2 * M + M]);
+                        B[(size_t)r * Nc + G * u + g] = cmk<C>(x[i][r][g * 2 * M], x[i][r][g * 2 * M + M]);
                 }
             }
             __threadfence_block();
@@ -1055,7 +1150,11 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
 #pragma unroll
                 for (int r = 0; r < RMAX; ++r)
                     gout[r] = (C*)((Real*)P.out + ((size_t)min(r0 + r, P.n_samples - 1) * P.n_theta + ring) * (size_t)P.n_phi);
-                grp_c2r<C, sizeof(Real) == 4>(P.lgNc, B, W, R, twp, pre, gout, ftid, NF);
+                if constexpr (sizeof(Real) == 4)
+                    hr_c2r<C, ws_lg_lo(UPT, M), ws_lg_hi(UPT, M)>(P.lgNc, B, W, R, twp, (const C*)P.tw2, pre, gout,
+                                                                   ftid, NF);
+                else
+                    grp_c2r_rt<C>(B, W, R, P.lgNc, twp, pre, gout, ftid, NF);
             }
             bar_arrive(kBarEmpty + (k & 1), nt);
         }
@@ -1063,7 +1162,7 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
 }
 
 template <class Real, class TabT, int M, int UPT, int RMAX>
-__global__ void __launch_bounds__(768) segment_ws_kernel(SampleParams P)
+__global__ void __launch_bounds__(SMERF_WS_MAXT) segment_ws_kernel(SampleParams P)
 {
     ws_body<Real, TabT, M, UPT, RMAX>(P, blockIdx.y, blockIdx.x);
 }
@@ -1071,7 +1170,7 @@ __global__ void __launch_bounds__(768) segment_ws_kernel(SampleParams P)
 // batched: item = (request, segment, realisation group); all requests of a launch share the
 // kernel shape (precision, p, n_phi, anchors or not) and hence the launch configuration
 template <class Real, class TabT, int M, int UPT, int RMAX>
-__global__ void __launch_bounds__(768) segment_ws_batched_kernel(const SampleParams* __restrict__ descs,
+__global__ void __launch_bounds__(SMERF_WS_MAXT) segment_ws_batched_kernel(const SampleParams* __restrict__ descs,
                                                                  const int4* __restrict__ items)
 {
     const int4 it = items[blockIdx.x];
@@ -1145,7 +1244,7 @@ template <class Real> inline bool ws_built(int upt, int rmax)
 }
 
 // Every warp-specialised configuration that fits the plan: producer threads np = units / upt
-// (<= 512, multiple of 32), FFT threads nf in {np/2, np, np/4} (np + nf <= 768).
+// (<= 512, multiple of 32), FFT threads nf in {np/2, np, np/4} (np + nf <= kWsMaxThreads).
 template <class Real>
 inline int tune_candidates(const smerf_plan* pl, int* cand, int max_n)
 {
@@ -1163,7 +1262,7 @@ inline int tune_candidates(const smerf_plan* pl, int* cand, int max_n)
             for (int d = 0; d < 3; ++d) {
                 int nf = ((np / div[d] + 31) / 32) * 32;
                 if (nf < 32) nf = 32;
-                if (np + nf > 768) continue;
+                if (np + nf > kWsMaxThreads) continue;
                 if (n < max_n) {
                     cand[4 * n + 0] = upt;
                     cand[4 * n + 1] = rmax;
@@ -1186,7 +1285,7 @@ inline SegConfig seg_config(const smerf_plan* pl)
     const int Nc = pl->n_phi / 2;
     if (pl->tune.valid && ws_built<Real>(pl->tune.upt, pl->tune.rmax) &&
         ws_smem<Real>(pl, pl->tune.rmax) <= 226 * 1024 &&
-        (n_units + pl->tune.upt - 1) / pl->tune.upt <= pl->tune.np && pl->tune.np + pl->tune.nf <= 768) {
+        (n_units + pl->tune.upt - 1) / pl->tune.upt <= pl->tune.np && pl->tune.np + pl->tune.nf <= kWsMaxThreads) {
         cfg.ws = 1;
         cfg.upt = pl->tune.upt;
         cfg.rmax = pl->tune.rmax;
@@ -1195,13 +1294,13 @@ inline SegConfig seg_config(const smerf_plan* pl)
         cfg.smem = ws_smem<Real>(pl, cfg.rmax);
         return cfg;
     }
+    auto np_of = [&](int u) { return (((n_units + u - 1) / u + 31) / 32) * 32; };
+    auto nf_of = [](int np) { return np / 2 > 32 ? ((np / 2 + 31) / 32) * 32 : 32; };
+    auto fits = [&](int u) { return np_of(u) <= 512 && np_of(u) + nf_of(np_of(u)) <= kWsMaxThreads; };
     int upt = 1;
-    while (upt < 8 && (n_units + upt - 1) / upt > 512) upt *= 2;
-    if ((n_units + upt - 1) / upt <= 512) {
-        int np = (n_units + upt - 1) / upt;
-        np = ((np + 31) / 32) * 32;
-        int nf = ((np / 2 + 31) / 32) * 32;
-        if (nf < 32) nf = 32;
+    while (upt < 8 && !fits(upt)) upt *= 2;
+    if (fits(upt)) {
+        const int np = np_of(upt), nf = nf_of(np);
         for (int rmax = ws_rmax_cap<Real>(upt); rmax >= 1; rmax /= 2) {
             const size_t smem = (size_t)3 * rmax * Nc * 2 * sizeof(Real) +
                                 (pl->H > 0 ? (size_t)rmax * Nc * 2 * M * sizeof(Real) : 0);
@@ -1274,6 +1373,7 @@ int fill_params(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scr
     P.beq = pl->beq;
     P.tw = pl->tw;
     P.pre = pl->pre;
+    P.tw2 = pl->tw2;
     P.anc = scratch;
     P.out = out;
     P.seed = seed;
@@ -1300,8 +1400,9 @@ int fill_params(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scr
     return SMERF_OK;
 }
 
-template <class Real, class TabT>
-int launch_sample_t(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch, cudaStream_t st,
+// Anchor and segment launches of one request (state size M = p).
+template <class Real, class TabT, int M>
+int launch_sample_m(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch, cudaStream_t st,
                     cudaEvent_t ev0, cudaEvent_t ev1)
 {
     SampleParams P;
@@ -1310,13 +1411,11 @@ int launch_sample_t(const smerf_plan* pl, uint64_t seed, int n, void* out, void*
     if (rc != SMERF_OK) return rc;
     {
         dim3 ga((P.n_units + 127) / 128, n, 2);
-        if (pl->p == 1) anchor_kernel<Real, TabT, 1><<<ga, 128, 0, st>>>(P);
-        else anchor_kernel<Real, TabT, 2><<<ga, 128, 0, st>>>(P);
+        anchor_kernel<Real, TabT, M><<<ga, 128, 0, st>>>(P);
         if (cudaGetLastError() != cudaSuccess) return SMERF_ECUDA;
     }
     if (ev0 && cudaEventRecord(ev0, st) != cudaSuccess) return SMERF_ECUDA;
-    rc = pl->p == 1 ? dispatch_segments<Real, TabT, 1>(P, pl->n_segments, cfg, st)
-                    : dispatch_segments<Real, TabT, 2>(P, pl->n_segments, cfg, st);
+    rc = dispatch_segments<Real, TabT, M>(P, pl->n_segments, cfg, st);
     if (rc == SMERF_OK && ev1 && cudaEventRecord(ev1, st) != cudaSuccess) return SMERF_ECUDA;
     return rc;
 }
@@ -1366,20 +1465,67 @@ int fill_params_c(const smerf_plan* pl, uint64_t seed, int n, void* out, void* s
     return rc;
 }
 
-template <class Real, class TabT>
-int launch_group_t(const smerf_plan* rep, const SampleParams* d, const int4* anc_items, int n_anc,
+// One anchor and one segment launch over a batched group's work items (state size M = p).
+template <class Real, class TabT, int M>
+int launch_group_m(const smerf_plan* rep, const SampleParams* d, const int4* anc_items, int n_anc,
                    const int4* seg_items, int n_seg, cudaStream_t st)
 {
     const SegConfig cfg = seg_config<Real>(rep);
     if (!cfg.ws) return SMERF_EUNSUPPORTED;
     if (n_anc > 0) {
-        if (rep->p == 1) anchor_batched_kernel<Real, TabT, 1><<<n_anc, 128, 0, st>>>(d, anc_items);
-        else anchor_batched_kernel<Real, TabT, 2><<<n_anc, 128, 0, st>>>(d, anc_items);
+        anchor_batched_kernel<Real, TabT, M><<<n_anc, 128, 0, st>>>(d, anc_items);
         if (cudaGetLastError() != cudaSuccess) return SMERF_ECUDA;
     }
     if (n_seg == 0) return SMERF_OK;
-    return rep->p == 1 ? group_segments<Real, TabT, 1>(cfg, d, seg_items, n_seg, st)
-                       : group_segments<Real, TabT, 2>(cfg, d, seg_items, n_seg, st);
+    return group_segments<Real, TabT, M>(cfg, d, seg_items, n_seg, st);
 }
 
 }  // namespace smerf
+
+// Kernel instantiations of one (recursion, table) precision pair XX and state size M, one
+// translation unit each (smerf_sample_XX_pM.cu).
+#define SMERF_INSTANTIATE(REAL, TABT, XX, M)                                                             \
+    int smerf_launch_sample_##XX##_p##M(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch, \
+                                        cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1)                \
+    {                                                                                                     \
+        return smerf::launch_sample_m<REAL, TABT, M>(pl, seed, n, out, scratch, st, ev0, ev1);           \
+    }                                                                                                     \
+    int smerf_launch_group_##XX##_p##M(const smerf_plan* rep, const smerf::SampleParams* d,               \
+                                       const int4* anc_items, int n_anc, const int4* seg_items, int n_seg, \
+                                       cudaStream_t st)                                                   \
+    {                                                                                                     \
+        return smerf::launch_group_m<REAL, TABT, M>(rep, d, anc_items, n_anc, seg_items, n_seg, st);     \
+    }
+
+// The precision pair's entry points (smerf_sample_XX.cu): dispatch on p to the instantiations.
+#define SMERF_PRECISION_PAIR(REAL, TABT, XX)                                                                \
+    int smerf_launch_sample_##XX##_p1(const smerf_plan*, uint64_t, int, void*, void*, cudaStream_t, cudaEvent_t, \
+                                      cudaEvent_t);                                                         \
+    int smerf_launch_sample_##XX##_p2(const smerf_plan*, uint64_t, int, void*, void*, cudaStream_t, cudaEvent_t, \
+                                      cudaEvent_t);                                                         \
+    int smerf_launch_group_##XX##_p1(const smerf_plan*, const smerf::SampleParams*, const int4*, int,       \
+                                     const int4*, int, cudaStream_t);                                       \
+    int smerf_launch_group_##XX##_p2(const smerf_plan*, const smerf::SampleParams*, const int4*, int,       \
+                                     const int4*, int, cudaStream_t);                                       \
+    int smerf_launch_sample_##XX(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch,      \
+                                 cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1)                         \
+    {                                                                                                       \
+        return pl->p == 1 ? smerf_launch_sample_##XX##_p1(pl, seed, n, out, scratch, st, ev0, ev1)          \
+                          : smerf_launch_sample_##XX##_p2(pl, seed, n, out, scratch, st, ev0, ev1);         \
+    }                                                                                                       \
+    int smerf_fill_params_##XX(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch,        \
+                               smerf::SampleParams* P, int* batchable, int* rmax)                           \
+    {                                                                                                       \
+        return smerf::fill_params_c<REAL, TABT>(pl, seed, n, out, scratch, P, batchable, rmax);             \
+    }                                                                                                       \
+    int smerf_launch_group_##XX(const smerf_plan* rep, const smerf::SampleParams* d_descs,                  \
+                                const int4* anc_items, int n_anc, const int4* seg_items, int n_seg,         \
+                                cudaStream_t st)                                                            \
+    {                                                                                                       \
+        return rep->p == 1 ? smerf_launch_group_##XX##_p1(rep, d_descs, anc_items, n_anc, seg_items, n_seg, st) \
+                           : smerf_launch_group_##XX##_p2(rep, d_descs, anc_items, n_anc, seg_items, n_seg, st); \
+    }                                                                                                       \
+    int smerf_tune_candidates_##XX(const smerf_plan* pl, int* cand, int max_n)                              \
+    {                                                                                                       \
+        return smerf::tune_candidates<REAL>(pl, cand, max_n);                                               \
+    }
