@@ -32,6 +32,29 @@ METRIC = "sphere grid points/s"
 FLUSH_BYTES = 256 << 20
 
 
+SMS, FP32_LANES, FP64_PER_SM = 152, 128, 2     # GB300: SMs, FP32 lanes per SM, FP64 FMAs per SM per clock
+
+
+def alg_ops_per_item(p, Nc, fp64=False):
+    """Algorithmic ALU operations of one (mode, realisation, ring) item of the method (an FMA
+    counts as one): Philox4x32-10 (10 rounds x 2 widening multiplies + 2 three-input XORs per
+    call of 4 normals), Box-Muller (12 per pair: 2 conversions, 2 scalings, log2, scaling,
+    rsqrt, product, sin, cos, 2 products), the recursion x = A x + B xi on the Re and Im
+    chains (Eq. (state_space)), and this item's share of the ring's C2R FFT (10 for the
+    packing, 3.5 log2 Nc for a radix-4 complex FFT).  With fp64 only the floating-point part
+    (Box-Muller, recursion, FFT), which runs on the FP64 pipe."""
+    philox = 40.0 * (2 * p) / 4.0
+    box_muller = 12.0 * p
+    recursion = 2.0 * (p * p + p * (p + 1) / 2.0)
+    fft = 10.0 + 3.5 * math.log2(Nc)
+    return (box_muller + recursion + fft) if fp64 else (philox + box_muller + recursion + fft)
+
+
+def alu_peak(fp64, sm_mhz):
+    """Lane operations per second: FP32 (and INT32) issue 128 lanes per SM per clock; FP64 2."""
+    return SMS * (FP64_PER_SM if fp64 else FP32_LANES) * sm_mhz * 1e6
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -135,7 +158,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.tables == "fp64" else WORKLOAD.replace("FP64 tables", "FP32 tables"),
+            "config": {"workload": WORKLOAD if (args.tables or "fp64") == "fp64" else WORKLOAD.replace("FP64 tables", "FP32 tables"),
                        "n_theta": N_THETA, "n_phi": N_PHI},
             "cpu_baseline": {"value": value, "unit": "points/s", "cores": cpu_cores(), "kind": "oracle",
                              "sample": sample},
@@ -148,7 +171,7 @@ def run_gb300(args, rank, world, local_rank):
     import torch.distributed as dist
     from paper_1709_10314_gb300 import Batch, Plan
     from paper_1709_10314_gb300.replicas import max_over_ranks, rank_seed
-    from paper_1709_10314_gb300.workloads import FIXED, flags_for, uneven_requests
+    from paper_1709_10314_gb300.workloads import FIXED, TUNED_LAUNCH, flags_for, uneven_requests
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -164,6 +187,9 @@ def run_gb300(args, rank, world, local_rank):
         outs = [torch.empty((n, p.n_theta, p.n_phi), dtype=torch.float32, device=dev) for p, n in zip(plans, counts)]
         batch = Batch(plans, counts)
         points = sum(n * p.n_theta * p.n_phi for p, n in zip(plans, counts))
+        fp64_alu = False
+        alg_ops = sum(n * p.n_theta * (p.n_phi // 2) * alg_ops_per_item(p.info()["p"], p.n_phi // 2)
+                      for p, n in zip(plans, counts))
         table_bytes = sum(p.info()["table_bytes"] for p in plans)
         out_bytes = points * 4
         workload = ("uneven batch: 256 requests, n_theta in {128,256,512,1024}, n_phi=2 n_theta, kappa in [5,200], "
@@ -207,14 +233,20 @@ def run_gb300(args, rank, world, local_rank):
         n = cfg["n"]
         # launch configuration of the segment kernel: timed candidates (set-up, untimed)
         ws_kernel = len(plan.launch_candidates()) > 0
+        stored = TUNED_LAUNCH.get((wl, recur, tables))
         if args.launch and ws_kernel:
             launch_cfg = [int(v) for v in args.launch.split(",")]
+            plan.set_launch(launch_cfg)
+        elif ws_kernel and not args.no_tune and not args.tune and stored in plan.launch_candidates():
+            launch_cfg = list(stored)
             plan.set_launch(launch_cfg)
         else:
             launch_cfg = list(plan.autotune(n)) if (ws_kernel and not args.no_tune) else None
         out = torch.empty((n, cfg["n_theta"], cfg["n_phi"]), dtype=plan.dtype, device=dev)
         points = n * cfg["n_theta"] * cfg["n_phi"]
         out_bytes = points * (8 if recur == "fp64" else 4)
+        fp64_alu = recur == "fp64"
+        alg_ops = n * cfg["n_theta"] * (cfg["n_phi"] // 2) * alg_ops_per_item(len(cfg["kappa"]), cfg["n_phi"] // 2, fp64_alu)
         table_bytes = info["table_bytes"]
         setup_ms = info["setup_ms"]
         dtype = "f64" if recur == "fp64" else "f32"
@@ -266,10 +298,15 @@ def run_gb300(args, rank, world, local_rank):
     step_ms, seg_ms = max_over_ranks([step_ms, seg_ms], device=dev)
     value = world * points / (step_ms / 1e3)
 
-    # roofline of the segment kernel: algorithmic bytes = field written once + tables read once
+    # Rooflines of the segment kernel.  It is bound by ALU issue (noise, recursion and FFT
+    # arithmetic), not by HBM: ALU = algorithmic operations / kernel time against the lane
+    # rate at the maximum SM clock; HBM = field written once + tables read once.
     alg_bytes = out_bytes + table_bytes
     peak, peak_kind = _peaks()
     achieved = alg_bytes / (seg_ms / 1e3) / 1e9
+    sm_max = float(clocks.get("sm_max_mhz") or 2070.0) if isinstance(clocks, dict) else 2070.0
+    alu_pk = alu_peak(fp64_alu, sm_max) / 1e9
+    alu_ach = alg_ops / (seg_ms / 1e3) / 1e9
     # DRAM traffic of one segment-kernel launch from the committed ncu record, only while the
     # kernel sources still hash to what was profiled (null otherwise)
     traffic = None
@@ -309,9 +346,13 @@ def run_gb300(args, rank, world, local_rank):
             "config": {"workload": workload, "name": wl, "points_per_gpu": points, "anchor_spacing": ANCHOR,
                        "launch": launch_cfg, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between timed steps (256 MiB write outside the step events)"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": kernel, "kernel_ms": seg_ms, "algorithmic_bytes": alg_bytes},
+            "roofline": {"bound": "alu", "achieved": alu_ach, "peak": alu_pk, "unit": "Gop/s",
+                         "frac": alu_ach / alu_pk, "traffic": traffic,
+                         "peak_kind": "derived: %d SMs x %d %s lanes x %.0f MHz" % (
+                             SMS, FP64_PER_SM if fp64_alu else FP32_LANES, "FP64" if fp64_alu else "FP32/INT32", sm_max),
+                         "algorithmic_ops": alg_ops, "kernel": kernel, "kernel_ms": seg_ms,
+                         "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                                 "peak_kind": peak_kind, "algorithmic_bytes": alg_bytes}},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches * args.steps,
@@ -331,6 +372,8 @@ def main():
                     help="override the workload's table storage precision")
     ap.add_argument("--recur", default=None, choices=["fp64", "fp32"],
                     help="override the workload's recursion precision")
+    ap.add_argument("--tune", action="store_true",
+                    help="time the launch candidates (smerf_plan_autotune) instead of the stored choice")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the built-in segment-kernel launch configuration (no autotuning)")
     ap.add_argument("--launch", default=None,

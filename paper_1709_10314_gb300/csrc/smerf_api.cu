@@ -35,6 +35,7 @@ void free_plan_memory(smerf_plan* pl)
     cudaFree(pl->tw);
     cudaFree(pl->pre);
     cudaFree(pl->tw2);
+    cudaFree(pl->tw3);
     cudaFree(pl->segs_dev);
     free(pl->segs_host);
 }

@@ -53,8 +53,9 @@ struct smerf_plan {
     // FFT tables in the recursion precision: per-pass twiddles, pre[Nc] = e^{2 pi i s / n_phi}
     void* tw;
     void* pre;
-    // per-pass twiddles of the high-radix plan (hr_* below), recursion precision
+    // per-pass twiddles of the high-radix plans (hr_* below, MB = 4 and 3), recursion precision
     void* tw2;
+    void* tw3;
     size_t table_bytes;
     double setup_ms;
     int dev;
@@ -81,7 +82,8 @@ struct SampleParams {
     const void* beq;
     const void* tw;   // per-pass complex twiddle tables (see pass_radix)
     const void* pre;  // complex e^{2 pi i s / n_phi}, s < Nc
-    const void* tw2;  // per-pass complex twiddles of the high-radix plan (hr_off)
+    const void* tw2;  // per-pass complex twiddles of the high-radix plan, MB = 4 (hr_off)
+    const void* tw3;  // the same for MB = 3
     void* anc;        // anchor states [c][r][j][2M][n_slots]
     void* out;
     uint64_t seed;
@@ -92,22 +94,27 @@ struct SampleParams {
     int lgNc;
 };
 
-// High-radix pass plan of the Nc = 2^L point inverse FFT: ceil(L / 4) Stockham passes whose
-// radices 2^bits split L as evenly as possible, largest first (L = 10: 16, 8, 8).  Pass i runs
-// with stride Ns = 2^hr_lgns(L, i); its twiddles e^{2 pi i a kk / (Ns RP)}, a in [1, RP),
-// kk < Ns, sit at tw2[hr_off(L, i) + (a - 1) Ns + kk] (pass 0 has none).
-__host__ __device__ constexpr int hr_passes(int L) { return (L + 3) / 4; }
-__host__ __device__ constexpr int hr_bits(int L, int i) { return L / hr_passes(L) + (i < L % hr_passes(L) ? 1 : 0); }
-__host__ __device__ constexpr int hr_lgns(int L, int i)
+// High-radix pass plan of the Nc = 2^L point inverse FFT with passes of at most 2^MB points:
+// ceil(L / MB) Stockham passes whose radices 2^bits split L as evenly as possible, largest
+// first (L = 10, MB = 4: 16, 8, 8).  Pass i runs with stride Ns = 2^hr_lgns(L, i); its
+// twiddles e^{2 pi i a kk / (Ns RP)}, a in [1, RP), kk < Ns, sit at
+// tw[hr_off(L, i) + (a - 1) Ns + kk] (pass 0 has none).  The warp-specialised kernel uses
+// MB = 4 (table tw2), the in-place kernel MB = 3 (table tw3).
+__host__ __device__ constexpr int hr_passes(int L, int MB = 4) { return (L + MB - 1) / MB; }
+__host__ __device__ constexpr int hr_bits(int L, int i, int MB = 4)
+{
+    return L / hr_passes(L, MB) + (i < L % hr_passes(L, MB) ? 1 : 0);
+}
+__host__ __device__ constexpr int hr_lgns(int L, int i, int MB = 4)
 {
     int s = 0;
-    for (int p = 0; p < i; ++p) s += hr_bits(L, p);
+    for (int p = 0; p < i; ++p) s += hr_bits(L, p, MB);
     return s;
 }
-__host__ __device__ constexpr int hr_off(int L, int i)
+__host__ __device__ constexpr int hr_off(int L, int i, int MB = 4)
 {
     int o = 0;
-    for (int p = 1; p < i; ++p) o += ((1 << hr_bits(L, p)) - 1) << hr_lgns(L, p);
+    for (int p = 1; p < i; ++p) o += ((1 << hr_bits(L, p, MB)) - 1) << hr_lgns(L, p, MB);
     return o;
 }
 

@@ -319,51 +319,6 @@ __device__ __forceinline__ C c2r_pack(const C* X, int s, int Nc, const C* pre)
 // entries); the tables are built with the plan (smerf_setup.cu, pass_twiddle_kernel).
 __host__ __device__ inline int pass_radix(int lgNc, int Ns) { return (1 << lgNc) / Ns >= 4 ? 4 : 2; }
 
-// One radix-RP Stockham pass over R rings of Nc points, src -> dst (distinct shared
-// buffers), or, for the last pass, straight to the rings' rows in global memory (gout[r]).
-// The first pass (Ns = 1) has unit twiddles and applies the C2R packing as it loads.
-template <class C, int RP, bool FIRST, bool LAST>
-__device__ __forceinline__ void fft_pass(const C* __restrict__ src, C* __restrict__ dst, int R, int lgNc,
-                                         int Ns, const C* __restrict__ twp, const C* __restrict__ pre,
-                                         C* const* gout)
-{
-    const int Nc = 1 << lgNc;
-    constexpr int LR = RP == 4 ? 2 : 1;
-    const int lgnb = lgNc - LR;
-    const int nb = 1 << lgnb;
-    const int total = R << lgnb;
-    for (int b = threadIdx.x; b < total; b += blockDim.x) {
-        const int r = b >> lgnb, j = b & (nb - 1);
-        const C* S = src + (r << lgNc);
-        C v[RP];
-        int kk = 0;
-        if (FIRST) {
-#pragma unroll
-            for (int i = 0; i < RP; ++i) v[i] = c2r_pack(S, j + i * nb, Nc, pre);
-        } else {
-            kk = j & (Ns - 1);
-#pragma unroll
-            for (int i = 0; i < RP; ++i) v[i] = S[j + i * nb];
-#pragma unroll
-            for (int i = 1; i < RP; ++i) v[i] = cmul(v[i], __ldg(twp + (i - 1) * Ns + kk));
-        }
-        dft<C, RP>(v);
-        const int idx = ((j - kk) << LR) + kk;
-        if (LAST) {
-            C* D = gout[r] + idx;
-#pragma unroll
-            for (int a = 0; a < RP; ++a) __stcs(D + a * Ns, v[a]);
-        } else {
-            C* D = dst + (r << lgNc) + idx;
-#pragma unroll
-            for (int a = 0; a < RP; ++a) D[a * Ns] = v[a];
-        }
-    }
-}
-
-template <class C>
-__device__ __forceinline__ C c2r_pack_g(const C* X, int s, int Nc, const C* pre) { return c2r_pack(X, s, Nc, pre); }
-
 // In-place variant: every thread reads all its butterflies before a barrier and writes after
 // it (BPT butterflies per thread at most).
 template <class C, int RP, int BPT, bool FIRST>
@@ -425,141 +380,74 @@ __device__ __forceinline__ void c2r_rings_inplace(C* buf, int R, int lgNc, const
     }
 }
 
-// Real inverse DFT (prefactor 1) of R rings straight into their output rows gout[r]:
-// buf0 holds the packed coefficients (slot 0 = (X_0, X_Nc), slot s = X_s); buf1 is the
-// second ping-pong buffer.  The last pass writes global memory (rows of n_phi reals viewed
-// as Nc complex (x_{2n}, x_{2n+1})).  One barrier per shared-memory pass; on return both
-// buffers may be reused after the caller's next barrier.
-template <class C>
-__device__ __forceinline__ void c2r_rings_to_global(C* buf0, C* buf1, int R, int lgNc, const C* twp,
-                                                    const C* pre, C* const* gout)
-{
-    const int Nc = 1 << lgNc;
-    C* src = buf0;
-    C* dst = buf1;
-    int Ns = 1, off = 0;
-    bool first = true;
-    while (Ns < Nc) {
-        const int RP = pass_radix(lgNc, Ns);
-        const bool last = Ns * RP == Nc;
-        if (RP == 4) {
-            if (first) {
-                if (last) fft_pass<C, 4, true, true>(src, dst, R, lgNc, Ns, twp + off, pre, gout);
-                else fft_pass<C, 4, true, false>(src, dst, R, lgNc, Ns, twp + off, pre, gout);
-            } else {
-                if (last) fft_pass<C, 4, false, true>(src, dst, R, lgNc, Ns, twp + off, pre, gout);
-                else fft_pass<C, 4, false, false>(src, dst, R, lgNc, Ns, twp + off, pre, gout);
-            }
-        } else {
-            if (first) {
-                if (last) fft_pass<C, 2, true, true>(src, dst, R, lgNc, Ns, twp + off, pre, gout);
-                else fft_pass<C, 2, true, false>(src, dst, R, lgNc, Ns, twp + off, pre, gout);
-            } else {
-                if (last) fft_pass<C, 2, false, true>(src, dst, R, lgNc, Ns, twp + off, pre, gout);
-                else fft_pass<C, 2, false, false>(src, dst, R, lgNc, Ns, twp + off, pre, gout);
-            }
-        }
-        if (!first) off += (RP - 1) * Ns;
-        Ns *= RP;
-        first = false;
-        if (!last) __syncthreads();
-        C* t = src;
-        src = dst;
-        dst = t;
-    }
-}
+// XOR swizzle of the high-radix plan's shared layout between passes: element e of a ring
+// sits at e ^ ((e >> 4) & 15).
+__device__ __forceinline__ int hr_swz(int e) { return e ^ ((e >> 4) & 15); }
 
-// Fixed-size variant of c2r_rings_to_global: the pass plan, strides and twiddle offsets
-// are compile-time constants (log2 Nc = LGNC).
-template <class C, int LGNC, int LGNS, bool FIRST>
-__device__ __forceinline__ void fft_pass_fixed(const C* __restrict__ src, C* __restrict__ dst, int R,
-                                               const C* __restrict__ twp, const C* __restrict__ pre,
-                                               C* const* gout)
+// In-place high-radix C2R (plan MB = 3: passes of at most 8 points) of one ring held in
+// `buf` (natural order in, swizzled between passes), last pass straight to HBM (gout).  Each thread keeps its butterflies' inputs in
+// registers across the barrier that separates a pass's reads from its writes; it holds at
+// most EPT points (EPT x threads >= Nc).
+template <class C, int LGNC, int EPT, int PASS = 0>
+__device__ __forceinline__ void hr_c2r_inplace(C* buf, const C* __restrict__ tw3, const C* __restrict__ pre, C* gout)
 {
-    constexpr int Nc = 1 << LGNC, Ns = 1 << LGNS;
-    constexpr int RP = (Nc / Ns >= 4) ? 4 : 2, LR = RP == 4 ? 2 : 1;
-    constexpr bool LAST = Ns * RP == Nc;
+    constexpr int MB = 3;
+    constexpr int Nc = 1 << LGNC;
+    constexpr int LR = hr_bits(LGNC, PASS, MB), RP = 1 << LR;
+    constexpr int Ns = 1 << hr_lgns(LGNC, PASS, MB);
+    constexpr bool FIRST = PASS == 0, LAST = PASS == hr_passes(LGNC, MB) - 1;
     constexpr int LGNB = LGNC - LR, nb = 1 << LGNB;
-    const int total = R << LGNB;
-    for (int b = threadIdx.x; b < total; b += blockDim.x) {
-        const int r = b >> LGNB, j = b & (nb - 1);
-        const C* S = src + (r << LGNC);
-        C v[RP];
-        int kk = 0;
-        if (FIRST) {
-            // element 0 is slot j: j = 0 holds (X_0, X_Nc); the others are never slot 0
-            {
-                const C a = S[j], bb = cconj(S[(Nc - j) & (Nc - 1)]);
-                const C g = cadd(cadd(a, bb), cmuli(cmul(__ldg(pre + j), csub(a, bb))));
-                const C z0 = cmk<C>(a.x + a.y, a.x - a.y);
-                v[0] = j == 0 ? z0 : g;
+    constexpr int KB = (EPT + RP - 1) / RP;  // butterflies per thread
+    const C* twp = tw3 + hr_off(LGNC, PASS, MB);
+    const int nt = blockDim.x;
+    C v[KB][RP];
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+        const int j = threadIdx.x + k * nt;
+        if (j < nb) {
+            if constexpr (FIRST) {
+                {
+                    const C a = buf[j], bb = cconj(buf[(Nc - j) & (Nc - 1)]);
+                    const C g = cadd(cadd(a, bb), cmuli(cmul(__ldg(pre + j), csub(a, bb))));
+                    v[k][0] = j == 0 ? cmk<C>(a.x + a.y, a.x - a.y) : g;
+                }
+#pragma unroll
+                for (int i = 1; i < RP; ++i) {
+                    const int sidx = j + i * nb;
+                    const C a = buf[sidx], bb = cconj(buf[Nc - sidx]);
+                    v[k][i] = cadd(cadd(a, bb), cmuli(cmul(__ldg(pre + sidx), csub(a, bb))));
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < RP; ++i) v[k][i] = buf[hr_swz(j + i * nb)];
             }
+        }
+    }
+    if constexpr (!LAST) __syncthreads();  // every read of this pass before any write
 #pragma unroll
-            for (int i = 1; i < RP; ++i) {
-                const int sidx = j + i * nb;
-                const C a = S[sidx], bb = cconj(S[Nc - sidx]);
-                v[i] = cadd(cadd(a, bb), cmuli(cmul(__ldg(pre + sidx), csub(a, bb))));
+    for (int k = 0; k < KB; ++k) {
+        const int j = threadIdx.x + k * nt;
+        if (j < nb) {
+            const int kk = FIRST ? 0 : (j & (Ns - 1));
+            if constexpr (!FIRST) {
+#pragma unroll
+                for (int i = 1; i < RP; ++i) v[k][i] = cmul(v[k][i], __ldg(twp + (i - 1) * Ns + kk));
             }
-        } else {
-            kk = j & (Ns - 1);
+            dft<C, RP>(v[k]);
+            const int idx = ((j - kk) << LR) + kk;
+            if constexpr (LAST) {
 #pragma unroll
-            for (int i = 0; i < RP; ++i) v[i] = S[j + i * nb];
+                for (int a = 0; a < RP; ++a) __stcs(gout + idx + a * Ns, v[k][a]);
+            } else {
 #pragma unroll
-            for (int i = 1; i < RP; ++i) v[i] = cmul(v[i], __ldg(twp + (i - 1) * Ns + kk));
-        }
-        dft<C, RP>(v);
-        const int idx = ((j - kk) << LR) + kk;
-        if (LAST) {
-            C* D = gout[r] + idx;
-#pragma unroll
-            for (int a = 0; a < RP; ++a) __stcs(D + a * Ns, v[a]);
-        } else {
-            C* D = dst + (r << LGNC) + idx;
-#pragma unroll
-            for (int a = 0; a < RP; ++a) D[a * Ns] = v[a];
+                for (int a = 0; a < RP; ++a) buf[hr_swz(idx + a * Ns)] = v[k][a];
+            }
         }
     }
-}
-
-template <class C, int LGNC, int LGNS = 0, int OFF = 0, bool FIRST = true>
-__device__ __forceinline__ void c2r_fixed(C* src, C* dst, int R, const C* twp, const C* pre, C* const* gout)
-{
-    constexpr int Nc = 1 << LGNC, Ns = 1 << LGNS;
-    constexpr int RP = (Nc / Ns >= 4) ? 4 : 2, LR = RP == 4 ? 2 : 1;
-    fft_pass_fixed<C, LGNC, LGNS, FIRST>(src, dst, R, twp + OFF, pre, gout);
-    if constexpr (Ns * RP < Nc) {
-        __syncthreads();
-        c2r_fixed<C, LGNC, LGNS + LR, OFF + (FIRST ? 0 : (RP - 1) * Ns), false>(dst, src, R, twp, pre, gout);
+    if constexpr (!LAST) {
+        __syncthreads();  // this pass's writes before the next pass's reads
+        hr_c2r_inplace<C, LGNC, EPT, PASS + 1>(buf, tw3, pre, gout);
     }
-}
-
-// Sizes with a fixed-size FFT for each units-per-thread width; others use the general one.
-template <class C, int UPT>
-__device__ __forceinline__ void c2r_dispatch(int lgNc, C* b0, C* b1, int R, const C* twp, const C* pre, C* const* gout)
-{
-    if (UPT == 1) {
-        switch (lgNc) {
-            case 7: c2r_fixed<C, 7>(b0, b1, R, twp, pre, gout); return;
-            case 8: c2r_fixed<C, 8>(b0, b1, R, twp, pre, gout); return;
-            case 9: c2r_fixed<C, 9>(b0, b1, R, twp, pre, gout); return;
-            case 10: c2r_fixed<C, 10>(b0, b1, R, twp, pre, gout); return;
-            case 11: c2r_fixed<C, 11>(b0, b1, R, twp, pre, gout); return;
-            default: break;
-        }
-    } else if (UPT == 2) {
-        switch (lgNc) {
-            case 11: c2r_fixed<C, 11>(b0, b1, R, twp, pre, gout); return;
-            case 12: c2r_fixed<C, 12>(b0, b1, R, twp, pre, gout); return;
-            default: break;
-        }
-    } else if (UPT == 4) {
-        switch (lgNc) {
-            case 12: c2r_fixed<C, 12>(b0, b1, R, twp, pre, gout); return;
-            case 13: c2r_fixed<C, 13>(b0, b1, R, twp, pre, gout); return;
-            default: break;
-        }
-    }
-    c2r_rings_to_global<C>(b0, b1, R, lgNc, twp, pre, gout);
 }
 
 // ------------------------------------------------------------------ segments
@@ -654,24 +542,27 @@ __device__ __forceinline__ void unit_normals_rk(const uint2* rk, uint32_t call, 
     box_muller(w.z, w.w, n[2], n[3]);
 }
 
-// Every ring of one segment of one chain for RMAX realisations.  Per ring: the recursion
-// for the thread's units (state in registers, tables read once per unit and shared by the
-// realisations), the coefficients into shared memory, the C2R FFT, the ring to HBM.
-template <class Real, class TabT, int M, int UPT, int RMAX, bool INPLACE>
-__global__ void __launch_bounds__(1024) segment_kernel(SampleParams P)
+// In-place segment kernel, for rings too long for the warp-specialised kernel's three
+// buffers (one realisation per CTA, one ring buffer).  Every ring of one segment of one
+// chain: the recursion for the thread's units (state in registers, tables read once per
+// unit), the coefficients into shared memory, the C2R FFT in place, the ring to HBM.  While
+// the FFT runs, the state of the upper half of each thread's units waits in shared memory,
+// which keeps the FFT's registers free of spills.  LG = log2 Nc of a fixed-size high-radix
+// FFT, or 0 for the runtime-size radix-4 one; PARK = units per thread parked (the last ones).
+template <class Real, class TabT, int M, int UPT, int LG, int PARK>
+__global__ void __launch_bounds__(1024, 1) segment_kernel(SampleParams P)
 {
     using C = cplx<Real>;
     constexpr int G = kG<M>;
     constexpr int ROW = step_row(M);
-    constexpr int EPT = RMAX * UPT * G;   // complex FFT points per thread (in-place mode)
+    constexpr int EPT = UPT * G;          // complex FFT points per thread
+    constexpr int UP = UPT - PARK;        // units whose state stays in registers during the FFT
     static_assert(2 * M * G == 4, "a unit holds four state values");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ uint2 rk[RMAX][10];     // Philox round keys of the CTA's realisations
-    __shared__ Real nyq[RMAX * M];     // Nyquist chain state per realisation (thread 0)
+    __shared__ uint2 rk[10];              // Philox round keys of the CTA's realisation
 
     const Segment sg = P.segs[blockIdx.y];
-    const int r0 = blockIdx.x * RMAX;
-    const int R = min(RMAX, P.n_samples - r0);
+    const int r0 = blockIdx.x;
     const int c = sg.chain;
     const int nt = blockDim.x, tid = threadIdx.x;
     const int Nc = P.Nc;
@@ -680,46 +571,27 @@ __global__ void __launch_bounds__(1024) segment_kernel(SampleParams P)
     const Real* anc = (const Real*)P.anc;
     const bool has_right = sg.right >= 0;
 
-    // shared memory: FFT buffer(s), then (ping-pong mode) the right-anchor states
+    // shared memory: the ring buffer, then the parked states [PARK][nt][4]
     C* buf0 = reinterpret_cast<C*>(smem_raw);
-    C* buf1 = buf0 + (size_t)RMAX * Nc;
-    Real* xRs = reinterpret_cast<Real*>(buf0 + (size_t)RMAX * Nc * (INPLACE ? 1 : 2));
+    Real* park = reinterpret_cast<Real*>(buf0 + Nc);
     const C* twp = (const C*)P.tw;
     const C* pre = (const C*)P.pre;
-    if (tid < RMAX * 10) {
-        const int r = tid / 10, i = tid % 10;
-        const uint64_t key = P.seed + (uint64_t)(r0 + r);
-        rk[r][i] = make_uint2((uint32_t)key + (uint32_t)i * 0x9E3779B9u, (uint32_t)(key >> 32) + (uint32_t)i * 0xBB67AE85u);
+    if (tid < 10) {
+        const uint64_t key = P.seed + (uint64_t)r0;
+        rk[tid] = make_uint2((uint32_t)key + (uint32_t)tid * 0x9E3779B9u, (uint32_t)(key >> 32) + (uint32_t)tid * 0xBB67AE85u);
     }
-    if (tid < R * M) nyq[tid] = anc[aoff<M>(P, c, r0 + tid / M, sg.left, M + tid % M, 0)];
-    // right-anchor states: shared memory in ping-pong mode, the scratch itself in place mode;
-    // layout [slot][2M] per realisation in both
-    const Real* xrg[RMAX];
-#pragma unroll
-    for (int r = 0; r < RMAX; ++r)
-        xrg[r] = anc + aoff<M>(P, c, min(r0 + r, P.n_samples - 1), has_right ? sg.right : 0, 0, 0);
-    if (!INPLACE && has_right) {
-        const int per = 2 * M * Nc;
-        for (int idx = 4 * tid; idx < R * per; idx += 4 * nt) {
-            const int r = idx / per, rest = idx - r * per;
-            Real v[4];
-            Vec4<Real>::ldg(xrg[r] + rest, v);
-            Vec4<Real>::st(xRs + idx, v);
-        }
-    }
+    // right-anchor states are read from the scratch ([slot][2M])
+    const Real* xrg = anc + aoff<M>(P, c, r0, has_right ? sg.right : 0, 0, 0);
 
-    Real x[UPT][RMAX][4];  // per unit: [g][part][q] flattened (g * 2M + part * M + q)
+    Real x[UPT][4];  // per unit: [g][part][q] flattened (g * 2M + part * M + q)
 #pragma unroll
     for (int i = 0; i < UPT; ++i) {
         const int u = tid + i * nt;
+        if (u < n_units) {
+            Vec4<Real>::ldg(anc + aoff<M>(P, c, r0, sg.left, 0, G * u), x[i]);
+        } else {
 #pragma unroll
-        for (int r = 0; r < RMAX; ++r) {
-            if (u < n_units && r < R) {
-                Vec4<Real>::ldg(anc + aoff<M>(P, c, r0 + r, sg.left, 0, G * u), x[i][r]);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) x[i][r][k] = 0;
-            }
+            for (int k = 0; k < 4; ++k) x[i][k] = 0;
         }
     }
     __syncthreads();
@@ -733,57 +605,31 @@ __global__ void __launch_bounds__(1024) segment_kernel(SampleParams P)
             for (int i = 0; i < UPT; ++i) {
                 const int u = tid + i * nt;
                 if (u >= n_units) continue;
-                // tables of the unit's slots (mode = slot).  Slot 0's second chain (the
-                // Nyquist mode) is stepped here with mode 0's tables and discarded; thread 0
-                // steps the real Nyquist chain separately below.
                 Real ta[G][ROW];
 #pragma unroll
                 for (int g = 0; g < G; ++g) load_row<Real, TabT, ROW>(tb + (size_t)(G * u + g) * ROW, ta[g]);
+                Real nr[4];
+                unit_normals_rk<Real>(rk, (uint32_t)u, (uint32_t)ring, nr);
+                Real xr[4];
+                if (has_right) Vec4<Real>::ldg(xrg + (size_t)G * u * 2 * M, xr);
 #pragma unroll
-                for (int r = 0; r < RMAX; ++r) {
-                    if (r >= R) continue;
-                    Real nr[4];
-                    unit_normals_rk<Real>(rk[r], (uint32_t)u, (uint32_t)ring, nr);
-                    if (has_right) {
-                        Real xr[4];
-                        if (INPLACE) Vec4<Real>::ldg(xrg[r] + (size_t)G * u * 2 * M, xr);
-                        else Vec4<Real>::ld(xRs + ((size_t)r * Nc + G * u) * 2 * M, xr);
+                for (int g = 0; g < G; ++g)
 #pragma unroll
-                        for (int g = 0; g < G; ++g)
-#pragma unroll
-                            for (int part = 0; part < 2; ++part) {
-                                Real* xs = &x[i][r][g * 2 * M + part * M];
-                                step_state<Real, M, true>(ta[g], *reinterpret_cast<Real(*)[M]>(xs),
-                                                          nr + g * 2 * M + part * M, xr + g * 2 * M + part * M);
-                            }
-                    } else {
-#pragma unroll
-                        for (int g = 0; g < G; ++g)
-#pragma unroll
-                            for (int part = 0; part < 2; ++part) {
-                                Real* xs = &x[i][r][g * 2 * M + part * M];
-                                step_state<Real, M, false>(ta[g], *reinterpret_cast<Real(*)[M]>(xs),
-                                                           nr + g * 2 * M + part * M, nullptr);
-                            }
+                    for (int part = 0; part < 2; ++part) {
+                        Real(&xs)[M] = *reinterpret_cast<Real(*)[M]>(&x[i][g * 2 * M + part * M]);
+                        const Real* xi = nr + g * 2 * M + part * M;
+                        if (g == 0 && part == 1 && u == 0) {
+                            // slot 0, second part: the Nyquist chain (mode Nc, own table row)
+                            Real tn[ROW];
+                            load_row<Real, TabT, ROW>(tb + (size_t)Nc * ROW, tn);
+                            if (has_right) step_state<Real, M, true>(tn, xs, xi, xr + M);
+                            else step_state<Real, M, false>(tn, xs, xi, nullptr);
+                        } else if (has_right) {
+                            step_state<Real, M, true>(ta[g], xs, xi, xr + g * 2 * M + part * M);
+                        } else {
+                            step_state<Real, M, false>(ta[g], xs, xi, nullptr);
+                        }
                     }
-                }
-            }
-            if (tid == 0) {  // the Nyquist chain (normals [M, 2M) of unit 0)
-                Real tn[ROW];
-                load_row<Real, TabT, ROW>(tb + (size_t)Nc * ROW, tn);
-                for (int r = 0; r < R; ++r) {
-                    Real nr[4], xs[M], xr[M];
-                    unit_normals_rk<Real>(rk[r], 0u, (uint32_t)ring, nr);
-#pragma unroll
-                    for (int q = 0; q < M; ++q) {
-                        xs[q] = nyq[r * M + q];
-                        xr[q] = has_right ? (INPLACE ? xrg[r][M + q] : xRs[(size_t)r * Nc * 2 * M + M + q]) : (Real)0;
-                    }
-                    if (has_right) step_state<Real, M, true>(tn, xs, nr + M, xr);
-                    else step_state<Real, M, false>(tn, xs, nr + M, nullptr);
-#pragma unroll
-                    for (int q = 0; q < M; ++q) nyq[r * M + q] = xs[q];
-                }
             }
         }
         // coefficients of this ring into shared memory (slot 0's imaginary part = Nyquist)
@@ -792,31 +638,24 @@ __global__ void __launch_bounds__(1024) segment_kernel(SampleParams P)
             const int u = tid + i * nt;
             if (u >= n_units) continue;
 #pragma unroll
-            for (int r = 0; r < RMAX; ++r) {
-                if (r >= R) continue;
-#pragma unroll
-                for (int g = 0; g < G; ++g)
-                    buf0[(size_t)r * Nc + G * u + g] =
-                        cmk<C>(x[i][r][g * 2 * M], (u == 0 && g == 0) ? nyq[r * M] : x[i][r][g * 2 * M + M]);
-            }
+            for (int g = 0; g < G; ++g) buf0[G * u + g] = cmk<C>(x[i][g * 2 * M], x[i][g * 2 * M + M]);
         }
+        // park the upper units' state
+#pragma unroll
+        for (int i = UP; i < UPT; ++i) Vec4<Real>::st(park + ((size_t)(i - UP) * nt + tid) * 4, x[i]);
         __syncthreads();
         if (!(c == 1 && pos == 0)) {  // the start ring is written by the northern chain
-            if constexpr (INPLACE) {
-                c2r_rings_inplace<C, EPT>(buf0, R, P.lgNc, twp, pre);
-                for (int r = 0; r < R; ++r) {
-                    Real* dst = (Real*)P.out + ((size_t)(r0 + r) * P.n_theta + ring) * (size_t)P.n_phi;
-                    store_ring<Real>(dst, buf0 + (size_t)r * Nc, Nc, tid, nt);
-                }
+            Real* dst = (Real*)P.out + ((size_t)r0 * P.n_theta + ring) * (size_t)P.n_phi;
+            if constexpr (LG > 0) {
+                hr_c2r_inplace<C, LG, EPT>(buf0, (const C*)P.tw3, pre, reinterpret_cast<C*>(dst));
             } else {
-                C* gout[RMAX];
-#pragma unroll
-                for (int r = 0; r < RMAX; ++r)
-                    gout[r] = (C*)((Real*)P.out + ((size_t)min(r0 + r, P.n_samples - 1) * P.n_theta + ring) * (size_t)P.n_phi);
-                c2r_dispatch<C, UPT>(P.lgNc, buf0, buf1, R, twp, pre, gout);
+                c2r_rings_inplace<C, EPT>(buf0, 1, P.lgNc, twp, pre);
+                store_ring<Real>(dst, buf0, Nc, tid, nt);
             }
         }
-        __syncthreads();  // buffers are rewritten by the next ring
+        __syncthreads();  // the buffer is rewritten by the next ring
+#pragma unroll
+        for (int i = UP; i < UPT; ++i) Vec4<Real>::ld(park + ((size_t)(i - UP) * nt + tid) * 4, x[i]);
     }
 }
 
@@ -912,10 +751,8 @@ __device__ __forceinline__ void grp_c2r_rt(C* buf0, C* buf1, int R, int lgNc, co
 // ---- high-radix plan (hr_passes / hr_bits): passes of radix up to 16 held in registers.
 // Between passes the rings sit in shared memory in an XOR-swizzled order, element e at
 // e ^ ((e >> 4) & 15), so that the strided stores of the early passes and the unit-stride
-// loads of the next pass are both free of bank conflicts.  The coefficient buffer the
-// producer fills (first pass input) is in natural order; the last pass writes HBM.
-__device__ __forceinline__ int hr_swz(int e) { return e ^ ((e >> 4) & 15); }
-
+// loads of the next pass are both free of bank conflicts (hr_swz).  The coefficient buffer
+// the producer fills (first pass input) is in natural order; the last pass writes HBM.
 template <class C, int LGNC, int PASS>
 __device__ __forceinline__ void hr_pass(const C* __restrict__ src, C* __restrict__ dst, int R,
                                         const C* __restrict__ tw2, const C* __restrict__ pre, C* const* gout,
@@ -1206,10 +1043,19 @@ int launch_ws(const SampleParams& P, int n_segments, int nt, size_t smem, cudaSt
     return cudaGetLastError() == cudaSuccess ? SMERF_OK : SMERF_ECUDA;
 }
 
-template <class Real, class TabT, int M, int UPT>
+template <class Real, class TabT, int M, int UPT, int PARK>
+auto pick_inplace(int lgNc)
+{
+    return lgNc == 14 ? segment_kernel<Real, TabT, M, UPT, 14, PARK>
+         : lgNc == 13 ? segment_kernel<Real, TabT, M, UPT, 13, PARK>
+         : lgNc == 12 ? segment_kernel<Real, TabT, M, UPT, 12, PARK>
+                      : segment_kernel<Real, TabT, M, UPT, 0, PARK>;
+}
+
+template <class Real, class TabT, int M, int UPT, int PARK>
 int launch_inplace(const SampleParams& P, int n_segments, int nt, size_t smem, cudaStream_t st)
 {
-    auto kern = segment_kernel<Real, TabT, M, UPT, 1, true>;
+    auto kern = pick_inplace<Real, TabT, M, UPT, PARK>(P.lgNc);
     if (set_smem_attr(kern, smem) != cudaSuccess) return SMERF_ECUDA;
     dim3 grid(P.n_samples, n_segments);
     kern<<<grid, nt, smem, st>>>(P);
@@ -1221,7 +1067,7 @@ int launch_inplace(const SampleParams& P, int n_segments, int nt, size_t smem, c
 // upt (<= 512), FFT threads np/2, rmax realisations per CTA (as many as registers and shared
 // memory allow).  Otherwise the in-place kernel (one FFT buffer, anchors read from the
 // scratch, one realisation per CTA, up to 1024 threads).
-struct SegConfig { int ws, upt, nt, np, rmax; size_t smem; };
+struct SegConfig { int ws, upt, nt, np, rmax, park; size_t smem; };
 
 template <class Real> constexpr int ws_rmax_cap(int upt)
 {
@@ -1325,7 +1171,10 @@ inline SegConfig seg_config(const smerf_plan* pl)
     cfg.upt = upt;
     cfg.nt = nt;
     cfg.rmax = 1;
-    cfg.smem = (size_t)Nc * 2 * sizeof(Real);
+    // park all but two units' states during the FFT if shared memory allows, else half, else none
+    const size_t ring = (size_t)Nc * 2 * sizeof(Real), per_unit = (size_t)nt * 4 * sizeof(Real);
+    cfg.park = ring + (upt - 2) * per_unit <= kMaxSmem ? upt - 2 : ring + (upt / 2) * per_unit <= kMaxSmem ? upt / 2 : 0;
+    cfg.smem = ring + cfg.park * per_unit;
     return cfg;
 }
 
@@ -1354,9 +1203,12 @@ int dispatch_segments(const SampleParams& P, int n_segments, const SegConfig& cf
         }
         }
     }
-    switch (cfg.upt) {
-        case 4: return launch_inplace<Real, TabT, M, 4>(P, n_segments, cfg.nt, cfg.smem, st);
-        case 8: return launch_inplace<Real, TabT, M, 8>(P, n_segments, cfg.nt, cfg.smem, st);
+    switch (cfg.upt * 16 + cfg.park) {
+        case 4 * 16 + 2: return launch_inplace<Real, TabT, M, 4, 2>(P, n_segments, cfg.nt, cfg.smem, st);
+        case 4 * 16 + 0: return launch_inplace<Real, TabT, M, 4, 0>(P, n_segments, cfg.nt, cfg.smem, st);
+        case 8 * 16 + 6: return launch_inplace<Real, TabT, M, 8, 6>(P, n_segments, cfg.nt, cfg.smem, st);
+        case 8 * 16 + 4: return launch_inplace<Real, TabT, M, 8, 4>(P, n_segments, cfg.nt, cfg.smem, st);
+        case 8 * 16 + 0: return launch_inplace<Real, TabT, M, 8, 0>(P, n_segments, cfg.nt, cfg.smem, st);
         default: return SMERF_EUNSUPPORTED;
     }
 }
@@ -1374,6 +1226,7 @@ int fill_params(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scr
     P.tw = pl->tw;
     P.pre = pl->pre;
     P.tw2 = pl->tw2;
+    P.tw3 = pl->tw3;
     P.anc = scratch;
     P.out = out;
     P.seed = seed;

@@ -358,7 +358,7 @@ __global__ void segment_tables_kernel(Spec sp, int c, int len, int H, const doub
 //   Ns > 1 (pass plan: radix 4 while Nc/Ns >= 4, then 2) the block
 //   tw[off + (i-1) Ns + kk] = e^{2 pi i i kk / (Ns RP)}, i = 1..RP-1, kk < Ns.
 template <class R>
-static int upload_fft_tables(int n_phi, void** tw, void** pre, void** tw2)
+static int upload_fft_tables(int n_phi, void** tw, void** pre, void** tw2, void** tw3)
 {
     const int Nc = n_phi / 2;
     std::vector<R> p(2 * (size_t)Nc), t;
@@ -379,22 +379,25 @@ static int upload_fft_tables(int n_phi, void** tw, void** pre, void** tw2)
         Ns *= RP;
     }
     if (t.empty()) t.assign(2, (R)0);
-    // high-radix plan
-    std::vector<R> t2;
+    // high-radix plans (passes of at most 16 and at most 8 points)
     int L = 0;
     while ((1 << L) < Nc) ++L;
-    for (int ps = 1; ps < smerf::hr_passes(L); ++ps) {
-        const int RP = 1 << smerf::hr_bits(L, ps), Ns2 = 1 << smerf::hr_lgns(L, ps);
-        for (int i = 1; i < RP; ++i)
-            for (int kk = 0; kk < Ns2; ++kk) {
-                const double a = 2.0 * SMERF_PI * (double)i * kk / ((double)Ns2 * RP);
-                t2.push_back((R)cos(a));
-                t2.push_back((R)sin(a));
-            }
+    for (int MB = 4; MB >= 3; --MB) {
+        std::vector<R> t2;
+        for (int ps = 1; ps < smerf::hr_passes(L, MB); ++ps) {
+            const int RP = 1 << smerf::hr_bits(L, ps, MB), Ns2 = 1 << smerf::hr_lgns(L, ps, MB);
+            for (int i = 1; i < RP; ++i)
+                for (int kk = 0; kk < Ns2; ++kk) {
+                    const double a = 2.0 * SMERF_PI * (double)i * kk / ((double)Ns2 * RP);
+                    t2.push_back((R)cos(a));
+                    t2.push_back((R)sin(a));
+                }
+        }
+        if (t2.empty()) t2.assign(2, (R)0);
+        void** dst = MB == 4 ? tw2 : tw3;
+        if (cudaMalloc(dst, t2.size() * sizeof(R)) != cudaSuccess) return SMERF_ENOMEM;
+        if (cudaMemcpy(*dst, t2.data(), t2.size() * sizeof(R), cudaMemcpyHostToDevice) != cudaSuccess) return SMERF_ECUDA;
     }
-    if (t2.empty()) t2.assign(2, (R)0);
-    if (cudaMalloc(tw2, t2.size() * sizeof(R)) != cudaSuccess) return SMERF_ENOMEM;
-    if (cudaMemcpy(*tw2, t2.data(), t2.size() * sizeof(R), cudaMemcpyHostToDevice) != cudaSuccess) return SMERF_ECUDA;
     if (cudaMalloc(tw, t.size() * sizeof(R)) != cudaSuccess) return SMERF_ENOMEM;
     if (cudaMalloc(pre, p.size() * sizeof(R)) != cudaSuccess) return SMERF_ENOMEM;
     if (cudaMemcpy(*tw, t.data(), t.size() * sizeof(R), cudaMemcpyHostToDevice) != cudaSuccess) return SMERF_ECUDA;
@@ -466,8 +469,8 @@ int setup_impl(smerf_plan* pl)
         CK(cudaMemset(pl->coarse[c], 0, cb > 0 ? cb : 16));
         pl->table_bytes += sb + cb;
     }
-    rc = pl->recur64 ? upload_fft_tables<double>(pl->n_phi, &pl->tw, &pl->pre, &pl->tw2)
-                     : upload_fft_tables<float>(pl->n_phi, &pl->tw, &pl->pre, &pl->tw2);
+    rc = pl->recur64 ? upload_fft_tables<double>(pl->n_phi, &pl->tw, &pl->pre, &pl->tw2, &pl->tw3)
+                     : upload_fft_tables<float>(pl->n_phi, &pl->tw, &pl->pre, &pl->tw2, &pl->tw3);
     if (rc != SMERF_OK) goto done;
     start_kernel<M><<<gm, threads>>>(sp, pl->beq, t64);
     CK(cudaGetLastError());
