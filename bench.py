@@ -311,11 +311,12 @@ def run_gb300(args, rank, world, local_rank):
     # kernel sources still hash to what was profiled (null otherwise)
     traffic = None
     prof = os.path.join(ROOT, "profiles", "segment_kernel_traffic.json")
-    if os.path.exists(prof) and wl == "1024x2048-p2" and (args.tables or "fp64") == "fp64" and not args.recur:
+    if os.path.exists(prof) and not args.recur and args.tables is None and batch is None:
         try:
             rec = json.load(open(prof))
-            if rec.get("csrc_sha256_16") == csrc_digest() and rec.get("launch") == launch_cfg:
-                traffic = rec.get("traffic_bytes_per_launch")
+            w = rec.get("workloads", {}).get(wl)
+            if w and rec.get("csrc_sha256_16") == csrc_digest() and w.get("launch") == launch_cfg:
+                traffic = w.get("traffic_bytes_per_launch")
         except Exception:
             traffic = None
 
