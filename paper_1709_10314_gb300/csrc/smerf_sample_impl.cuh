@@ -637,8 +637,8 @@ __global__ void __launch_bounds__(1024, 1) segment_kernel(SampleParams P)
         for (int i = 0; i < UPT; ++i) {
             const int u = tid + i * nt;
             if (u >= n_units) continue;
-#pragma unroll
-            for (int g = 0; g < G; ++g) buf0[G * u + g] = cmk<C>(x[i][g * 2 * M], x[i][g * 2 * M + M]);
+            if constexpr (G == 2) Vec4<Real>::st(reinterpret_cast<Real*>(buf0 + 2 * u), x[i]);
+            else buf0[u] = cmk<C>(x[i][0], x[i][M]);
         }
         // park the upper units' state
 #pragma unroll
@@ -966,9 +966,12 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
 #pragma unroll
                 for (int r = 0; r < RMAX; ++r) {
                     if (r >= R) continue;
-#pragma unroll
-                    for (int g = 0; g < G; ++g)
-                        B[(size_t)r * Nc + G * u + g] = cmk<C>(x[i][r][g * 2 * M], x[i][r][g * 2 * M + M]);
+                    if constexpr (G == 2) {
+                        // p = 1: the unit's two slots (Re, Im, Re, Im) in one vector store
+                        Vec4<Real>::st(reinterpret_cast<Real*>(B + (size_t)r * Nc + 2 * u), x[i][r]);
+                    } else {
+                        B[(size_t)r * Nc + u] = cmk<C>(x[i][r][0], x[i][r][M]);
+                    }
                 }
             }
             __threadfence_block();
