@@ -196,28 +196,29 @@ int smerf_plan_info(const smerf_plan* plan, smerf_plan_info_t* info);
 
 /*
  * smerf_plan_autotune -- time every built launch configuration of the segment kernel that
- * fits this plan (units per producer thread, realisations per CTA, FFT-group threads) on
- * n_samples realisations and keep the fastest for later calls.  Launch parameters only: the
- * output of later calls is unchanged.  Synchronous; allocates a temporary output; must not
- * run while other calls use the plan.  chosen (may be NULL) receives (units per thread,
- * realisations per CTA, producer threads, FFT threads), all 0 when the plan's shape has no
- * tunable kernel.
+ * fits this plan on n_samples realisations and keep the fastest for later calls.  A launch
+ * configuration is SMERF_LAUNCH_INTS integers: (units per producer thread, realisations per
+ * CTA, producer threads, FFT threads, CTAs per SM the kernel is built for).  Launch
+ * parameters only: the output of later calls is unchanged.  Synchronous; allocates a
+ * temporary output; must not run while other calls use the plan.  chosen (may be NULL)
+ * receives the chosen configuration, all 0 when the plan's shape has no tunable kernel.
  */
+#define SMERF_LAUNCH_INTS 5
 int smerf_plan_autotune(smerf_plan* plan, int n_samples, void* stream, int* chosen);
 
 /*
  * smerf_plan_launch_candidates -- the launch configurations smerf_plan_autotune chooses from,
- * as (units per thread, realisations per CTA, producer threads, FFT threads) quadruples in
- * cand[4 * i ...] for i < min(count, max_n).  Returns the count (0: no tunable kernel) or
- * SMERF_EINVAL.  Host only.
+ * SMERF_LAUNCH_INTS integers each, in cand[SMERF_LAUNCH_INTS * i ...] for
+ * i < min(count, max_n).  Returns the count (0: no tunable kernel) or SMERF_EINVAL.  Host
+ * only.
  */
 int smerf_plan_launch_candidates(const smerf_plan* plan, int* cand, int max_n);
 
 /*
- * smerf_plan_set_launch -- fix the segment-kernel launch configuration to one of the
- * candidates (e.g. a choice smerf_plan_autotune made in an earlier process), or with
- * config == NULL return to the built-in choice.  SMERF_EINVAL if config is not a candidate.
- * Host only; the output of later calls is unchanged.
+ * smerf_plan_set_launch -- fix the segment-kernel launch configuration (SMERF_LAUNCH_INTS
+ * integers) to one of the candidates (e.g. a choice smerf_plan_autotune made in an earlier
+ * process), or with config == NULL return to the built-in choice.  SMERF_EINVAL if config is
+ * not a candidate.  Host only; the output of later calls is unchanged.
  */
 int smerf_plan_set_launch(smerf_plan* plan, const int* config);
 

@@ -331,10 +331,10 @@ static int tune_candidates(const smerf_plan* plan, int* cand, int max_n)
 int smerf_plan_launch_candidates(const smerf_plan* plan, int* cand, int max_n)
 {
     if (!plan || max_n < 0 || (max_n > 0 && !cand)) return SMERF_EINVAL;
-    int tmp[4 * 64];
+    int tmp[smerf::kLaunchInts * 64];
     const int n = tune_candidates(plan, tmp, 64);
     for (int i = 0; i < n && i < max_n; ++i)
-        for (int k = 0; k < 4; ++k) cand[4 * i + k] = tmp[4 * i + k];
+        for (int k = 0; k < smerf::kLaunchInts; ++k) cand[smerf::kLaunchInts * i + k] = tmp[smerf::kLaunchInts * i + k];
     return n;
 }
 
@@ -345,16 +345,17 @@ int smerf_plan_set_launch(smerf_plan* plan, const int* config)
         plan->tune.valid = 0;
         return SMERF_OK;
     }
-    int cand[4 * 64];
+    int cand[smerf::kLaunchInts * 64];
     const int n = tune_candidates(plan, cand, 64);
     for (int i = 0; i < n; ++i) {
-        if (cand[4 * i] == config[0] && cand[4 * i + 1] == config[1] && cand[4 * i + 2] == config[2] &&
-            cand[4 * i + 3] == config[3]) {
+        const int* c = cand + smerf::kLaunchInts * i;
+        if (c[0] == config[0] && c[1] == config[1] && c[2] == config[2] && c[3] == config[3] && c[4] == config[4]) {
             plan->tune.valid = 1;
             plan->tune.upt = config[0];
             plan->tune.rmax = config[1];
             plan->tune.np = config[2];
             plan->tune.nf = config[3];
+            plan->tune.minb = config[4];
             plan->tune.ms = 0.0f;
             return SMERF_OK;
         }
@@ -368,11 +369,12 @@ int smerf_plan_autotune(smerf_plan* plan, int n_samples, void* stream, int* chos
     int dev = -1;
     cudaGetDevice(&dev);
     if (dev != plan->dev) return SMERF_EINVAL;
-    int cand[4 * 64];
+    int cand[smerf::kLaunchInts * 64];
     const int nc = tune_candidates(plan, cand, 64);
     plan->tune.valid = 0;
     if (nc == 0) {
-        if (chosen) chosen[0] = chosen[1] = chosen[2] = chosen[3] = 0;
+        if (chosen)
+            for (int k = 0; k < smerf::kLaunchInts; ++k) chosen[k] = 0;
         return SMERF_OK;  // no warp-specialised configuration: the built-in choice stays
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -388,10 +390,12 @@ int smerf_plan_autotune(smerf_plan* plan, int n_samples, void* stream, int* chos
     int bi = -1;
     for (int i = 0; rc == SMERF_OK && i < nc; ++i) {
         plan->tune.valid = 1;
-        plan->tune.upt = cand[4 * i];
-        plan->tune.rmax = cand[4 * i + 1];
-        plan->tune.np = cand[4 * i + 2];
-        plan->tune.nf = cand[4 * i + 3];
+        const int* ci = cand + smerf::kLaunchInts * i;
+        plan->tune.upt = ci[0];
+        plan->tune.rmax = ci[1];
+        plan->tune.np = ci[2];
+        plan->tune.nf = ci[3];
+        plan->tune.minb = ci[4];
         float tot = 0.0f;
         for (int it = 0; rc == SMERF_OK && it < 4; ++it) {
             rc = smerf_launch_sample(plan, 1 + it, n_samples, out, scratch, st, e0, e1);
@@ -408,13 +412,15 @@ int smerf_plan_autotune(smerf_plan* plan, int n_samples, void* stream, int* chos
     plan->tune.valid = 0;
     if (rc == SMERF_OK && bi >= 0) {
         plan->tune.valid = 1;
-        plan->tune.upt = cand[4 * bi];
-        plan->tune.rmax = cand[4 * bi + 1];
-        plan->tune.np = cand[4 * bi + 2];
-        plan->tune.nf = cand[4 * bi + 3];
+        const int* cb = cand + smerf::kLaunchInts * bi;
+        plan->tune.upt = cb[0];
+        plan->tune.rmax = cb[1];
+        plan->tune.np = cb[2];
+        plan->tune.nf = cb[3];
+        plan->tune.minb = cb[4];
         plan->tune.ms = best / 3.0f;
         if (chosen)
-            for (int k = 0; k < 4; ++k) chosen[k] = cand[4 * bi + k];
+            for (int k = 0; k < smerf::kLaunchInts; ++k) chosen[k] = cb[k];
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

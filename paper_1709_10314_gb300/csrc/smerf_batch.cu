@@ -118,7 +118,7 @@ int smerf_batch_create(const smerf_plan* const* plans, const int* n_samples, int
     // group by kernel shape; build the work lists
     // requests share a group when their kernels and launch configurations coincide: same
     // precision pair, p, n_phi, anchoring and tuned launch parameters (if any)
-    std::map<std::tuple<int, int, int, int, int, int, int, int>, int> gidx;
+    std::map<std::tuple<int, int, int, int, int, int, int, int, int>, int> gidx;
     std::vector<std::vector<int4>> anc, seg;
     for (int i = 0; rc == SMERF_OK && i < n_req; ++i) {
         const smerf_plan* pl = plans[i];
@@ -133,7 +133,8 @@ int smerf_batch_create(const smerf_plan* const* plans, const int* n_samples, int
         }
         const bool tuned = pl->tune.valid != 0;
         const auto key = std::make_tuple(kind, pl->p, pl->n_phi, pl->H > 0 ? 1 : 0, tuned ? pl->tune.upt : 0,
-                                         tuned ? pl->tune.rmax : 0, tuned ? pl->tune.np : 0, tuned ? pl->tune.nf : 0);
+                                         tuned ? pl->tune.rmax : 0, tuned ? pl->tune.np : 0, tuned ? pl->tune.nf : 0,
+                                         tuned ? pl->tune.minb : 0);
         auto it = gidx.find(key);
         int g;
         if (it == gidx.end()) {

@@ -60,10 +60,12 @@ struct smerf_plan {
     double setup_ms;
     int dev;
     // launch parameters chosen by smerf_plan_autotune (valid = 0: built-in heuristic)
-    struct { int valid, upt, rmax, np, nf; float ms; } tune;
+    struct { int valid, upt, rmax, np, nf, minb; float ms; } tune;
 };
 
 namespace smerf {
+
+constexpr int kLaunchInts = SMERF_LAUNCH_INTS;  // integers per launch configuration
 
 __host__ __device__ constexpr int tri(int M) { return M * (M + 1) / 2; }
 __host__ __device__ constexpr int step_elems(int M) { return 2 * M * M + tri(M); }
@@ -212,7 +214,7 @@ SMERF_DECLARE_GROUP(dd)
 SMERF_DECLARE_GROUP(df)
 
 // launch-configuration candidates of a plan for the autotuner (per precision pair XX):
-// writes up to max_n (upt, rmax, np, nf) quadruples, returns how many
+// writes up to max_n (upt, rmax, np, nf, minb) tuples of kLaunchInts, returns how many
 #define SMERF_DECLARE_TUNE(XX) int smerf_tune_candidates_##XX(const smerf_plan* pl, int* cand, int max_n);
 SMERF_DECLARE_TUNE(ff)
 SMERF_DECLARE_TUNE(fd)

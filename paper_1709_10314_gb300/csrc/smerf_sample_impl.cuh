@@ -27,6 +27,11 @@
 #ifndef SMERF_WS_MAXT
 #define SMERF_WS_MAXT 768
 #endif
+// Resident 128-thread blocks per SM the anchor kernels are compiled for (7 x 152 SMs covers
+// the 1024 blocks of a 64-realisation, 1024-unit request in one wave).
+#ifndef SMERF_ANCHOR_MINB
+#define SMERF_ANCHOR_MINB 7
+#endif
 // Realisations per interleaved group of Philox generators in the producer loop.
 #ifndef SMERF_RB
 #define SMERF_RB 1
@@ -35,6 +40,9 @@
 namespace smerf {
 
 constexpr int kWsMaxThreads = SMERF_WS_MAXT;
+// Thread limit of the warp-specialised kernels built for MINB resident CTAs per SM: one CTA
+// gets 65536 / SMERF_WS_MAXT registers per thread, two get 64 (512 threads each).
+__host__ __device__ constexpr int ws_max_threads(int minb) { return minb == 1 ? kWsMaxThreads : 512; }
 
 template <int M> constexpr int kG = unit_slots(M);
 
@@ -144,11 +152,14 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
     // anchors: x_j = Phi x_{j-1} + chol(S) xi.  The table values and normals of anchor j + 1
     // are fetched before the matrix-vector products of anchor j (the loads come from L2 and
     // do not depend on the state), so consecutive anchors overlap their latencies.
-    const TabT* cs = (const TabT*)P.coarse[c];
-    const int na = P.n_anchors[c];
+    // (selects, not P.x[c]: indexing a kernel parameter's array with a runtime index copies
+    // the whole parameter block to local memory)
+    const TabT* cs = (const TabT*)(c == 0 ? P.coarse[0] : P.coarse[1]);
+    const int na = c == 0 ? P.n_anchors[0] : P.n_anchors[1];
     TabT tv[G][2][Ec];
-    auto fetch = [&](int j, TabT (&t)[G][2][Ec], Real (&xi)[4]) {
-        const int ring = c == 0 ? P.k0 - j * P.H : P.k0 + j * P.H;
+    const int k0 = P.k0, H = P.H, Ncm = P.Nc;  // copies: the lambda must not take P's address
+    auto fetch = [=](int j, TabT (&t)[G][2][Ec], Real (&xi)[4]) {
+        const int ring = c == 0 ? k0 - j * H : k0 + j * H;
         unit_normals<Real>(key, (uint32_t)u, (uint32_t)ring, xi);
         const TabT* tb = cs + (size_t)j * Ec * mp;
 #pragma unroll
@@ -156,7 +167,7 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
 #pragma unroll
             for (int part = 0; part < 2; ++part) {
                 const int s = G * u + g;
-                const int mode = (part == 1 && s == 0) ? P.Nc : s;
+                const int mode = (part == 1 && s == 0) ? Ncm : s;
 #pragma unroll
                 for (int e = 0; e < Ec; ++e) t[g][part][e] = __ldg(tb + (size_t)e * mp + mode);
             }
@@ -210,14 +221,14 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
 
 // one thread per (chain c, realisation r, unit u)
 template <class Real, class TabT, int M>
-__global__ void __launch_bounds__(128) anchor_kernel(SampleParams P)
+__global__ void __launch_bounds__(128, SMERF_ANCHOR_MINB) anchor_kernel(SampleParams P)
 {
     anchor_body<Real, TabT, M>(P, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // batched: item = (request, block of 128 units, realisation, chain)
 template <class Real, class TabT, int M>
-__global__ void __launch_bounds__(128) anchor_batched_kernel(const SampleParams* __restrict__ descs,
+__global__ void __launch_bounds__(128, SMERF_ANCHOR_MINB) anchor_batched_kernel(const SampleParams* __restrict__ descs,
                                                              const int4* __restrict__ items)
 {
     const int4 it = items[blockIdx.x];
@@ -226,6 +237,14 @@ __global__ void __launch_bounds__(128) anchor_batched_kernel(const SampleParams*
 }
 
 // ------------------------------------------------------------------ FFT
+// Output rows of ring `ring` for the realisations of a CTA: gout[r] = base + r * stride
+// (complex elements; stride = one realisation, n_theta x n_phi / 2).
+template <class C> struct RingOut {
+    C* base;
+    size_t stride;
+    __device__ __forceinline__ C* operator[](int r) const { return base + (size_t)r * stride; }
+};
+
 template <class C>
 __device__ __forceinline__ void dft2(C& a, C& b) { const C t = a; a = cadd(t, b); b = csub(t, b); }
 
@@ -596,7 +615,7 @@ __global__ void __launch_bounds__(1024, 1) segment_kernel(SampleParams P)
     }
     __syncthreads();
 
-    const TabT* steps = (const TabT*)P.steps[c];
+    const TabT* steps = (const TabT*)(c == 0 ? P.steps[0] : P.steps[1]);
     for (int pos = sg.p0; pos < sg.p1; ++pos) {
         const int ring = c == 0 ? P.k0 - pos : P.k0 + pos;
         if (pos > sg.p0) {
@@ -672,7 +691,7 @@ constexpr int kBarFft = 5;    // FFT group internal
 // general size (runtime log2 Nc)
 template <class C, int RP, bool FIRST, bool LAST>
 __device__ __forceinline__ void grp_pass_rt(const C* __restrict__ src, C* __restrict__ dst, int R, int lgNc, int Ns,
-                                            const C* __restrict__ twp, const C* __restrict__ pre, C* const* gout,
+                                            const C* __restrict__ twp, const C* __restrict__ pre, RingOut<C> gout,
                                             int ftid, int nf)
 {
     const int Nc = 1 << lgNc;
@@ -711,7 +730,7 @@ __device__ __forceinline__ void grp_pass_rt(const C* __restrict__ src, C* __rest
 
 template <class C>
 __device__ __forceinline__ void grp_c2r_rt(C* buf0, C* buf1, int R, int lgNc, const C* twp, const C* pre,
-                                           C* const* gout, int ftid, int nf)
+                                           RingOut<C> gout, int ftid, int nf)
 {
     const int Nc = 1 << lgNc;
     C* src = buf0;
@@ -755,7 +774,7 @@ __device__ __forceinline__ void grp_c2r_rt(C* buf0, C* buf1, int R, int lgNc, co
 // the producer fills (first pass input) is in natural order; the last pass writes HBM.
 template <class C, int LGNC, int PASS>
 __device__ __forceinline__ void hr_pass(const C* __restrict__ src, C* __restrict__ dst, int R,
-                                        const C* __restrict__ tw2, const C* __restrict__ pre, C* const* gout,
+                                        const C* __restrict__ tw2, const C* __restrict__ pre, RingOut<C> gout,
                                         int ftid, int nf)
 {
     constexpr int Nc = 1 << LGNC;
@@ -806,7 +825,7 @@ __device__ __forceinline__ void hr_pass(const C* __restrict__ src, C* __restrict
 }
 
 template <class C, int LGNC, int PASS = 0>
-__device__ __forceinline__ void hr_c2r_fixed(C* src, C* dst, int R, const C* tw2, const C* pre, C* const* gout,
+__device__ __forceinline__ void hr_c2r_fixed(C* src, C* dst, int R, const C* tw2, const C* pre, RingOut<C> gout,
                                              int ftid, int nf)
 {
     hr_pass<C, LGNC, PASS>(src, dst, R, tw2, pre, gout, ftid, nf);
@@ -819,7 +838,7 @@ __device__ __forceinline__ void hr_c2r_fixed(C* src, C* dst, int R, const C* tw2
 // high-radix fixed-size FFTs for log2 Nc in [LO, HI], the runtime-size radix-4 one otherwise
 template <class C, int LO, int HI>
 __device__ __forceinline__ void hr_c2r(int lgNc, C* b0, C* b1, int R, const C* twp, const C* tw2, const C* pre,
-                                       C* const* gout, int ftid, int nf)
+                                       RingOut<C> gout, int ftid, int nf)
 {
     if constexpr (LO <= HI) {
         if (lgNc == LO) {
@@ -909,7 +928,7 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
                 }
             }
         }
-        const TabT* steps = (const TabT*)P.steps[c];
+        const TabT* steps = (const TabT*)(c == 0 ? P.steps[0] : P.steps[1]);
         for (int k = 0; k < nrings + 2; ++k) {
             if (k >= 2) bar_sync(kBarEmpty + (k & 1), nt);
             if (k >= nrings) continue;
@@ -986,10 +1005,8 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
             const int ring = c == 0 ? P.k0 - pos : P.k0 + pos;
             C* B = bufs + (size_t)(k & 1) * RMAX * Nc;
             if (!(c == 1 && pos == 0)) {  // the start ring is written by the northern chain
-                C* gout[RMAX];
-#pragma unroll
-                for (int r = 0; r < RMAX; ++r)
-                    gout[r] = (C*)((Real*)P.out + ((size_t)min(r0 + r, P.n_samples - 1) * P.n_theta + ring) * (size_t)P.n_phi);
+                const RingOut<C> gout{(C*)((Real*)P.out + ((size_t)r0 * P.n_theta + ring) * (size_t)P.n_phi),
+                                      (size_t)P.n_theta * (size_t)(P.n_phi / 2)};
                 if constexpr (sizeof(Real) == 4)
                     hr_c2r<C, ws_lg_lo(UPT, M), ws_lg_hi(UPT, M)>(P.lgNc, B, W, R, twp, (const C*)P.tw2, pre, gout,
                                                                    ftid, NF);
@@ -1001,16 +1018,16 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
     }
 }
 
-template <class Real, class TabT, int M, int UPT, int RMAX>
-__global__ void __launch_bounds__(SMERF_WS_MAXT) segment_ws_kernel(SampleParams P)
+template <class Real, class TabT, int M, int UPT, int RMAX, int MINB>
+__global__ void __launch_bounds__(ws_max_threads(MINB), MINB) segment_ws_kernel(SampleParams P)
 {
     ws_body<Real, TabT, M, UPT, RMAX>(P, blockIdx.y, blockIdx.x);
 }
 
 // batched: item = (request, segment, realisation group); all requests of a launch share the
 // kernel shape (precision, p, n_phi, anchors or not) and hence the launch configuration
-template <class Real, class TabT, int M, int UPT, int RMAX>
-__global__ void __launch_bounds__(SMERF_WS_MAXT) segment_ws_batched_kernel(const SampleParams* __restrict__ descs,
+template <class Real, class TabT, int M, int UPT, int RMAX, int MINB>
+__global__ void __launch_bounds__(ws_max_threads(MINB), MINB) segment_ws_batched_kernel(const SampleParams* __restrict__ descs,
                                                                  const int4* __restrict__ items)
 {
     const int4 it = items[blockIdx.x];
@@ -1036,10 +1053,10 @@ inline cudaError_t set_smem_attr(K kern, size_t smem)
 constexpr int kMaxThreads = 1024;
 constexpr size_t kMaxSmem = 226 * 1024;  // leaves room for the static shared arrays
 
-template <class Real, class TabT, int M, int UPT, int RMAX>
+template <class Real, class TabT, int M, int UPT, int RMAX, int MINB = 1>
 int launch_ws(const SampleParams& P, int n_segments, int nt, size_t smem, cudaStream_t st)
 {
-    auto kern = segment_ws_kernel<Real, TabT, M, UPT, RMAX>;
+    auto kern = segment_ws_kernel<Real, TabT, M, UPT, RMAX, MINB>;
     if (set_smem_attr(kern, smem) != cudaSuccess) return SMERF_ECUDA;
     dim3 grid((P.n_samples + RMAX - 1) / RMAX, n_segments);
     kern<<<grid, nt, smem, st>>>(P);
@@ -1070,7 +1087,7 @@ int launch_inplace(const SampleParams& P, int n_segments, int nt, size_t smem, c
 // upt (<= 512), FFT threads np/2, rmax realisations per CTA (as many as registers and shared
 // memory allow).  Otherwise the in-place kernel (one FFT buffer, anchors read from the
 // scratch, one realisation per CTA, up to 1024 threads).
-struct SegConfig { int ws, upt, nt, np, rmax, park; size_t smem; };
+struct SegConfig { int ws, upt, nt, np, rmax, park, minb; size_t smem; };
 
 template <class Real> constexpr int ws_rmax_cap(int upt)
 {
@@ -1084,44 +1101,51 @@ inline size_t ws_smem(const smerf_plan* pl, int rmax)
     return (size_t)3 * rmax * Nc * 2 * sizeof(Real) + (pl->H > 0 ? (size_t)rmax * Nc * 2 * pl->p * sizeof(Real) : 0);
 }
 
-// (units per thread, realisations per CTA) pairs with a built warp-specialised kernel
-template <class Real> inline bool ws_built(int upt, int rmax)
+// (units per thread, realisations per CTA, CTAs per SM) with a built warp-specialised kernel
+template <class Real> inline bool ws_built(int upt, int rmax, int minb = 1)
 {
+    if (minb == 2) return sizeof(Real) == 4 && ((upt == 4 && (rmax == 1 || rmax == 2)) || (upt == 8 && rmax == 1));
+    if (minb != 1) return false;
     if (sizeof(Real) == 8) return rmax == 1 && (upt == 1 || upt == 2 || upt == 4 || upt == 8);
     return (upt == 1 && rmax == 4) || (upt == 2 && (rmax == 4 || rmax == 2)) || (upt == 4 && (rmax == 2 || rmax == 1)) ||
            (upt == 8 && rmax == 1);
 }
 
-// Every warp-specialised configuration that fits the plan: producer threads np = units / upt
-// (<= 512, multiple of 32), FFT threads nf in {np/2, np, np/4} (np + nf <= kWsMaxThreads).
+// Every warp-specialised configuration that fits the plan, as kLaunchInts integers (units per
+// producer thread, realisations per CTA, producer threads np = units / upt (<= 512, multiple
+// of 32), FFT threads nf in {np/2, np, np/4}, CTAs per SM the kernel is built for; np + nf
+// within that build's thread limit).
 template <class Real>
 inline int tune_candidates(const smerf_plan* pl, int* cand, int max_n)
 {
     const int n_units = pl->n_slots / unit_slots(pl->p);
     int n = 0;
     const int rm[3] = {4, 2, 1};
-    for (int upt = 1; upt <= 8; upt *= 2) {
-        int np = (n_units + upt - 1) / upt;
-        np = ((np + 31) / 32) * 32;
-        if (np > 512 || (upt > 1 && (n_units + upt / 2 - 1) / (upt / 2) <= 32)) continue;
-        for (int k = 0; k < 3; ++k) {
-            const int rmax = rm[k];
-            if (!ws_built<Real>(upt, rmax) || ws_smem<Real>(pl, rmax) > 226 * 1024) continue;
-            const int div[3] = {2, 1, 4};
-            for (int d = 0; d < 3; ++d) {
-                int nf = ((np / div[d] + 31) / 32) * 32;
-                if (nf < 32) nf = 32;
-                if (np + nf > kWsMaxThreads) continue;
-                if (n < max_n) {
-                    cand[4 * n + 0] = upt;
-                    cand[4 * n + 1] = rmax;
-                    cand[4 * n + 2] = np;
-                    cand[4 * n + 3] = nf;
+    for (int minb = 1; minb <= 2; ++minb)
+        for (int upt = 1; upt <= 8; upt *= 2) {
+            int np = (n_units + upt - 1) / upt;
+            np = ((np + 31) / 32) * 32;
+            if (np > 512 || (upt > 1 && (n_units + upt / 2 - 1) / (upt / 2) <= 32)) continue;
+            for (int k = 0; k < 3; ++k) {
+                const int rmax = rm[k];
+                if (!ws_built<Real>(upt, rmax, minb) || ws_smem<Real>(pl, rmax) > 226 * 1024) continue;
+                const int div[3] = {2, 1, 4};
+                for (int d = 0; d < 3; ++d) {
+                    int nf = ((np / div[d] + 31) / 32) * 32;
+                    if (nf < 32) nf = 32;
+                    if (np + nf > ws_max_threads(minb)) continue;
+                    if (n < max_n) {
+                        int* c = cand + kLaunchInts * n;
+                        c[0] = upt;
+                        c[1] = rmax;
+                        c[2] = np;
+                        c[3] = nf;
+                        c[4] = minb;
+                    }
+                    ++n;
                 }
-                ++n;
             }
         }
-    }
     return n < max_n ? n : max_n;
 }
 
@@ -1132,12 +1156,14 @@ inline SegConfig seg_config(const smerf_plan* pl)
     const int M = pl->p;
     const int n_units = pl->n_slots / unit_slots(M);
     const int Nc = pl->n_phi / 2;
-    if (pl->tune.valid && ws_built<Real>(pl->tune.upt, pl->tune.rmax) &&
+    if (pl->tune.valid && ws_built<Real>(pl->tune.upt, pl->tune.rmax, pl->tune.minb) &&
         ws_smem<Real>(pl, pl->tune.rmax) <= 226 * 1024 &&
-        (n_units + pl->tune.upt - 1) / pl->tune.upt <= pl->tune.np && pl->tune.np + pl->tune.nf <= kWsMaxThreads) {
+        (n_units + pl->tune.upt - 1) / pl->tune.upt <= pl->tune.np &&
+        pl->tune.np + pl->tune.nf <= ws_max_threads(pl->tune.minb)) {
         cfg.ws = 1;
         cfg.upt = pl->tune.upt;
         cfg.rmax = pl->tune.rmax;
+        cfg.minb = pl->tune.minb;
         cfg.np = pl->tune.np;
         cfg.nt = pl->tune.np + pl->tune.nf;
         cfg.smem = ws_smem<Real>(pl, cfg.rmax);
@@ -1159,6 +1185,7 @@ inline SegConfig seg_config(const smerf_plan* pl)
                 cfg.np = np;
                 cfg.nt = np + nf;
                 cfg.rmax = rmax;
+                cfg.minb = 1;
                 cfg.smem = smem;
                 return cfg;
             }
@@ -1194,6 +1221,14 @@ int dispatch_segments(const SampleParams& P, int n_segments, const SegConfig& cf
                 default: return SMERF_EUNSUPPORTED;
             }
         } else {
+        if (cfg.minb == 2) {
+            switch (cfg.upt * 8 + cfg.rmax) {
+                case 4 * 8 + 2: return launch_ws<Real, TabT, M, 4, 2, 2>(P, n_segments, cfg.nt, cfg.smem, st);
+                case 4 * 8 + 1: return launch_ws<Real, TabT, M, 4, 1, 2>(P, n_segments, cfg.nt, cfg.smem, st);
+                case 8 * 8 + 1: return launch_ws<Real, TabT, M, 8, 1, 2>(P, n_segments, cfg.nt, cfg.smem, st);
+                default: return SMERF_EUNSUPPORTED;
+            }
+        }
         const int key = cfg.upt * 8 + cfg.rmax;
         switch (key) {
             case 1 * 8 + 4: return launch_ws<Real, TabT, M, 1, 4>(P, n_segments, cfg.nt, cfg.smem, st);
@@ -1277,10 +1312,10 @@ int launch_sample_m(const smerf_plan* pl, uint64_t seed, int n, void* out, void*
 }
 
 // ---- batched groups: requests of one shape share one anchor and one segment launch
-template <class Real, class TabT, int M, int UPT, int RMAX>
+template <class Real, class TabT, int M, int UPT, int RMAX, int MINB = 1>
 int launch_ws_batched(const SampleParams* d, const int4* items, int n_items, int nt, size_t smem, cudaStream_t st)
 {
-    auto kern = segment_ws_batched_kernel<Real, TabT, M, UPT, RMAX>;
+    auto kern = segment_ws_batched_kernel<Real, TabT, M, UPT, RMAX, MINB>;
     if (set_smem_attr(kern, smem) != cudaSuccess) return SMERF_ECUDA;
     kern<<<n_items, nt, smem, st>>>(d, items);
     return cudaGetLastError() == cudaSuccess ? SMERF_OK : SMERF_ECUDA;
@@ -1298,6 +1333,14 @@ int group_segments(const SegConfig& cfg, const SampleParams* d, const int4* item
             default: return SMERF_EUNSUPPORTED;
         }
     } else {
+        if (cfg.minb == 2) {
+            switch (cfg.upt * 8 + cfg.rmax) {
+                case 4 * 8 + 2: return launch_ws_batched<Real, TabT, M, 4, 2, 2>(d, items, n_items, cfg.nt, cfg.smem, st);
+                case 4 * 8 + 1: return launch_ws_batched<Real, TabT, M, 4, 1, 2>(d, items, n_items, cfg.nt, cfg.smem, st);
+                case 8 * 8 + 1: return launch_ws_batched<Real, TabT, M, 8, 1, 2>(d, items, n_items, cfg.nt, cfg.smem, st);
+                default: return SMERF_EUNSUPPORTED;
+            }
+        }
         switch (cfg.upt * 8 + cfg.rmax) {
             case 1 * 8 + 4: return launch_ws_batched<Real, TabT, M, 1, 4>(d, items, n_items, cfg.nt, cfg.smem, st);
             case 2 * 8 + 4: return launch_ws_batched<Real, TabT, M, 2, 4>(d, items, n_items, cfg.nt, cfg.smem, st);

@@ -34,6 +34,7 @@ class _Info(ctypes.Structure):
 
 
 _LIB = None
+LAUNCH_INTS = 5  # SMERF_LAUNCH_INTS
 
 
 def library_path():
@@ -152,25 +153,29 @@ class Plan:
                 "scratch_bytes_per_sample": inf.scratch_bytes_per_sample, "setup_ms": inf.setup_ms}
 
     def autotune(self, n_samples, stream=None):
-        """smerf_plan_autotune: returns (units/thread, realisations/CTA, producer, FFT threads)."""
-        ch = (ctypes.c_int * 4)()
+        """smerf_plan_autotune: returns (units/thread, realisations/CTA, producer threads, FFT
+        threads, CTAs per SM)."""
+        ch = (ctypes.c_int * LAUNCH_INTS)()
         _check("smerf_plan_autotune", _lib().smerf_plan_autotune(self._h, int(n_samples), _stream_ptr(stream), ch))
         return tuple(ch)
 
     def launch_candidates(self):
-        """smerf_plan_launch_candidates: list of (units/thread, realisations/CTA, producer, FFT threads)."""
-        buf = (ctypes.c_int * (4 * 64))()
+        """smerf_plan_launch_candidates: list of (units/thread, realisations/CTA, producer
+        threads, FFT threads, CTAs per SM)."""
+        buf = (ctypes.c_int * (LAUNCH_INTS * 64))()
         n = _lib().smerf_plan_launch_candidates(self._h, buf, 64)
         if n < 0:
             _check("smerf_plan_launch_candidates", n)
-        return [tuple(buf[4 * i:4 * i + 4]) for i in range(n)]
+        return [tuple(buf[LAUNCH_INTS * i:LAUNCH_INTS * i + LAUNCH_INTS]) for i in range(n)]
 
     def set_launch(self, config):
         """smerf_plan_set_launch: fix a launch configuration (None: built-in choice)."""
         if config is None:
             ptr = None
         else:
-            ptr = (ctypes.c_int * 4)(*[int(v) for v in config])
+            if len(config) != LAUNCH_INTS:
+                raise ValueError("a launch configuration has %d integers" % LAUNCH_INTS)
+            ptr = (ctypes.c_int * LAUNCH_INTS)(*[int(v) for v in config])
         _check("smerf_plan_set_launch", _lib().smerf_plan_set_launch(self._h, ptr))
 
     def tables(self, which, chain=0, pos=0):

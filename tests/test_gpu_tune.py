@@ -1,5 +1,6 @@
 """Launch-configuration autotuning: every candidate configuration of the segment kernel
-(units per producer thread, realisations per CTA, producer and FFT threads) produces the same
+(units per producer thread, realisations per CTA, producer and FFT threads, CTAs per SM the
+kernel is built for) produces the same
 field as the built-in choice, the autotuner picks one of the candidates, a fixed choice can be
 set and cleared, and a batch mixing a tuned and an untuned plan of one shape is still exact."""
 import pytest
@@ -24,8 +25,8 @@ def test_every_candidate_gives_the_same_field(flags_name):
         ref = plan.sample(7, 5)   # 5 realisations: a ragged last group for 2 and 4 per CTA
         torch.cuda.synchronize()
         for cfg in cands:
-            upt, rmax, n_prod, n_fft = cfg
-            assert n_prod % 32 == 0 and n_fft % 32 == 0 and n_prod + n_fft <= 768
+            upt, rmax, n_prod, n_fft, per_sm = cfg
+            assert n_prod % 32 == 0 and n_fft % 32 == 0 and n_prod + n_fft <= (768 if per_sm == 1 else 512)
             plan.set_launch(cfg)
             got = plan.sample(7, 5)
             torch.cuda.synchronize()
@@ -48,9 +49,11 @@ def test_set_launch_rejects_non_candidates():
     from paper_1709_10314_gb300 import SmerfError
     plan = _plan()
     with pytest.raises(SmerfError):
-        plan.set_launch((3, 1, 96, 64))
+        plan.set_launch((3, 1, 96, 64, 1))
     with pytest.raises(SmerfError):
-        plan.set_launch((1, 4, 32, 800))
+        plan.set_launch((1, 4, 32, 800, 1))
+    with pytest.raises(SmerfError):
+        plan.set_launch((2, 4, 512, 128, 2))   # not built for two CTAs per SM
 
 
 def test_batch_with_tuned_and_untuned_plans_of_one_shape():
