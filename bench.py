@@ -282,15 +282,14 @@ def run_gb300(args, rank, world, local_rank):
     e1 = [ev() for _ in range(args.steps)]
     s0 = [ev() for _ in range(args.steps)]
     s1 = [ev() for _ in range(args.steps)]
-    for w in range(args.warmup):
-        step(args.steps + w)
-        flush.fill_(float(w))
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    # the clock sampler starts first, so that the warm-up steps (not an idle pause) directly
+    # precede the timed ones
     clk = Clocks(local_rank)
     clk.start()
     time.sleep(0.3)
+    for w in range(args.warmup):
+        step(args.steps + w)
+        flush.fill_(float(w))
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()

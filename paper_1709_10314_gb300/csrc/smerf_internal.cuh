@@ -101,7 +101,10 @@ struct SampleParams {
 // first (L = 10, MB = 4: 16, 8, 8).  Pass i runs with stride Ns = 2^hr_lgns(L, i); its
 // twiddles e^{2 pi i a kk / (Ns RP)}, a in [1, RP), kk < Ns, sit at
 // tw[hr_off(L, i) + (a - 1) Ns + kk] (pass 0 has none).  The warp-specialised kernel uses
-// MB = 4 (table tw2), the in-place kernel MB = 3 (table tw3).
+// MB = 4 (table tw2), the in-place kernel MB = SMERF_INPLACE_MB (table tw3).
+#ifndef SMERF_INPLACE_MB
+#define SMERF_INPLACE_MB 3
+#endif
 __host__ __device__ constexpr int hr_passes(int L, int MB = 4) { return (L + MB - 1) / MB; }
 __host__ __device__ constexpr int hr_bits(int L, int i, int MB = 4)
 {

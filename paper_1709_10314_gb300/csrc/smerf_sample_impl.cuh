@@ -27,7 +27,7 @@
 #ifndef SMERF_WS_MAXT
 #define SMERF_WS_MAXT 768
 #endif
-// Resident 128-thread blocks per SM the anchor kernels are compiled for (7 x 152 SMs covers
+// Resident 128-thread blocks per SM the FP32 anchor kernels are compiled for (7 x 152 SMs covers
 // the 1024 blocks of a 64-realisation, 1024-unit request in one wave).
 #ifndef SMERF_ANCHOR_MINB
 #define SMERF_ANCHOR_MINB 7
@@ -156,25 +156,31 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
     // the whole parameter block to local memory)
     const TabT* cs = (const TabT*)(c == 0 ? P.coarse[0] : P.coarse[1]);
     const int na = c == 0 ? P.n_anchors[0] : P.n_anchors[1];
-    TabT tv[G][2][Ec];
+    Real tv[G][2][Ec];
     const int k0 = P.k0, H = P.H, Ncm = P.Nc;  // copies: the lambda must not take P's address
-    auto fetch = [=](int j, TabT (&t)[G][2][Ec], Real (&xi)[4]) {
+    // table values of anchor j, converted; both chains of a slot share its mode's values except
+    // slot 0, whose second chain is the Nyquist mode
+    auto fetch = [=](int j, Real (&t)[G][2][Ec], Real (&xi)[4]) {
         const int ring = c == 0 ? k0 - j * H : k0 + j * H;
         unit_normals<Real>(key, (uint32_t)u, (uint32_t)ring, xi);
         const TabT* tb = cs + (size_t)j * Ec * mp;
 #pragma unroll
-        for (int g = 0; g < G; ++g)
+        for (int g = 0; g < G; ++g) {
+            const int s = G * u + g;
 #pragma unroll
-            for (int part = 0; part < 2; ++part) {
-                const int s = G * u + g;
-                const int mode = (part == 1 && s == 0) ? Ncm : s;
+            for (int e = 0; e < Ec; ++e) t[g][0][e] = tabcvt<Real, TabT>(__ldg(tb + (size_t)e * mp + s));
+            if (s == 0) {
 #pragma unroll
-                for (int e = 0; e < Ec; ++e) t[g][part][e] = __ldg(tb + (size_t)e * mp + mode);
+                for (int e = 0; e < Ec; ++e) t[g][1][e] = tabcvt<Real, TabT>(__ldg(tb + (size_t)e * mp + Ncm));
+            } else {
+#pragma unroll
+                for (int e = 0; e < Ec; ++e) t[g][1][e] = t[g][0][e];
             }
+        }
     };
     if (na >= 1) fetch(1, tv, nr);
     for (int j = 1; j <= na; ++j) {
-        TabT tn[G][2][Ec];
+        Real tn[G][2][Ec];
         Real nn[4];
         if (j < na) fetch(j + 1, tn, nn);
 #pragma unroll
@@ -188,10 +194,10 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
                 for (int p = 0; p < M; ++p) {
                     Real acc = 0;
 #pragma unroll
-                    for (int q = 0; q < M; ++q) acc += tabcvt<Real, TabT>(tv[g][part][p * M + q]) * x[g][part][q];
+                    for (int q = 0; q < M; ++q) acc += tv[g][part][p * M + q] * x[g][part][q];
                     int e = M * M + p * (p + 1) / 2;
 #pragma unroll
-                    for (int q = 0; q <= p; ++q, ++e) acc += tabcvt<Real, TabT>(tv[g][part][e]) * xi[q];
+                    for (int q = 0; q <= p; ++q, ++e) acc += tv[g][part][e] * xi[q];
                     xn[p] = acc;
                 }
 #pragma unroll
@@ -221,14 +227,14 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
 
 // one thread per (chain c, realisation r, unit u)
 template <class Real, class TabT, int M>
-__global__ void __launch_bounds__(128, SMERF_ANCHOR_MINB) anchor_kernel(SampleParams P)
+__global__ void __launch_bounds__(128, sizeof(Real) == 8 ? 4 : SMERF_ANCHOR_MINB) anchor_kernel(SampleParams P)
 {
     anchor_body<Real, TabT, M>(P, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // batched: item = (request, block of 128 units, realisation, chain)
 template <class Real, class TabT, int M>
-__global__ void __launch_bounds__(128, SMERF_ANCHOR_MINB) anchor_batched_kernel(const SampleParams* __restrict__ descs,
+__global__ void __launch_bounds__(128, sizeof(Real) == 8 ? 4 : SMERF_ANCHOR_MINB) anchor_batched_kernel(const SampleParams* __restrict__ descs,
                                                              const int4* __restrict__ items)
 {
     const int4 it = items[blockIdx.x];
@@ -410,7 +416,7 @@ __device__ __forceinline__ int hr_swz(int e) { return e ^ ((e >> 4) & 15); }
 template <class C, int LGNC, int EPT, int PASS = 0>
 __device__ __forceinline__ void hr_c2r_inplace(C* buf, const C* __restrict__ tw3, const C* __restrict__ pre, C* gout)
 {
-    constexpr int MB = 3;
+    constexpr int MB = SMERF_INPLACE_MB;
     constexpr int Nc = 1 << LGNC;
     constexpr int LR = hr_bits(LGNC, PASS, MB), RP = 1 << LR;
     constexpr int Ns = 1 << hr_lgns(LGNC, PASS, MB);

@@ -382,7 +382,8 @@ static int upload_fft_tables(int n_phi, void** tw, void** pre, void** tw2, void*
     // high-radix plans (passes of at most 16 and at most 8 points)
     int L = 0;
     while ((1 << L) < Nc) ++L;
-    for (int MB = 4; MB >= 3; --MB) {
+    for (int t = 0; t < 2; ++t) {
+        const int MB = t == 0 ? 4 : SMERF_INPLACE_MB;
         std::vector<R> t2;
         for (int ps = 1; ps < smerf::hr_passes(L, MB); ++ps) {
             const int RP = 1 << smerf::hr_bits(L, ps, MB), Ns2 = 1 << smerf::hr_lgns(L, ps, MB);
@@ -394,7 +395,7 @@ static int upload_fft_tables(int n_phi, void** tw, void** pre, void** tw2, void*
                 }
         }
         if (t2.empty()) t2.assign(2, (R)0);
-        void** dst = MB == 4 ? tw2 : tw3;
+        void** dst = t == 0 ? tw2 : tw3;
         if (cudaMalloc(dst, t2.size() * sizeof(R)) != cudaSuccess) return SMERF_ENOMEM;
         if (cudaMemcpy(*dst, t2.data(), t2.size() * sizeof(R), cudaMemcpyHostToDevice) != cudaSuccess) return SMERF_ECUDA;
     }
