@@ -2,7 +2,7 @@
 """Throughput of the GB300 sphere-GMRF sampler on its headline workload.
 
 Workload (default): 1024 x 2048 equiangular grid, C_l = 1/((l(l+1)+20^2)(l(l+1)+50^2))
-(p = 2), 64 realisations per step, FP64 tables, FP32 recursion + FFT, anchors every 32
+(p = 2), 64 realisations per step, FP64 tables, FP32 recursion + FFT, anchors every 16
 rings.  A step is one smerf_sample call: the anchor kernel and the segment kernel that
 synthesises and writes every ring.  Metric: sphere grid points per second.
 
