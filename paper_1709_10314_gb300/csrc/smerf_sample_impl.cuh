@@ -149,14 +149,16 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
                 for (int q = 0; q < M; ++q) v[g * 2 * M + part * M + q] = x[g][part][q];
         Vec4<Real>::st(anc + aoff<M>(P, c, r, 0, 0, G * u), v);
     }
-    // anchors: x_j = Phi x_{j-1} + chol(S) xi.  The table values and normals of anchor j + 1
-    // are fetched before the matrix-vector products of anchor j (the loads come from L2 and
-    // do not depend on the state), so consecutive anchors overlap their latencies.
+    // anchors: x_j = Phi x_{j-1} + chol(S) xi.  The table values and normals of the next AD
+    // anchors are fetched ahead of the matrix-vector products (they do not depend on the
+    // state), so the load latencies of consecutive anchors overlap.
     // (selects, not P.x[c]: indexing a kernel parameter's array with a runtime index copies
     // the whole parameter block to local memory)
     const TabT* cs = (const TabT*)(c == 0 ? P.coarse[0] : P.coarse[1]);
     const int na = c == 0 ? P.n_anchors[0] : P.n_anchors[1];
-    Real tv[G][2][Ec];
+    constexpr int AD = M == 1 ? 4 : 2;  // anchors prefetched ahead (the loads come from L2 or HBM)
+    Real tq[AD][G][2][Ec];
+    Real nq[AD][4];
     const int k0 = P.k0, H = P.H, Ncm = P.Nc;  // copies: the lambda must not take P's address
     // table values of anchor j, converted; both chains of a slot share its mode's values except
     // slot 0, whose second chain is the Nyquist mode
@@ -178,48 +180,42 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
             }
         }
     };
-    if (na >= 1) fetch(1, tv, nr);
-    for (int j = 1; j <= na; ++j) {
-        Real tn[G][2][Ec];
-        Real nn[4];
-        if (j < na) fetch(j + 1, tn, nn);
+    // a ring of D prefetched anchors: slot d holds anchor j's tables and normals for j = d mod D
 #pragma unroll
-        for (int g = 0; g < G; ++g)
+    for (int d = 0; d < AD; ++d)
+        if (1 + d <= na) fetch(1 + d, tq[d], nq[d]);
+    for (int j0 = 1; j0 <= na; j0 += AD) {
 #pragma unroll
-            for (int part = 0; part < 2; ++part) {
-                Real xi[M], xn[M];
+        for (int d = 0; d < AD; ++d) {
+            const int j = j0 + d;
+            if (j > na) break;
 #pragma unroll
-                for (int q = 0; q < M; ++q) xi[q] = nr[g * 2 * M + part * M + q];
+            for (int g = 0; g < G; ++g)
 #pragma unroll
-                for (int p = 0; p < M; ++p) {
-                    Real acc = 0;
+                for (int part = 0; part < 2; ++part) {
+                    Real xn[M];
 #pragma unroll
-                    for (int q = 0; q < M; ++q) acc += tv[g][part][p * M + q] * x[g][part][q];
-                    int e = M * M + p * (p + 1) / 2;
+                    for (int p = 0; p < M; ++p) {
+                        Real acc = 0;
 #pragma unroll
-                    for (int q = 0; q <= p; ++q, ++e) acc += tv[g][part][e] * xi[q];
-                    xn[p] = acc;
+                        for (int q = 0; q < M; ++q) acc += tq[d][g][part][p * M + q] * x[g][part][q];
+                        int e = M * M + p * (p + 1) / 2;
+#pragma unroll
+                        for (int q = 0; q <= p; ++q, ++e) acc += tq[d][g][part][e] * nq[d][g * 2 * M + part * M + q];
+                        xn[p] = acc;
+                    }
+#pragma unroll
+                    for (int q = 0; q < M; ++q) x[g][part][q] = xn[q];
                 }
-#pragma unroll
-                for (int q = 0; q < M; ++q) x[g][part][q] = xn[q];
-            }
-        Real v[4];
-#pragma unroll
-        for (int g = 0; g < G; ++g)
-#pragma unroll
-            for (int part = 0; part < 2; ++part)
-#pragma unroll
-                for (int q = 0; q < M; ++q) v[g * 2 * M + part * M + q] = x[g][part][q];
-        Vec4<Real>::st(anc + aoff<M>(P, c, r, j, 0, G * u), v);
-        if (j < na) {
+            Real v[4];
 #pragma unroll
             for (int g = 0; g < G; ++g)
 #pragma unroll
                 for (int part = 0; part < 2; ++part)
 #pragma unroll
-                    for (int e = 0; e < Ec; ++e) tv[g][part][e] = tn[g][part][e];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) nr[i] = nn[i];
+                    for (int q = 0; q < M; ++q) v[g * 2 * M + part * M + q] = x[g][part][q];
+            Vec4<Real>::st(anc + aoff<M>(P, c, r, j, 0, G * u), v);
+            if (j + AD <= na) fetch(j + AD, tq[d], nq[d]);
         }
     }
     (void)T;
