@@ -112,9 +112,11 @@ int smerf_sample_timed(const smerf_plan* plan, uint64_t seed, int n_samples, voi
                        void* event_before_segments, void* event_after_segments);
 
 /*
- * smerf_sample_host -- smerf_sample into HOST memory: allocates device output on the stream,
- * samples, copies to `host_out` (n_samples * n_theta * n_phi elements) and synchronises the
- * stream before returning.  For callers without device buffers; includes the copies.
+ * smerf_sample_host -- smerf_sample into HOST memory `host_out` (n_samples * n_theta * n_phi
+ * elements), synchronising the stream before returning.  For callers without device buffers.
+ * Page-locked host memory (cudaHostAlloc, cudaHostRegister, pinned torch tensors) is written
+ * directly by the kernels over the CPU-GPU link; other host memory gets a stream-ordered
+ * device buffer and one device-to-host copy.
  */
 int smerf_sample_host(const smerf_plan* plan, uint64_t seed, int n_samples, void* host_out,
                       void* stream);

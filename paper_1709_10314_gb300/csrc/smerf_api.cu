@@ -253,6 +253,16 @@ int smerf_sample_host(const smerf_plan* plan, uint64_t seed, int n_samples, void
     if (!plan || n_samples < 0 || (n_samples > 0 && !host_out)) return SMERF_EINVAL;
     if (n_samples == 0) return SMERF_OK;
     cudaStream_t st = (cudaStream_t)stream;
+    // Page-locked host memory the GPU can address: the last FFT pass streams the field into it
+    // directly over the CPU-GPU link (no device copy of the output, no separate transfer).
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, host_out) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer && !((uintptr_t)at.devicePointer & 15u)) {
+        int rc = smerf_sample(plan, seed, n_samples, at.devicePointer, stream);
+        if (cudaStreamSynchronize(st) != cudaSuccess && rc == SMERF_OK) rc = SMERF_ECUDA;
+        return rc;
+    }
+    cudaGetLastError();  // an unregistered pointer is not an error here
     const size_t bytes = (size_t)n_samples * plan->n_theta * plan->n_phi * (plan->recur64 ? 8 : 4);
     void* dout = nullptr;
     cudaError_t e = cudaMallocAsync(&dout, bytes, st);

@@ -95,6 +95,19 @@ def test_host_entry_matches_device():
     assert np.array_equal(dev, host)
 
 
+def test_host_entry_pinned_memory_written_directly():
+    # page-locked host output: the kernels write it over the CPU-GPU link; same field, twice
+    import torch
+    from paper_1709_10314_gb300 import SMERF_RECUR_FP64
+    for flags, dt in ((0, torch.float32), (SMERF_RECUR_FP64, torch.float64)):
+        plan = _plan([20.0, 50.0], 64, 256, 16, flags)
+        dev = plan.sample(7, 5).cpu()
+        pinned = torch.full((5, 64, 256), float("nan"), dtype=dt, pin_memory=True)
+        for _ in range(2):
+            plan.sample_host(7, 5, pinned)
+            assert torch.equal(pinned, dev)
+
+
 def test_batched_matches_single_calls():
     import torch
     from paper_1709_10314_gb300 import SMERF_RECUR_FP64, sample_batched
