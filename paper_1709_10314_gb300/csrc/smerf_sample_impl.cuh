@@ -441,8 +441,13 @@ __device__ __forceinline__ void hr_c2r_inplace(C* buf, const C* __restrict__ tw3
             } else {
 #pragma unroll
                 for (int i = 0; i < RP; ++i) v[k][i] = buf[hr_swz(j + i * nb)];
+                const int kk = j & (Ns - 1);
+#pragma unroll
+                for (int i = 1; i < RP; ++i) v[k][i] = cmul(v[k][i], __ldg(twp + (i - 1) * Ns + kk));
             }
+            dft<C, RP>(v[k]);  // before the barrier: only results stay live across it
         }
+        asm volatile("" ::: "memory");  // one butterfly's twiddles at a time
     }
     if constexpr (!LAST) __syncthreads();  // every read of this pass before any write
 #pragma unroll
@@ -450,11 +455,6 @@ __device__ __forceinline__ void hr_c2r_inplace(C* buf, const C* __restrict__ tw3
         const int j = threadIdx.x + k * nt;
         if (j < nb) {
             const int kk = FIRST ? 0 : (j & (Ns - 1));
-            if constexpr (!FIRST) {
-#pragma unroll
-                for (int i = 1; i < RP; ++i) v[k][i] = cmul(v[k][i], __ldg(twp + (i - 1) * Ns + kk));
-            }
-            dft<C, RP>(v[k]);
             const int idx = ((j - kk) << LR) + kk;
             if constexpr (LAST) {
 #pragma unroll
@@ -565,10 +565,10 @@ __device__ __forceinline__ void unit_normals_rk(const uint2* rk, uint32_t call, 
 
 // In-place segment kernel, for rings too long for the warp-specialised kernel's three
 // buffers (one realisation per CTA, one ring buffer).  Every ring of one segment of one
-// chain: the recursion for the thread's units (state in registers, tables read once per
-// unit), the coefficients into shared memory, the C2R FFT in place, the ring to HBM.  While
-// the FFT runs, the state of the upper half of each thread's units waits in shared memory,
-// which keeps the FFT's registers free of spills.  LG = log2 Nc of a fixed-size high-radix
+// chain: the recursion for the thread's units (tables read once per unit), the coefficients
+// into shared memory, the C2R FFT in place, the ring to HBM.  The states of all but UPT - PARK
+// of each thread's units live in shared memory (loaded for their step, stored after it),
+// which keeps the registers of the recursion and of the FFT free of spills.  LG = log2 Nc of a fixed-size high-radix
 // FFT, or 0 for the runtime-size radix-4 one; PARK = units per thread parked (the last ones).
 template <class Real, class TabT, int M, int UPT, int LG, int PARK>
 __global__ void __launch_bounds__(1024, 1) segment_kernel(SampleParams P)
@@ -604,15 +604,19 @@ __global__ void __launch_bounds__(1024, 1) segment_kernel(SampleParams P)
     // right-anchor states are read from the scratch ([slot][2M])
     const Real* xrg = anc + aoff<M>(P, c, r0, has_right ? sg.right : 0, 0, 0);
 
-    Real x[UPT][4];  // per unit: [g][part][q] flattened (g * 2M + part * M + q)
+    // states: units i < UP in registers, the others in the park area ([PARK][nt][4]) between
+    // their steps
+    Real xreg[UP > 0 ? UP : 1][4];
 #pragma unroll
     for (int i = 0; i < UPT; ++i) {
         const int u = tid + i * nt;
-        if (u < n_units) {
-            Vec4<Real>::ldg(anc + aoff<M>(P, c, r0, sg.left, 0, G * u), x[i]);
-        } else {
+        Real v[4] = {0, 0, 0, 0};
+        if (u < n_units) Vec4<Real>::ldg(anc + aoff<M>(P, c, r0, sg.left, 0, G * u), v);
+        if (i < UP) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) x[i][k] = 0;
+            for (int k = 0; k < 4; ++k) xreg[i < UP ? i : 0][k] = v[k];
+        } else {
+            Vec4<Real>::st(park + ((size_t)(i - UP) * nt + tid) * 4, v);
         }
     }
     __syncthreads();
@@ -620,12 +624,20 @@ __global__ void __launch_bounds__(1024, 1) segment_kernel(SampleParams P)
     const TabT* steps = (const TabT*)(c == 0 ? P.steps[0] : P.steps[1]);
     for (int pos = sg.p0; pos < sg.p1; ++pos) {
         const int ring = c == 0 ? P.k0 - pos : P.k0 + pos;
-        if (pos > sg.p0) {
-            const TabT* tb = steps + (size_t)pos * mp * ROW;
+        const TabT* tb = steps + (size_t)pos * mp * ROW;
 #pragma unroll
-            for (int i = 0; i < UPT; ++i) {
-                const int u = tid + i * nt;
-                if (u >= n_units) continue;
+        for (int i = 0; i < UPT; ++i) {
+            const int u = tid + i * nt;
+            if (u >= n_units) continue;
+            Real x[4];
+            Real* pk = park + ((size_t)(i - UP) * nt + tid) * 4;
+            if (i < UP) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) x[k] = xreg[i < UP ? i : 0][k];
+            } else {
+                Vec4<Real>::ld(pk, x);
+            }
+            if (pos > sg.p0) {
                 Real ta[G][ROW];
 #pragma unroll
                 for (int g = 0; g < G; ++g) load_row<Real, TabT, ROW>(tb + (size_t)(G * u + g) * ROW, ta[g]);
@@ -637,7 +649,7 @@ __global__ void __launch_bounds__(1024, 1) segment_kernel(SampleParams P)
                 for (int g = 0; g < G; ++g)
 #pragma unroll
                     for (int part = 0; part < 2; ++part) {
-                        Real(&xs)[M] = *reinterpret_cast<Real(*)[M]>(&x[i][g * 2 * M + part * M]);
+                        Real(&xs)[M] = *reinterpret_cast<Real(*)[M]>(&x[g * 2 * M + part * M]);
                         const Real* xi = nr + g * 2 * M + part * M;
                         if (g == 0 && part == 1 && u == 0) {
                             // slot 0, second part: the Nyquist chain (mode Nc, own table row)
@@ -651,19 +663,17 @@ __global__ void __launch_bounds__(1024, 1) segment_kernel(SampleParams P)
                             step_state<Real, M, false>(ta[g], xs, xi, nullptr);
                         }
                     }
+                if (i < UP) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) xreg[i < UP ? i : 0][k] = x[k];
+                } else {
+                    Vec4<Real>::st(pk, x);
+                }
             }
+            // the unit's coefficients of this ring (slot 0's imaginary part = Nyquist)
+            if constexpr (G == 2) Vec4<Real>::st(reinterpret_cast<Real*>(buf0 + 2 * u), x);
+            else buf0[u] = cmk<C>(x[0], x[M]);
         }
-        // coefficients of this ring into shared memory (slot 0's imaginary part = Nyquist)
-#pragma unroll
-        for (int i = 0; i < UPT; ++i) {
-            const int u = tid + i * nt;
-            if (u >= n_units) continue;
-            if constexpr (G == 2) Vec4<Real>::st(reinterpret_cast<Real*>(buf0 + 2 * u), x[i]);
-            else buf0[u] = cmk<C>(x[i][0], x[i][M]);
-        }
-        // park the upper units' state
-#pragma unroll
-        for (int i = UP; i < UPT; ++i) Vec4<Real>::st(park + ((size_t)(i - UP) * nt + tid) * 4, x[i]);
         __syncthreads();
         if (!(c == 1 && pos == 0)) {  // the start ring is written by the northern chain
             Real* dst = (Real*)P.out + ((size_t)r0 * P.n_theta + ring) * (size_t)P.n_phi;
@@ -675,8 +685,6 @@ __global__ void __launch_bounds__(1024, 1) segment_kernel(SampleParams P)
             }
         }
         __syncthreads();  // the buffer is rewritten by the next ring
-#pragma unroll
-        for (int i = UP; i < UPT; ++i) Vec4<Real>::ld(park + ((size_t)(i - UP) * nt + tid) * 4, x[i]);
     }
 }
 
