@@ -475,26 +475,31 @@ int setup_impl(smerf_plan* pl)
     if (rc != SMERF_OK) goto done;
     start_kernel<M><<<gm, threads>>>(sp, pl->beq, t64);
     CK(cudaGetLastError());
-    for (int c = 0; c < 2; ++c) {
-        const int len = pl->chain[c].len;
-        if (len == 0) continue;
-        const size_t nb = (size_t)(len + 1) * pl->n_modes * M * M * sizeof(double);
-        CK(cudaMalloc(&phi, nb));
-        CK(cudaMalloc(&qv, nb));
-        // positions in chunks of the grid's y-dimension limit
-        for (int p0 = 0; p0 < len; p0 += 65535) {
-            const int cnt = (len - p0) < 65535 ? (len - p0) : 65535;
-            dim3 grid(gm, cnt);
-            // shift positions by p0 through the chain offset: launch with len and an offset
-            step_kernel<M><<<grid, threads>>>(sp, c, len, phi, qv);
+    {
+        // Step transitions and covariances of the northern chain.  The southern chain's steps are
+        // their mirror images (z -> -z): in the northern frame its step pos is the northern step
+        // pos + shift, shift = 1 for even n_theta (start ring south of the equator) and 0 for
+        // odd n_theta, so one computation serves both chains.
+        const int len0 = pl->chain[0].len, len1 = pl->chain[1].len;
+        const int shift = (pl->n_theta % 2 == 0) ? 1 : 0;
+        if (len1 + shift > len0) { rc = SMERF_EUNSUPPORTED; goto done; }
+        if (len0 > 0) {
+            const size_t nb = (size_t)(len0 + 1) * pl->n_modes * M * M * sizeof(double);
+            CK(cudaMalloc(&phi, nb));
+            CK(cudaMalloc(&qv, nb));
+            if (len0 > 65535) { rc = SMERF_EUNSUPPORTED; goto done; }
+            dim3 grid(gm, len0);
+            step_kernel<M><<<grid, threads>>>(sp, 0, len0, phi, qv);
             CK(cudaGetLastError());
-            if (p0 + cnt < len) { rc = SMERF_EUNSUPPORTED; goto done; }
         }
-        {
+        for (int c = 0; c < 2; ++c) {
+            const int len = pl->chain[c].len;
+            if (len == 0) continue;
+            const size_t off = c == 0 ? 0 : (size_t)shift * pl->n_modes * M * M;
             const int H = pl->H;
             const int nseg = H > 0 ? (len / H + 1) : 1;
             dim3 grid(gm, nseg);
-            segment_tables_kernel<M><<<grid, threads>>>(sp, c, len, H, phi, qv, pl->steps[c],
+            segment_tables_kernel<M><<<grid, threads>>>(sp, c, len, H, phi + off, qv + off, pl->steps[c],
                                                          pl->coarse[c], t64);
             CK(cudaGetLastError());
         }
