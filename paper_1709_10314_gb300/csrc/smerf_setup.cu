@@ -194,7 +194,7 @@ __global__ void step_kernel(Spec sp, int c, int len, double* phi, double* qout)
     const double vmax = cexp > 0.0 ? fmin(du, 46.0 / cexp) : du;
     const double sinmax = th1 > 0.5 * SMERF_PI ? 1.0 : sin(th1);
     const double rho = cexp + 2.0 * sp.kmax * sinmax + 1.0;
-    int nsub = (int)ceil(0.5 * rho * vmax);
+    int nsub = (int)ceil(0.25 * rho * vmax);  // one 8-point panel per 4 / rho (twice finer agrees to rounding)
     nsub = nsub < 1 ? 1 : (nsub > 256 ? 256 : nsub);
     const double h = vmax / nsub;
     Mat<M> acc = mzero<M>();
