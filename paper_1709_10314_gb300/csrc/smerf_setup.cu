@@ -51,19 +51,50 @@ struct Spec {
     int n_theta, k0, n_modes, n_modes_pad;
 };
 
-// log of 2F1(-l, l+1; 1+mu; x) for kappa^2 = k2 (positive series).
+// 2F1(-l, l+1; 1+mu; x) for kappa^2 = k2 (a positive series) as S * 1e250^E.  Terms are
+// taken two at a time with one division: r0 = a0/d0 and r1 = a1/d1 from 1/(d0 d1).
+__device__ void hyp_scaled(double k2, int mu, double x, double& S, int& E)
+{
+    double s = 1.0, t = 1.0;
+    int e = 0;
+    const double m1 = (double)mu + 1.0;
+    for (int n = 0; n < 1000000; n += 2) {
+        const double dn = (double)n;
+        const double a0 = (dn * (dn + 1.0) + k2) * x, d0 = (dn + m1) * (dn + 1.0);
+        const double a1 = ((dn + 1.0) * (dn + 2.0) + k2) * x, d1 = (dn + 1.0 + m1) * (dn + 2.0);
+        const double inv = 1.0 / (d0 * d1);
+        const double r0 = a0 * d1 * inv, r1 = a1 * d0 * inv;
+        t *= r0;
+        s += t;
+        if (t < 1e-17 * s && r0 < 0.9) break;
+        t *= r1;
+        s += t;
+        if (t < 1e-17 * s && r1 < 0.9) break;
+        if (s > 1e250) { s *= 1e-250; t *= 1e-250; ++e; }
+    }
+    S = s;
+    E = e;
+}
+
+// log of the same series
 __device__ double log_hyp(double k2, int mu, double x)
 {
-    double s = 1.0, t = 1.0, e = 0.0;
-    for (int n = 0; n < 1000000; ++n) {
-        const double dn = (double)n;
-        const double ratio = (dn * (dn + 1.0) + k2) * x / ((dn + 1.0 + mu) * (dn + 1.0));
-        t *= ratio;
-        s += t;
-        if (t < 1e-17 * s && ratio < 0.9) break;
-        if (s > 1e250) { s *= 1e-250; t *= 1e-250; e += 575.64627324851142; }
-    }
-    return log(s) + e;
+    double s;
+    int e;
+    hyp_scaled(k2, mu, x, s, e);
+    return log(s) + e * 575.64627324851142;
+}
+
+// the series relative to a reference value sref * 1e250^eref (given as 1/sref and eref)
+__device__ inline double hyp_rel(double k2, int mu, double x, double sref_inv, int eref)
+{
+    double s;
+    int e;
+    hyp_scaled(k2, mu, x, s, e);
+    double v = s * sref_inv;
+    for (int d = e - eref; d > 0; --d) v *= 1e250;
+    for (int d = e - eref; d < 0; ++d) v *= 1e-250;
+    return v;
 }
 
 // ring angle of position pos in chain c, in the northern frame
@@ -140,8 +171,9 @@ template <int M> __device__ inline Mat<M> mspd_inv(const Mat<M>& x)
     return mmul<M>(mT<M>(Li), Li);
 }
 
-// H_{q,i}(x) = r_{q,i} F^i_{m+q}(x) exp(-lsc_i); r_{q,i} = prod_{j=m}^{m+q-1} (j(j+1)+kappa_i^2)/(j+1)
-template <int M> __device__ inline Mat<M> hmat(const Spec& sp, int m, double x, const double* lsc)
+// H_{q,i}(x) = r_{q,i} F^i_{m+q}(x) / F^i_m(x_ref); r_{q,i} = prod_{j=m}^{m+q-1} (j(j+1)+kappa_i^2)/(j+1)
+// (the reference series value F^i_m(x_ref) = sref * 1e250^eref, given as 1/sref and eref)
+template <int M> __device__ inline Mat<M> hmat(const Spec& sp, int m, double x, const double* sinv, const int* eref)
 {
     Mat<M> H;
     for (int i = 0; i < M; ++i) {
@@ -151,7 +183,7 @@ template <int M> __device__ inline Mat<M> hmat(const Spec& sp, int m, double x, 
                 const double j = (double)(m + q - 1);
                 r *= (j * (j + 1.0) + sp.k2[i]) / (j + 1.0);
             }
-            H.a[q][i] = r * exp(log_hyp(sp.k2[i], m + q, x) - lsc[i]);
+            H.a[q][i] = r * hyp_rel(sp.k2[i], m + q, x, sinv[i], eref[i]);
         }
     }
     return H;
@@ -175,10 +207,15 @@ __global__ void step_kernel(Spec sp, int c, int len, double* phi, double* qout)
     const double u1 = log(t1), u2 = log(t2);
     const double s1 = sin(0.5 * th1), s2 = sin(0.5 * th2);
     const double x1 = s1 * s1, x2 = s2 * s2;
-    double lsc[M];
-    for (int i = 0; i < M; ++i) lsc[i] = log_hyp(sp.k2[i], m, x2);
-    const Mat<M> H2 = hmat<M>(sp, m, x2, lsc);
-    const Mat<M> H1 = hmat<M>(sp, m, x1, lsc);
+    double sinv[M];
+    int eref[M];
+    for (int i = 0; i < M; ++i) {
+        double sr;
+        hyp_scaled(sp.k2[i], m, x2, sr, eref[i]);
+        sinv[i] = 1.0 / sr;
+    }
+    const Mat<M> H2 = hmat<M>(sp, m, x2, sinv, eref);
+    const Mat<M> H1 = hmat<M>(sp, m, x1, sinv, eref);
     // A = (t2/t1)^m diag(t2^q) H2 H1^{-1} diag(t1^-q)
     Mat<M> A = mmul<M>(H2, minv<M>(H1));
     const double g = exp((double)m * (u2 - u1));
@@ -204,7 +241,7 @@ __global__ void step_kernel(Spec sp, int c, int len, double* phi, double* qout)
             const double w = 0.5 * h * kGL8w[n] * exp(-cexp * v);
             const double u = u2 + v;
             const double x = 1.0 / (1.0 + exp(-2.0 * u));   // sin^2(theta/2), tan(theta/2) = e^u
-            const Mat<M> Hs = hmat<M>(sp, m, x, lsc);
+            const Mat<M> Hs = hmat<M>(sp, m, x, sinv, eref);
             const Mat<M> Hi = minv<M>(Hs);
             double ph[M];
             for (int p = 0; p < M; ++p) {
