@@ -2,7 +2,9 @@
 
 What it computes, step by step, in the paper's notation:
 
-1. Spectrum C_l = A / prod_i (l(l+1) + kappa_i^2)             -- Eq. (Cl), kappa-hat_i = kappa_i^2.
+1. Spectrum C_l = A / prod_i (l(l+1) + kappa-hat_i)            -- Eq. (Cl); kappa-hat_i = kappa_i^2
+   for a list of real kappa, or complex kappa-hat given as KHat([...]) (real values or
+   complex-conjugate pairs, so that C_l is real; Sec. 5 uses +-i sqrt(10)).
 2. For each azimuthal mode m = 0..n_phi/2, the joint covariance of the U-basis state
    vector g_m^{(0..M-1)} at every ring, by direct spectral summation over normalised
    associated Legendre functions                              -- Lemma 2.1 + Eq. (Jmatrix_more_efficient)
@@ -42,7 +44,7 @@ __all__ = [
     "cov_partial", "cov_m", "default_levels", "ring_theta", "chain_layout",
     "conditioning_order", "normal_index", "joint_factor", "joint_factors", "cov_modes",
     "sample", "field_std", "mode_variances",
-    "conditional_tables", "dft_ring",
+    "conditional_tables", "dft_ring", "KHat",
 ]
 
 _lib = None
@@ -124,9 +126,25 @@ def normal_index(n_phi, M, m, part, q):
 
 
 # --------------------------------------------------------------- spectrum
+class KHat(tuple):
+    """kappa-hat_i given directly (complex allowed), in place of a list of real kappa."""
+
+
+def _spec(kappa):
+    """The C core's spectrum argument: kappa-hat_i as (re, im) pairs, and p."""
+    if isinstance(kappa, KHat):
+        kh = [complex(v) for v in kappa]
+    else:
+        kh = [complex(float(k) * float(k), 0.0) for k in np.atleast_1d(np.asarray(kappa, dtype=np.float64))]
+    out = np.zeros(2 * len(kh))
+    out[0::2] = [v.real for v in kh]
+    out[1::2] = [v.imag for v in kh]
+    return np.ascontiguousarray(out), len(kh)
+
+
 def Cl(l, kappa, A=1.0):
-    k = np.ascontiguousarray(kappa, dtype=np.float64)
-    return lib().oracle_Cl(int(l), len(k), _dp(k), float(A))
+    k, M = _spec(kappa)
+    return lib().oracle_Cl(int(l), M, _dp(k), float(A))
 
 
 def legendre_row(mu, z, lmax):
@@ -138,8 +156,8 @@ def legendre_row(mu, z, lmax):
 
 def cov_partial(m, kappa, A, z1, z2, p, q, lmax):
     """Plain partial sum of J^m_pq(z1, z2) up to l = lmax (no window)."""
-    k = np.ascontiguousarray(kappa, dtype=np.float64)
-    return lib().oracle_cov_partial(m, len(k), _dp(k), float(A), float(z1), float(z2), p, q, int(lmax))
+    k, M = _spec(kappa)
+    return lib().oracle_cov_partial(m, M, _dp(k), float(A), float(z1), float(z2), p, q, int(lmax))
 
 
 def default_levels(m, M, theta, c_turn_off=8.0, c_turn_diag=32.0, c_osc=400.0, lmin=2000):
@@ -168,8 +186,7 @@ def default_levels(m, M, theta, c_turn_off=8.0, c_turn_diag=32.0, c_osc=400.0, l
 def cov_m(m, kappa, A, theta, K=6, levels=None):
     """Joint covariance of the U-basis state of mode m at rings theta (any order).
     Returns (n*M, n*M), index (k*M+p, k2*M+q)."""
-    k = np.ascontiguousarray(kappa, dtype=np.float64)
-    M = len(k)
+    k, M = _spec(kappa)
     th = np.ascontiguousarray(theta, dtype=np.float64)
     z = np.ascontiguousarray(np.cos(th))
     n = len(z)
@@ -186,8 +203,7 @@ def cov_m(m, kappa, A, theta, K=6, levels=None):
 def cov_modes(ms, kappa, A, theta, K=6, **level_kw):
     """cov_m for every mode in `ms` (computed in parallel in the C core).
     Returns an array [len(ms), n*M, n*M]."""
-    k = np.ascontiguousarray(kappa, dtype=np.float64)
-    M = len(k)
+    k, M = _spec(kappa)
     th = np.ascontiguousarray(theta, dtype=np.float64)
     z = np.ascontiguousarray(np.cos(th))
     n = len(z)
@@ -296,8 +312,7 @@ def sample(kappa, A, n_theta, n_phi, seed, n_samples=1, H=0, K=6, rings=None,
 
     Returns float64 [n_samples][n_rings][n_phi]: every ring north to south (default),
     or the rings of `rings` (a leading subset of the conditioning order) in that order."""
-    kappa = np.asarray(kappa, dtype=np.float64)
-    M = len(kappa)
+    M = _spec(kappa)[1]
     Hm = n_phi // 2
     order_full = conditioning_order(n_theta, H)
     if rings is None:
@@ -345,8 +360,7 @@ def sample(kappa, A, n_theta, n_phi, seed, n_samples=1, H=0, K=6, rings=None,
 def mode_variances(kappa, A, n_theta, n_phi, K=6, rings=None, **level_kw):
     """J^m_00(z_k, z_k) = E|g_m(z_k)|^2 for m = 0..n_phi/2 at the given rings
     (Lemma 2.1).  Returns [n_phi/2+1][n_rings]."""
-    kappa = np.asarray(kappa, dtype=np.float64)
-    M = len(kappa)
+    M = _spec(kappa)[1]
     idx = list(range(n_theta)) if rings is None else list(rings)
     th = ring_theta(n_theta)[idx]
     ms = list(range(n_phi // 2 + 1))

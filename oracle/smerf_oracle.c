@@ -20,7 +20,8 @@
  *    Eq. (Jmatrix_more_efficient)):
  *        J^m_pq(z,z') = sum_{l>=m} C_l N_lm^2 P_l^{m+p}(z) P_l^{m+q}(z'),
  *    where N_lm P_l^{m+q} = s_lmq L_{l,m+q}, s_lmq^2 = prod_{j<q} (l-m-j)(l+m+1+j),
- *    and C_l = A / prod_i (l(l+1) + kappa_i^2) (Eq. (Cl) with kappa-hat_i = kappa_i^2).
+ *    and C_l = A / prod_i (l(l+1) + kappa-hat_i) (Eq. (Cl)); every function takes the
+ *    kappa-hat_i as (re, im) pairs ("khat"), kappa-hat_i = kappa_i^2 for a real kappa.
  *    The series is summed with a smooth cut-off window w((l+1/2)/L) and, on the
  *    same-ring blocks (whose tail does not oscillate), Richardson-extrapolated in 1/L
  *    over K levels L, 2L, ..., 2^(K-1) L.
@@ -99,11 +100,19 @@ void oracle_raw_uint32(uint64_t key64, uint32_t ring, int64_t ncalls, uint32_t *
 }
 
 /* ------------------------------------------------------ spectrum and the window */
-double oracle_Cl(int l, int M, const double *kappa, double A)
+/* khat: kappa-hat_i as (re, im) pairs.  The product prod_i (l(l+1) + kappa-hat_i) is real
+   when the kappa-hat are real or come in complex-conjugate pairs (Eq. (Cl); Sec. 5 uses the
+   pair +-i sqrt(10)); its real part is taken. */
+double oracle_Cl(int l, int M, const double *khat, double A)
 {
-    double d = 1.0, ll = (double)l * (double)(l + 1);
-    for (int i = 0; i < M; ++i) d *= ll + kappa[i] * kappa[i];
-    return A / d;
+    double dr = 1.0, di = 0.0, ll = (double)l * (double)(l + 1);
+    for (int i = 0; i < M; ++i) {
+        const double ar = ll + khat[2 * i], ai = khat[2 * i + 1];
+        const double nr = dr * ar - di * ai, ni = dr * ai + di * ar;
+        dr = nr;
+        di = ni;
+    }
+    return A / dr;
 }
 
 /* Smooth cut-off: 1 on [0,1/2], 0 on [1,inf), C-infinity in between. */
@@ -181,7 +190,7 @@ static double s_factor(int l, int m, int q)
  * extrapolated in 1/L.
  * Returns 0 on success, -1 on bad arguments.
  */
-int oracle_cov_m(int m, int M, const double *kappa, double A, int n, const double *z,
+int oracle_cov_m(int m, int M, const double *khat, double A, int n, const double *z,
                  long Loff, const long *Ld, int K, double *Sigma)
 {
     if (M < 1 || M > 4 || n < 1 || m < 0 || K < 1 || K > 8) return -1;
@@ -197,7 +206,7 @@ int oracle_cov_m(int m, int M, const double *kappa, double A, int n, const doubl
         for (long l = m; l <= Loff; ++l) {
             double w = window((l + 0.5) / (double)Loff);
             if (w == 0.0) break;
-            double c = oracle_Cl((int)l, M, kappa, A) * w;
+            double c = oracle_Cl((int)l, M, khat, A) * w;
             for (int k = 0; k < n; ++k)
                 for (int q = 0; q < M; ++q) {
                     legrec *r = &rec[k * M + q];
@@ -232,7 +241,7 @@ int oracle_cov_m(int m, int M, const double *kappa, double A, int n, const doubl
             for (long l = m; l <= L; ++l) {
                 double w = window((l + 0.5) / (double)L);
                 if (w == 0.0) break;
-                double c = oracle_Cl((int)l, M, kappa, A) * w;
+                double c = oracle_Cl((int)l, M, khat, A) * w;
                 for (int q = 0; q < M; ++q) {
                     while (rr[q].l < l) legrec_step(&rr[q]);
                     vv[q] = (rr[q].l == l) ? s_factor((int)l, m, q) * legrec_value(&rr[q]) : 0.0;
@@ -262,7 +271,7 @@ int oracle_cov_m(int m, int M, const double *kappa, double A, int n, const doubl
 
 /* Plain (no window, no extrapolation) partial sum up to lmax of the same cross
  * covariance between two points; used by tests to show the tail behaviour. */
-double oracle_cov_partial(int m, int M, const double *kappa, double A, double z1, double z2,
+double oracle_cov_partial(int m, int M, const double *khat, double A, double z1, double z2,
                           int p, int q, long lmax)
 {
     legrec r1, r2;
@@ -274,7 +283,7 @@ double oracle_cov_partial(int m, int M, const double *kappa, double A, double z1
         while (r2.l < l) legrec_step(&r2);
         double a = (r1.l == l) ? s_factor((int)l, m, p) * legrec_value(&r1) : 0.0;
         double b = (r2.l == l) ? s_factor((int)l, m, q) * legrec_value(&r2) : 0.0;
-        s += oracle_Cl((int)l, M, kappa, A) * a * b;
+        s += oracle_Cl((int)l, M, khat, A) * a * b;
     }
     return s;
 }
@@ -310,14 +319,14 @@ void oracle_dft_ring(int N, const double *re, const double *im, double *out)
 /* The same cross covariance for several modes at once (independent problems, run in
  * parallel over modes).  ms[i] is the mode of problem i; Loff[i] and Ld[i*n..] its
  * cut-offs; Sigma receives nmodes blocks of (n*M)^2 doubles.  Returns 0 or -1. */
-int oracle_cov_modes(int nmodes, const int *ms, int M, const double *kappa, double A, int n,
+int oracle_cov_modes(int nmodes, const int *ms, int M, const double *khat, double A, int n,
                      const double *z, const long *Loff, const long *Ld, int K, double *Sigma)
 {
     int bad = 0;
     size_t blk = (size_t)n * M * n * M;
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
     for (int i = 0; i < nmodes; ++i)
-        bad |= oracle_cov_m(ms[i], M, kappa, A, n, z, Loff[i], Ld + (size_t)i * n, K,
+        bad |= oracle_cov_m(ms[i], M, khat, A, n, z, Loff[i], Ld + (size_t)i * n, K,
                             Sigma + blk * (size_t)i) != 0;
     return bad ? -1 : 0;
 }

@@ -11,25 +11,25 @@ import oracle
 mp = pytest.importorskip("mpmath")
 
 
-def closed_form_J(m, kappas, A, z1, z2, p, q, dps=30):
+def closed_form_J(m, kappas, A, z1, z2, p, q, dps=30, khat=None):
     """J^m_pq(z1, z2) = 1/(4 pi) sum_i b_i Gamma(1+l_i-m) Gamma(-l_i-m) *
     { (-1)^p P^{m+p}(-z1) P^{m+q}(z2)  if z1 <= z2 ;  (-1)^q P^{m+p}(z1) P^{m+q}(-z2) otherwise },
     kappa-hat_i = kappa_i^2 = -l_i (l_i + 1), b_i the partial-fraction weights (Eq. (C_ell_efficient))."""
     with mp.workdps(dps):
         tot = mp.mpf(0)
-        for i, ki in enumerate(kappas):
-            ki = mp.mpf(ki)
+        kh = [mp.mpc(v) for v in khat] if khat is not None else [mp.mpf(k) ** 2 for k in kappas]
+        for i, khi in enumerate(kh):
             b = mp.mpf(A)
-            for j, kj in enumerate(kappas):
+            for j, khj in enumerate(kh):
                 if j != i:
-                    b /= mp.mpf(kj) ** 2 - ki ** 2
-            lam = mp.mpf(-0.5) + mp.sqrt(mp.mpf(0.25) - ki ** 2 + 0j)
+                    b /= khj - khi
+            lam = mp.mpf(-0.5) + mp.sqrt(mp.mpf(0.25) - khi + 0j)
             G = mp.gamma(1 + lam - m) * mp.gamma(-lam - m)
 
             def P(mu, z):
                 Q = mp.mpf(1)
                 for jj in range(mu):
-                    Q *= jj * (jj + 1) + ki ** 2
+                    Q *= jj * (jj + 1) + khi
                 return (Q / mp.factorial(mu)) * ((1 - z) / (1 + z)) ** (mp.mpf(mu) / 2) \
                     * mp.hyp2f1(-lam, lam + 1, 1 + mu, (1 - z) / 2)
             a1, a2 = mp.mpf(z1), mp.mpf(z2)
@@ -96,3 +96,37 @@ def test_windowed_sum_beats_truncation():
     assert p1 < p2 < S
     # 1/L tail: S - p(L) ~ c/L, so (S-p1)/(S-p2) ~ 10
     assert 8.0 < (S - p1) / (S - p2) < 12.0
+
+
+KHAT_CASES = [
+    # the spectrum of the paper's Sec. 5 example, C_l = (10 + l^2 (l+1)^2)^-1: kappa-hat = +-i sqrt(10)
+    ([complex(0.0, math.sqrt(10.0)), complex(0.0, -math.sqrt(10.0))], 16, [0, 1, 5, 16]),
+    ([complex(40.0, 300.0), complex(40.0, -300.0)], 32, [0, 7, 32]),
+]
+
+
+@pytest.mark.parametrize("khat,n_theta,ms", KHAT_CASES)
+def test_spectral_sum_matches_closed_form_complex_kappa_hat(khat, n_theta, ms):
+    th = oracle.ring_theta(n_theta)
+    M = len(khat)
+    pairs = [(0, 0), (0, 1), (n_theta // 2, n_theta // 2 - 1), (n_theta // 2, n_theta // 2), (2, 5)]
+    S_all = oracle.cov_modes(ms, oracle.KHat(khat), 1.0, th)
+    for mi, m in enumerate(ms):
+        S = S_all[mi]
+        for k1, k2 in pairs:
+            for p in range(M):
+                for q in range(M):
+                    ex = closed_form_J(m, None, 1.0, math.cos(th[k1]), math.cos(th[k2]), p, q, khat=khat)
+                    got = S[k1 * M + p, k2 * M + q]
+                    scale = math.sqrt(abs(S[k1 * M + p, k1 * M + p] * S[k2 * M + q, k2 * M + q]))
+                    assert abs(got - ex) <= 1e-10 * scale, (m, k1, k2, p, q, got, ex)
+
+
+def test_complex_kappa_hat_spectrum_values():
+    kh = oracle.KHat([complex(0.0, math.sqrt(10.0)), complex(0.0, -math.sqrt(10.0))])
+    for l in (0, 1, 2, 7, 100, 5000):
+        L = l * (l + 1)
+        assert abs(oracle.Cl(l, kh, 2.5) - 2.5 / (10.0 + L * L)) <= 1e-15 * 2.5 / (10.0 + L * L)
+    # real kappa-hat given directly equals the kappa form
+    for l in (0, 3, 40):
+        assert oracle.Cl(l, oracle.KHat([400.0, 2500.0])) == oracle.Cl(l, [20.0, 50.0])

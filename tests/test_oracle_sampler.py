@@ -118,9 +118,11 @@ def exact_oracle_field_cov(kappa, A, n_theta, n_phi, H=0):
     return C
 
 
-@pytest.mark.parametrize("n_theta,n_phi", [(3, 4), (4, 8)])
-def test_field_covariance_tiny_bruteforce(n_theta, n_phi):
-    kappa = [2.0, 5.0]  # C_l ~ l^-4: the direct sum converges like lmax^-3
+@pytest.mark.parametrize("n_theta,n_phi,spectrum", [(3, 4, "real"), (4, 8, "real"), (4, 8, "sec5")])
+def test_field_covariance_tiny_bruteforce(n_theta, n_phi, spectrum):
+    # C_l ~ l^-4: the direct sum converges like lmax^-3.  "sec5": the paper's Sec. 5 spectrum
+    # (10 + l^2 (l+1)^2)^-1, complex kappa-hat = +-i sqrt(10)
+    kappa = [2.0, 5.0] if spectrum == "real" else oracle.KHat([complex(0, math.sqrt(10)), complex(0, -math.sqrt(10))])
     A = 1.0
     Cb = truncated_field_cov(kappa, A, n_theta, n_phi, 400)
     Co = exact_oracle_field_cov(kappa, A, n_theta, n_phi)
