@@ -77,6 +77,22 @@ typedef struct smerf_plan smerf_plan;
 int smerf_plan_create_ex(const double* kappa, int p, double A, int n_theta, int n_phi,
                          unsigned flags, int anchor_spacing, smerf_plan** out_plan);
 
+/*
+ * smerf_plan_create_khat -- smerf_plan_create_ex with the spectrum given by kappa-hat_i
+ * directly (Eq. (Cl): C_l = A / prod_i (l(l+1) + kappa-hat_i)), which may be complex as in the
+ * paper's Sec. 5 example C_l = (10 + l^2 (l+1)^2)^-1, kappa-hat = +-i sqrt(10).
+ *   khat_re, khat_im  host arrays of p doubles: real and imaginary parts of kappa-hat_i.
+ *                     Either all real and > 0 (the same plan as smerf_plan_create_ex with
+ *                     kappa_i = sqrt(kappa-hat_i)), or p = 2 and one complex-conjugate pair
+ *                     (a + ib, a - ib), b != 0, for which C_l > 0 at every l.
+ * The set-up runs the same construction in complex arithmetic (l_i, 2F1, the solution
+ * matrices, the partial-fraction weights and Gamma factors complex); the tables are real.
+ * Other arguments, ownership and errors as for smerf_plan_create_ex (SMERF_EINVAL for other
+ * complex patterns, SMERF_EILLCOND when |b| < 5e-7 |kappa-hat|).
+ */
+int smerf_plan_create_khat(const double* khat_re, const double* khat_im, int p, double A, int n_theta, int n_phi,
+                           unsigned flags, int anchor_spacing, smerf_plan** out_plan);
+
 /* smerf_plan_create -- smerf_plan_create_ex with the default anchor spacing. */
 int smerf_plan_create(const double* kappa, int p, double A, int n_theta, int n_phi,
                       unsigned flags, smerf_plan** out_plan);

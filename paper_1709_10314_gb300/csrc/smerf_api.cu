@@ -130,18 +130,29 @@ const char* smerf_status_string(int status)
     }
 }
 
-int smerf_plan_create_ex(const double* kappa, int p, double A, int n_theta, int n_phi,
-                         unsigned flags, int anchor_spacing, smerf_plan** out_plan)
+static int check_grid(int p, double A, int n_theta, int n_phi, unsigned flags, int anchor_spacing)
 {
-    if (!out_plan) return SMERF_EINVAL;
-    *out_plan = nullptr;
-    if (!kappa || p < 1 || p > 3) return SMERF_EINVAL;
+    if (p < 1 || p > 3) return SMERF_EINVAL;
     if (!(A > 0.0) || !isfinite(A)) return SMERF_EINVAL;
     if (n_theta < 2 || n_theta > 65536) return SMERF_EINVAL;
     if (n_phi < 2 || (n_phi & 1)) return SMERF_EINVAL;
     if ((flags & ~0xFu) != 0) return SMERF_EINVAL;
     if ((flags & SMERF_TABLES_FP64) && (flags & SMERF_TABLES_FP32)) return SMERF_EINVAL;
     if (anchor_spacing < 0) return SMERF_EINVAL;
+    return SMERF_OK;
+}
+
+static int create_plan(const double* kappa, const double* kh_re, const double* kh_im, int complex_spec, int p,
+                       double A, int n_theta, int n_phi, unsigned flags, int anchor_spacing, smerf_plan** out_plan);
+
+int smerf_plan_create_ex(const double* kappa, int p, double A, int n_theta, int n_phi,
+                         unsigned flags, int anchor_spacing, smerf_plan** out_plan)
+{
+    if (!out_plan) return SMERF_EINVAL;
+    *out_plan = nullptr;
+    if (!kappa) return SMERF_EINVAL;
+    int rc = check_grid(p, A, n_theta, n_phi, flags, anchor_spacing);
+    if (rc != SMERF_OK) return rc;
     for (int i = 0; i < p; ++i)
         if (!(kappa[i] > 0.0) || !isfinite(kappa[i])) return SMERF_EINVAL;
     for (int i = 0; i < p; ++i)
@@ -149,6 +160,43 @@ int smerf_plan_create_ex(const double* kappa, int p, double A, int n_theta, int 
             const double a = kappa[i] * kappa[i], b = kappa[j] * kappa[j];
             if (fabs(a - b) < 1e-6 * fmax(a, b)) return SMERF_EILLCOND;
         }
+    double kr[kMaxP + 1] = {0}, ki[kMaxP + 1] = {0};
+    for (int i = 0; i < p && i <= kMaxP; ++i) kr[i] = kappa[i] * kappa[i];
+    return create_plan(kappa, kr, ki, 0, p, A, n_theta, n_phi, flags, anchor_spacing, out_plan);
+}
+
+int smerf_plan_create_khat(const double* khat_re, const double* khat_im, int p, double A, int n_theta, int n_phi,
+                           unsigned flags, int anchor_spacing, smerf_plan** out_plan)
+{
+    if (!out_plan) return SMERF_EINVAL;
+    *out_plan = nullptr;
+    if (!khat_re || !khat_im) return SMERF_EINVAL;
+    int rc = check_grid(p, A, n_theta, n_phi, flags, anchor_spacing);
+    if (rc != SMERF_OK) return rc;
+    if (p > kMaxP) return SMERF_EUNSUPPORTED;
+    int complex_spec = 0;
+    for (int i = 0; i < p; ++i) {
+        if (!isfinite(khat_re[i]) || !isfinite(khat_im[i])) return SMERF_EINVAL;
+        if (khat_im[i] != 0.0) complex_spec = 1;
+    }
+    if (!complex_spec) {
+        // real kappa-hat: the real construction with kappa_i = sqrt(kappa-hat_i)
+        double kappa[kMaxP];
+        for (int i = 0; i < p; ++i) {
+            if (!(khat_re[i] > 0.0)) return SMERF_EINVAL;
+            kappa[i] = sqrt(khat_re[i]);
+        }
+        return smerf_plan_create_ex(kappa, p, A, n_theta, n_phi, flags, anchor_spacing, out_plan);
+    }
+    // complex kappa-hat: exactly one conjugate pair (p = 2), so that C_l is real and positive
+    if (p != 2 || khat_re[0] != khat_re[1] || khat_im[0] != -khat_im[1]) return SMERF_EINVAL;
+    if (fabs(2.0 * khat_im[0]) < 1e-6 * hypot(khat_re[0], khat_im[0])) return SMERF_EILLCOND;
+    return create_plan(nullptr, khat_re, khat_im, 1, p, A, n_theta, n_phi, flags, anchor_spacing, out_plan);
+}
+
+static int create_plan(const double* kappa, const double* kh_re, const double* kh_im, int complex_spec, int p,
+                       double A, int n_theta, int n_phi, unsigned flags, int anchor_spacing, smerf_plan** out_plan)
+{
     if (p > kMaxP) return SMERF_EUNSUPPORTED;
     if (!is_pow2(n_phi) || n_phi < 8 || n_phi > 32768) return SMERF_EUNSUPPORTED;
 
@@ -156,7 +204,12 @@ int smerf_plan_create_ex(const double* kappa, int p, double A, int n_theta, int 
     if (!pl) return SMERF_ENOMEM;
     memset(pl, 0, sizeof(*pl));
     pl->p = p;
-    for (int i = 0; i < p; ++i) pl->kappa[i] = kappa[i];
+    for (int i = 0; i < p; ++i) {
+        if (kappa) pl->kappa[i] = kappa[i];
+        pl->khat_re[i] = kh_re[i];
+        pl->khat_im[i] = kh_im[i];
+    }
+    pl->complex_spec = complex_spec;
     pl->A = A;
     pl->n_theta = n_theta;
     pl->n_phi = n_phi;

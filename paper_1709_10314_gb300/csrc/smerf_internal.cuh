@@ -35,7 +35,9 @@ struct Segment {      // one independently sampled run of rings
 
 struct smerf_plan {
     int p;                 // M
-    double kappa[smerf::kMaxP];
+    double kappa[smerf::kMaxP];   // real spectra: kappa_i (kappa-hat_i = kappa_i^2)
+    double khat_re[smerf::kMaxP], khat_im[smerf::kMaxP];  // kappa-hat_i
+    int complex_spec;              // some kappa-hat_i is complex (a conjugate pair)
     double A;
     int n_theta, n_phi, n_modes, n_modes_pad, n_slots;
     int k0;

@@ -35,6 +35,8 @@
 #include <chrono>
 #include <vector>
 
+#include <cuda/std/complex>
+
 #include "smerf_internal.cuh"
 
 using namespace smerf;
@@ -443,6 +445,247 @@ static int upload_fft_tables(int n_phi, void** tw, void** pre, void** tw2, void*
     return SMERF_OK;
 }
 
+// ---------------------------------------------------------------- complex kappa-hat
+// Spectra with complex kappa-hat (Eq. (Cl) with complex-conjugate pairs, as in the paper's
+// Sec. 5 example (10 + l^2 (l+1)^2)^-1, kappa-hat = +-i sqrt(10)).  The same construction in
+// complex arithmetic: l_i, 2F1, U, the partial-fraction weights b_i and the Gamma factors are
+// complex; A, Q and J(z0, z0) are real (the two columns of U of a conjugate pair are complex
+// conjugates) and their real parts are kept.
+using cdbl = cuda::std::complex<double>;
+
+struct SpecC {
+    cdbl k2[kMaxP], b[kMaxP], lG0[kMaxP];  // kappa-hat_i, b_i, log(Gamma(1+l_i) Gamma(-l_i))
+    double A, kmax;
+    int n_theta, k0, n_modes, n_modes_pad;
+};
+
+template <int M> struct MatC { cdbl a[M][M]; };
+
+template <int M> __device__ inline MatC<M> cmmul(const MatC<M>& x, const MatC<M>& y)
+{
+    MatC<M> r;
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) {
+            cdbl s = 0.0;
+            for (int k = 0; k < M; ++k) s += x.a[i][k] * y.a[k][j];
+            r.a[i][j] = s;
+        }
+    return r;
+}
+template <int M> __device__ inline MatC<M> cminv(const MatC<M>& x);
+template <> __device__ inline MatC<1> cminv<1>(const MatC<1>& x) { MatC<1> r; r.a[0][0] = 1.0 / x.a[0][0]; return r; }
+template <> __device__ inline MatC<2> cminv<2>(const MatC<2>& x)
+{
+    const cdbl d = x.a[0][0] * x.a[1][1] - x.a[0][1] * x.a[1][0];
+    MatC<2> r;
+    r.a[0][0] = x.a[1][1] / d; r.a[0][1] = -x.a[0][1] / d;
+    r.a[1][0] = -x.a[1][0] / d; r.a[1][1] = x.a[0][0] / d;
+    return r;
+}
+
+// 2F1(-l, l+1; 1+mu; x) with kappa-hat = k2 complex, as S * 1e250^E (terms two per division)
+__device__ void hyp_scaled_c(cdbl k2, int mu, double x, cdbl& S, int& E)
+{
+    cdbl s = 1.0, t = 1.0;
+    int e = 0;
+    const double m1 = (double)mu + 1.0;
+    for (int n = 0; n < 1000000; n += 2) {
+        const double dn = (double)n;
+        const cdbl a0 = (dn * (dn + 1.0) + k2) * x, a1 = ((dn + 1.0) * (dn + 2.0) + k2) * x;
+        const double d0 = (dn + m1) * (dn + 1.0), d1 = (dn + 1.0 + m1) * (dn + 2.0);
+        const double inv = 1.0 / (d0 * d1);
+        const cdbl r0 = a0 * (d1 * inv), r1 = a1 * (d0 * inv);
+        t *= r0;
+        s += t;
+        if (cuda::std::abs(t) < 1e-17 * cuda::std::abs(s) && cuda::std::abs(r0) < 0.9) break;
+        t *= r1;
+        s += t;
+        if (cuda::std::abs(t) < 1e-17 * cuda::std::abs(s) && cuda::std::abs(r1) < 0.9) break;
+        if (cuda::std::abs(s) > 1e250) { s *= 1e-250; t *= 1e-250; ++e; }
+    }
+    S = s;
+    E = e;
+}
+
+__device__ inline cdbl log_hyp_c(cdbl k2, int mu, double x)
+{
+    cdbl s;
+    int e;
+    hyp_scaled_c(k2, mu, x, s, e);
+    return cuda::std::log(s) + e * 575.64627324851142;
+}
+
+__device__ inline cdbl hyp_rel_c(cdbl k2, int mu, double x, cdbl sref_inv, int eref)
+{
+    cdbl s;
+    int e;
+    hyp_scaled_c(k2, mu, x, s, e);
+    cdbl v = s * sref_inv;
+    for (int d = e - eref; d > 0; --d) v *= 1e250;
+    for (int d = e - eref; d < 0; ++d) v *= 1e-250;
+    return v;
+}
+
+template <int M> __device__ inline MatC<M> hmat_c(const SpecC& sp, int m, double x, const cdbl* sinv, const int* eref)
+{
+    MatC<M> H;
+    for (int i = 0; i < M; ++i) {
+        cdbl r = 1.0;
+        for (int q = 0; q < M; ++q) {
+            if (q > 0) {
+                const double j = (double)(m + q - 1);
+                r *= (j * (j + 1.0) + sp.k2[i]) / (j + 1.0);
+            }
+            H.a[q][i] = r * hyp_rel_c(sp.k2[i], m + q, x, sinv[i], eref[i]);
+        }
+    }
+    return H;
+}
+
+// step_kernel in complex arithmetic (same construction, real parts stored)
+template <int M>
+__global__ void step_kernel_c(SpecC sp, int len, double* phi, double* qout)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pos = blockIdx.y + 1;
+    if (m >= sp.n_modes || pos > len) return;
+    const double th1 = SMERF_PI * ((double)(sp.k0 - pos + 1) + 0.5) / (double)sp.n_theta;
+    const double th2 = SMERF_PI * ((double)(sp.k0 - pos) + 0.5) / (double)sp.n_theta;
+    const double t1 = tan(0.5 * th1), t2 = tan(0.5 * th2);
+    const double u1 = log(t1), u2 = log(t2);
+    const double s1 = sin(0.5 * th1), s2 = sin(0.5 * th2);
+    const double x1 = s1 * s1, x2 = s2 * s2;
+    cdbl sinv[M];
+    int eref[M];
+    for (int i = 0; i < M; ++i) {
+        cdbl sr;
+        hyp_scaled_c(sp.k2[i], m, x2, sr, eref[i]);
+        sinv[i] = 1.0 / sr;
+    }
+    const MatC<M> H2 = hmat_c<M>(sp, m, x2, sinv, eref);
+    const MatC<M> H1 = hmat_c<M>(sp, m, x1, sinv, eref);
+    MatC<M> A = cmmul<M>(H2, cminv<M>(H1));
+    const double g = exp((double)m * (u2 - u1));
+    for (int p = 0; p < M; ++p)
+        for (int q = 0; q < M; ++q) A.a[p][q] *= g * pow(t2, (double)p) / pow(t1, (double)q);
+    MatC<M> W = H2;
+    for (int p = 0; p < M; ++p)
+        for (int q = 0; q < M; ++q) W.a[p][q] *= pow(t2, (double)(p - M + 1));
+    const double cexp = 2.0 * (double)(m + M - 1);
+    const double du = u1 - u2;
+    const double vmax = cexp > 0.0 ? fmin(du, 46.0 / cexp) : du;
+    const double sinmax = th1 > 0.5 * SMERF_PI ? 1.0 : sin(th1);
+    const double rho = cexp + 2.0 * sp.kmax * sinmax + 1.0;
+    int nsub = (int)ceil(0.25 * rho * vmax);
+    nsub = nsub < 1 ? 1 : (nsub > 256 ? 256 : nsub);
+    const double h = vmax / nsub;
+    double acc[M][M];
+    for (int p = 0; p < M; ++p)
+        for (int q = 0; q < M; ++q) acc[p][q] = 0.0;
+    for (int j = 0; j < nsub; ++j)
+        for (int n = 0; n < 8; ++n) {
+            const double v = (j + 0.5 * (kGL8x[n] + 1.0)) * h;
+            const double w = 0.5 * h * kGL8w[n] * exp(-cexp * v);
+            const double u = u2 + v;
+            const double x = 1.0 / (1.0 + exp(-2.0 * u));
+            const MatC<M> Hi = cminv<M>(hmat_c<M>(sp, m, x, sinv, eref));
+            double ph[M];
+            for (int p = 0; p < M; ++p) {
+                cdbl s = 0.0;
+                for (int k = 0; k < M; ++k) s += W.a[p][k] * Hi.a[k][M - 1];
+                ph[p] = s.real();  // phi is real (conjugate columns)
+            }
+            for (int p = 0; p < M; ++p)
+                for (int q = 0; q < M; ++q) acc[p][q] += w * ph[p] * ph[q];
+        }
+    const double f = sp.A / (2.0 * SMERF_PI);
+    const size_t o = (((size_t)pos) * sp.n_modes + m) * (M * M);
+    for (int p = 0; p < M; ++p)
+        for (int q = 0; q < M; ++q) {
+            phi[o + p * M + q] = A.a[p][q].real();
+            qout[o + p * M + q] = f * acc[p][q];
+        }
+}
+
+// log sin z on any branch, without overflow for large |Im z|
+__device__ inline cdbl log_sin(cdbl z)
+{
+    const cdbl I(0.0, 1.0);
+    if (z.imag() > 0.0) return -I * z + cuda::std::log(I * 0.5) + cuda::std::log(1.0 - cuda::std::exp(2.0 * I * z));
+    return I * z + cuda::std::log(-I * 0.5) + cuda::std::log(1.0 - cuda::std::exp(-2.0 * I * z));
+}
+
+// start_kernel in complex arithmetic
+template <int M>
+__global__ void start_kernel_c(SpecC sp, void* beq, bool tab64)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= sp.n_modes) return;
+    const double th0 = SMERF_PI * ((double)sp.k0 + 0.5) / (double)sp.n_theta;
+    const double t0 = tan(0.5 * th0);
+    const double sx = sin(0.5 * th0), cx = cos(0.5 * th0);
+    const double x0 = sx * sx, xb0 = cx * cx;
+    Mat<M> J = mzero<M>();
+    for (int i = 0; i < M; ++i) {
+        const cdbl k2 = sp.k2[i];
+        cdbl lq = 0.0;  // log Q_m / (m!)^2
+        for (int j = 0; j < m; ++j) lq += cuda::std::log((j * (j + 1.0) + k2) / ((j + 1.0) * (j + 1.0)));
+        cdbl lF0[M], lF1[M], r[M];
+        cdbl rr = 1.0;
+        for (int q = 0; q < M; ++q) {
+            if (q > 0) {
+                const double j = (double)(m + q - 1);
+                rr *= (j * (j + 1.0) + k2) / (j + 1.0);
+            }
+            r[q] = rr;
+            lF0[q] = log_hyp_c(k2, m + q, x0);
+            lF1[q] = log_hyp_c(k2, m + q, xb0);
+        }
+        const cdbl lb = cuda::std::log(sp.b[i]) + sp.lG0[i] - log(4.0 * SMERF_PI) + lq;
+        for (int p = 0; p < M; ++p)
+            for (int q = 0; q < M; ++q) {
+                const cdbl v = cuda::std::exp(lb + lF1[p] + lF0[q]) * r[p] * r[q] * pow(t0, (double)(q - p));
+                J.a[p][q] += ((p & 1) ? -v : v).real();
+            }
+    }
+    const Mat<M> L = mchol<M>(msym<M>(J));
+    const double sc = m > 0 ? 0.70710678118654752440 : 1.0;
+    int e = 0;
+    for (int p = 0; p < M; ++p)
+        for (int q = 0; q <= p; ++q, ++e)
+            put<double>(beq, tab64, (size_t)e * sp.n_modes_pad + m, L.a[p][q] * sc);
+}
+
+// host: the complex spectrum's constants
+static SpecC make_spec_c(const smerf_plan* pl)
+{
+    SpecC sc;
+    memset(&sc, 0, sizeof(sc));
+    const int M = pl->p;
+    sc.A = pl->A;
+    sc.kmax = 0.0;
+    for (int i = 0; i < M; ++i) {
+        const cdbl kh(pl->khat_re[i], pl->khat_im[i]);
+        sc.k2[i] = kh;
+        sc.kmax = fmax(sc.kmax, sqrt(cuda::std::abs(kh)));
+        cdbl b = pl->A;
+        for (int j = 0; j < M; ++j)
+            if (j != i) b /= cdbl(pl->khat_re[j], pl->khat_im[j]) - kh;
+        sc.b[i] = b;
+        // l = -1/2 + sqrt(1/4 - kappa-hat); Gamma(1+l) Gamma(-l) = -pi / sin(pi l)
+        const cdbl lam = -0.5 + cuda::std::sqrt(0.25 - kh);
+        const cdbl I(0.0, 1.0), z = SMERF_PI * lam;
+        const cdbl ls = z.imag() > 0.0 ? -I * z + cuda::std::log(I * 0.5) + cuda::std::log(1.0 - cuda::std::exp(2.0 * I * z))
+                                       : I * z + cuda::std::log(-I * 0.5) + cuda::std::log(1.0 - cuda::std::exp(-2.0 * I * z));
+        sc.lG0[i] = cuda::std::log(cdbl(-SMERF_PI, 0.0)) - ls;
+    }
+    sc.n_theta = pl->n_theta;
+    sc.k0 = pl->k0;
+    sc.n_modes = pl->n_modes;
+    sc.n_modes_pad = pl->n_modes_pad;
+    return sc;
+}
+
 #define CK(x)                                                                     \
     do {                                                                          \
         cudaError_t e_ = (x);                                                     \
@@ -463,7 +706,7 @@ int setup_impl(smerf_plan* pl)
     sp.M = M;
     sp.A = pl->A;
     sp.kmax = 0.0;
-    for (int i = 0; i < M; ++i) {
+    for (int i = 0; i < M && !pl->complex_spec; ++i) {
         const double k = pl->kappa[i];
         sp.k2[i] = k * k;
         sp.kmax = fmax(sp.kmax, k);
@@ -510,7 +753,8 @@ int setup_impl(smerf_plan* pl)
     rc = pl->recur64 ? upload_fft_tables<double>(pl->n_phi, &pl->tw, &pl->pre, &pl->tw2, &pl->tw3)
                      : upload_fft_tables<float>(pl->n_phi, &pl->tw, &pl->pre, &pl->tw2, &pl->tw3);
     if (rc != SMERF_OK) goto done;
-    start_kernel<M><<<gm, threads>>>(sp, pl->beq, t64);
+    if (pl->complex_spec) start_kernel_c<M><<<gm, threads>>>(make_spec_c(pl), pl->beq, t64);
+    else start_kernel<M><<<gm, threads>>>(sp, pl->beq, t64);
     CK(cudaGetLastError());
     {
         // Step transitions and covariances of the northern chain.  The southern chain's steps are
@@ -526,7 +770,8 @@ int setup_impl(smerf_plan* pl)
             CK(cudaMalloc(&qv, nb));
             if (len0 > 65535) { rc = SMERF_EUNSUPPORTED; goto done; }
             dim3 grid(gm, len0);
-            step_kernel<M><<<grid, threads>>>(sp, 0, len0, phi, qv);
+            if (pl->complex_spec) step_kernel_c<M><<<grid, threads>>>(make_spec_c(pl), len0, phi, qv);
+            else step_kernel<M><<<grid, threads>>>(sp, 0, len0, phi, qv);
             CK(cudaGetLastError());
         }
         for (int c = 0; c < 2; ++c) {

@@ -52,6 +52,8 @@ def _lib():
         L.smerf_plan_create_ex.argtypes = [dp, ip, ctypes.c_double, ip, ip, ctypes.c_uint, ip,
                                            ctypes.POINTER(vp)]
         L.smerf_plan_create_ex.restype = ip
+        L.smerf_plan_create_khat.argtypes = [dp, dp, ip, ctypes.c_double, ip, ip, ctypes.c_uint, ip, ctypes.POINTER(vp)]
+        L.smerf_plan_create_khat.restype = ip
         L.smerf_plan_destroy.argtypes = [vp]
         L.smerf_plan_destroy.restype = ip
         L.smerf_sample.argtypes = [vp, ctypes.c_uint64, ip, vp, vp]
@@ -112,14 +114,27 @@ def _stream_ptr(stream):
 class Plan:
     """A sampling plan (device-resident conditional-covariance tables)."""
 
-    def __init__(self, kappa, A=1.0, n_theta=64, n_phi=128, flags=0, anchor_spacing=0):
+    def __init__(self, kappa=None, A=1.0, n_theta=64, n_phi=128, flags=0, anchor_spacing=0, khat=None):
+        """Spectrum C_l = A / prod_i (l(l+1) + kappa-hat_i): real `kappa` (kappa-hat_i =
+        kappa_i^2), or `khat` given directly (real values, or one complex-conjugate pair)."""
         L = _lib()
-        k = np.ascontiguousarray(np.atleast_1d(kappa), dtype=np.float64)
         h = ctypes.c_void_p()
-        _check("smerf_plan_create_ex",
-               L.smerf_plan_create_ex(k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(k),
-                                      float(A), int(n_theta), int(n_phi), int(flags),
-                                      int(anchor_spacing), ctypes.byref(h)))
+        dp = ctypes.POINTER(ctypes.c_double)
+        if khat is not None:
+            kh = [complex(v) for v in np.atleast_1d(khat)]
+            re = np.ascontiguousarray([v.real for v in kh], dtype=np.float64)
+            im = np.ascontiguousarray([v.imag for v in kh], dtype=np.float64)
+            _check("smerf_plan_create_khat",
+                   L.smerf_plan_create_khat(re.ctypes.data_as(dp), im.ctypes.data_as(dp), len(kh), float(A),
+                                            int(n_theta), int(n_phi), int(flags), int(anchor_spacing),
+                                            ctypes.byref(h)))
+            k = np.asarray(kh)
+        else:
+            k = np.ascontiguousarray(np.atleast_1d(kappa), dtype=np.float64)
+            _check("smerf_plan_create_ex",
+                   L.smerf_plan_create_ex(k.ctypes.data_as(dp), len(k),
+                                          float(A), int(n_theta), int(n_phi), int(flags),
+                                          int(anchor_spacing), ctypes.byref(h)))
         self._h = h
         self.kappa = k
         self.A = float(A)

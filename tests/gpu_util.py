@@ -6,15 +6,20 @@ import numpy as np
 import oracle
 
 
+def _k(kappa):
+    """The oracle's spectrum argument: a KHat as it is, real kappa as a list."""
+    return kappa if isinstance(kappa, oracle.KHat) else list(kappa)
+
+
 @functools.lru_cache(maxsize=None)
 def oracle_field(kappa, A, n_theta, n_phi, seed, n, H, rings=None):
-    return oracle.sample(list(kappa), A, n_theta, n_phi, seed, n, H=H,
+    return oracle.sample(_k(kappa), A, n_theta, n_phi, seed, n, H=H,
                          rings=None if rings is None else list(rings))
 
 
 @functools.lru_cache(maxsize=None)
 def oracle_std(kappa, A, n_theta, n_phi):
-    return oracle.field_std(list(kappa), A, n_theta, n_phi)
+    return oracle.field_std(_k(kappa), A, n_theta, n_phi)
 
 
 def rel_err(got, ref, std):

@@ -72,3 +72,20 @@ def test_status_strings(lib):
     assert lib.smerf_status_string(0) == b"ok"
     assert b"argument" in lib.smerf_status_string(-1)
     assert lib.smerf_plan_destroy(None) == 0
+
+
+def test_khat_validation_without_gpu(lib):
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.smerf_plan_create_khat.restype = ctypes.c_int
+    out = ctypes.c_void_p()
+
+    def call(re, im, p):
+        r = (ctypes.c_double * len(re))(*re)
+        i = (ctypes.c_double * len(im))(*im)
+        return lib.smerf_plan_create_khat(ctypes.cast(r, dp), ctypes.cast(i, dp), p, ctypes.c_double(1.0), 16, 32,
+                                          0, 0, ctypes.byref(out))
+    assert call([1.0, 1.0], [2.0, 3.0], 2) == -1      # not a conjugate pair
+    assert call([1.0], [2.0], 1) == -1                # a single complex value
+    assert call([1.0, 2.0], [2.0, -2.0], 2) == -1     # real parts differ
+    assert call([1.0, 1.0], [1e-9, -1e-9], 2) == -2   # nearly a double root: ill-conditioned
+    assert call([-1.0], [0.0], 1) == -1               # real kappa-hat must be > 0
