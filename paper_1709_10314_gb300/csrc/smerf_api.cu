@@ -89,6 +89,57 @@ size_t smerf_scratch_bytes(const smerf_plan* pl, int n_samples)
     return (size_t)2 * n_samples * (na + 1) * 2 * pl->p * (size_t)(pl->n_phi / 2) * rs;
 }
 
+int smerf_stage_tables(const double* src, float* dst, size_t n, cudaStream_t st);
+
+// ---- FP64 tables with FP32 recursion: the tables the float kernels read are staged once per
+// call as FP32 (the kernels' own truncating conversion, so the field is bit-identical) instead
+// of being converted by every realisation group's CTAs.
+namespace {
+struct StageLayout {
+    size_t steps[2], coarse[2], beq, total;  // element counts; total in bytes (256-aligned parts)
+};
+
+StageLayout stage_layout(const smerf_plan* pl)
+{
+    StageLayout L;
+    const size_t mp = pl->n_modes_pad;
+    size_t off = 0;
+    auto add = [&](size_t elems) { off += ((elems * sizeof(float) + 255) / 256) * 256; return elems; };
+    for (int c = 0; c < 2; ++c) L.steps[c] = add((size_t)(pl->chain[c].len + 1) * step_row(pl->p) * mp);
+    for (int c = 0; c < 2; ++c) L.coarse[c] = add((size_t)(pl->chain[c].n_anchors + 1) * coarse_elems(pl->p) * mp);
+    L.beq = add((size_t)tri(pl->p) * mp);
+    L.total = off;
+    return L;
+}
+}  // namespace
+
+// whether a call stages its tables (FP64 tables, FP32 recursion, enough realisations to share them)
+static bool use_stage(const smerf_plan* pl, int n) { return !pl->recur64 && pl->tab64 && n >= 4; }
+
+size_t smerf_stage_bytes(const smerf_plan* pl, int n) { return use_stage(pl, n) ? stage_layout(pl).total : 0; }
+
+// smerf_launch_sample with the tables staged in `stage` (smerf_stage_bytes bytes) when the call
+// qualifies, else the plain launch
+int smerf_launch_sample_staged(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch, void* stage,
+                               cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1)
+{
+    if (!use_stage(pl, n) || !stage) return smerf_launch_sample(pl, seed, n, out, scratch, st, ev0, ev1);
+    const StageLayout L = stage_layout(pl);
+    smerf_plan sh = *pl;  // shallow copy: the same plan reading FP32 copies of its tables
+    unsigned char* p = (unsigned char*)stage;
+    auto take = [&](const void* src, size_t elems) {
+        float* dst = (float*)p;
+        p += ((elems * sizeof(float) + 255) / 256) * 256;
+        return smerf_stage_tables((const double*)src, dst, elems, st) == SMERF_OK ? (void*)dst : nullptr;
+    };
+    for (int c = 0; c < 2; ++c) sh.steps[c] = take(pl->steps[c], L.steps[c]);
+    for (int c = 0; c < 2; ++c) sh.coarse[c] = take(pl->coarse[c], L.coarse[c]);
+    sh.beq = take(pl->beq, L.beq);
+    if (!sh.steps[0] || !sh.steps[1] || !sh.coarse[0] || !sh.coarse[1] || !sh.beq) return SMERF_ECUDA;
+    sh.tab64 = false;
+    return smerf_launch_sample_ff(&sh, seed, n, out, scratch, st, ev0, ev1);
+}
+
 int smerf_launch_sample(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch, cudaStream_t st,
                         cudaEvent_t ev0, cudaEvent_t ev1)
 {
@@ -292,11 +343,13 @@ int smerf_sample_timed(const smerf_plan* plan, uint64_t seed, int n_samples, voi
     if (dev != plan->dev) return SMERF_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     void* scratch = nullptr;
-    const size_t sb = smerf_scratch_bytes(plan, n_samples);
-    cudaError_t e = cudaMallocAsync(&scratch, sb, st);
+    const size_t sb = (smerf_scratch_bytes(plan, n_samples) + 255) / 256 * 256;
+    const size_t tb = smerf_stage_bytes(plan, n_samples);
+    cudaError_t e = cudaMallocAsync(&scratch, sb + tb, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? SMERF_ENOMEM : SMERF_ECUDA;
-    const int rc = smerf_launch_sample(plan, seed, n_samples, out, scratch, st, (cudaEvent_t)event_before_segments,
-                                       (cudaEvent_t)event_after_segments);
+    const int rc = smerf_launch_sample_staged(plan, seed, n_samples, out, scratch,
+                                              tb ? (void*)((unsigned char*)scratch + sb) : nullptr, st,
+                                              (cudaEvent_t)event_before_segments, (cudaEvent_t)event_after_segments);
     cudaFreeAsync(scratch, st);
     return rc;
 }
@@ -446,7 +499,9 @@ int smerf_plan_autotune(smerf_plan* plan, int n_samples, void* stream, int* chos
     void* scratch = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc = SMERF_OK;
-    if (cudaMalloc(&out, ob) != cudaSuccess || cudaMalloc(&scratch, smerf_scratch_bytes(plan, n_samples)) != cudaSuccess)
+    const size_t sb = (smerf_scratch_bytes(plan, n_samples) + 255) / 256 * 256;
+    const size_t tb = smerf_stage_bytes(plan, n_samples);
+    if (cudaMalloc(&out, ob) != cudaSuccess || cudaMalloc(&scratch, sb + tb) != cudaSuccess)
         rc = SMERF_ENOMEM;
     if (rc == SMERF_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = SMERF_ECUDA;
     float best = 1e30f;
@@ -461,7 +516,8 @@ int smerf_plan_autotune(smerf_plan* plan, int n_samples, void* stream, int* chos
         plan->tune.minb = ci[4];
         float tot = 0.0f;
         for (int it = 0; rc == SMERF_OK && it < 4; ++it) {
-            rc = smerf_launch_sample(plan, 1 + it, n_samples, out, scratch, st, e0, e1);
+            rc = smerf_launch_sample_staged(plan, 1 + it, n_samples, out, scratch,
+                                            tb ? (void*)((unsigned char*)scratch + sb) : nullptr, st, e0, e1);
             if (rc == SMERF_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = SMERF_ECUDA;
             float ms = 0.0f;
             if (rc == SMERF_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = SMERF_ECUDA;

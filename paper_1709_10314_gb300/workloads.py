@@ -28,7 +28,7 @@ FIXED = {
 # producer threads, FFT threads, CTAs per SM) that smerf_plan_autotune chose on a GB300, per
 # (workload, recursion precision, table precision); bench.py uses them unless asked to re-tune.
 TUNED_LAUNCH = {
-    ("1024x2048-p2", "fp32", "fp64"): (2, 4, 512, 128, 1),
+    ("1024x2048-p2", "fp32", "fp64"): (4, 1, 256, 64, 2),
     ("1024x2048-p2", "fp32", "fp32"): (4, 1, 256, 64, 2),
     ("1024x2048-p2", "fp64", "fp64"): (4, 1, 256, 128, 1),
     ("4096x8192-p1", "fp32", "fp64"): (4, 1, 512, 256, 1),

@@ -119,3 +119,17 @@ def test_batched_matches_single_calls():
     torch.cuda.synchronize()
     assert torch.equal(o1, p1.sample(5, 3))
     assert torch.equal(o2, p2.sample(6, 2))
+
+
+def test_staged_fp64_tables_equal_in_kernel_conversion():
+    # FP64 tables with FP32 recursion: a call with several realisations converts the tables to
+    # FP32 once (staged); a batched launch converts them in the kernels.  Same field, bit for bit.
+    import torch
+    from paper_1709_10314_gb300 import SMERF_TABLES_FP64, sample_batched
+    for kappa, nt, nphi, H in (([20.0, 50.0], 40, 128, 8), ([30.0], 33, 64, 4)):
+        plan = _plan(kappa, nt, nphi, H, SMERF_TABLES_FP64)
+        staged = plan.sample(5, 6)
+        out = torch.empty_like(staged)
+        sample_batched([plan], [5], [6], [out])
+        torch.cuda.synchronize()
+        assert torch.equal(staged, out)
