@@ -261,12 +261,14 @@ def run_gb300(args, rank, world, local_rank):
         fp64_alu = recur == "fp64"
         alg_ops = n * cfg["n_theta"] * (cfg["n_phi"] // 2) * alg_ops_per_item(len(cfg["kappa"]), cfg["n_phi"] // 2, fp64_alu)
         table_bytes = info["table_bytes"]
+        # what the segment kernel reads: the step tables and the anchor states
+        seg_read_bytes = info["step_table_bytes"], n * info["scratch_bytes_per_sample"]
         setup_ms = info["setup_ms"]
         dtype = "f64" if recur == "fp64" else "f32"
         workload = "%dx%d equiangular grid, C_l=1/prod(l(l+1)+kappa^2) kappa=%s (p=%d), %d realisations, %s tables, %s recursion+FFT" % (
             cfg["n_theta"], cfg["n_phi"], "(" + ",".join("%g" % k for k in cfg["kappa"]) + ")", len(cfg["kappa"]), n,
             tables.upper(), recur.upper())
-        launches = 2
+        launches = plan.launches(n)
         seed0 = rank_seed(cfg["seed"], rank, n * (args.warmup + args.steps + 8))
 
         def step(i, ev0=None, ev1=None):
@@ -312,12 +314,17 @@ def run_gb300(args, rank, world, local_rank):
 
     # Rooflines of the segment kernel.  It is bound by ALU issue (noise, recursion and FFT
     # arithmetic), not by HBM: ALU = algorithmic operations / kernel time against the lane
-    # rate at the maximum SM clock; HBM = field written once + tables read once.
-    # (FP64 tables with FP32 recursion: each call stages the tables as FP32 once; the segment
-    # kernel reads that copy, half the plan's table bytes)
+    # rate at the maximum SM clock; HBM = field written once + step tables and anchor states
+    # read once.  (FP64 tables with FP32 recursion: each call stages the step tables as FP32
+    # once; the segment kernel reads that copy, half their bytes.)  The batched graph replay
+    # (anchor and segment launches) counts the field and all of its plans' tables.
     staged = batch is None and (args.recur or FIXED[wl]["recur"]) == "fp32" and \
         (args.tables or FIXED[wl]["tables"]) == "fp64" and FIXED[wl]["n"] >= 4
-    alg_bytes = out_bytes + (table_bytes // 2 if staged else table_bytes)
+    if batch is None:
+        step_b, anc_b = seg_read_bytes
+        alg_bytes = out_bytes + (step_b // 2 if staged else step_b) + anc_b
+    else:
+        alg_bytes = out_bytes + table_bytes
     peak, peak_kind = _peaks()
     achieved = alg_bytes / (seg_ms / 1e3) / 1e9
     sm_max = float(clocks.get("sm_max_mhz") or 2070.0) if isinstance(clocks, dict) else 2070.0

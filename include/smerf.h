@@ -128,6 +128,25 @@ int smerf_sample_timed(const smerf_plan* plan, uint64_t seed, int n_samples, voi
                        void* event_before_segments, void* event_after_segments);
 
 /*
+ * smerf_scratch_trim -- return to the device the memory that the library's per-call scratch
+ * pool on the current device holds and no call is using.  smerf_sample and smerf_sample_host
+ * take their temporary device memory (anchor states, FP32 copies of FP64 tables, the field on
+ * the host path) stream-ordered from that pool, which keeps it between calls so that a call
+ * after a synchronisation maps no new memory; the pool holds at most the largest amount that
+ * calls in flight used together.  SMERF_OK, or SMERF_ECUDA.
+ */
+int smerf_scratch_trim(void);
+
+/*
+ * smerf_sample_launches -- how many kernels one smerf_sample(plan, ., n_samples, ...) call
+ * launches on its stream: the anchor kernel and the segment kernel, and, when the plan keeps
+ * FP64 tables, recurses in FP32 and n_samples >= 4, one short conversion of the coarse and
+ * start tables to FP32 ahead of them (the anchor kernel's threads convert the step tables).
+ * 0 for n_samples == 0; SMERF_EINVAL (negative) for a NULL plan or a negative count.
+ */
+int smerf_sample_launches(const smerf_plan* plan, int n_samples);
+
+/*
  * smerf_sample_host -- smerf_sample into HOST memory `host_out` (n_samples * n_theta * n_phi
  * elements), synchronising the stream before returning.  For callers without device buffers.
  * Page-locked host memory (cudaHostAlloc, cudaHostRegister, pinned torch tensors) is written
@@ -208,6 +227,8 @@ typedef struct smerf_plan_info_t {
     size_t table_bytes;                    /* device bytes of step + coarse + start tables      */
     size_t scratch_bytes_per_sample;       /* anchor-state scratch per realisation              */
     double setup_ms;                       /* wall time of the set-up kernels                   */
+    size_t step_table_bytes;               /* the step tables' part of table_bytes (the tables  */
+                                           /* the segment kernel reads)                         */
 } smerf_plan_info_t;
 
 int smerf_plan_info(const smerf_plan* plan, smerf_plan_info_t* info);

@@ -89,11 +89,10 @@ size_t smerf_scratch_bytes(const smerf_plan* pl, int n_samples)
     return (size_t)2 * n_samples * (na + 1) * 2 * pl->p * (size_t)(pl->n_phi / 2) * rs;
 }
 
-int smerf_stage_tables(const double* src, float* dst, size_t n, cudaStream_t st);
-
 // ---- FP64 tables with FP32 recursion: the tables the float kernels read are staged once per
 // call as FP32 (the kernels' own truncating conversion, so the field is bit-identical) instead
-// of being converted by every realisation group's CTAs.
+// of being converted by every realisation group's CTAs: the coarse and start tables by a short
+// launch, the step tables by the anchor launch's threads beside their anchors.
 namespace {
 struct StageLayout {
     size_t steps[2], coarse[2], beq, total;  // element counts; total in bytes (256-aligned parts)
@@ -125,19 +124,47 @@ int smerf_launch_sample_staged(const smerf_plan* pl, uint64_t seed, int n, void*
 {
     if (!use_stage(pl, n) || !stage) return smerf_launch_sample(pl, seed, n, out, scratch, st, ev0, ev1);
     const StageLayout L = stage_layout(pl);
+    // the anchor threads index groups of eight elements and themselves in 32 bits (no index
+    // reaches 2^31 while both counts are below 2^30), the short launch elements; larger tables
+    // are converted by the segment kernels instead
+    const unsigned long long groups = (L.steps[0] + 7) / 8 + (L.steps[1] + 7) / 8;
+    const unsigned long long small = (unsigned long long)L.coarse[0] + L.coarse[1] + L.beq;
+    const unsigned long long threads = 2ull * n * ((pl->n_phi / 2 / unit_slots(pl->p) + 127) / 128) * 128;
+    if (groups >= (1ull << 30) || threads >= (1ull << 30) || small >= (1ull << 31))
+        return smerf_launch_sample(pl, seed, n, out, scratch, st, ev0, ev1);
     smerf_plan sh = *pl;  // shallow copy: the same plan reading FP32 copies of its tables
     unsigned char* p = (unsigned char*)stage;
-    auto take = [&](const void* src, size_t elems) {
-        float* dst = (float*)p;
+    auto take = [&](size_t elems) {
+        float* d = (float*)p;
         p += ((elems * sizeof(float) + 255) / 256) * 256;
-        return smerf_stage_tables((const double*)src, dst, elems, st) == SMERF_OK ? (void*)dst : nullptr;
+        return d;
     };
-    for (int c = 0; c < 2; ++c) sh.steps[c] = take(pl->steps[c], L.steps[c]);
-    for (int c = 0; c < 2; ++c) sh.coarse[c] = take(pl->coarse[c], L.coarse[c]);
-    sh.beq = take(pl->beq, L.beq);
-    if (!sh.steps[0] || !sh.steps[1] || !sh.coarse[0] || !sh.coarse[1] || !sh.beq) return SMERF_ECUDA;
+    StageJob job;
+    for (int c = 0; c < 2; ++c) {
+        job.src[c] = (const double*)pl->steps[c];
+        job.dst[c] = take(L.steps[c]);
+        job.n[c] = L.steps[c];
+        sh.steps[c] = job.dst[c];
+    }
+    job.rounds0 = job.rounds = 0;  // set by the launch
+    job.every = 1;
+    job.k_loop = 0;
+    StageSmall sm;
+    const void* ssrc[3] = {pl->coarse[0], pl->coarse[1], pl->beq};
+    const size_t sel[3] = {L.coarse[0], L.coarse[1], L.beq};
+    unsigned end = 0;
+    for (int q = 0; q < 3; ++q) {
+        sm.src[q] = (const double*)ssrc[q];
+        sm.dst[q] = take(sel[q]);
+        end += (unsigned)sel[q];
+        sm.end[q] = end;
+    }
+    sh.coarse[0] = sm.dst[0];
+    sh.coarse[1] = sm.dst[1];
+    sh.beq = sm.dst[2];
     sh.tab64 = false;
-    return smerf_launch_sample_ff(&sh, seed, n, out, scratch, st, ev0, ev1);
+    return pl->p == 1 ? smerf_launch_sample_staged_p1(&sh, sm, job, seed, n, out, scratch, st, ev0, ev1)
+                      : smerf_launch_sample_staged_p2(&sh, sm, job, seed, n, out, scratch, st, ev0, ev1);
 }
 
 int smerf_launch_sample(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch, cudaStream_t st,
@@ -164,6 +191,47 @@ int smerf_launch_normals(uint64_t key64, uint32_t ring, int64_t n, int fp64, voi
     else normals_kernel<float><<<(unsigned)((calls + 255) / 256), 256, 0, s>>>(key64, ring, n, (float*)out);
     return cudaGetLastError() == cudaSuccess ? SMERF_OK : SMERF_ECUDA;
 }
+
+// ---- per-call scratch (anchor states, staged tables, host-path field) comes from a memory
+// pool the library owns, one per device, that keeps its memory between calls: the default
+// pool returns its memory at every synchronisation, after which the next call's allocation
+// maps fresh memory on the stream.  smerf_scratch_trim returns what is not in use.
+namespace {
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+
+cudaMemPool_t scratch_pool(int dev, bool create)
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) return it->second;
+    if (!create) return nullptr;
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = UINT64_MAX;
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+        cudaMemPoolDestroy(pool);
+        return nullptr;
+    }
+    g_pools[dev] = pool;
+    return pool;
+}
+
+// stream-ordered scratch from the device's pool; under stream capture (a graph records the
+// allocation as its own node) and if the pool cannot be made, the stream's default pool
+cudaError_t scratch_alloc(void** p, size_t bytes, int dev, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return cudaGetLastError();
+    cudaMemPool_t pool = cs == cudaStreamCaptureStatusNone ? scratch_pool(dev, true) : nullptr;
+    return pool ? cudaMallocFromPoolAsync(p, bytes, pool, st) : cudaMallocAsync(p, bytes, st);
+}
+}  // namespace
 
 extern "C" {
 
@@ -345,13 +413,31 @@ int smerf_sample_timed(const smerf_plan* plan, uint64_t seed, int n_samples, voi
     void* scratch = nullptr;
     const size_t sb = (smerf_scratch_bytes(plan, n_samples) + 255) / 256 * 256;
     const size_t tb = smerf_stage_bytes(plan, n_samples);
-    cudaError_t e = cudaMallocAsync(&scratch, sb + tb, st);
+    cudaError_t e = scratch_alloc(&scratch, sb + tb, dev, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? SMERF_ENOMEM : SMERF_ECUDA;
     const int rc = smerf_launch_sample_staged(plan, seed, n_samples, out, scratch,
                                               tb ? (void*)((unsigned char*)scratch + sb) : nullptr, st,
                                               (cudaEvent_t)event_before_segments, (cudaEvent_t)event_after_segments);
     cudaFreeAsync(scratch, st);
     return rc;
+}
+
+int smerf_scratch_trim(void)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SMERF_ECUDA;
+    cudaMemPool_t pool = scratch_pool(dev, false);
+    if (pool && cudaMemPoolTrimTo(pool, 0) != cudaSuccess) return SMERF_ECUDA;
+    return SMERF_OK;
+}
+
+int smerf_sample_launches(const smerf_plan* plan, int n_samples)
+{
+    if (!plan || n_samples < 0) return SMERF_EINVAL;
+    if (n_samples == 0) return 0;
+    // anchor and segment launches, and ahead of them the short conversion of the coarse and
+    // start tables when the call stages FP64 tables (the anchor launch converts the step tables)
+    return use_stage(plan, n_samples) ? 3 : 2;
 }
 
 int smerf_sample_host(const smerf_plan* plan, uint64_t seed, int n_samples, void* host_out, void* stream)
@@ -371,7 +457,7 @@ int smerf_sample_host(const smerf_plan* plan, uint64_t seed, int n_samples, void
     cudaGetLastError();  // an unregistered pointer is not an error here
     const size_t bytes = (size_t)n_samples * plan->n_theta * plan->n_phi * (plan->recur64 ? 8 : 4);
     void* dout = nullptr;
-    cudaError_t e = cudaMallocAsync(&dout, bytes, st);
+    cudaError_t e = scratch_alloc(&dout, bytes, plan->dev, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? SMERF_ENOMEM : SMERF_ECUDA;
     int rc = smerf_sample(plan, seed, n_samples, dout, stream);
     if (rc == SMERF_OK && cudaMemcpyAsync(host_out, dout, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -398,6 +484,7 @@ int smerf_plan_info(const smerf_plan* plan, smerf_plan_info_t* info)
     info->n_segments = plan->n_segments;
     info->flags = plan->flags;
     info->table_bytes = plan->table_bytes;
+    info->step_table_bytes = plan->step_table_bytes;
     info->scratch_bytes_per_sample = smerf_scratch_bytes(plan, 1);
     info->setup_ms = plan->setup_ms;
     return SMERF_OK;

@@ -59,6 +59,7 @@ struct smerf_plan {
     void* tw2;
     void* tw3;
     size_t table_bytes;
+    size_t step_table_bytes;  // the two step tables' part of table_bytes
     double setup_ms;
     int dev;
     // launch parameters chosen by smerf_plan_autotune (valid = 0: built-in heuristic)
@@ -225,6 +226,36 @@ SMERF_DECLARE_TUNE(ff)
 SMERF_DECLARE_TUNE(fd)
 SMERF_DECLARE_TUNE(dd)
 SMERF_DECLARE_TUNE(df)
+
+// FP64 tables with FP32 recursion: the plan's two FP64 step tables (one per chain; the
+// tables the segment kernels read) converted to FP32 by the threads of the call's anchor
+// launch (smerf_sample_impl.cuh, anchor_stage_kernel).  The work is groups of eight elements,
+// taken in rounds of one group per thread: rounds [0, rounds0) cover table 0, [rounds0,
+// rounds) table 1; every anchor thread converts k_loop groups during its anchors, one every
+// `every` anchors, and the rest after them.
+constexpr int kStageParts = 2;
+struct StageJob {
+    const double* src[kStageParts];
+    float* dst[kStageParts];
+    unsigned long long n[kStageParts];  // elements
+    unsigned rounds0, rounds;           // set by the launch (they depend on its thread count)
+    int every, k_loop;                  // a round every `every` anchors, k_loop rounds in all
+};
+// the coarse and start tables (small: one row per anchor, one for the start ring) are staged
+// by a short launch ahead of the anchor launch, which reads them in FP32
+struct StageSmall {
+    const double* src[3];
+    float* dst[3];
+    unsigned end[3];  // cumulative element counts of coarse[0], coarse[1], beq
+};
+// the staged call for p = 1, 2 (smerf_sample_ff_p1.cu, smerf_sample_ff_p2.cu): plan `sh` reads
+// the FP32 copies S.dst and J.dst
+#define SMERF_DECLARE_STAGED(M)                                                                     \
+    int smerf_launch_sample_staged_p##M(const smerf_plan* sh, const StageSmall& S, const StageJob& J,      \
+                                        uint64_t seed, int n, void* out, void* scratch, cudaStream_t st,    \
+                                        cudaEvent_t ev0, cudaEvent_t ev1);
+SMERF_DECLARE_STAGED(1)
+SMERF_DECLARE_STAGED(2)
 
 // dynamic shared-memory attribute bookkeeping (smerf_api.cu)
 int smerf_smem_attr_done(const void* kern, int dev, size_t smem, bool record);

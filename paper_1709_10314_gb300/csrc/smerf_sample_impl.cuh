@@ -109,8 +109,123 @@ __device__ __forceinline__ void load_row(const TabT* p, Real (&t)[ROW])
 }
 
 // ------------------------------------------------------------------ anchors
-template <class Real, class TabT, int M>
-__device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r, int c)
+// anchors whose table values and normals are fetched ahead of the one being stepped
+__host__ __device__ constexpr int anchor_ahead(int M) { return M == 1 ? 4 : 2; }
+
+// Work an anchor thread carries out beside its anchors: prologue() before the first anchor,
+// step(j, d) at the end of anchor j's step (d = (j - 1) mod anchor_ahead(M)).  NoStage: none.
+struct NoStage {
+    __device__ __forceinline__ void prologue() {}
+    __device__ __forceinline__ void step(int, int) {}
+};
+
+// FP64 -> FP32 conversion of a plan's step tables carried by the anchor threads (StageJob),
+// so that the copies overlap the anchors' arithmetic instead of taking a launch of their own.
+// In round k thread g of T converts group l = (k - k_0) T + g (kStageGroup elements) of table
+// q (k_0 = 0 for q = 0, rounds0 for q = 1).  Rounds k < k_loop run during the thread's
+// anchors: the group is copied asynchronously into one of the thread's two shared-memory
+// slots (its destination noted beside the slot), then converted (tabcvt, the kernels' own
+// conversion) and stored at the end of anchor (k + 1) every, two rounds after its copy
+// started.  rest() runs the thread's remaining rounds one at a time (all of them if it had no
+// anchors to step).
+constexpr int kStageGroup = 8;      // elements per group: 64 bytes of FP64, 32 of FP32
+constexpr int kStageSlots = 2;      // groups in flight per thread
+struct StageCarrier {
+    const StageJob& J;
+    unsigned g, T;  // thread index and thread count of the launch (the host keeps both < 2^30)
+    unsigned sa;    // shared address of the thread's data slot 0 (slot s at + s * kDataStride)
+    unsigned sm;    // shared address of the thread's destination note 0 (+ s * kMetaStride)
+    int k = 0;          // next round to convert during the anchors
+    int countdown = 0;  // anchors until the next conversion
+
+    static constexpr unsigned kDataStride = 128 * 8 * kStageGroup;  // 128 threads x 64 bytes
+    static constexpr unsigned kMetaStride = 128 * 8;                // 128 threads x 8 bytes
+
+    // start round k's copy into slot s and note its destination (null: nothing to store; a
+    // group at a table's ragged end is converted at once); commits one copy group in every
+    // case, so that the counts of committed groups stay uniform
+    __device__ __forceinline__ void issue(int k, unsigned s) const
+    {
+        float* note = nullptr;
+        if ((unsigned)k < J.rounds) {
+            const bool q1 = (unsigned)k >= J.rounds0;
+            const unsigned l = ((unsigned)k - (q1 ? J.rounds0 : 0u)) * T + g;
+            const unsigned long long n = q1 ? J.n[1] : J.n[0];
+            const unsigned long long i = (unsigned long long)kStageGroup * l;
+            if (i < n) {
+                const double* src = (q1 ? J.src[1] : J.src[0]) + i;
+                float* dst = (q1 ? J.dst[1] : J.dst[0]) + i;
+                if (n - i >= kStageGroup) {
+                    const unsigned a = sa + s * kDataStride;
+#pragma unroll
+                    for (int e = 0; e < kStageGroup / 2; ++e)
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a + 16u * e), "l"(src + 2 * e));
+                    note = dst;
+                } else {
+                    for (int e = 0; e < (int)(n - i); ++e) dst[e] = tabcvt<float, double>(src[e]);
+                }
+            }
+        }
+        asm volatile("st.shared.u64 [%0], %1;\n" ::"r"(sm + s * kMetaStride), "l"(note));
+        asm volatile("cp.async.commit_group;\n" ::);
+    }
+    // convert and store the group in slot s (its copy has landed)
+    __device__ __forceinline__ void finish(unsigned s) const
+    {
+        float* dst;
+        asm volatile("ld.shared.u64 %0, [%1];\n" : "=l"(dst) : "r"(sm + s * kMetaStride));
+        if (!dst) return;
+        const unsigned a = sa + s * kDataStride;
+#pragma unroll
+        for (int e = 0; e < kStageGroup / 4; ++e) {
+            double x0, x1, x2, x3;
+            asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(x0), "=d"(x1) : "r"(a + 32u * e));
+            asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(x2), "=d"(x3) : "r"(a + 32u * e + 16u));
+            reinterpret_cast<float4*>(dst)[e] = make_float4(tabcvt<float, double>(x0), tabcvt<float, double>(x1),
+                                                            tabcvt<float, double>(x2), tabcvt<float, double>(x3));
+        }
+    }
+    __device__ __forceinline__ void issue_loop(int k, unsigned s) const
+    {
+        if (k < J.k_loop) {
+            issue(k, s);
+        } else {
+            asm volatile("cp.async.commit_group;\n" ::);
+        }
+    }
+    __device__ __forceinline__ void prologue()
+    {
+#pragma unroll
+        for (int s = 0; s < kStageSlots; ++s) issue_loop(s, s);
+        k = 0;
+        countdown = J.every;
+    }
+    // end of an anchor: every J.every anchors, round k (copied kStageSlots rounds ago) is
+    // converted and round k + kStageSlots started in its slot, spreading the copies over the
+    // anchors instead of crowding them into the first ones
+    __device__ __forceinline__ void step(int, int)
+    {
+        if (--countdown > 0) return;
+        countdown = J.every;
+        const unsigned s = (unsigned)k % kStageSlots;
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kStageSlots - 1));  // round k has landed
+        if (k < J.k_loop) finish(s);
+        issue_loop(k + kStageSlots, s);
+        ++k;
+    }
+    __device__ __forceinline__ void rest(bool stepped) const
+    {
+        asm volatile("cp.async.wait_all;\n" ::);
+        for (int k = stepped ? J.k_loop : 0; (unsigned)k < J.rounds; ++k) {
+            issue(k, 0);
+            asm volatile("cp.async.wait_all;\n" ::);
+            finish(0);
+        }
+    }
+};
+
+template <class Real, class TabT, int M, class Hook>
+__device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r, int c, Hook& hook)
 {
     constexpr int G = kG<M>;
     constexpr int T = tri(M);
@@ -156,7 +271,7 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
     // the whole parameter block to local memory)
     const TabT* cs = (const TabT*)(c == 0 ? P.coarse[0] : P.coarse[1]);
     const int na = c == 0 ? P.n_anchors[0] : P.n_anchors[1];
-    constexpr int AD = M == 1 ? 4 : 2;  // anchors prefetched ahead (the loads come from L2 or HBM)
+    constexpr int AD = anchor_ahead(M);  // anchors prefetched ahead (the loads come from L2 or HBM)
     Real tq[AD][G][2][Ec];
     Real nq[AD][4];
     const int k0 = P.k0, H = P.H, Ncm = P.Nc;  // copies: the lambda must not take P's address
@@ -184,6 +299,7 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
 #pragma unroll
     for (int d = 0; d < AD; ++d)
         if (1 + d <= na) fetch(1 + d, tq[d], nq[d]);
+    hook.prologue();
     for (int j0 = 1; j0 <= na; j0 += AD) {
 #pragma unroll
         for (int d = 0; d < AD; ++d) {
@@ -216,6 +332,7 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
                     for (int q = 0; q < M; ++q) v[g * 2 * M + part * M + q] = x[g][part][q];
             Vec4<Real>::st(anc + aoff<M>(P, c, r, j, 0, G * u), v);
             if (j + AD <= na) fetch(j + AD, tq[d], nq[d]);
+            hook.step(j, d);
         }
     }
     (void)T;
@@ -225,7 +342,26 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
 template <class Real, class TabT, int M>
 __global__ void __launch_bounds__(128, sizeof(Real) == 8 ? 4 : SMERF_ANCHOR_MINB) anchor_kernel(SampleParams P)
 {
-    anchor_body<Real, TabT, M>(P, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, blockIdx.z);
+    NoStage h;
+    anchor_body<Real, TabT, M>(P, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, blockIdx.z, h);
+}
+
+// anchor_kernel that also converts the plan's FP64 step tables to FP32 (StageCarrier); its
+// anchors read the coarse and start tables already staged as FP32
+template <class Real, class TabT, int M>
+__global__ void __launch_bounds__(128, SMERF_ANCHOR_MINB) anchor_stage_kernel(SampleParams P, StageJob J)
+{
+    static_assert(sizeof(Real) == 4 && sizeof(TabT) == 4, "staging converts FP64 tables for FP32 recursion");
+    __shared__ __align__(16) double slots[kStageSlots * 128 * kStageGroup];  // [slot][thread][group]
+    __shared__ __align__(8) unsigned long long notes[kStageSlots * 128];      // [slot][thread]
+    const unsigned T = gridDim.x * blockDim.x * gridDim.y * gridDim.z;
+    const unsigned g = ((blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
+    StageCarrier h{J, g, T, (unsigned)__cvta_generic_to_shared(slots + kStageGroup * threadIdx.x),
+                   (unsigned)__cvta_generic_to_shared(notes + threadIdx.x), 0, 0};
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool stepped = u < P.n_units && (int)blockIdx.y < P.n_samples;  // anchor_body's own test
+    if (stepped) anchor_body<Real, TabT, M>(P, u, blockIdx.y, blockIdx.z, h);
+    h.rest(stepped);
 }
 
 // batched: item = (request, block of 128 units, realisation, chain)
@@ -235,7 +371,8 @@ __global__ void __launch_bounds__(128, sizeof(Real) == 8 ? 4 : SMERF_ANCHOR_MINB
 {
     const int4 it = items[blockIdx.x];
     const SampleParams P = descs[it.x];
-    anchor_body<Real, TabT, M>(P, it.y * blockDim.x + threadIdx.x, it.z, it.w);
+    NoStage h;
+    anchor_body<Real, TabT, M>(P, it.y * blockDim.x + threadIdx.x, it.z, it.w, h);
 }
 
 // ------------------------------------------------------------------ FFT
@@ -1317,6 +1454,58 @@ int launch_sample_m(const smerf_plan* pl, uint64_t seed, int n, void* out, void*
     }
     if (ev0 && cudaEventRecord(ev0, st) != cudaSuccess) return SMERF_ECUDA;
     rc = dispatch_segments<Real, TabT, M>(P, pl->n_segments, cfg, st);
+    if (rc == SMERF_OK && ev1 && cudaEventRecord(ev1, st) != cudaSuccess) return SMERF_ECUDA;
+    return rc;
+}
+
+// FP64 coarse and start tables -> FP32 (a few rows per mode; one element per thread)
+static __global__ void __launch_bounds__(256) stage_small_kernel(StageSmall S)
+{
+    const unsigned total = S.end[2];
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int q = (i >= S.end[0]) + (i >= S.end[1]);
+        const unsigned i0 = q == 0 ? 0u : q == 1 ? S.end[0] : S.end[1];
+        const double* src = q == 0 ? S.src[0] : q == 1 ? S.src[1] : S.src[2];
+        float* dst = q == 0 ? S.dst[0] : q == 1 ? S.dst[1] : S.dst[2];
+        dst[i - i0] = tabcvt<float, double>(src[i - i0]);
+    }
+}
+
+// FP64 tables, FP32 recursion, tables staged: a short launch converting the coarse and start
+// tables, the anchor launch (FP32 tables) that also converts the step tables, then the segment
+// launch of the plan `sh`, whose table pointers are the FP32 copies.
+template <int M>
+int launch_sample_staged_m(const smerf_plan* sh, const StageSmall& S, StageJob J, uint64_t seed, int n, void* out,
+                           void* scratch, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1)
+{
+    SampleParams P;
+    SegConfig cfg;
+    int rc = fill_params<float, float>(sh, seed, n, out, scratch, P, cfg);
+    if (rc != SMERF_OK) return rc;
+    if (S.end[2] > 0) {
+        const unsigned blocks = (S.end[2] + 255) / 256;
+        stage_small_kernel<<<blocks < 152 * 8 ? blocks : 152 * 8, 256, 0, st>>>(S);
+        if (cudaGetLastError() != cudaSuccess) return SMERF_ECUDA;
+    }
+    {
+        dim3 ga((P.n_units + 127) / 128, n, 2);
+        // rounds per step table, and the rounds run during the anchors: one per anchor that
+        // every thread steps, no more than there are
+        const unsigned long long T = (unsigned long long)ga.x * 128 * ga.y * ga.z;
+        const unsigned long long r0 = ((J.n[0] + kStageGroup - 1) / kStageGroup + T - 1) / T;
+        const unsigned long long r1 = ((J.n[1] + kStageGroup - 1) / kStageGroup + T - 1) / T;
+        J.rounds0 = (unsigned)r0;
+        J.rounds = (unsigned)(r0 + r1);
+        // rounds converted during the anchors, one every `every` anchors, spread over the
+        // anchors that every thread steps
+        const int na_min = P.n_anchors[0] < P.n_anchors[1] ? P.n_anchors[0] : P.n_anchors[1];
+        J.every = J.rounds > 0 && (unsigned)na_min > J.rounds ? na_min / (int)J.rounds : 1;
+        J.k_loop = na_min / J.every < (int)J.rounds ? na_min / J.every : (int)J.rounds;
+        anchor_stage_kernel<float, float, M><<<ga, 128, 0, st>>>(P, J);
+        if (cudaGetLastError() != cudaSuccess) return SMERF_ECUDA;
+    }
+    if (ev0 && cudaEventRecord(ev0, st) != cudaSuccess) return SMERF_ECUDA;
+    rc = dispatch_segments<float, float, M>(P, sh->n_segments, cfg, st);
     if (rc == SMERF_OK && ev1 && cudaEventRecord(ev1, st) != cudaSuccess) return SMERF_ECUDA;
     return rc;
 }

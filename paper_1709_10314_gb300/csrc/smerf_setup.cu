@@ -737,6 +737,7 @@ int setup_impl(smerf_plan* pl)
     auto t_start = std::chrono::steady_clock::now();
 
     pl->table_bytes = 0;
+    pl->step_table_bytes = 0;
     CK(cudaMalloc(&pl->beq, (size_t)tri(M) * mp * es));
     CK(cudaMemset(pl->beq, 0, (size_t)tri(M) * mp * es));
     pl->table_bytes += (size_t)tri(M) * mp * es;
@@ -749,6 +750,7 @@ int setup_impl(smerf_plan* pl)
         CK(cudaMalloc(&pl->coarse[c], cb > 0 ? cb : 16));
         CK(cudaMemset(pl->coarse[c], 0, cb > 0 ? cb : 16));
         pl->table_bytes += sb + cb;
+        pl->step_table_bytes += sb;
     }
     rc = pl->recur64 ? upload_fft_tables<double>(pl->n_phi, &pl->tw, &pl->pre, &pl->tw2, &pl->tw3)
                      : upload_fft_tables<float>(pl->n_phi, &pl->tw, &pl->pre, &pl->tw2, &pl->tw3);

@@ -30,7 +30,8 @@ class _Info(ctypes.Structure):
                 ("chain_len", ctypes.c_int * 2), ("anchor_spacing", ctypes.c_int),
                 ("n_anchors", ctypes.c_int * 2), ("n_segments", ctypes.c_int),
                 ("flags", ctypes.c_uint), ("table_bytes", ctypes.c_size_t),
-                ("scratch_bytes_per_sample", ctypes.c_size_t), ("setup_ms", ctypes.c_double)]
+                ("scratch_bytes_per_sample", ctypes.c_size_t), ("setup_ms", ctypes.c_double),
+                ("step_table_bytes", ctypes.c_size_t)]
 
 
 _LIB = None
@@ -62,6 +63,10 @@ def _lib():
         L.smerf_sample_timed.restype = ip
         L.smerf_sample_noalloc.argtypes = [vp, ctypes.c_uint64, ip, vp, vp]
         L.smerf_sample_noalloc.restype = ip
+        L.smerf_scratch_trim.argtypes = []
+        L.smerf_scratch_trim.restype = ip
+        L.smerf_sample_launches.argtypes = [vp, ip]
+        L.smerf_sample_launches.restype = ip
         L.smerf_sample_host.argtypes = [vp, ctypes.c_uint64, ip, vp, vp]
         L.smerf_sample_host.restype = ip
         L.smerf_sample_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_uint64),
@@ -165,7 +170,15 @@ class Plan:
                 "start_ring": inf.start_ring, "chain_len": list(inf.chain_len),
                 "anchor_spacing": inf.anchor_spacing, "n_anchors": list(inf.n_anchors),
                 "n_segments": inf.n_segments, "flags": inf.flags, "table_bytes": inf.table_bytes,
-                "scratch_bytes_per_sample": inf.scratch_bytes_per_sample, "setup_ms": inf.setup_ms}
+                "scratch_bytes_per_sample": inf.scratch_bytes_per_sample, "setup_ms": inf.setup_ms,
+                "step_table_bytes": inf.step_table_bytes}
+
+    def launches(self, n_samples):
+        """smerf_sample_launches: kernels one sample() call of n_samples launches."""
+        v = _lib().smerf_sample_launches(self._h, int(n_samples))
+        if v < 0:
+            _check("smerf_sample_launches", v)
+        return v
 
     def autotune(self, n_samples, stream=None):
         """smerf_plan_autotune: returns (units/thread, realisations/CTA, producer threads, FFT
@@ -250,6 +263,11 @@ class Plan:
                                                               int(n_samples), ctypes.c_void_p(ptr),
                                                               _stream_ptr(stream)))
         return out
+
+
+def scratch_trim():
+    """smerf_scratch_trim: release the idle memory of the per-call scratch pool (current device)."""
+    _check("smerf_scratch_trim", _lib().smerf_scratch_trim())
 
 
 def sample_batched(plans, seeds, n_samples, outs, stream=None):

@@ -128,8 +128,27 @@ def test_staged_fp64_tables_equal_in_kernel_conversion():
     from paper_1709_10314_gb300 import SMERF_TABLES_FP64, sample_batched
     for kappa, nt, nphi, H in (([20.0, 50.0], 40, 128, 8), ([30.0], 33, 64, 4)):
         plan = _plan(kappa, nt, nphi, H, SMERF_TABLES_FP64)
+        # staged: a short conversion launch ahead of the anchor (which converts the step
+        # tables) and segment launches
+        assert (plan.launches(6), plan.launches(3), plan.launches(0)) == (3, 2, 0)
         staged = plan.sample(5, 6)
         out = torch.empty_like(staged)
         sample_batched([plan], [5], [6], [out])
         torch.cuda.synchronize()
         assert torch.equal(staged, out)
+
+
+def test_scratch_pool_kept_and_trimmed_between_calls():
+    # per-call scratch comes from the library's pool; trimming it between calls changes nothing
+    import torch
+    from paper_1709_10314_gb300 import SMERF_TABLES_FP64, scratch_trim
+    plan = _plan([20.0, 50.0], 40, 128, 8, SMERF_TABLES_FP64)
+    a = plan.sample(3, 6)
+    torch.cuda.synchronize()
+    scratch_trim()
+    b = plan.sample(3, 6)
+    host = plan.sample_host(3, 6)
+    torch.cuda.synchronize()
+    scratch_trim()
+    assert torch.equal(a, b)
+    assert np.array_equal(a.cpu().numpy(), host)
