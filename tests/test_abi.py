@@ -67,6 +67,12 @@ def test_bad_flags_and_spacing(lib):
     assert _create(lib, [1.0], 1, 1.0, 16, 32, H=-3)[0] == -1
 
 
+def test_launch_count_validation(lib):
+    lib.smerf_sample_launches.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.smerf_sample_launches.restype = ctypes.c_int
+    assert lib.smerf_sample_launches(None, 4) == -1
+
+
 def test_status_strings(lib):
     lib.smerf_status_string.restype = ctypes.c_char_p
     assert lib.smerf_status_string(0) == b"ok"
