@@ -263,6 +263,162 @@ __global__ void step_kernel(Spec sp, int c, int len, double* phi, double* qout)
         }
 }
 
+// ---- p = 1 with a real spectrum: the step tables by a recurrence in m (Alg. 1 sets up the
+// hypergeometric functions of every order m).  For fixed x the series of
+// Eq. (Legendre_hypergeometric), F_m(x) = 2F1(-lambda, lambda+1; 1+m; x) with
+// (-lambda)(lambda+1) = kappa^2, satisfy Gauss's contiguous relation in the third parameter,
+//   F_{m-1} = [(1-2x) F_m + (1 + kappa^2/(m(m+1))) x F_{m+1}] / (1-x),   m >= 1.
+// F_m tends to 1 as m grows while the relation's other solutions grow factorially, so taken
+// downward from two series values it is stable (relative error of order m eps; ratios of F at
+// nearby x, which is what the tables use, to a few 1e-13 over 16384 orders).  Per step the
+// construction is step_kernel's for M = 1: A = (t2/t1)^m F_m(x2)/F_m(x1) and
+// Q = (A_amp/2 pi) int_0^du e^{-2 m v} (F_m(x2)/F_m(x(v)))^2 dv, on one node set for all m:
+// composite 8-point Gauss-Legendre panels no wider than 4/rho(m) for every m whose weight
+// e^{-2 m v} at the panel's start is above e^-46 (the same panel rule as step_kernel).
+constexpr int kRecWarps = 4;         // warps per block, one step each
+constexpr int kRecMaxPanels = 8192;  // node-set cap (reached only by grids far beyond 16384 rings)
+
+// the series F_mu(x) as S * 2^(250 E)
+__device__ void hyp_scaled2(double k2, int mu, double x, double& S, int& E)
+{
+    double s = 1.0, t = 1.0;
+    int e = 0;
+    const double m1 = (double)mu + 1.0;
+    for (int n = 0; n < 1000000; n += 2) {
+        const double dn = (double)n;
+        const double a0 = (dn * (dn + 1.0) + k2) * x, d0 = (dn + m1) * (dn + 1.0);
+        const double a1 = ((dn + 1.0) * (dn + 2.0) + k2) * x, d1 = (dn + 1.0 + m1) * (dn + 2.0);
+        const double inv = 1.0 / (d0 * d1);
+        const double r0 = a0 * d1 * inv, r1 = a1 * d0 * inv;
+        t *= r0;
+        s += t;
+        if (t < 1e-17 * s && r0 < 0.9) break;
+        t *= r1;
+        s += t;
+        if (t < 1e-17 * s && r1 < 0.9) break;
+        if (s > 0x1p250) { s *= 0x1p-250; t *= 0x1p-250; ++e; }
+    }
+    S = s;
+    E = e;
+}
+
+// width of the panel that starts at v: 4/rho(m*), m* the largest order whose weight e^{-2 m v}
+// is above e^-46 at v, rho(m) = 2m + kap
+__device__ inline double rec_panel_width(double v, int mtop, double kap)
+{
+    const double ms = v > 0.0 ? fmin((double)mtop, floor(23.0 / v)) : (double)mtop;
+    return 4.0 / (2.0 * ms + kap);
+}
+
+// One warp per step of the northern chain (pos = 1..len).  Lane 0 holds x2 (the step's
+// poleward ring), lane 1 x1, lanes 2..31 up to 30 quadrature nodes (further nodes in further
+// passes, which start at the highest order whose weight at their nodes is above e^-46).  The
+// lanes run the recurrence downward in m together; per block of 32 orders they leave
+// w_j e^{-2 m v_j} / F_m(x_j)^2 in shared memory, and lane l then sums order m_l's row in a
+// fixed order, so that Q_m = (A_amp/2 pi) F_m(x2)^2 sum_j ... (the common scale of the F's
+// cancels).
+__global__ void __launch_bounds__(32 * kRecWarps) step_kernel_rec(Spec sp, int len, double* phi, double* qout)
+{
+    __shared__ double tile[kRecWarps][32][33];  // [order in block][lane]
+    __shared__ double fr2[kRecWarps][32], fr1[kRecWarps][32], alph[kRecWarps][32];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pos = blockIdx.x * kRecWarps + wib + 1;
+    if (pos > len) return;  // whole warps
+    const unsigned full = 0xffffffffu;
+    const double th1 = chain_theta(sp, 0, pos - 1), th2 = chain_theta(sp, 0, pos);
+    const double u1 = log(tan(0.5 * th1)), u2 = log(tan(0.5 * th2));
+    const double du = u1 - u2;
+    const double sa = sin(0.5 * th1), sb = sin(0.5 * th2);
+    const double x1r = sa * sa, x2r = sb * sb;
+    const double sinmax = th1 > 0.5 * SMERF_PI ? 1.0 : sin(th1);
+    const double kap = 2.0 * sp.kmax * sinmax + 1.0;
+    const double k2 = sp.k2[0];
+    const double f = sp.A / (2.0 * SMERF_PI);
+    const int mtop = sp.n_modes - 1;
+    int np = 0;
+    for (double v = 0.0; v < du && np < kRecMaxPanels; ++np) v += rec_panel_width(v, mtop, kap);
+    const int K = 8 * np;
+    const int passes = (K + 29) / 30;
+    const size_t base = (size_t)pos * sp.n_modes;
+    for (int ch = 0; ch < passes; ++ch) {
+        // this lane's point: x, quadrature weight, v
+        double x = x2r, wt = 0.0, v = 0.0;
+        if (lane == 1) {
+            x = x1r;
+            v = du;
+        } else if (lane >= 2 && 30 * ch + lane - 2 < K) {
+            const int i = 30 * ch + lane - 2, j = i >> 3, n = i & 7;
+            double b = 0.0;
+            for (int q = 0; q < j; ++q) b += rec_panel_width(b, mtop, kap);
+            const double h = (j == np - 1 || b + rec_panel_width(b, mtop, kap) > du) ? du - b
+                                                                                       : rec_panel_width(b, mtop, kap);
+            v = b + 0.5 * (kGL8x[n] + 1.0) * h;
+            wt = 0.5 * h * kGL8w[n];
+            x = 1.0 / (1.0 + exp(-2.0 * (u2 + v)));
+        }
+        // highest order of the pass: every order for the first (it also gives A), else the
+        // last whose weight at the pass's first node is above e^-46
+        int mstart = mtop;
+        if (ch > 0) {
+            const double vmin = __shfl_sync(full, v, 2);
+            mstart = vmin > 0.0 ? (int)fmin((double)mtop, floor(23.0 / vmin)) : mtop;
+        }
+        double S0, S1;
+        int E0, E1;
+        hyp_scaled2(k2, mstart, x, S0, E0);
+        hyp_scaled2(k2, mstart + 1, x, S1, E1);
+        int W = E0;  // common scale of the lanes' values
+        for (int o = 16; o > 0; o >>= 1) W = max(W, __shfl_xor_sync(full, W, o));
+        double F = ldexp(S0, 250 * (E0 - W)), Fp = ldexp(S1, 250 * (E1 - W));
+        const double beta = (1.0 - 2.0 * x) / (1.0 - x), gam = x / (1.0 - x);
+        const double e2v = exp(2.0 * v);
+        for (int mb = mstart; mb >= 0; mb -= 32) {
+            {
+                const int ml = mb - lane;
+                alph[wib][lane] = ml >= 1 ? k2 / ((double)ml * (double)(ml + 1)) : 0.0;
+            }
+            __syncwarp();
+            double Ew = exp(-2.0 * (double)mb * v);  // e^{-2 m v}, exact at the block's first order
+            for (int k = 0; k < 32; ++k) {
+                const int m = mb - k;
+                if (m < 0) break;
+                const double r = 1.0 / F;
+                tile[wib][k][lane] = wt * Ew * r * r;
+                if (lane == 0) fr2[wib][k] = F;
+                if (lane == 1) fr1[wib][k] = F;
+                if (m >= 1) {
+                    const double t = gam + gam * alph[wib][k];
+                    const double Fn = beta * F + t * Fp;
+                    Fp = F;
+                    F = Fn;
+                    // a common rescale keeps the values, their squares and the squares of their
+                    // reciprocals in range (ratios are unchanged)
+                    if (__any_sync(full, (__double2hiint(F) & 0x7ff00000) > ((1023 + 250) << 20))) {
+                        F *= 0x1p-250;
+                        Fp *= 0x1p-250;
+                    }
+                }
+                Ew *= e2v;
+            }
+            __syncwarp();
+            const int m = mb - lane;
+            if (m >= 0) {
+                double sum = 0.0;
+                for (int j = 2; j < 32; ++j) sum += tile[wib][lane][j];
+                const double F2 = fr2[wib][lane];
+                const double q = f * F2 * F2 * sum;
+                if (ch == 0) {
+                    qout[base + m] = q;
+                    phi[base + m] = exp(-(double)m * du) * F2 / fr1[wib][lane];
+                } else {
+                    qout[base + m] += q;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
 // Table store.  FP64 tables keep every entry at magnitude >= 2^-120 (zeros and smaller
 // values become +-2^-120, a change far below any effect on the field): FP32-recursion
 // kernels then convert them to FP32 with three integer instructions and no range check.
@@ -773,6 +929,7 @@ int setup_impl(smerf_plan* pl)
             if (len0 > 65535) { rc = SMERF_EUNSUPPORTED; goto done; }
             dim3 grid(gm, len0);
             if (pl->complex_spec) step_kernel_c<M><<<grid, threads>>>(make_spec_c(pl), len0, phi, qv);
+            else if (M == 1) step_kernel_rec<<<(len0 + kRecWarps - 1) / kRecWarps, 32 * kRecWarps>>>(sp, len0, phi, qv);
             else step_kernel<M><<<grid, threads>>>(sp, 0, len0, phi, qv);
             CK(cudaGetLastError());
         }
