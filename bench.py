@@ -117,11 +117,14 @@ class Clocks:
 
 
 def csrc_digest():
+    """Digest of the sources the sampling kernels are built from (their templates and their
+    instantiation units); the committed DRAM-traffic record is valid while it matches."""
     import glob
     import hashlib
     h = hashlib.sha256()
     base = os.path.join(ROOT, "paper_1709_10314_gb300", "csrc")
-    for f in sorted(glob.glob(os.path.join(base, "*.cu")) + glob.glob(os.path.join(base, "*.cuh"))):
+    for f in sorted(glob.glob(os.path.join(base, "smerf_sample_*.cu")) +
+                    [os.path.join(base, "smerf_sample_impl.cuh"), os.path.join(base, "smerf_internal.cuh")]):
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -268,9 +268,12 @@ __global__ void step_kernel(Spec sp, int c, int len, double* phi, double* qout)
 // Eq. (Legendre_hypergeometric), F_m(x) = 2F1(-lambda, lambda+1; 1+m; x) with
 // (-lambda)(lambda+1) = kappa^2, satisfy Gauss's contiguous relation in the third parameter,
 //   F_{m-1} = [(1-2x) F_m + (1 + kappa^2/(m(m+1))) x F_{m+1}] / (1-x),   m >= 1.
-// F_m tends to 1 as m grows while the relation's other solutions grow factorially, so taken
-// downward from two series values it is stable (relative error of order m eps; ratios of F at
-// nearby x, which is what the tables use, to a few 1e-13 over 16384 orders).  Per step the
+// For large m its solutions behave like 1 (F_m itself) and like (-(1-x)/x)^m, so for x < 1/2
+// F_m is the minimal solution and the relation taken downward from two series values is
+// stable (relative error of order m eps; ratios of F at nearby x, which is what the tables
+// use, to a few 1e-13 over 16384 orders).  For x > 1/2 it is not: the first step, whose
+// equatorward ring lies south of the equator for even n_theta, keeps step_kernel's per-mode
+// series (and every later step of the northern chain has x < 1/2).  Per step the
 // construction is step_kernel's for M = 1: A = (t2/t1)^m F_m(x2)/F_m(x1) and
 // Q = (A_amp/2 pi) int_0^du e^{-2 m v} (F_m(x2)/F_m(x(v)))^2 dv, on one node set for all m:
 // composite 8-point Gauss-Legendre panels no wider than 4/rho(m) for every m whose weight
@@ -310,7 +313,7 @@ __device__ inline double rec_panel_width(double v, int mtop, double kap)
     return 4.0 / (2.0 * ms + kap);
 }
 
-// One warp per step of the northern chain (pos = 1..len).  Lane 0 holds x2 (the step's
+// One warp per step of the northern chain (pos = 2..len).  Lane 0 holds x2 (the step's
 // poleward ring), lane 1 x1, lanes 2..31 up to 30 quadrature nodes (further nodes in further
 // passes, which start at the highest order whose weight at their nodes is above e^-46).  The
 // lanes run the recurrence downward in m together; per block of 32 orders they leave
@@ -322,7 +325,7 @@ __global__ void __launch_bounds__(32 * kRecWarps) step_kernel_rec(Spec sp, int l
     __shared__ double tile[kRecWarps][32][33];  // [order in block][lane]
     __shared__ double fr2[kRecWarps][32], fr1[kRecWarps][32], alph[kRecWarps][32];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int pos = blockIdx.x * kRecWarps + wib + 1;
+    const int pos = blockIdx.x * kRecWarps + wib + 2;
     if (pos > len) return;  // whole warps
     const unsigned full = 0xffffffffu;
     const double th1 = chain_theta(sp, 0, pos - 1), th2 = chain_theta(sp, 0, pos);
@@ -929,8 +932,13 @@ int setup_impl(smerf_plan* pl)
             if (len0 > 65535) { rc = SMERF_EUNSUPPORTED; goto done; }
             dim3 grid(gm, len0);
             if (pl->complex_spec) step_kernel_c<M><<<grid, threads>>>(make_spec_c(pl), len0, phi, qv);
-            else if (M == 1) step_kernel_rec<<<(len0 + kRecWarps - 1) / kRecWarps, 32 * kRecWarps>>>(sp, len0, phi, qv);
-            else step_kernel<M><<<grid, threads>>>(sp, 0, len0, phi, qv);
+            else if (M == 1) {
+                // the first step by the per-mode series, the rest by the recurrence in m
+                step_kernel<M><<<dim3(gm, 1), threads>>>(sp, 0, 1, phi, qv);
+                if (len0 > 1) step_kernel_rec<<<(len0 - 1 + kRecWarps - 1) / kRecWarps, 32 * kRecWarps>>>(sp, len0, phi, qv);
+            } else {
+                step_kernel<M><<<grid, threads>>>(sp, 0, len0, phi, qv);
+            }
             CK(cudaGetLastError());
         }
         for (int c = 0; c < 2; ++c) {

@@ -93,3 +93,24 @@ def test_tables_match_gaussian_conditioning(kappa, n_theta, H):
                 A_, B_ = _unpack(plan.tables(2, c, j + 1)[:, m], M, "coarse")
                 prev = k0 if j == 0 else ch[anchors[j - 1] - 1]
                 _check_block(S, M, pos_of[ch[a - 1]], [pos_of[prev]], A_, None, B_, sign, tol, m)
+
+
+@pytest.mark.parametrize("kappa", [[40.0], [150.0]])
+def test_p1_tables_at_high_orders(kappa):
+    # p = 1 step tables come from a downward recurrence over every order m (Alg. 1 with the
+    # contiguous relation); check them at orders spread over 0..512 on a 24-ring grid
+    from paper_1709_10314_gb300 import SMERF_RECUR_FP64, SMERF_ORDER_PAPER, Plan
+    M, n_theta, n_phi = 1, 24, 1024
+    plan = Plan(kappa, 1.0, n_theta, n_phi, flags=SMERF_RECUR_FP64 | SMERF_ORDER_PAPER, anchor_spacing=0)
+    ms = [0, 1, 2, 37, 200, 511, 512]
+    order, Ss, _ = oracle.joint_factors(kappa, 1.0, n_theta, n_phi, H=0, modes=ms)
+    pos_of = _ring_pos(order)
+    k0, north, south, _, _ = oracle.chain_layout(n_theta, 0)
+    for i, m in enumerate(ms):
+        S = Ss[i]
+        for c, ch in enumerate([north, south]):
+            sign = np.array([-1.0 if c == 1 else 1.0])
+            for p in range(1, len(ch) + 1):
+                left = k0 if p == 1 else ch[p - 2]
+                A_, C_, B_ = _unpack(plan.tables(1, c, p)[:, m], M, "step")
+                _check_block(S, M, pos_of[ch[p - 1]], [pos_of[left]], A_, None, B_, sign, 2e-8, m)
