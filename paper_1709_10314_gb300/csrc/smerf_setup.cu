@@ -271,9 +271,10 @@ __global__ void step_kernel(Spec sp, int c, int len, double* phi, double* qout)
 // For large m its solutions behave like 1 (F_m itself) and like (-(1-x)/x)^m, so for x < 1/2
 // F_m is the minimal solution and the relation taken downward from two series values is
 // stable (relative error of order m eps; ratios of F at nearby x, which is what the tables
-// use, to a few 1e-13 over 16384 orders).  For x > 1/2 it is not: the first step, whose
-// equatorward ring lies south of the equator for even n_theta, keeps step_kernel's per-mode
-// series (and every later step of the northern chain has x < 1/2).  Per step the
+// use, to a few 1e-13 over 16384 orders).  For x > 1/2 the error grows by x/(1-x) per order:
+// only the first step's equatorward ring can have x > 1/2 (south of the equator, even n_theta);
+// that step keeps step_kernel's per-mode series unless the growth over all orders,
+// (x/(1-x))^m_max, stays below 1e3 (it is about e^pi = 23 when n_phi = 2 n_theta).  Per step the
 // construction is step_kernel's for M = 1: A = (t2/t1)^m F_m(x2)/F_m(x1) and
 // Q = (A_amp/2 pi) int_0^du e^{-2 m v} (F_m(x2)/F_m(x(v)))^2 dv, on one node set for all m:
 // composite 8-point Gauss-Legendre panels no wider than 4/rho(m) for every m whose weight
@@ -313,19 +314,19 @@ __device__ inline double rec_panel_width(double v, int mtop, double kap)
     return 4.0 / (2.0 * ms + kap);
 }
 
-// One warp per step of the northern chain (pos = 2..len).  Lane 0 holds x2 (the step's
+// One warp per step of the northern chain (pos = first..len).  Lane 0 holds x2 (the step's
 // poleward ring), lane 1 x1, lanes 2..31 up to 30 quadrature nodes (further nodes in further
 // passes, which start at the highest order whose weight at their nodes is above e^-46).  The
 // lanes run the recurrence downward in m together; per block of 32 orders they leave
 // w_j e^{-2 m v_j} / F_m(x_j)^2 in shared memory, and lane l then sums order m_l's row in a
 // fixed order, so that Q_m = (A_amp/2 pi) F_m(x2)^2 sum_j ... (the common scale of the F's
 // cancels).
-__global__ void __launch_bounds__(32 * kRecWarps) step_kernel_rec(Spec sp, int len, double* phi, double* qout)
+__global__ void __launch_bounds__(32 * kRecWarps) step_kernel_rec(Spec sp, int first, int len, double* phi, double* qout)
 {
     __shared__ double tile[kRecWarps][32][33];  // [order in block][lane]
     __shared__ double fr2[kRecWarps][32], fr1[kRecWarps][32], alph[kRecWarps][32];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int pos = blockIdx.x * kRecWarps + wib + 2;
+    const int pos = blockIdx.x * kRecWarps + wib + first;
     if (pos > len) return;  // whole warps
     const unsigned full = 0xffffffffu;
     const double th1 = chain_theta(sp, 0, pos - 1), th2 = chain_theta(sp, 0, pos);
@@ -415,6 +416,149 @@ __global__ void __launch_bounds__(32 * kRecWarps) step_kernel_rec(Spec sp, int l
                     phi[base + m] = exp(-(double)m * du) * F2 / fr1[wib][lane];
                 } else {
                     qout[base + m] += q;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// p = 2 with a real spectrum: the same recurrence for both kappa_i.  Per order m a lane's
+// point x has H(x) = [[F^1_m, F^2_m], [r_1 F^1_{m+1}, r_2 F^2_{m+1}]], r_i = (m(m+1)+kappa_i^2)/(m+1)
+// (step_kernel's H up to a scale per column, which cancels in A = H2 H1^-1 and in
+// phi = W H^-1 e_1), each column with its own common rescale.  A node's
+// phi = diag(t2^-1, 1) H2 H(x)^-1 e_1 is formed from H2's entries (broadcast from lane 0) and
+// the node's own before squaring (no cancellation); its three products go through shared
+// memory as in step_kernel_rec.  One warp per block (three transposition tiles).
+__global__ void __launch_bounds__(32) step_kernel_rec2(Spec sp, int first, int len, double* phi, double* qout)
+{
+    constexpr int M = 2;
+    __shared__ double tile[3][32][33];  // [product][order in block][lane]
+    __shared__ double h2[4][32], h1[4][32], alph[2][32], rr[2][32];
+    const int lane = threadIdx.x & 31;
+    const int pos = blockIdx.x + first;
+    if (pos > len) return;
+    const unsigned full = 0xffffffffu;
+    const double th1 = chain_theta(sp, 0, pos - 1), th2 = chain_theta(sp, 0, pos);
+    const double t1 = tan(0.5 * th1), t2 = tan(0.5 * th2);
+    const double u1 = log(t1), u2 = log(t2);
+    const double du = u1 - u2;
+    const double sa = sin(0.5 * th1), sb = sin(0.5 * th2);
+    const double x1r = sa * sa, x2r = sb * sb;
+    const double sinmax = th1 > 0.5 * SMERF_PI ? 1.0 : sin(th1);
+    const double kap = 2.0 * sp.kmax * sinmax + 1.0;
+    const double f = sp.A / (2.0 * SMERF_PI);
+    const int mtop = sp.n_modes - 1;
+    // panel width at v: 4/rho(m*), rho(m) = 2(m + M - 1) + kap, m* the largest order whose
+    // weight e^{-2(m+M-1)v} is above e^-46 at v
+    auto width = [&](double v) {
+        const double ms = v > 0.0 ? fmax(0.0, fmin((double)mtop, floor(23.0 / v) - (M - 1))) : (double)mtop;
+        return 4.0 / (2.0 * (ms + M - 1) + kap);
+    };
+    int np = 0;
+    for (double v = 0.0; v < du && np < kRecMaxPanels; ++np) v += width(v);
+    const int K = 8 * np;
+    const int passes = (K + 29) / 30;
+    const size_t base = (size_t)pos * sp.n_modes;
+    for (int ch = 0; ch < passes; ++ch) {
+        double x = x2r, wt = 0.0, v = 0.0;
+        if (lane == 1) {
+            x = x1r;
+            v = du;
+        } else if (lane >= 2 && 30 * ch + lane - 2 < K) {
+            const int i = 30 * ch + lane - 2, j = i >> 3, n = i & 7;
+            double b = 0.0;
+            for (int q = 0; q < j; ++q) b += width(b);
+            const double h = (j == np - 1 || b + width(b) > du) ? du - b : width(b);
+            v = b + 0.5 * (kGL8x[n] + 1.0) * h;
+            wt = 0.5 * h * kGL8w[n];
+            x = 1.0 / (1.0 + exp(-2.0 * (u2 + v)));
+        }
+        int mstart = mtop;
+        if (ch > 0) {
+            const double vmin = __shfl_sync(full, v, 2);
+            mstart = vmin > 0.0 ? (int)fmax(0.0, fmin((double)mtop, floor(23.0 / vmin) - (M - 1))) : mtop;
+        }
+        double F[2], Fp[2];
+        for (int c = 0; c < 2; ++c) {
+            double S0, S1;
+            int E0, E1;
+            hyp_scaled2(sp.k2[c], mstart, x, S0, E0);
+            hyp_scaled2(sp.k2[c], mstart + 1, x, S1, E1);
+            int W = E0;
+            for (int o = 16; o > 0; o >>= 1) W = max(W, __shfl_xor_sync(full, W, o));
+            F[c] = ldexp(S0, 250 * (E0 - W));
+            Fp[c] = ldexp(S1, 250 * (E1 - W));
+        }
+        const double beta = (1.0 - 2.0 * x) / (1.0 - x), gam = x / (1.0 - x);
+        const double e2v = exp(2.0 * v);
+        for (int mb = mstart; mb >= 0; mb -= 32) {
+            {
+                const int ml = mb - lane;
+                for (int c = 0; c < 2; ++c) {
+                    alph[c][lane] = ml >= 1 ? sp.k2[c] / ((double)ml * (double)(ml + 1)) : 0.0;
+                    rr[c][lane] = ml >= 0 ? ((double)ml * (double)(ml + 1) + sp.k2[c]) / (double)(ml + 1) : 0.0;
+                }
+            }
+            __syncwarp();
+            double Ew = exp(-2.0 * (double)(mb + M - 1) * v);
+            for (int k = 0; k < 32; ++k) {
+                const int m = mb - k;
+                if (m < 0) break;
+                const double a = F[0], b = F[1], c = rr[0][k] * Fp[0], d = rr[1][k] * Fp[1];
+                const double a2 = __shfl_sync(full, a, 0), b2 = __shfl_sync(full, b, 0);
+                const double c2 = __shfl_sync(full, c, 0), d2 = __shfl_sync(full, d, 0);
+                const double rdet = 1.0 / (a * d - b * c);
+                const double p0 = (b2 * a - a2 * b) * rdet, p1 = (d2 * a - c2 * b) * rdet;
+                const double we = wt * Ew;
+                tile[0][k][lane] = we * p0 * p0;
+                tile[1][k][lane] = we * p0 * p1;
+                tile[2][k][lane] = we * p1 * p1;
+                if (lane == 0) { h2[0][k] = a; h2[1][k] = b; h2[2][k] = c; h2[3][k] = d; }
+                if (lane == 1) { h1[0][k] = a; h1[1][k] = b; h1[2][k] = c; h1[3][k] = d; }
+                if (m >= 1) {
+                    for (int cc = 0; cc < 2; ++cc) {
+                        const double t = gam + gam * alph[cc][k];
+                        const double Fn = beta * F[cc] + t * Fp[cc];
+                        Fp[cc] = F[cc];
+                        F[cc] = Fn;
+                        if (__any_sync(full, (__double2hiint(F[cc]) & 0x7ff00000) > ((1023 + 250) << 20))) {
+                            F[cc] *= 0x1p-250;
+                            Fp[cc] *= 0x1p-250;
+                        }
+                    }
+                }
+                Ew *= e2v;
+            }
+            __syncwarp();
+            const int m = mb - lane;
+            if (m >= 0) {
+                double s00 = 0.0, s01 = 0.0, s11 = 0.0;
+                for (int j = 2; j < 32; ++j) {
+                    s00 += tile[0][lane][j];
+                    s01 += tile[1][lane][j];
+                    s11 += tile[2][lane][j];
+                }
+                const size_t o = (base + m) * (M * M);
+                const double q00 = f * s00 / (t2 * t2), q01 = f * s01 / t2, q11 = f * s11;
+                if (ch == 0) {
+                    qout[o + 0] = q00;
+                    qout[o + 1] = q01;
+                    qout[o + 2] = q01;
+                    qout[o + 3] = q11;
+                    // A = (t2/t1)^m diag(t2^p) H2 H1^-1 diag(t1^-q)
+                    const double a2 = h2[0][lane], b2 = h2[1][lane], c2 = h2[2][lane], d2 = h2[3][lane];
+                    const double a1 = h1[0][lane], b1 = h1[1][lane], c1 = h1[2][lane], d1 = h1[3][lane];
+                    const double g = exp(-(double)m * du) / (a1 * d1 - b1 * c1);
+                    phi[o + 0] = g * (a2 * d1 - b2 * c1);
+                    phi[o + 1] = g * (b2 * a1 - a2 * b1) / t1;
+                    phi[o + 2] = g * t2 * (c2 * d1 - d2 * c1);
+                    phi[o + 3] = g * t2 * (d2 * a1 - c2 * b1) / t1;
+                } else {
+                    qout[o + 0] += q00;
+                    qout[o + 1] += q01;
+                    qout[o + 2] += q01;
+                    qout[o + 3] += q11;
                 }
             }
             __syncwarp();
@@ -932,12 +1076,19 @@ int setup_impl(smerf_plan* pl)
             if (len0 > 65535) { rc = SMERF_EUNSUPPORTED; goto done; }
             dim3 grid(gm, len0);
             if (pl->complex_spec) step_kernel_c<M><<<grid, threads>>>(make_spec_c(pl), len0, phi, qv);
-            else if (M == 1) {
-                // the first step by the per-mode series, the rest by the recurrence in m
-                step_kernel<M><<<dim3(gm, 1), threads>>>(sp, 0, 1, phi, qv);
-                if (len0 > 1) step_kernel_rec<<<(len0 - 1 + kRecWarps - 1) / kRecWarps, 32 * kRecWarps>>>(sp, len0, phi, qv);
-            } else {
-                step_kernel<M><<<grid, threads>>>(sp, 0, len0, phi, qv);
+            else {
+                // the recurrence in m, but for a first step whose equatorward ring (x > 1/2) would
+                // amplify rounding errors by more than 1e3 over the orders: that one by the
+                // per-mode series
+                const double th = chain_theta(sp, 0, 0), x1 = sin(0.5 * th) * sin(0.5 * th);
+                const bool first_series = x1 > 0.5 && (double)(pl->n_modes - 1) * log(x1 / (1.0 - x1)) > log(1e3);
+                const int first = first_series ? 2 : 1;
+                if (first_series) step_kernel<M><<<dim3(gm, 1), threads>>>(sp, 0, 1, phi, qv);
+                if (len0 >= first) {
+                    const int n = len0 - first + 1;
+                    if (M == 1) step_kernel_rec<<<(n + kRecWarps - 1) / kRecWarps, 32 * kRecWarps>>>(sp, first, len0, phi, qv);
+                    else step_kernel_rec2<<<n, 32>>>(sp, first, len0, phi, qv);
+                }
             }
             CK(cudaGetLastError());
         }

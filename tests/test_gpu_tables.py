@@ -95,12 +95,12 @@ def test_tables_match_gaussian_conditioning(kappa, n_theta, H):
                 _check_block(S, M, pos_of[ch[a - 1]], [pos_of[prev]], A_, None, B_, sign, tol, m)
 
 
-@pytest.mark.parametrize("kappa", [[40.0], [150.0]])
-def test_p1_tables_at_high_orders(kappa):
-    # p = 1 step tables come from a downward recurrence over every order m (Alg. 1 with the
-    # contiguous relation); check them at orders spread over 0..512 on a 24-ring grid
+@pytest.mark.parametrize("kappa", [[40.0], [150.0], [20.0, 50.0], [40.0, 130.0]])
+def test_tables_at_high_orders(kappa):
+    # step tables (real spectra) come from a downward recurrence over every order m (Alg. 1
+    # with the contiguous relation); check them at orders spread over 0..512 on a 24-ring grid
     from paper_1709_10314_gb300 import SMERF_RECUR_FP64, SMERF_ORDER_PAPER, Plan
-    M, n_theta, n_phi = 1, 24, 1024
+    M, n_theta, n_phi = len(kappa), 24, 1024
     plan = Plan(kappa, 1.0, n_theta, n_phi, flags=SMERF_RECUR_FP64 | SMERF_ORDER_PAPER, anchor_spacing=0)
     ms = [0, 1, 2, 37, 200, 511, 512]
     order, Ss, _ = oracle.joint_factors(kappa, 1.0, n_theta, n_phi, H=0, modes=ms)
@@ -109,7 +109,7 @@ def test_p1_tables_at_high_orders(kappa):
     for i, m in enumerate(ms):
         S = Ss[i]
         for c, ch in enumerate([north, south]):
-            sign = np.array([-1.0 if c == 1 else 1.0])
+            sign = np.array([(-1.0) ** q if c == 1 else 1.0 for q in range(M)])
             for p in range(1, len(ch) + 1):
                 left = k0 if p == 1 else ch[p - 2]
                 A_, C_, B_ = _unpack(plan.tables(1, c, p)[:, m], M, "step")
