@@ -910,14 +910,6 @@ __global__ void step_kernel_c(SpecC sp, int len, double* phi, double* qout)
         }
 }
 
-// log sin z on any branch, without overflow for large |Im z|
-__device__ inline cdbl log_sin(cdbl z)
-{
-    const cdbl I(0.0, 1.0);
-    if (z.imag() > 0.0) return -I * z + cuda::std::log(I * 0.5) + cuda::std::log(1.0 - cuda::std::exp(2.0 * I * z));
-    return I * z + cuda::std::log(-I * 0.5) + cuda::std::log(1.0 - cuda::std::exp(-2.0 * I * z));
-}
-
 // start_kernel in complex arithmetic
 template <int M>
 __global__ void start_kernel_c(SpecC sp, void* beq, bool tab64)
