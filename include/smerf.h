@@ -174,8 +174,10 @@ int smerf_sample_batched(const smerf_plan* const* plans, const uint64_t* seeds,
  * smerf_batch_create: groups the requests (plans[i], n_samples[i]) by kernel shape, builds
  *   the device work lists and allocates all scratch.  Synchronous.  The plans must outlive
  *   the batch.
- * smerf_batch_set: stores seeds[i] and device outputs outs[i] (16-byte aligned) in the
- *   batch's pinned staging memory.  Host-only; the previous launch's copy of the staging
+ * smerf_batch_set: stores seeds[i] and outputs outs[i] (16-byte aligned; device memory, or
+ *   page-locked host memory that the GPU addresses with the same pointer, such as
+ *   cudaHostAlloc memory or pinned torch tensors, which the kernels then write over the
+ *   CPU-GPU link) in the batch's pinned staging memory.  Host-only; the previous launch's copy of the staging
  *   memory must have completed (synchronise its stream first).
  * smerf_batch_launch: copies the staging memory to the device and launches every group on
  *   `stream` (asynchronous).  Capturable into a CUDA graph: a replay re-reads the staging

@@ -80,3 +80,22 @@ def test_batch_cuda_graph_replay():
         torch.cuda.synchronize()
         for p, sd, n, o in zip(plans, seeds, counts, outs):
             assert torch.equal(o, p.sample(sd, n))
+
+
+def test_batch_writes_pinned_host_outputs():
+    # page-locked host outputs: the kernels write them over the CPU-GPU link; the same fields
+    import torch
+    from paper_1709_10314_gb300 import SMERF_RECUR_FP64, Batch, Plan
+    plans = [Plan([10.0], 1.0, 32, 64, anchor_spacing=8), Plan([3.0, 8.0], 1.0, 17, 32, anchor_spacing=4),
+             Plan([4.0], 1.0, 16, 32, flags=SMERF_RECUR_FP64, anchor_spacing=4)]
+    counts = [3, 2, 2]
+    b = Batch(plans, counts)
+    dev = [torch.empty((n, p.n_theta, p.n_phi), dtype=p.dtype, device="cuda") for p, n in zip(plans, counts)]
+    host = [torch.full((n, p.n_theta, p.n_phi), float("nan"), dtype=p.dtype, pin_memory=True)
+            for p, n in zip(plans, counts)]
+    b.sample([5, 6, 7], dev)
+    torch.cuda.synchronize()
+    b.sample([5, 6, 7], host)
+    torch.cuda.synchronize()
+    for d, h in zip(dev, host):
+        assert torch.equal(d.cpu(), h)
