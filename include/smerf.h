@@ -44,6 +44,8 @@ typedef struct smerf_plan smerf_plan;
 #define SMERF_ECUDA (-4)       /* a CUDA runtime call or kernel launch failed                    */
 #define SMERF_EUNSUPPORTED (-5) /* valid but not built (e.g. p > 2, n_phi not a power of two)   */
 #define SMERF_ESCRATCH (-6)    /* smerf_sample_noalloc: request exceeds its fixed 16 MiB scratch */
+#define SMERF_ETIMEOUT (-7)    /* reserved for a device wait that runs out (none can: see
+                                  smerf_last_device_status)                                     */
 
 /* plan flags */
 #define SMERF_RECUR_FP64 0x1u    /* recursion, FFT and output in FP64 (default FP32, float out)   */
@@ -126,6 +128,16 @@ int smerf_sample(const smerf_plan* plan, uint64_t seed, int n_samples, void* out
  */
 int smerf_sample_timed(const smerf_plan* plan, uint64_t seed, int n_samples, void* out, void* stream,
                        void* event_before_segments, void* event_after_segments);
+
+/*
+ * smerf_last_device_status -- synchronises `stream` (cudaStream_t as void*, NULL = legacy
+ * default stream) and reports how the work queued on it ended: SMERF_OK, or SMERF_ECUDA if a
+ * kernel or copy on it failed (a non-sticky CUDA error is cleared).  The sampling kernels keep
+ * no device error word: none waits on a flag or on another CTA (the producer/FFT hand-off
+ * uses the CTA's own named barriers, the table staging cp.async groups, both complete by
+ * construction), so no wait can run out and SMERF_ETIMEOUT is never returned.
+ */
+int smerf_last_device_status(void* stream);
 
 /*
  * smerf_scratch_trim -- return to the device the memory that the library's per-call scratch

@@ -245,6 +245,7 @@ const char* smerf_status_string(int status)
         case SMERF_ECUDA: return "CUDA error";
         case SMERF_EUNSUPPORTED: return "unsupported configuration";
         case SMERF_ESCRATCH: return "request exceeds the fixed scratch of smerf_sample_noalloc";
+        case SMERF_ETIMEOUT: return "a device wait ran out";
         default: return "unknown status";
     }
 }
@@ -420,6 +421,15 @@ int smerf_sample_timed(const smerf_plan* plan, uint64_t seed, int n_samples, voi
                                               (cudaEvent_t)event_before_segments, (cudaEvent_t)event_after_segments);
     cudaFreeAsync(scratch, st);
     return rc;
+}
+
+int smerf_last_device_status(void* stream)
+{
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return SMERF_ECUDA;
+    }
+    return SMERF_OK;
 }
 
 int smerf_scratch_trim(void)

@@ -63,6 +63,8 @@ def _lib():
         L.smerf_sample_timed.restype = ip
         L.smerf_sample_noalloc.argtypes = [vp, ctypes.c_uint64, ip, vp, vp]
         L.smerf_sample_noalloc.restype = ip
+        L.smerf_last_device_status.argtypes = [vp]
+        L.smerf_last_device_status.restype = ip
         L.smerf_scratch_trim.argtypes = []
         L.smerf_scratch_trim.restype = ip
         L.smerf_sample_launches.argtypes = [vp, ip]
@@ -263,6 +265,11 @@ class Plan:
                                                               int(n_samples), ctypes.c_void_p(ptr),
                                                               _stream_ptr(stream)))
         return out
+
+
+def last_device_status(stream=None):
+    """smerf_last_device_status: synchronise the stream and return 0 or SMERF_ECUDA."""
+    return _lib().smerf_last_device_status(_stream_ptr(stream))
 
 
 def scratch_trim():

@@ -141,10 +141,10 @@ def test_staged_fp64_tables_equal_in_kernel_conversion():
 def test_scratch_pool_kept_and_trimmed_between_calls():
     # per-call scratch comes from the library's pool; trimming it between calls changes nothing
     import torch
-    from paper_1709_10314_gb300 import SMERF_TABLES_FP64, scratch_trim
+    from paper_1709_10314_gb300 import SMERF_TABLES_FP64, last_device_status, scratch_trim
     plan = _plan([20.0, 50.0], 40, 128, 8, SMERF_TABLES_FP64)
     a = plan.sample(3, 6)
-    torch.cuda.synchronize()
+    assert last_device_status() == 0
     scratch_trim()
     b = plan.sample(3, 6)
     host = plan.sample_host(3, 6)
