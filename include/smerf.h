@@ -229,6 +229,25 @@ int smerf_batch_destroy(smerf_batch* batch);
  */
 int smerf_sample_noalloc(const smerf_plan* plan, uint64_t seed, int n_samples, void* out, void* stream);
 
+/*
+ * smerf_plan_create_many -- n plans at once, each as smerf_plan_create_ex would make it from
+ * specs[i] (the same tables, bit for bit), with the n set-ups overlapping on the GPU (they go
+ * round-robin onto up to 16 internal streams; one synchronisation at the end).  For many
+ * small plans, whose set-up kernels alone occupy a fraction of the GPU.  out_plans[i]
+ * receives plan i; each plan's setup_ms (smerf_plan_info) is the wall time of the whole call.
+ * Errors as for smerf_plan_create_ex; on any error every plan made is destroyed, all
+ * out_plans[i] are NULL and the first error is returned.  Synchronous.
+ */
+typedef struct smerf_plan_spec {
+    const double* kappa;  /* p values, as for smerf_plan_create_ex */
+    int p;
+    double A;
+    int n_theta, n_phi;
+    unsigned flags;
+    int anchor_spacing;
+} smerf_plan_spec;
+int smerf_plan_create_many(const smerf_plan_spec* specs, int n, smerf_plan** out_plans);
+
 /* Plan description, filled by smerf_plan_info. */
 typedef struct smerf_plan_info_t {
     int p, n_theta, n_phi, n_modes;       /* n_modes = n_phi/2 + 1                              */

@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <chrono>
 #include <map>
 #include <mutex>
 #include <new>
@@ -263,10 +264,12 @@ static int check_grid(int p, double A, int n_theta, int n_phi, unsigned flags, i
 }
 
 static int create_plan(const double* kappa, const double* kh_re, const double* kh_im, int complex_spec, int p,
-                       double A, int n_theta, int n_phi, unsigned flags, int anchor_spacing, smerf_plan** out_plan);
+                       double A, int n_theta, int n_phi, unsigned flags, int anchor_spacing, smerf_plan** out_plan,
+                       cudaStream_t st = 0, bool sync = true);
 
-int smerf_plan_create_ex(const double* kappa, int p, double A, int n_theta, int n_phi,
-                         unsigned flags, int anchor_spacing, smerf_plan** out_plan)
+// smerf_plan_create_ex with the set-up ordered on `st` (sync: wait for it)
+static int create_ex_on(const double* kappa, int p, double A, int n_theta, int n_phi, unsigned flags,
+                        int anchor_spacing, smerf_plan** out_plan, cudaStream_t st, bool sync)
 {
     if (!out_plan) return SMERF_EINVAL;
     *out_plan = nullptr;
@@ -282,7 +285,48 @@ int smerf_plan_create_ex(const double* kappa, int p, double A, int n_theta, int 
         }
     double kr[kMaxP + 1] = {0}, ki[kMaxP + 1] = {0};
     for (int i = 0; i < p && i <= kMaxP; ++i) kr[i] = kappa[i] * kappa[i];
-    return create_plan(kappa, kr, ki, 0, p, A, n_theta, n_phi, flags, anchor_spacing, out_plan);
+    return create_plan(kappa, kr, ki, 0, p, A, n_theta, n_phi, flags, anchor_spacing, out_plan, st, sync);
+}
+
+int smerf_plan_create_ex(const double* kappa, int p, double A, int n_theta, int n_phi,
+                         unsigned flags, int anchor_spacing, smerf_plan** out_plan)
+{
+    return create_ex_on(kappa, p, A, n_theta, n_phi, flags, anchor_spacing, out_plan, 0, true);
+}
+
+int smerf_plan_create_many(const smerf_plan_spec* specs, int n, smerf_plan** out_plans)
+{
+    if (n < 0 || (n > 0 && (!specs || !out_plans))) return SMERF_EINVAL;
+    for (int i = 0; i < n; ++i) out_plans[i] = nullptr;
+    if (n == 0) return SMERF_OK;
+    // the set-ups go round-robin onto a few non-blocking streams and overlap on the GPU
+    const int ns = n < 16 ? n : 16;
+    std::vector<cudaStream_t> streams((size_t)ns, nullptr);
+    int rc = SMERF_OK;
+    for (int k = 0; k < ns && rc == SMERF_OK; ++k)
+        if (cudaStreamCreateWithFlags(&streams[k], cudaStreamNonBlocking) != cudaSuccess) rc = SMERF_ECUDA;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (int i = 0; i < n && rc == SMERF_OK; ++i) {
+        const smerf_plan_spec& q = specs[i];
+        rc = create_ex_on(q.kappa, q.p, q.A, q.n_theta, q.n_phi, q.flags, q.anchor_spacing, &out_plans[i],
+                          streams[i % ns], false);
+    }
+    for (int k = 0; k < ns; ++k) {
+        if (!streams[k]) continue;
+        if (cudaStreamSynchronize(streams[k]) != cudaSuccess && rc == SMERF_OK) rc = SMERF_ECUDA;
+        cudaStreamDestroy(streams[k]);
+    }
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (int i = 0; i < n; ++i) {
+        if (!out_plans[i]) continue;
+        if (rc != SMERF_OK) {
+            smerf_plan_destroy(out_plans[i]);
+            out_plans[i] = nullptr;
+        } else {
+            out_plans[i]->setup_ms = ms;
+        }
+    }
+    return rc;
 }
 
 int smerf_plan_create_khat(const double* khat_re, const double* khat_im, int p, double A, int n_theta, int n_phi,
@@ -315,7 +359,8 @@ int smerf_plan_create_khat(const double* khat_re, const double* khat_im, int p, 
 }
 
 static int create_plan(const double* kappa, const double* kh_re, const double* kh_im, int complex_spec, int p,
-                       double A, int n_theta, int n_phi, unsigned flags, int anchor_spacing, smerf_plan** out_plan)
+                       double A, int n_theta, int n_phi, unsigned flags, int anchor_spacing, smerf_plan** out_plan,
+                       cudaStream_t st, bool sync)
 {
     if (p > kMaxP) return SMERF_EUNSUPPORTED;
     if (!is_pow2(n_phi) || n_phi < 8 || n_phi > 32768) return SMERF_EUNSUPPORTED;
@@ -372,7 +417,7 @@ static int create_plan(const double* kappa, const double* kh_re, const double* k
     if (cudaMalloc(&pl->segs_dev, sizeof(Segment) * segs.size()) != cudaSuccess) rc = SMERF_ENOMEM;
     else if (cudaMemcpy(pl->segs_dev, segs.data(), sizeof(Segment) * segs.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         rc = SMERF_ECUDA;
-    if (rc == SMERF_OK) rc = smerf_setup_tables(pl);
+    if (rc == SMERF_OK) rc = smerf_setup_tables(pl, st, sync);
     if (rc != SMERF_OK) {
         free_plan_memory(pl);
         delete pl;

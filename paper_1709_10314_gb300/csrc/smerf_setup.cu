@@ -993,7 +993,7 @@ static SpecC make_spec_c(const smerf_plan* pl)
     } while (0)
 
 template <int M>
-int setup_impl(smerf_plan* pl)
+int setup_impl(smerf_plan* pl, cudaStream_t st, bool sync)
 {
     int rc = SMERF_OK;
     Spec sp;
@@ -1034,24 +1034,24 @@ int setup_impl(smerf_plan* pl)
     pl->table_bytes = 0;
     pl->step_table_bytes = 0;
     CK(cudaMalloc(&pl->beq, (size_t)tri(M) * mp * es));
-    CK(cudaMemset(pl->beq, 0, (size_t)tri(M) * mp * es));
+    CK(cudaMemsetAsync(pl->beq, 0, (size_t)tri(M) * mp * es, st));
     pl->table_bytes += (size_t)tri(M) * mp * es;
     for (int c = 0; c < 2; ++c) {
         const int len = pl->chain[c].len;
         const size_t sb = (size_t)(len + 1) * step_row(M) * mp * es;
         const size_t cb = (size_t)(pl->chain[c].n_anchors + 1) * coarse_elems(M) * mp * es;
         CK(cudaMalloc(&pl->steps[c], sb > 0 ? sb : 16));
-        CK(cudaMemset(pl->steps[c], 0, sb > 0 ? sb : 16));
+        CK(cudaMemsetAsync(pl->steps[c], 0, sb > 0 ? sb : 16, st));
         CK(cudaMalloc(&pl->coarse[c], cb > 0 ? cb : 16));
-        CK(cudaMemset(pl->coarse[c], 0, cb > 0 ? cb : 16));
+        CK(cudaMemsetAsync(pl->coarse[c], 0, cb > 0 ? cb : 16, st));
         pl->table_bytes += sb + cb;
         pl->step_table_bytes += sb;
     }
     rc = pl->recur64 ? upload_fft_tables<double>(pl->n_phi, &pl->tw, &pl->pre, &pl->tw2, &pl->tw3)
                      : upload_fft_tables<float>(pl->n_phi, &pl->tw, &pl->pre, &pl->tw2, &pl->tw3);
     if (rc != SMERF_OK) goto done;
-    if (pl->complex_spec) start_kernel_c<M><<<gm, threads>>>(make_spec_c(pl), pl->beq, t64);
-    else start_kernel<M><<<gm, threads>>>(sp, pl->beq, t64);
+    if (pl->complex_spec) start_kernel_c<M><<<gm, threads, 0, st>>>(make_spec_c(pl), pl->beq, t64);
+    else start_kernel<M><<<gm, threads, 0, st>>>(sp, pl->beq, t64);
     CK(cudaGetLastError());
     {
         // Step transitions and covariances of the northern chain.  The southern chain's steps are
@@ -1063,11 +1063,11 @@ int setup_impl(smerf_plan* pl)
         if (len1 + shift > len0) { rc = SMERF_EUNSUPPORTED; goto done; }
         if (len0 > 0) {
             const size_t nb = (size_t)(len0 + 1) * pl->n_modes * M * M * sizeof(double);
-            CK(cudaMalloc(&phi, nb));
-            CK(cudaMalloc(&qv, nb));
+            CK(cudaMallocAsync((void**)&phi, nb, st));
+            CK(cudaMallocAsync((void**)&qv, nb, st));
             if (len0 > 65535) { rc = SMERF_EUNSUPPORTED; goto done; }
             dim3 grid(gm, len0);
-            if (pl->complex_spec) step_kernel_c<M><<<grid, threads>>>(make_spec_c(pl), len0, phi, qv);
+            if (pl->complex_spec) step_kernel_c<M><<<grid, threads, 0, st>>>(make_spec_c(pl), len0, phi, qv);
             else {
                 // the recurrence in m, but for a first step whose equatorward ring (x > 1/2) would
                 // amplify rounding errors by more than 1e3 over the orders: that one by the
@@ -1075,11 +1075,11 @@ int setup_impl(smerf_plan* pl)
                 const double th = chain_theta(sp, 0, 0), x1 = sin(0.5 * th) * sin(0.5 * th);
                 const bool first_series = x1 > 0.5 && (double)(pl->n_modes - 1) * log(x1 / (1.0 - x1)) > log(1e3);
                 const int first = first_series ? 2 : 1;
-                if (first_series) step_kernel<M><<<dim3(gm, 1), threads>>>(sp, 0, 1, phi, qv);
+                if (first_series) step_kernel<M><<<dim3(gm, 1), threads, 0, st>>>(sp, 0, 1, phi, qv);
                 if (len0 >= first) {
                     const int n = len0 - first + 1;
-                    if (M == 1) step_kernel_rec<<<(n + kRecWarps - 1) / kRecWarps, 32 * kRecWarps>>>(sp, first, len0, phi, qv);
-                    else step_kernel_rec2<<<n, 32>>>(sp, first, len0, phi, qv);
+                    if (M == 1) step_kernel_rec<<<(n + kRecWarps - 1) / kRecWarps, 32 * kRecWarps, 0, st>>>(sp, first, len0, phi, qv);
+                    else step_kernel_rec2<<<n, 32, 0, st>>>(sp, first, len0, phi, qv);
                 }
             }
             CK(cudaGetLastError());
@@ -1091,30 +1091,34 @@ int setup_impl(smerf_plan* pl)
             const int H = pl->H;
             const int nseg = H > 0 ? (len / H + 1) : 1;
             dim3 grid(gm, nseg);
-            segment_tables_kernel<M><<<grid, threads>>>(sp, c, len, H, phi + off, qv + off, pl->steps[c],
+            segment_tables_kernel<M><<<grid, threads, 0, st>>>(sp, c, len, H, phi + off, qv + off, pl->steps[c],
                                                          pl->coarse[c], t64);
             CK(cudaGetLastError());
         }
-        CK(cudaDeviceSynchronize());
-        cudaFree(phi);
-        cudaFree(qv);
+        CK(cudaFreeAsync(phi, st));
+        CK(cudaFreeAsync(qv, st));
         phi = qv = nullptr;
     }
-    CK(cudaDeviceSynchronize());
-    pl->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    if (sync) {
+        CK(cudaStreamSynchronize(st));
+        pl->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    }
 done:
-    if (phi) cudaFree(phi);
-    if (qv) cudaFree(qv);
+    if (phi || qv) {
+        cudaStreamSynchronize(st);
+        if (phi) cudaFree(phi);
+        if (qv) cudaFree(qv);
+    }
     return rc;
 }
 
 }  // namespace
 
-int smerf_setup_tables(smerf_plan* pl)
+int smerf_setup_tables(smerf_plan* pl, cudaStream_t st, bool sync)
 {
     switch (pl->p) {
-        case 1: return setup_impl<1>(pl);
-        case 2: return setup_impl<2>(pl);
+        case 1: return setup_impl<1>(pl, st, sync);
+        case 2: return setup_impl<2>(pl, st, sync);
         default: return SMERF_EUNSUPPORTED;
     }
 }

@@ -63,6 +63,8 @@ def _lib():
         L.smerf_sample_timed.restype = ip
         L.smerf_sample_noalloc.argtypes = [vp, ctypes.c_uint64, ip, vp, vp]
         L.smerf_sample_noalloc.restype = ip
+        L.smerf_plan_create_many.argtypes = [ctypes.POINTER(_PlanSpec), ip, ctypes.POINTER(vp)]
+        L.smerf_plan_create_many.restype = ip
         L.smerf_last_device_status.argtypes = [vp]
         L.smerf_last_device_status.restype = ip
         L.smerf_scratch_trim.argtypes = []
@@ -116,6 +118,12 @@ def _stream_ptr(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+class _PlanSpec(ctypes.Structure):
+    _fields_ = [("kappa", ctypes.POINTER(ctypes.c_double)), ("p", ctypes.c_int), ("A", ctypes.c_double),
+                ("n_theta", ctypes.c_int), ("n_phi", ctypes.c_int), ("flags", ctypes.c_uint),
+                ("anchor_spacing", ctypes.c_int)]
 
 
 class Plan:
@@ -265,6 +273,32 @@ class Plan:
                                                               int(n_samples), ctypes.c_void_p(ptr),
                                                               _stream_ptr(stream)))
         return out
+
+
+def create_plans(specs):
+    """smerf_plan_create_many: Plans for a list of dicts with the keys of Plan(kappa, A, n_theta,
+    n_phi, flags, anchor_spacing), their set-ups overlapping on the GPU."""
+    n = len(specs)
+    ks = [np.ascontiguousarray(np.atleast_1d(d["kappa"]), dtype=np.float64) for d in specs]
+    arr = (_PlanSpec * max(n, 1))()
+    dp = ctypes.POINTER(ctypes.c_double)
+    for i, (d, k) in enumerate(zip(specs, ks)):
+        arr[i] = _PlanSpec(k.ctypes.data_as(dp), len(k), float(d.get("A", 1.0)), int(d["n_theta"]),
+                           int(d["n_phi"]), int(d.get("flags", 0)), int(d.get("anchor_spacing", 0)))
+    hs = (ctypes.c_void_p * max(n, 1))()
+    _check("smerf_plan_create_many", _lib().smerf_plan_create_many(arr, n, hs))
+    plans = []
+    for i, (d, k) in enumerate(zip(specs, ks)):
+        pl = Plan.__new__(Plan)
+        pl._h = ctypes.c_void_p(hs[i])
+        pl.kappa = k
+        pl.A = float(d.get("A", 1.0))
+        pl.n_theta = int(d["n_theta"])
+        pl.n_phi = int(d["n_phi"])
+        pl.flags = int(d.get("flags", 0))
+        pl.fp64 = bool(pl.flags & SMERF_RECUR_FP64)
+        plans.append(pl)
+    return plans
 
 
 def last_device_status(stream=None):
