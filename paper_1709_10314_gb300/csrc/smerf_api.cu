@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "smerf_internal.cuh"
+#include "smerf_setup.h"
 
 int smerf_launch_sample_ff(const smerf_plan*, uint64_t, int, void*, void*, cudaStream_t, cudaEvent_t, cudaEvent_t);
 int smerf_launch_sample_fd(const smerf_plan*, uint64_t, int, void*, void*, cudaStream_t, cudaEvent_t, cudaEvent_t);

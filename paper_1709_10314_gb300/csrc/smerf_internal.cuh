@@ -199,10 +199,7 @@ template <class C> __device__ __forceinline__ C cmuli(C a) { return cmk<C>(-a.y,
 
 }  // namespace smerf
 
-// set-up (smerf_setup.cu) and sampling (smerf_sample.cu) entry points used by smerf_api.cu
-// set-up of a plan's tables, every device step ordered on `st`; sync: wait for it and record
-// setup_ms (else the caller synchronises st before the plan is used)
-int smerf_setup_tables(smerf_plan* plan, cudaStream_t st, bool sync);
+// sampling entry points used by smerf_api.cu (the set-up's are in smerf_setup.h)
 int smerf_launch_sample(const smerf_plan* plan, uint64_t seed, int n_samples, void* out,
                         void* scratch, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
                         cudaEvent_t ev1 = nullptr);

@@ -38,6 +38,7 @@
 #include <cuda/std/complex>
 
 #include "smerf_internal.cuh"
+#include "smerf_setup.h"
 
 using namespace smerf;
 
