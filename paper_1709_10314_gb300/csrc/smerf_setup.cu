@@ -581,9 +581,40 @@ __device__ inline void put(void* base, bool is64, size_t idx, double v)
     }
 }
 
+// The start ring's Pochhammer factors, log[(-l_i)_m (l_i+1)_m / (m!)^2]
+// = sum_{j<m} log((j(j+1) + kappa_i^2) / (j+1)^2) (Eq. (Legendre_hypergeometric)), for every m at
+// once: one block sums contiguous chunks of the terms, scans the chunk sums and writes each
+// chunk's prefixes (a fixed order; start_kernel reads lq[i * n_modes + m]).
+__global__ void __launch_bounds__(1024) lq_prefix_kernel(Spec sp, double* lq)
+{
+    __shared__ double part[1024];
+    const int n = sp.n_modes, t = threadIdx.x, nt = blockDim.x;
+    const int chunk = (n + nt - 1) / nt;
+    const int j0 = min(n, t * chunk), j1 = min(n, j0 + chunk);
+    for (int i = 0; i < sp.M; ++i) {
+        const double k2 = sp.k2[i];
+        double s = 0.0;
+        for (int j = j0; j < j1; ++j) s += log((j * (j + 1.0) + k2) / ((j + 1.0) * (j + 1.0)));
+        part[t] = s;
+        __syncthreads();
+        for (int o = 1; o < nt; o <<= 1) {  // inclusive scan of the chunk sums
+            const double v = t >= o ? part[t - o] : 0.0;
+            __syncthreads();
+            part[t] += v;
+            __syncthreads();
+        }
+        double acc = t > 0 ? part[t - 1] : 0.0;  // the terms j < j0
+        for (int j = j0; j < j1; ++j) {
+            lq[(size_t)i * n + j] = acc;
+            acc += log((j * (j + 1.0) + k2) / ((j + 1.0) * (j + 1.0)));
+        }
+        __syncthreads();
+    }
+}
+
 // Start factor B_eq = chol J(z0, z0) (Eq. (state_initial)), one thread per mode.
 template <int M>
-__global__ void start_kernel(Spec sp, void* beq, bool tab64)
+__global__ void start_kernel(Spec sp, const double* lqa, void* beq, bool tab64)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= sp.n_modes) return;
@@ -594,8 +625,7 @@ __global__ void start_kernel(Spec sp, void* beq, bool tab64)
     Mat<M> J = mzero<M>();
     for (int i = 0; i < M; ++i) {
         const double k2 = sp.k2[i];
-        double lq = 0.0;  // log Q_m / (m!)^2
-        for (int j = 0; j < m; ++j) lq += log((j * (j + 1.0) + k2) / ((j + 1.0) * (j + 1.0)));
+        const double lq = lqa[(size_t)i * sp.n_modes + m];  // log Q_m / (m!)^2
         double lF0[M], lF1[M], r[M];
         double rr = 1.0;
         for (int q = 0; q < M; ++q) {
@@ -1028,6 +1058,7 @@ int setup_impl(smerf_plan* pl, cudaStream_t st, bool sync)
     const size_t mp = pl->n_modes_pad;
     double* phi = nullptr;
     double* qv = nullptr;
+    double* lqa = nullptr;
     const int threads = 128;
     const int gm = (pl->n_modes + threads - 1) / threads;
     auto t_start = std::chrono::steady_clock::now();
@@ -1052,7 +1083,13 @@ int setup_impl(smerf_plan* pl, cudaStream_t st, bool sync)
                      : upload_fft_tables<float>(pl->n_phi, &pl->tw, &pl->pre, &pl->tw2, &pl->tw3);
     if (rc != SMERF_OK) goto done;
     if (pl->complex_spec) start_kernel_c<M><<<gm, threads, 0, st>>>(make_spec_c(pl), pl->beq, t64);
-    else start_kernel<M><<<gm, threads, 0, st>>>(sp, pl->beq, t64);
+    else {
+        CK(cudaMallocAsync((void**)&lqa, (size_t)M * pl->n_modes * sizeof(double), st));
+        lq_prefix_kernel<<<1, 1024, 0, st>>>(sp, lqa);
+        start_kernel<M><<<gm, threads, 0, st>>>(sp, lqa, pl->beq, t64);
+        CK(cudaFreeAsync(lqa, st));
+        lqa = nullptr;
+    }
     CK(cudaGetLastError());
     {
         // Step transitions and covariances of the northern chain.  The southern chain's steps are
@@ -1105,10 +1142,11 @@ int setup_impl(smerf_plan* pl, cudaStream_t st, bool sync)
         pl->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     }
 done:
-    if (phi || qv) {
+    if (phi || qv || lqa) {
         cudaStreamSynchronize(st);
         if (phi) cudaFree(phi);
         if (qv) cudaFree(qv);
+        if (lqa) cudaFree(lqa);
     }
     return rc;
 }
