@@ -30,6 +30,10 @@ Pins (tests/test_oracle_*.py, run with -m "not gpu"):
                            tiny-grid brute force over (l, m) spherical-harmonic sums,
                            Im(g_0) and Im(g_{n_phi/2}) invariants
   dft_ring                 pinned: numpy.fft.irfft (library routine)
+  fft_ring                 pinned: numpy.fft.irfft and dft_ring
+  recursion_sample         pinned: equals sample() (the dense factor applied to the same
+                           noise) on small grids in both orders, which holds only if the
+                           tables, the parents and the noise layout are all right
 """
 import ctypes
 import math
@@ -44,7 +48,8 @@ __all__ = [
     "cov_partial", "cov_m", "default_levels", "ring_theta", "chain_layout",
     "conditioning_order", "normal_index", "joint_factor", "joint_factors", "cov_modes",
     "sample", "field_std", "mode_variances",
-    "conditional_tables", "dft_ring", "KHat",
+    "conditional_tables", "dft_ring", "fft_ring", "KHat",
+    "order_parents", "recursion_tables", "recursion_sample",
 ]
 
 _lib = None
@@ -75,6 +80,12 @@ def lib():
         L.oracle_cov_partial.restype = ctypes.c_double
         L.oracle_legendre_row.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, dp]
         L.oracle_dft_ring.argtypes = [ctypes.c_int, dp, dp, dp]
+        L.oracle_fft_ring.argtypes = [ctypes.c_int, dp, dp, dp]
+        L.oracle_fft_ring.restype = ctypes.c_int
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.oracle_recursion_sample.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip, ip, dp, dp,
+                                              ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+        L.oracle_recursion_sample.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -297,6 +308,16 @@ def conditional_tables(S, M, pos, parents):
     return coef, cov
 
 
+def fft_ring(N, re, im):
+    """The real synthesis of dft_ring through a plain radix-2 FFT (N a power of two)."""
+    re = np.ascontiguousarray(re, dtype=np.float64)
+    im = np.ascontiguousarray(im, dtype=np.float64)
+    out = np.zeros(N)
+    if lib().oracle_fft_ring(N, _dp(re), _dp(im), _dp(out)) != 0:
+        raise ValueError("oracle_fft_ring: N must be a power of two")
+    return out
+
+
 def dft_ring(N, re, im):
     re = np.ascontiguousarray(re, dtype=np.float64)
     im = np.ascontiguousarray(im, dtype=np.float64)
@@ -381,3 +402,71 @@ def field_std(kappa, A, n_theta, n_phi, K=6, rings=None):
     w[0] = 1.0
     w[Hm] = 0.5
     return float(math.sqrt((w[:, None] * V).sum(axis=0).mean()))
+
+
+# ------------------------------------------------------- Alg. 2 with tables
+def order_parents(order):
+    """For each position of a conditioning order, its nearest earlier neighbours in ring
+    index on each side (at most two): the Markov blanket among the rings drawn before it
+    (Sec. 2), i.e. the parents of the recursion x_i = sum_j T_ij x_par(j) + B_i xi_i."""
+    par = []
+    for i, r in enumerate(order):
+        before = order[:i]
+        lo = [b for b in before if b < r]
+        hi = [b for b in before if b > r]
+        p = []
+        if hi:
+            p.append(order.index(min(hi)))
+        if lo:
+            p.append(order.index(max(lo)))
+        par.append(p)
+    return par
+
+
+def recursion_tables(kappa, A, n_theta, n_phi, H=0, K=6, rings=None, modes=None, **level_kw):
+    """Tables of Alg. 2's recursion for every mode and every position of the conditioning
+    order (or of its leading subset `rings`), from the oracle's joint covariance: the
+    transition onto each parent by Gaussian conditioning (Eq. (trans_matrix)) and, as the
+    innovation factor (Eq. (innov_matrix)), the position's diagonal block of the dense
+    lower Cholesky factor (the factor of the conditional covariance).
+    Returns (order, parents, T [n_modes][n_pos][2][M][M], B [n_modes][n_pos][M][M]) for the
+    modes `modes` (default 0..n_phi/2)."""
+    M = _spec(kappa)[1]
+    order, S, L = joint_factors(kappa, A, n_theta, n_phi, H, K, rings=rings, modes=modes, **level_kw)
+    par = order_parents(order)
+    n = len(order)
+    T = np.zeros((len(S), n, 2, M, M))
+    B = np.zeros((len(S), n, M, M))
+    for mi in range(len(S)):
+        for i in range(n):
+            B[mi, i] = L[mi][i * M:(i + 1) * M, i * M:(i + 1) * M]
+            if par[i]:
+                coef, _ = conditional_tables(S[mi], M, i, par[i])
+                for j in range(len(par[i])):
+                    T[mi, i, j] = coef[:, j * M:(j + 1) * M]
+    return order, par, T, B
+
+
+def recursion_sample(M, n_phi, order, parents, T, B, seed, n_samples=1, nthreads=1, use_fft=True):
+    """Alg. 2: the per-sample recursion over the positions of `order` with the given tables
+    (recursion_tables), the same Philox noise as sample(), and the per-ring synthesis
+    (fft_ring, or the naive dft_ring).  Returns float64 [n_samples][len(order)][n_phi], rings
+    in the order's order."""
+    n = len(order)
+    ring = np.ascontiguousarray(order, dtype=np.int32)
+    npar = np.ascontiguousarray([len(p) for p in parents], dtype=np.int32)
+    par = np.zeros((n, 2), dtype=np.int32)
+    for i, p in enumerate(parents):
+        par[i, :len(p)] = p
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    assert T.shape[0] == n_phi // 2 + 1 and T.shape[1] == n and B.shape[:2] == T.shape[:2]
+    out = np.zeros((n_samples, n, n_phi))
+    ip = ctypes.POINTER(ctypes.c_int)
+    rc = lib().oracle_recursion_sample(M, n_phi, n, ring.ctypes.data_as(ip), npar.ctypes.data_as(ip),
+                                       par.ctypes.data_as(ip), _dp(T), _dp(B),
+                                       ctypes.c_uint64(seed & (2**64 - 1)), n_samples, int(nthreads),
+                                       1 if use_fft else 0, _dp(out))
+    if rc != 0:
+        raise ValueError("oracle_recursion_sample: bad arguments")
+    return out

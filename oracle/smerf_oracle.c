@@ -25,7 +25,10 @@
  *    The series is summed with a smooth cut-off window w((l+1/2)/L) and, on the
  *    same-ring blocks (whose tail does not oscillate), Richardson-extrapolated in 1/L
  *    over K levels L, 2L, ..., 2^(K-1) L.
- *  - The naive O(n_phi^2) real DFT of one ring (Alg. 2, last step; prefactor 1).
+ *  - The naive O(n_phi^2) real DFT of one ring (Alg. 2, last step; prefactor 1), and the
+ *    same synthesis through a textbook radix-2 FFT.
+ *  - Alg. 2's per-sample recursion with tables given (the oracle derives them by Gaussian
+ *    conditioning of its spectral-sum covariance): the CPU baseline of the sampler.
  */
 #include <math.h>
 #include <stdint.h>
@@ -328,5 +331,154 @@ int oracle_cov_modes(int nmodes, const int *ms, int M, const double *khat, doubl
     for (int i = 0; i < nmodes; ++i)
         bad |= oracle_cov_m(ms[i], M, khat, A, n, z, Loff[i], Ld + (size_t)i * n, K,
                             Sigma + blk * (size_t)i) != 0;
+    return bad ? -1 : 0;
+}
+
+/* ------------------------------------------- plain FFT for the ring synthesis
+ * The same real synthesis as oracle_dft_ring, through a textbook iterative radix-2
+ * complex FFT (bit reversal, then log2 N butterfly stages with e^{+2 pi i k / len}):
+ * the Hermitian spectrum Y_0 = Re X_0, Y_m = X_m, Y_{N-m} = conj X_m (0 < m < N/2),
+ * Y_{N/2} = Re X_{N/2} is transformed and the real part kept.  N a power of two. */
+static int ilog2_exact(int N)
+{
+    int L = 0;
+    while ((1 << L) < N) ++L;
+    return (1 << L) == N ? L : -1;
+}
+
+int oracle_fft_ring(int N, const double *re, const double *im, double *out)
+{
+    const int L = ilog2_exact(N);
+    if (L < 1) return -1;
+    const int H = N / 2;
+    double *yr = (double *)malloc(sizeof(double) * (size_t)N);
+    double *yi = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!yr || !yi) { free(yr); free(yi); return -1; }
+    for (int k = 0; k < N; ++k) {
+        double a, b;
+        if (k == 0) { a = re[0]; b = 0.0; }
+        else if (k < H) { a = re[k]; b = im[k]; }
+        else if (k == H) { a = re[H]; b = 0.0; }
+        else { a = re[N - k]; b = -im[N - k]; }
+        /* bit-reversed position of k */
+        int r = 0;
+        for (int t = 0; t < L; ++t) r |= ((k >> t) & 1) << (L - 1 - t);
+        yr[r] = a;
+        yi[r] = b;
+    }
+    for (int len = 2; len <= N; len <<= 1) {
+        const int half = len / 2;
+        for (int j = 0; j < half; ++j) {
+            const double ang = 2.0 * M_PI * (double)j / (double)len;
+            const double wr = cos(ang), wi = sin(ang);
+            for (int s = 0; s < N; s += len) {
+                const int a = s + j, b = s + j + half;
+                const double tr = wr * yr[b] - wi * yi[b];
+                const double ti = wr * yi[b] + wi * yr[b];
+                yr[b] = yr[a] - tr;
+                yi[b] = yi[a] - ti;
+                yr[a] += tr;
+                yi[a] += ti;
+            }
+        }
+    }
+    memcpy(out, yr, sizeof(double) * (size_t)N);
+    free(yr);
+    free(yi);
+    return 0;
+}
+
+/* ------------------------------------------- Alg. 2: the per-sample recursion
+ * Given tables for every mode m = 0..N/2 and every position i of a conditioning order
+ * (the start ring first), draw each realisation's states position by position,
+ *     x_{m,i} = sum_{j < npar[i]} T_{m,i,j} x_{m,par[i][j]} + B_{m,i} xi_{m,i}
+ * (Eq. (state_space); with no parent it is the start state B_eq xi of Eq. (state_initial)),
+ * for the Re and Im chains of each mode, then synthesise each position's ring
+ * (Alg. 2, last step; prefactor 1).  The tables come from the oracle's Gaussian conditioning
+ * of its spectral-sum covariance: T the transition of Eq. (trans_matrix) onto each parent,
+ * B the lower factor of the conditional covariance of Eq. (innov_matrix).
+ *
+ *   M, N               state size p and ring length n_phi (power of two)
+ *   n_pos, ring[n_pos] positions of the order and their ring indices (noise counters)
+ *   npar[n_pos], par[n_pos][2]  parents (earlier positions, at most two)
+ *   T[m][i][j][M][M]   transition onto parent j (row-major M x M), j < 2
+ *   B[m][i][M][M]      lower factor (row-major; upper part ignored)
+ *   seed, n_samples    realisation r uses the Philox key seed + r (noise layout of the
+ *                      sampler: slot s in [1, N/2) takes normals [2Ms, 2Ms+2M), Re then Im;
+ *                      slot 0 the real m = 0 chain [0, M) and the Nyquist Re chain [M, 2M))
+ *   nthreads           OpenMP threads over modes (and over rings for the synthesis)
+ *   use_fft            1: oracle_fft_ring, 0: the naive oracle_dft_ring
+ *   out[r][i][N]       the field on each position's ring
+ * Modes m >= 1 carry the complex normal's 1/sqrt(2) (Re and Im parts each N(0, 1/2)).
+ * Returns 0, or -1 on bad arguments or allocation failure. */
+int oracle_recursion_sample(int M, int N, int n_pos, const int *ring, const int *npar, const int *par,
+                            const double *T, const double *B, uint64_t seed, int n_samples, int nthreads,
+                            int use_fft, double *out)
+{
+    if (M < 1 || M > 4 || N < 4 || n_pos < 1 || n_samples < 0 || nthreads < 1) return -1;
+    if (use_fft && ilog2_exact(N) < 1) return -1;
+    const int H = N / 2, nm = H + 1;
+    const size_t tstride = (size_t)2 * M * M, bstride = (size_t)M * M;
+    /* states [position][mode][part][M] and complex coefficients [position][mode] */
+    double *x = (double *)malloc(sizeof(double) * (size_t)n_pos * nm * 2 * M);
+    double *cre = (double *)malloc(sizeof(double) * (size_t)n_pos * nm);
+    double *cim = (double *)malloc(sizeof(double) * (size_t)n_pos * nm);
+    double *nrm = (double *)malloc(sizeof(double) * (size_t)M * N);
+    if (!x || !cre || !cim || !nrm) { free(x); free(cre); free(cim); free(nrm); return -1; }
+    const double half = sqrt(0.5);
+    int bad = 0;
+    for (int r = 0; r < n_samples && !bad; ++r) {
+        const uint64_t key64 = seed + (uint64_t)r;
+        const uint32_t key[2] = {(uint32_t)key64, (uint32_t)(key64 >> 32)};
+        for (int i = 0; i < n_pos; ++i) {
+            const int ncalls = (M * N + 3) / 4;
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+            for (int c = 0; c < ncalls; ++c) {
+                uint32_t ctr[4] = {(uint32_t)c, (uint32_t)ring[i], 0u, 0u}, w[4];
+                double v[4];
+                oracle_philox4x32_10(ctr, key, w);
+                box_muller(w[0], w[1], &v[0], &v[1]);
+                box_muller(w[2], w[3], &v[2], &v[3]);
+                for (int e = 0; e < 4 && 4 * c + e < M * N; ++e) nrm[4 * c + e] = v[e];
+            }
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+            for (int m = 0; m < nm; ++m) {
+                const double *Tm = T + ((size_t)m * n_pos + i) * tstride;
+                const double *Bm = B + ((size_t)m * n_pos + i) * bstride;
+                const int nparts = (m == 0 || m == H) ? 1 : 2;
+                double g[2] = {0.0, 0.0};
+                for (int part = 0; part < nparts; ++part) {
+                    /* the normals driving this chain */
+                    const double *xi = m == 0 ? nrm : (m == H ? nrm + M : nrm + 2 * M * m + M * part);
+                    double *xs = x + (((size_t)i * nm + m) * 2 + part) * M;
+                    for (int p = 0; p < M; ++p) {
+                        double acc = 0.0;
+                        for (int j = 0; j < npar[i]; ++j) {
+                            const double *xp = x + (((size_t)par[2 * i + j] * nm + m) * 2 + part) * M;
+                            for (int q = 0; q < M; ++q) acc += Tm[j * bstride + p * M + q] * xp[q];
+                        }
+                        for (int q = 0; q <= p; ++q) acc += Bm[p * M + q] * xi[q];
+                        xs[p] = acc;
+                    }
+                    g[part] = xs[0];
+                }
+                const double s = m == 0 ? 1.0 : half;
+                cre[(size_t)i * nm + m] = s * g[0];
+                cim[(size_t)i * nm + m] = s * g[1];
+            }
+        }
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 1) reduction(| : bad)
+        for (int i = 0; i < n_pos; ++i) {
+            double *dst = out + ((size_t)r * n_pos + i) * N;
+            if (use_fft)
+                bad |= oracle_fft_ring(N, cre + (size_t)i * nm, cim + (size_t)i * nm, dst) != 0;
+            else
+                oracle_dft_ring(N, cre + (size_t)i * nm, cim + (size_t)i * nm, dst);
+        }
+    }
+    free(x);
+    free(cre);
+    free(cim);
+    free(nrm);
     return bad ? -1 : 0;
 }

@@ -11,6 +11,25 @@ import oracle
 mp = pytest.importorskip("mpmath")
 
 
+def gauss_2f1(a, b, c, x):
+    """2F1(a, b; c; x) for 0 <= x < 1: mpmath's hyp2f1, or, where it gives up (the high orders
+    with arguments above about 3/4 that the large grids need), the defining Gauss series summed
+    in the current precision until a term falls below 10^-(dps+5) of the sum."""
+    try:
+        return mp.hyp2f1(a, b, c, x)
+    except mp.libmp.libhyper.NoConvergence:
+        pass
+    s = mp.mpc(0)
+    t = mp.mpc(1)
+    eps = mp.mpf(10) ** (-(mp.mp.dps + 5))
+    for n in range(10 ** 6):
+        s += t
+        t *= (a + n) * (b + n) / ((c + n) * (n + 1)) * x
+        if n > 8 and abs(t) < eps * abs(s):
+            return s
+    raise ArithmeticError("Gauss series did not converge")
+
+
 def closed_form_J(m, kappas, A, z1, z2, p, q, dps=30, khat=None):
     """J^m_pq(z1, z2) = 1/(4 pi) sum_i b_i Gamma(1+l_i-m) Gamma(-l_i-m) *
     { (-1)^p P^{m+p}(-z1) P^{m+q}(z2)  if z1 <= z2 ;  (-1)^q P^{m+p}(z1) P^{m+q}(-z2) otherwise },
@@ -31,7 +50,7 @@ def closed_form_J(m, kappas, A, z1, z2, p, q, dps=30, khat=None):
                 for jj in range(mu):
                     Q *= jj * (jj + 1) + khi
                 return (Q / mp.factorial(mu)) * ((1 - z) / (1 + z)) ** (mp.mpf(mu) / 2) \
-                    * mp.hyp2f1(-lam, lam + 1, 1 + mu, (1 - z) / 2)
+                    * gauss_2f1(-lam, lam + 1, 1 + mu, (1 - z) / 2)
             a1, a2 = mp.mpf(z1), mp.mpf(z2)
             if z1 <= z2:
                 v = (-1) ** p * P(m + p, -a1) * P(m + q, a2)

@@ -167,3 +167,18 @@ def test_im_parts_do_not_reach_field():
     c2[4] = c2[4].real + 123.0j
     b = oracle.dft_ring(8, c2.real, c2.imag)
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("n_theta,n_phi", [(3, 4), (4, 8)])
+def test_field_std_is_the_mean_pointwise_variance(n_theta, n_phi):
+    """field_std (the scale of every FP64 and FP32 parity tolerance) squared is the mean over
+    the grid of the pointwise variance of the m-truncated field: the mean diagonal of the
+    direct spherical-harmonic double sum (weights 1, 2, ..., 2, 1/2 of J^m_00 follow from the
+    real-DFT convention; a wrong Nyquist weight or a lost factor 2 fails here)."""
+    kappa = [2.0, 5.0]
+    Cb = truncated_field_cov(kappa, 1.0, n_theta, n_phi, 400)
+    v = oracle.field_std(kappa, 1.0, n_theta, n_phi) ** 2
+    assert v == pytest.approx(float(np.mean(np.diag(Cb))), rel=2e-5)
+    # the Nyquist term is large enough here for a wrong weight to show
+    V = oracle.mode_variances(kappa, 1.0, n_theta, n_phi)
+    assert 0.25 * V[-1].mean() > 1e-3 * v
