@@ -1,15 +1,17 @@
 #!/usr/bin/env python
-"""Throughput of the GB300 sphere-GMRF sampler on its headline workload.
+"""Throughput of the GB300 sphere-GMRF sampler on its largest single-GPU workload.
 
-Workload (default): 1024 x 2048 equiangular grid, C_l = 1/((l(l+1)+20^2)(l(l+1)+50^2))
-(p = 2), 64 realisations per step, FP64 tables, FP32 recursion + FFT, anchors every 16
-rings.  A step is one smerf_sample call: the anchor kernel and the segment kernel that
-synthesises and writes every ring.  Metric: sphere grid points per second.
+Workload (default): 16384 x 32768 equiangular grid, C_l = 1/(l(l+1)+300^2) (p = 1), 4
+realisations per step, FP32 tables (set up once in FP64 on the device), FP32 recursion + FFT.
+A step is one smerf_sample call: the anchor kernel and the segment kernel that synthesises and
+writes every ring.  Metric: sphere grid points per second, with the segment kernel's fraction
+of the HBM roofline (the method's algorithmic bytes) and of the ALU issue roofline.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--workload W]
 
-Prints one JSON line (rank 0).  --impl reference times the oracle (the FP64 CPU
-restatement of the method) on a bounded sample of the same workload.
+Prints one JSON line (rank 0).  The CPU baseline, and --impl reference, time the oracle's
+per-sample recursion of Alg. 2 (FP64, plain C, tables from the oracle's own Gaussian
+conditioning, a plain radix-2 FFT per ring) on a bounded sample of the same workload.
 """
 import argparse
 import json
@@ -23,11 +25,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-KAPPA = [20.0, 50.0]
-AMP = 1.0
-N_THETA, N_PHI, N_REAL, ANCHOR, SEED = 1024, 2048, 64, 16, 1
-WORKLOAD = ("1024x2048 equiangular grid, C_l=1/((l(l+1)+20^2)(l(l+1)+50^2)) (p=2), 64 realisations, "
-            "FP64 tables, FP32 recursion+FFT")
+DEFAULT_WORKLOAD = "16384x32768-p1"
 METRIC = "sphere grid points/s"
 FLUSH_BYTES = 256 << 20
 
@@ -48,6 +46,22 @@ def alg_ops_per_item(p, Nc, fp64=False):
     recursion = 2.0 * (p * p + p * (p + 1) / 2.0)
     fft = 10.0 + 3.5 * math.log2(Nc)
     return (box_muller + recursion + fft) if fp64 else (philox + box_muller + recursion + fft)
+
+
+def sfu_ops_per_item(p):
+    """Special-function operations of one item: Box-Muller's log2, rsqrt, sin and cos per pair
+    of normals (p pairs per item)."""
+    return 4.0 * p
+
+
+SFU_LANES = 16  # special-function (MUFU) lanes per SM per clock
+
+
+def alg_table_bytes(p, n_theta, n_phi, fp64):
+    """The method's table bytes per launch: A (p x p) and the lower factor B (p(p+1)/2 values) per
+    (mode, ring), read once, in the recursion precision (8 bytes per (mode, ring) for p = 1, 28
+    for p = 2 in FP32)."""
+    return (n_phi // 2 + 1) * n_theta * (p * p + p * (p + 1) // 2) * (8 if fp64 else 4)
 
 
 def alu_peak(fp64, sm_mhz):
@@ -130,16 +144,6 @@ def csrc_digest():
     return h.hexdigest()[:16]
 
 
-def oracle_sample_step(n_real=1, seed=SEED):
-    """The oracle on a bounded sample of the workload: the start ring (k0) of n_real
-    realisations, including the oracle's own covariance construction for that ring."""
-    import oracle
-    order = oracle.conditioning_order(N_THETA, ANCHOR)
-    t0 = time.perf_counter()
-    oracle.sample(KAPPA, AMP, N_THETA, N_PHI, seed, n_real, H=ANCHOR, rings=order[:1])
-    return time.perf_counter() - t0, n_real * N_PHI
-
-
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -147,26 +151,104 @@ def cpu_cores():
         return os.cpu_count()
 
 
+class CpuBaseline:
+    """The oracle's per-sample recursion (Alg. 2) on a bounded sample of a workload: the first
+    h rings of the chain in Alg. 2's order (the start ring k0 and the next rings north) of R
+    realisations, every mode, then a plain radix-2 FFT per ring (oracle.recursion_sample).  Its
+    tables come from the oracle's Gaussian conditioning of its spectral-sum covariance
+    (oracle.recursion_tables); on grids with more than 129 modes they are computed for every
+    s-th mode and shared by the modes up to the next (the recursion's cost does not depend on
+    the table values).  The set-up is not timed."""
+
+    def __init__(self, kappa, A, n_theta, n_phi, h=4):
+        import numpy as np
+        import oracle
+        self.oracle = oracle
+        nm = n_phi // 2 + 1
+        self.full = n_theta <= 64 and nm <= 129
+        self.h = n_theta if self.full else min(h, n_theta)
+        self.stride = 1 if nm <= 129 else (nm - 1) // 16
+        modes = list(range(0, nm, self.stride))
+        order = oracle.conditioning_order(n_theta, 0)[:self.h]
+        o, par, T, B = oracle.recursion_tables(list(kappa), A, n_theta, n_phi, H=0, rings=order, modes=modes)
+        idx = np.minimum(np.arange(nm) // self.stride, len(modes) - 1)
+        self.args = (len(kappa), n_phi, o, par, np.ascontiguousarray(T[idx]), np.ascontiguousarray(B[idx]))
+        self.n_phi = n_phi
+        self.cores = cpu_cores()
+
+    def run(self, seed, R, threads):
+        t0 = time.perf_counter()
+        self.oracle.recursion_sample(*self.args, seed=seed, n_samples=R, nthreads=threads)
+        return time.perf_counter() - t0
+
+    def calibrate(self, budget_s):
+        """Realisations per sample so that one single-threaded sample takes about budget_s."""
+        t = self.run(1, 1, 1)
+        return max(1, int(budget_s / max(t, 1e-6)))
+
+    def points(self, R):
+        return R * self.h * self.n_phi
+
+    def sample_text(self, R):
+        what = ("the whole grid (%d rings), every mode's tables exact" % self.h) if self.full else \
+            ("the first %d rings of the chain (start ring and the next rings north), every mode; tables "
+             "computed for every %d-th mode and shared by the modes up to the next" % (self.h, self.stride))
+        return ("Alg. 2 on the host: %s, %d realisation(s) per sample (%d points); FP64 recursion with the "
+                "oracle's Philox/Box-Muller noise, plain radix-2 FFT per ring" % (what, R, self.points(R)))
+
+    def measure(self, budget_s=1.5):
+        R = self.calibrate(budget_s)
+        t1 = self.run(2, R, 1)
+        tn = self.run(3, R, self.cores)
+        return {"value": self.points(R) / tn, "unit": "points/s", "cores": self.cores,
+                "kind": "oracle recursion (Alg. 2)", "single_thread_value": self.points(R) / t1,
+                "sample": self.sample_text(R)}
+
+
+def workload_spec(wl):
+    from paper_1709_10314_gb300.workloads import FIXED, uneven_requests
+    if wl == "uneven-256":
+        r = uneven_requests()[0]
+        return dict(kappa=r["kappa"], A=r["A"], n_theta=r["n_theta"], n_phi=r["n_phi"]), "request 0 of the batch"
+    c = FIXED[wl]
+    return dict(kappa=c["kappa"], A=c["A"], n_theta=c["n_theta"], n_phi=c["n_phi"]), None
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    spec, note = workload_spec(args.workload)
+    cb = CpuBaseline(spec["kappa"], spec["A"], spec["n_theta"], spec["n_phi"])
+    R = cb.calibrate(0.5)  # realisations per step: a few seconds of work per step on all cores
+    R = max(1, R * min(cb.cores, 16) // 2)
     dts = []
     for i in range(args.warmup + args.steps):
-        dt, pts = oracle_sample_step()
+        dt = cb.run(100 + i, R, cb.cores)
         if i >= args.warmup:
             dts.append(dt)
     ms = 1e3 * sum(dts) / len(dts)
-    value = pts / (ms / 1e3)
-    sample = "start ring (k0=512) of 1 realisation of the workload per step (2048 points), oracle incl. its covariance sums"
+    value = cb.points(R) / (ms / 1e3)
+    sample = cb.sample_text(R) + ("; " + note if note else "")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD if (args.tables or "fp64") == "fp64" else WORKLOAD.replace("FP64 tables", "FP32 tables"),
-                       "n_theta": N_THETA, "n_phi": N_PHI},
-            "cpu_baseline": {"value": value, "unit": "points/s", "cores": cpu_cores(), "kind": "oracle",
+            "config": {"workload": workload_name(args.workload), "name": args.workload,
+                       "n_theta": spec["n_theta"], "n_phi": spec["n_phi"]},
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": cb.cores, "kind": "oracle recursion (Alg. 2)",
                              "sample": sample},
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def workload_name(wl):
+    from paper_1709_10314_gb300.workloads import FIXED
+    if wl == "uneven-256":
+        return ("uneven batch: 256 requests, n_theta in {128,256,512,1024}, n_phi=2 n_theta, kappa in [5,200], "
+                "p in {1,2}, 1-8 realisations, FP32 recursion, one CUDA-graph replay per step")
+    c = FIXED[wl]
+    return "%dx%d equiangular grid, C_l=1/prod(l(l+1)+kappa^2) kappa=%s (p=%d), %d realisations, %s tables, %s recursion+FFT" % (
+        c["n_theta"], c["n_phi"], "(" + ",".join("%g" % k for k in c["kappa"]) + ")", len(c["kappa"]), c["n"],
+        c["tables"].upper(), c["recur"].upper())
 
 
 def run_gb300(args, rank, world, local_rank):
@@ -208,11 +290,14 @@ def run_gb300(args, rank, world, local_rank):
         alg_ops = sum(n * p.n_theta * (p.n_phi // 2) * alg_ops_per_item(p.info()["p"], p.n_phi // 2)
                       for p, n in zip(plans, counts))
         table_bytes = sum(p.info()["table_bytes"] for p in plans)
+        alg_tab = sum(alg_table_bytes(p.info()["p"], p.n_theta, p.n_phi, False) for p in plans)
+        sfu_ops = sum(n * p.n_theta * (p.n_phi // 2) * sfu_ops_per_item(p.info()["p"]) for p, n in zip(plans, counts))
         out_bytes = points * 4
         workload = ("uneven batch: 256 requests, n_theta in {128,256,512,1024}, n_phi=2 n_theta, kappa in [5,200], "
                     "p in {1,2}, 1-8 realisations, FP32 recursion, FP%s tables, one CUDA-graph replay per step"
                     % ("64" if args.tables == "fp64" else "32"))
         dtype = "f32"
+        anchor = 16  # the plans' default anchor spacing
         setup_ms = plans[0].info()["setup_ms"]  # the wall time of the one call that made them all
         s_cap = torch.cuda.Stream(device=dev)
 
@@ -243,9 +328,10 @@ def run_gb300(args, rank, world, local_rank):
         tables = args.tables or cfg["tables"]
         from paper_1709_10314_gb300 import SMERF_ORDER_PAPER
         paper_order = cfg.get("order") == "paper"
+        anchor = 0 if paper_order else (args.anchor or cfg.get("H", 16))
         plan = Plan(cfg["kappa"], cfg["A"], cfg["n_theta"], cfg["n_phi"],
                     flags=flags_for(recur, tables) | (SMERF_ORDER_PAPER if paper_order else 0),
-                    anchor_spacing=0 if paper_order else ANCHOR)
+                    anchor_spacing=anchor)
         info = plan.info()
         n = cfg["n"]
         # launch configuration of the segment kernel: timed candidates (set-up, untimed)
@@ -272,6 +358,9 @@ def run_gb300(args, rank, world, local_rank):
         workload = "%dx%d equiangular grid, C_l=1/prod(l(l+1)+kappa^2) kappa=%s (p=%d), %d realisations, %s tables, %s recursion+FFT" % (
             cfg["n_theta"], cfg["n_phi"], "(" + ",".join("%g" % k for k in cfg["kappa"]) + ")", len(cfg["kappa"]), n,
             tables.upper(), recur.upper())
+        p_ = len(cfg["kappa"])
+        alg_tab = alg_table_bytes(p_, cfg["n_theta"], cfg["n_phi"], fp64_alu)
+        sfu_ops = n * cfg["n_theta"] * (cfg["n_phi"] // 2) * sfu_ops_per_item(p_)
         launches = plan.launches(n)
         seed0 = rank_seed(cfg["seed"], rank, n * (args.warmup + args.steps + 8))
 
@@ -316,24 +405,33 @@ def run_gb300(args, rank, world, local_rank):
     step_ms, seg_ms = max_over_ranks([step_ms, seg_ms], device=dev)
     value = world * points / (step_ms / 1e3)
 
-    # Rooflines of the segment kernel.  It is bound by ALU issue (noise, recursion and FFT
-    # arithmetic), not by HBM: ALU = algorithmic operations / kernel time against the lane
-    # rate at the maximum SM clock; HBM = field written once + step tables and anchor states
-    # read once.  (FP64 tables with FP32 recursion: each call stages the step tables as FP32
-    # once; the segment kernel reads that copy, half their bytes.)  The batched graph replay
-    # (anchor and segment launches) counts the field and all of its plans' tables.
+    # Rooflines of the segment kernel (the kernel that synthesises and writes the field).
+    # HBM: the method's algorithmic bytes per launch -- the field written once plus the tables
+    # read once at the method's bytes per (mode, ring) (A and the lower factor B) -- against the
+    # measured copy bandwidth.  The bytes this design adds (bridge C blocks and row padding of
+    # the step tables, anchor states) are reported beside it, not counted as algorithmic.  ALU:
+    # algorithmic operations / kernel time against the FP32/INT32 lane rate at the maximum SM
+    # clock; the kernel is bound by instruction issue (noise, recursion and FFT arithmetic).
+    # SFU: Box-Muller's special functions against the 16 MUFU lanes per SM.  The batched graph
+    # replay (anchor and segment launches of every group) counts the field and all of its
+    # plans' tables.
     staged = batch is None and (args.recur or FIXED[wl]["recur"]) == "fp32" and \
         (args.tables or FIXED[wl]["tables"]) == "fp64" and FIXED[wl]["n"] >= 4
+    alg_bytes = out_bytes + alg_tab
     if batch is None:
         step_b, anc_b = seg_read_bytes
-        alg_bytes = out_bytes + (step_b // 2 if staged else step_b) + anc_b
+        step_read = step_b // 2 if staged else step_b
+        design = {"step_tables_as_read": step_read, "anchor_states": anc_b,
+                  "extra_over_algorithmic": step_read - alg_tab + anc_b}
     else:
-        alg_bytes = out_bytes + table_bytes
+        design = {"tables_stored": table_bytes, "extra_over_algorithmic": table_bytes - alg_tab}
     peak, peak_kind = _peaks()
     achieved = alg_bytes / (seg_ms / 1e3) / 1e9
     sm_max = float(clocks.get("sm_max_mhz") or 2070.0) if isinstance(clocks, dict) else 2070.0
     alu_pk = alu_peak(fp64_alu, sm_max) / 1e9
     alu_ach = alg_ops / (seg_ms / 1e3) / 1e9
+    sfu_pk = SMS * SFU_LANES * sm_max * 1e6 / 1e9
+    sfu_ach = sfu_ops / (seg_ms / 1e3) / 1e9
     # DRAM traffic of one segment-kernel launch from the committed ncu record, only while the
     # kernel sources still hash to what was profiled (null otherwise)
     traffic = None
@@ -342,13 +440,16 @@ def run_gb300(args, rank, world, local_rank):
         try:
             rec = json.load(open(prof))
             w = rec.get("workloads", {}).get(wl)
-            if w and rec.get("csrc_sha256_16") == csrc_digest() and w.get("launch") == launch_cfg:
+            if w and rec.get("csrc_sha256_16") == csrc_digest() and w.get("launch") == launch_cfg \
+                    and w.get("anchor_spacing", 16) == anchor:
                 traffic = w.get("traffic_bytes_per_launch")
         except Exception:
             traffic = None
 
     # end to end through the C ABI with host buffers (the field crosses the CPU-GPU link inside
-    # the timed region): smerf_sample_host, or the batch writing page-locked host outputs
+    # the timed region): smerf_sample_host, or the batch writing page-locked host outputs.  The
+    # link's own rate is measured beside it: one device-to-host copy of the same field into
+    # page-locked memory.
     e2e = None
     if batch is not None:
         host_outs = [torch.empty(tuple(o.shape), dtype=o.dtype, pin_memory=True) for o in outs]
@@ -363,6 +464,7 @@ def run_gb300(args, rank, world, local_rank):
         e2e_s = (time.perf_counter() - t0) / ne
         e2e = {"value": world * points / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": out_bytes}
+        del host_outs
     else:
         host = torch.empty(tuple(out.shape), dtype=out.dtype, pin_memory=True)
         plan.sample_host(seed0, n, host)
@@ -373,21 +475,37 @@ def run_gb300(args, rank, world, local_rank):
         e2e_s = (time.perf_counter() - t0) / ne
         e2e = {"value": world * points / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": out_bytes}
+        # link ceiling: cudaMemcpyAsync of the device field into the same page-locked buffer
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        host.copy_(out, non_blocking=True)
+        c0.record()
+        for _ in range(2):
+            host.copy_(out, non_blocking=True)
+        c1.record()
+        torch.cuda.synchronize()
+        link_s = c0.elapsed_time(c1) / 2 / 1e3
+        e2e["link"] = {"d2h_copy_gbs": out_bytes / link_s / 1e9, "host_path_gbs": out_bytes / e2e_s / 1e9,
+                       "what": "cudaMemcpyAsync of the field into page-locked host memory (CUDA events) vs "
+                               "the host-output sampling path (wall clock, synchronised per call)"}
+        del host
 
     if rank != 0:
         return
     cpu = None
-    if world == 1 and not args.no_cpu_baseline and wl == "1024x2048-p2":
-        dt, pts = oracle_sample_step(n_real=4)
-        cpu = {"value": pts / dt, "unit": "points/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": "start ring (k0=512) of realisations 1-4 of the workload (4 x 2048 points), "
-                         "the oracle's spectral-sum covariance, Cholesky, Philox noise and naive DFT"}
+    if world == 1 and not args.no_cpu_baseline:
+        spec, note = workload_spec(wl)
+        cb = CpuBaseline(spec["kappa"], spec["A"], spec["n_theta"], spec["n_phi"])
+        cpu = cb.measure()
+        if note:
+            cpu["sample"] += "; " + note
     line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-            "config": {"workload": workload, "name": wl, "points_per_gpu": points, "anchor_spacing": ANCHOR,
+            "config": {"workload": workload, "name": wl, "points_per_gpu": points, "anchor_spacing": anchor,
                        "launch": launch_cfg, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between timed steps (256 MiB write outside the step events)"},
+            "hbm_roofline_frac": achieved / peak,
             "roofline": {"bound": "alu", "achieved": alu_ach, "peak": alu_pk, "unit": "Gop/s",
                          "frac": alu_ach / alu_pk, "traffic": traffic,
                          "peak_kind": "derived: %d SMs x %d %s lanes x %.0f MHz" % (
@@ -395,7 +513,12 @@ def run_gb300(args, rank, world, local_rank):
                          "algorithmic_ops": alg_ops, "kernel": kernel, "kernel_ms": seg_ms,
                          "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                                  "peak_kind": peak_kind, "algorithmic_bytes": alg_bytes,
-                                 "tables_staged_fp32": staged}},
+                                 "algorithmic": "field written once + tables A, B read once per (mode, ring)",
+                                 "design_bytes": design, "tables_staged_fp32": staged,
+                                 "target_frac": 0.6},
+                         "sfu": {"achieved": sfu_ach, "peak": sfu_pk, "unit": "Gop/s", "frac": sfu_ach / sfu_pk,
+                                 "peak_kind": "derived: %d SMs x %d MUFU lanes x %.0f MHz" % (SMS, SFU_LANES, sm_max),
+                                 "ops": "log2, rsqrt, sin, cos per pair of normals"}},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches * args.steps,
@@ -422,8 +545,11 @@ def main():
     ap.add_argument("--launch", default=None,
                     help="fix the segment-kernel launch configuration: units/thread,realisations/CTA,"
                          "producer threads,FFT threads (one of the plan's candidates)")
-    ap.add_argument("--workload", default="1024x2048-p2",
-                    choices=["1024x2048-p2", "plain-64x128-p1-fp64", "4096x8192-p1", "16384x32768-p1", "uneven-256"])
+    ap.add_argument("--anchor", type=int, default=0,
+                    help="anchor spacing H of the plan (0: the workload's default)")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=["1024x2048-p2", "plain-64x128-p1-fp64", "4096x8192-p1", "16384x32768-p1", "4096x32768-p1",
+                             "uneven-256"])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -194,8 +194,10 @@ int smerf_sample_batched(const smerf_plan* const* plans, const uint64_t* seeds,
  * smerf_batch_launch: copies the staging memory to the device and launches every group on
  *   `stream` (asynchronous).  Capturable into a CUDA graph: a replay re-reads the staging
  *   memory, so smerf_batch_set between replays changes seeds and outputs.  Requests whose
- *   shape has no batched kernel (n_phi = 32768 in FP32) are launched individually with the
- *   seeds and outputs current at capture.
+ *   shape has no batched kernel (n_phi = 32768 in FP32) are launched individually, with their
+ *   seed and output passed by value; a batch that holds such requests returns
+ *   SMERF_EUNSUPPORTED when `stream` is capturing (a replay could not see later seeds and
+ *   outputs) and launches normally otherwise.
  * smerf_batch_sample: smerf_batch_set + smerf_batch_launch.
  * smerf_batch_info: number of batched groups and of individually launched requests.
  * smerf_batch_destroy: frees the batch; synchronise its streams first.  NULL is accepted.
@@ -221,9 +223,11 @@ int smerf_batch_destroy(smerf_batch* batch);
  * bytes of it (smerf_plan_info: scratch_bytes_per_sample * n_samples); larger requests
  * return SMERF_ESCRATCH and launch nothing.
  *
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any stream
- * capture.  All calls share the one array and it keeps the last call's contents: two calls
+ * Each call made outside stream capture looks up the array's device address
+ * (cudaGetSymbolAddress) with the plan's device current, so a context that was reset and
+ * reloaded the library's device image is followed; a call made while `stream` is capturing
+ * reuses the address found by the last call outside capture on that device (SMERF_EUNSUPPORTED
+ * if there was none), so make one call before any capture.  All calls share the one array and it keeps the last call's contents: two calls
  * whose kernels overlap on the GPU (different streams, no ordering between them) race on
  * it, so serialise them.  Calls no cudaMalloc, cudaFree or other allocating routine.
  */

@@ -198,6 +198,14 @@ int smerf_batch_launch(smerf_batch* b, void* stream)
     if (dev != b->dev) return SMERF_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     if (b->n_req == 0) return SMERF_OK;
+    if (!b->singles.empty()) {
+        // individually launched requests take their seed and output by value: a captured
+        // graph would replay them with the values current at capture, whatever
+        // smerf_batch_set changes later, so such batches are not captured
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return SMERF_ECUDA;
+        if (cs != cudaStreamCaptureStatusNone) return SMERF_EUNSUPPORTED;
+    }
     if (cudaMemcpyAsync(b->d_descs, b->h_descs, sizeof(SampleParams) * b->n_req, cudaMemcpyHostToDevice, st) !=
         cudaSuccess)
         return SMERF_ECUDA;

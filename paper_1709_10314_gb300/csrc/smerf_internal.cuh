@@ -197,6 +197,7 @@ template <class C> __device__ __forceinline__ C cmul(C a, C b) { return cmk<C>(a
 template <class C> __device__ __forceinline__ C cconj(C a) { return cmk<C>(a.x, -a.y); }
 template <class C> __device__ __forceinline__ C cmuli(C a) { return cmk<C>(-a.y, a.x); }  // i * a
 
+
 }  // namespace smerf
 
 // sampling entry points used by smerf_api.cu (the set-up's are in smerf_setup.h)

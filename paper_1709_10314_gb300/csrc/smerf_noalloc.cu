@@ -17,8 +17,8 @@
 namespace {
 
 // The fixed scratch.  Host code must not use this name as a pointer: on the host it
-// denotes a stand-in object, not the device address.  The device address is obtained
-// once per device with cudaGetSymbolAddress (scratch_address below).
+// denotes a stand-in object, not the device address.  The device address comes from
+// cudaGetSymbolAddress (scratch_address below).
 constexpr size_t kNoAllocBytes = (size_t)16 << 20;  // 16 MiB per device
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -26,17 +26,23 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void* g_address[kMaxDevices] = {};
 
-// Device address of g_noalloc_scratch on device `dev`, which must be current.  The first
-// call on each device looks it up; later calls reuse it.
-int scratch_address(int dev, void** out)
+// Device address of g_noalloc_scratch on device `dev`, which must be current.  Outside stream
+// capture it is looked up on every call (cheap, and it follows a context that was reset and
+// reloaded the device image); while `st` is capturing, the address found by the last lookup on
+// this device is reused, since a capture should make no such runtime queries.
+int scratch_address(int dev, cudaStream_t st, void** out)
 {
     if (dev < 0 || dev >= kMaxDevices) return SMERF_EINVAL;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return SMERF_ECUDA;
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_address[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return SMERF_ECUDA;
         g_address[dev] = p;
+    } else if (!g_address[dev]) {
+        return SMERF_EUNSUPPORTED;  // no lookup outside capture yet on this device
     }
     *out = g_address[dev];
     return SMERF_OK;
@@ -55,7 +61,7 @@ extern "C" int smerf_sample_noalloc(const smerf_plan* plan, uint64_t seed, int n
     if (dev != plan->dev) return SMERF_EINVAL;
     if (smerf_scratch_bytes(plan, n_samples) > kNoAllocBytes) return SMERF_ESCRATCH;
     void* scratch = nullptr;
-    const int rc = scratch_address(dev, &scratch);
+    const int rc = scratch_address(dev, (cudaStream_t)stream, &scratch);
     if (rc != SMERF_OK) return rc;
     // Every anchor state the segment kernel reads is first written by the anchor kernel of
     // the same call, so the array needs no clearing between calls.

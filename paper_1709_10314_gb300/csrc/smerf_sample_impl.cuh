@@ -1182,13 +1182,21 @@ __global__ void __launch_bounds__(ws_max_threads(MINB), MINB) segment_ws_batched
     ws_body<Real, TabT, M, UPT, RMAX>(P, it.y, it.z);
 }
 
+}  // namespace smerf
+
+#include "smerf_ring.cuh"
+
+namespace smerf {
+
 // ------------------------------------------------------------------ launch
 // Raise a kernel's dynamic shared-memory limit to what it needs, once per kernel and size
 // (so that later launches, e.g. under stream capture, make no attribute calls).
 template <class K>
 inline cudaError_t set_smem_attr(K kern, size_t smem)
 {
-    if (smem <= 48 * 1024) return cudaSuccess;
+    // the 48 KiB default covers dynamic plus static shared memory; the sampling kernels'
+    // static arrays (round keys) take well under 1 KiB
+    if (smem + 1024 <= 48 * 1024) return cudaSuccess;
     int dev = 0;
     cudaGetDevice(&dev);
     if (::smerf_smem_attr_done((const void*)kern, dev, smem, false)) return cudaSuccess;
@@ -1219,6 +1227,16 @@ auto pick_inplace(int lgNc)
                       : segment_kernel<Real, TabT, M, UPT, 0, PARK>;
 }
 
+template <class TabT, int LG, int PARK, int MINB>
+int launch_ring(const SampleParams& P, int n_segments, size_t smem, cudaStream_t st)
+{
+    auto kern = ring_kernel<TabT, LG, PARK, MINB>;
+    if (set_smem_attr(kern, smem) != cudaSuccess) return SMERF_ECUDA;
+    dim3 grid(P.n_samples, n_segments);
+    kern<<<grid, RingPass<LG>::NT, smem, st>>>(P);
+    return cudaGetLastError() == cudaSuccess ? SMERF_OK : SMERF_ECUDA;
+}
+
 template <class Real, class TabT, int M, int UPT, int PARK>
 int launch_inplace(const SampleParams& P, int n_segments, int nt, size_t smem, cudaStream_t st)
 {
@@ -1234,7 +1252,29 @@ int launch_inplace(const SampleParams& P, int n_segments, int nt, size_t smem, c
 // upt (<= 512), FFT threads np/2, rmax realisations per CTA (as many as registers and shared
 // memory allow).  Otherwise the in-place kernel (one FFT buffer, anchors read from the
 // scratch, one realisation per CTA, up to 1024 threads).
-struct SegConfig { int ws, upt, nt, np, rmax, park, minb; size_t smem; };
+struct SegConfig { int ws, upt, nt, np, rmax, park, minb; size_t smem; int ring; };
+
+// Long rings with p = 1 in FP32 (Nc = 8192 or 16384): the ring kernel (smerf_ring.cuh), NT =
+// Nc / 16 threads, 8 units per thread of which 6 are parked in shared memory; at Nc = 8192 two
+// CTAs fit on an SM.
+#ifndef SMERF_RING_KERNEL
+#define SMERF_RING_KERNEL 1
+#endif
+template <class Real>
+inline bool ring_config(const smerf_plan* pl, SegConfig& cfg)
+{
+    const int Nc = pl->n_phi / 2;
+    if (!SMERF_RING_KERNEL || sizeof(Real) != 4 || pl->p != 1 || (Nc != 8192 && Nc != 16384)) return false;
+    cfg = SegConfig{};
+    cfg.ring = 1;
+    cfg.nt = Nc / 16;
+    cfg.upt = 8;
+    cfg.rmax = 1;
+    cfg.park = 6;
+    cfg.minb = Nc == 8192 ? 2 : 1;
+    cfg.smem = (size_t)Nc * 8 + (size_t)cfg.park * cfg.nt * 16;
+    return true;
+}
 
 template <class Real> constexpr int ws_rmax_cap(int upt)
 {
@@ -1338,9 +1378,11 @@ inline SegConfig seg_config(const smerf_plan* pl)
             }
         }
     }
+    if (ring_config<Real>(pl, cfg)) return cfg;
     upt = 1;
     while (upt < 8 && (n_units + upt - 1) / upt > kMaxThreads) upt *= 2;
     if (upt < 4) upt = 4;
+
     int nt = (n_units + upt - 1) / upt;
     nt = ((nt + 31) / 32) * 32;
     if (nt < 64) nt = 64;
@@ -1387,6 +1429,13 @@ int dispatch_segments(const SampleParams& P, int n_segments, const SegConfig& cf
             default: return SMERF_EUNSUPPORTED;
         }
         }
+    }
+    if (cfg.ring) {
+        if constexpr (sizeof(Real) == 4 && M == 1) {
+            if (P.lgNc == 14) return launch_ring<TabT, 14, 6, 1>(P, n_segments, cfg.smem, st);
+            if (P.lgNc == 13) return launch_ring<TabT, 13, 6, 2>(P, n_segments, cfg.smem, st);
+        }
+        return SMERF_EUNSUPPORTED;
     }
     switch (cfg.upt * 16 + cfg.park) {
         case 4 * 16 + 2: return launch_inplace<Real, TabT, M, 4, 2>(P, n_segments, cfg.nt, cfg.smem, st);

@@ -231,13 +231,28 @@ class Plan:
         import torch
         return torch.float64 if self.fp64 else torch.float32
 
+    def _check_out(self, out, n_samples):
+        """The C ABI cannot see a buffer's length: a device tensor of this plan's dtype, dense,
+        on the current device, with room for n_samples realisations, or ValueError."""
+        import torch
+        if not isinstance(out, torch.Tensor) or not out.is_cuda:
+            raise ValueError("out must be a CUDA tensor")
+        if out.dtype != self.dtype:
+            raise ValueError("out has dtype %s; this plan writes %s" % (out.dtype, self.dtype))
+        if not out.is_contiguous():
+            raise ValueError("out must be contiguous")
+        if out.device.index != torch.cuda.current_device():
+            raise ValueError("out is on %s, the current device is cuda:%d" % (out.device, torch.cuda.current_device()))
+        if int(n_samples) < 0 or out.numel() < int(n_samples) * self.n_theta * self.n_phi:
+            raise ValueError("out holds %d elements; %d realisations need %d" % (
+                out.numel(), int(n_samples), int(n_samples) * self.n_theta * self.n_phi))
+
     def sample(self, seed, n_samples, out=None, stream=None):
         """Device realisations [n_samples][n_theta][n_phi] (torch tensor on the current device)."""
         import torch
         if out is None:
             out = torch.empty((n_samples, self.n_theta, self.n_phi), dtype=self.dtype, device="cuda")
-        assert out.is_cuda and out.is_contiguous() and out.dtype == self.dtype
-        assert out.numel() >= n_samples * self.n_theta * self.n_phi
+        self._check_out(out, n_samples)
         _check("smerf_sample", _lib().smerf_sample(self._h, ctypes.c_uint64(seed & (2**64 - 1)), int(n_samples),
                                                     ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out
@@ -245,8 +260,7 @@ class Plan:
     def sample_noalloc(self, seed, n_samples, out, stream=None):
         """smerf_sample_noalloc: like sample() but the library allocates nothing (its scratch
         is a fixed 16 MiB device array; larger requests raise SmerfError SMERF_ESCRATCH)."""
-        assert out.is_cuda and out.is_contiguous() and out.dtype == self.dtype
-        assert out.numel() >= n_samples * self.n_theta * self.n_phi
+        self._check_out(out, n_samples)
         _check("smerf_sample_noalloc",
                _lib().smerf_sample_noalloc(self._h, ctypes.c_uint64(seed & (2**64 - 1)), int(n_samples),
                                            ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
@@ -254,6 +268,7 @@ class Plan:
 
     def sample_timed(self, seed, n_samples, out, ev_before, ev_after, stream=None):
         """smerf_sample_timed: records the two torch.cuda.Event objects around the segment kernel."""
+        self._check_out(out, n_samples)
         for ev in (ev_before, ev_after):
             if not ev.cuda_event:
                 ev.record()  # torch creates the event handle lazily

@@ -103,7 +103,8 @@ def test_16384x32768_ring_variance(big):
     plan, out = big
     nt, nphi = 16384, 32768
     rings = [8192, 4000]
-    V = oracle.mode_variances([300.0], 1.0, nt, nphi, K=3, rings=rings, c_turn_diag=2.0)
+    # cut-off levels pinned at these rings and orders (tests/test_oracle_cov_high_order.py)
+    V = oracle.mode_variances([300.0], 1.0, nt, nphi, K=4, rings=rings, c_turn_diag=4.0)
     w = np.full(nphi // 2 + 1, 2.0)
     w[0], w[-1] = 1.0, 0.5
     for i, k in enumerate(rings):

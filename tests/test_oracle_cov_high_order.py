@@ -34,6 +34,16 @@ PINS = [
     ([300.0], 16384, 16384, [4000], 4, dict(c_turn_diag=4.0), 2e-5),
     ([300.0], 16384, 4000, [8183, 8184, 8176], 6, {}, 1e-10),
     ([300.0], 16384, 16384, [8171, 8172, 8160], 6, {}, 1e-10),
+    # stepped-ring parity grids (tests/test_gpu_stepped.py): 48 x 2048, p = 2, anchors every 16
+    # rings (start ring, both anchors, the first bridge rings; K = 4, c_turn_diag = 8), and
+    # 4 x 32768, p = 1 (start ring and its neighbour; K = 4, c_turn_diag = 4)
+    ([20.0, 50.0], 48, 300, [24, 8, 40, 23, 22], 4, dict(c_turn_diag=8.0), 1e-6),
+    ([20.0, 50.0], 48, 1024, [24, 8, 40, 23, 22], 4, dict(c_turn_diag=8.0), 1e-6),
+    ([300.0], 4, 4000, [2, 1], 4, dict(c_turn_diag=4.0), 2e-5),
+    ([300.0], 4, 16384, [2, 1], 4, dict(c_turn_diag=4.0), 2e-5),
+    # 24 x 16384, p = 1, anchors every 8 rings: start ring, anchors, first bridge rings
+    ([300.0], 24, 3000, [12, 4, 20, 11, 10], 4, dict(c_turn_diag=4.0), 2e-5),
+    ([300.0], 24, 8192, [12, 4, 20, 11, 10], 4, dict(c_turn_diag=4.0), 2e-5),
 ]
 
 
