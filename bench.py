@@ -138,7 +138,8 @@ def csrc_digest():
     h = hashlib.sha256()
     base = os.path.join(ROOT, "paper_1709_10314_gb300", "csrc")
     for f in sorted(glob.glob(os.path.join(base, "smerf_sample_*.cu")) +
-                    [os.path.join(base, "smerf_sample_impl.cuh"), os.path.join(base, "smerf_internal.cuh")]):
+                    [os.path.join(base, "smerf_sample_impl.cuh"), os.path.join(base, "smerf_internal.cuh"),
+                     os.path.join(base, "smerf_ring.cuh")]):
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -312,7 +313,7 @@ def run_gb300(args, rank, world, local_rank):
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=s_cap, capture_error_mode="relaxed"):
             batch.launch(stream=s_cap)
-        launches = 2 * batch.info()["groups"] + batch.info()["singles"] * 2
+        launches = batch.info()["launches"]  # one anchor launch + one persistent segment launch
 
         def step(i, ev0=None, ev1=None):
             torch.cuda.synchronize()
@@ -398,7 +399,9 @@ def run_gb300(args, rank, world, local_rank):
     step_ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / args.steps
     if batch is None:
         seg_ms = sum(a.elapsed_time(b) for a, b in zip(s0, s1)) / args.steps
-        kernel = "segment_ws_kernel" if ws_kernel else "segment_kernel"
+        ring = (not ws_kernel) and len(FIXED[wl]["kappa"]) == 1 and (args.recur or FIXED[wl]["recur"]) == "fp32" \
+            and FIXED[wl]["n_phi"] in (16384, 32768)
+        kernel = "segment_ws_kernel" if ws_kernel else ("ring_kernel" if ring else "segment_kernel")
     else:
         seg_ms = step_ms  # the graph replay: all groups' anchor + segment launches
         kernel = "batched graph replay (anchor + segment launches of every group)"

@@ -191,15 +191,22 @@ int smerf_sample_batched(const smerf_plan* const* plans, const uint64_t* seeds,
  *   cudaHostAlloc memory or pinned torch tensors, which the kernels then write over the
  *   CPU-GPU link) in the batch's pinned staging memory.  Host-only; the previous launch's copy of the staging
  *   memory must have completed (synchronise its stream first).
- * smerf_batch_launch: copies the staging memory to the device and launches every group on
- *   `stream` (asynchronous).  Capturable into a CUDA graph: a replay re-reads the staging
+ * smerf_batch_launch: copies the staging memory to the device and launches the batch on
+ *   `stream` (asynchronous): for FP32 recursion, one anchor launch over all requests' anchor
+ *   items, a reset of the work queue, and one launch of persistent CTAs that take the segment
+ *   items of every shape from that queue (Alg. 2's two steps, the anchors before the segments
+ *   by stream order); for FP64 recursion, an anchor and a segment launch per kernel shape.  Capturable into a CUDA graph: a replay re-reads the staging
  *   memory, so smerf_batch_set between replays changes seeds and outputs.  Requests whose
  *   shape has no batched kernel (n_phi = 32768 in FP32) are launched individually, with their
  *   seed and output passed by value; a batch that holds such requests returns
  *   SMERF_EUNSUPPORTED when `stream` is capturing (a replay could not see later seeds and
  *   outputs) and launches normally otherwise.
  * smerf_batch_sample: smerf_batch_set + smerf_batch_launch.
- * smerf_batch_info: number of batched groups and of individually launched requests.
+ * smerf_batch_info: number of kernel shapes among the batched requests (groups) and of
+ *   individually launched requests.
+ * smerf_batch_launch_count: kernels one smerf_batch_launch starts (requests with FP32
+ *   recursion: one anchor launch and one persistent segment launch per table precision, every
+ *   shape together; FP64 recursion: two per shape; plus the individually launched requests').
  * smerf_batch_destroy: frees the batch; synchronise its streams first.  NULL is accepted.
  */
 typedef struct smerf_batch smerf_batch;
@@ -208,6 +215,7 @@ int smerf_batch_set(smerf_batch* batch, const uint64_t* seeds, void* const* outs
 int smerf_batch_launch(smerf_batch* batch, void* stream);
 int smerf_batch_sample(smerf_batch* batch, const uint64_t* seeds, void* const* outs, void* stream);
 int smerf_batch_info(const smerf_batch* batch, int* n_groups, int* n_singles);
+int smerf_batch_launch_count(const smerf_batch* batch);
 int smerf_batch_destroy(smerf_batch* batch);
 
 /*
@@ -283,6 +291,21 @@ int smerf_plan_info(const smerf_plan* plan, smerf_plan_info_t* info);
 int smerf_plan_autotune(smerf_plan* plan, int n_samples, void* stream, int* chosen);
 
 /*
+ * smerf_plan_autotune_anchor -- choose the anchor spacing H (the band of rings one segment CTA
+ * samples between two anchors) by timing: for each of the n_cand (1..16) spacings in
+ * candidates[] (each >= 1) the plan's tables are built again with that spacing and whole
+ * smerf_sample calls of n_samples realisations are timed on `stream`; the plan keeps the
+ * fastest spacing's tables (the same handle; its launch configuration, if fixed, is kept).  H
+ * changes the order in which rings are conditioned, hence the map from noise to field, not the
+ * field's law (Markov property, Sec. 2).  Synchronous; allocates a temporary output; must not
+ * run while other calls use the plan.  *chosen (may be NULL) receives the chosen H, or 0 for a
+ * plan in Alg. 2's order (SMERF_ORDER_PAPER), which has no anchors and is left unchanged.
+ * Errors as for smerf_plan_create_ex, plus SMERF_EINVAL for bad candidates.
+ */
+int smerf_plan_autotune_anchor(smerf_plan* plan, int n_samples, const int* candidates, int n_cand, void* stream,
+                               int* chosen);
+
+/*
  * smerf_plan_launch_candidates -- the launch configurations smerf_plan_autotune chooses from,
  * SMERF_LAUNCH_INTS integers each, in cand[SMERF_LAUNCH_INTS * i ...] for
  * i < min(count, max_n).  Returns the count (0: no tunable kernel) or SMERF_EINVAL.  Host
@@ -320,6 +343,12 @@ int smerf_plan_copy_tables(const smerf_plan* plan, int which, int chain, int pos
  *   in FP32 (fp64 = 0, float out) or FP64 (fp64 = 1, double out).  Asynchronous. */
 int smerf_philox_uint32(uint64_t key64, uint32_t ring, int64_t ncalls, uint32_t* out, void* stream);
 int smerf_ring_normals(uint64_t key64, uint32_t ring, int64_t n, int fp64, void* out, void* stream);
+
+/* Test hook: the device or page-locked allocation that the library makes after k more from now
+ * (k = 0: the next one) fails as if memory were exhausted; k < 0 turns the injection off.  The
+ * failing call returns SMERF_ENOMEM and releases what it had allocated.  Process-wide; returns
+ * SMERF_OK. */
+int smerf_debug_fail_alloc(int k);
 
 /* Human-readable name of a status code. */
 const char* smerf_status_string(int status);

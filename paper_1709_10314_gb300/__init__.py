@@ -9,5 +9,6 @@ the library has not been built (``python -m paper_1709_10314_gb300.build``).
 """
 from .smerf import (  # noqa: F401
     SMERF_ORDER_PAPER, SMERF_RECUR_FP64, SMERF_TABLES_FP32, SMERF_TABLES_FP64, Batch, Plan, SmerfError,
-    create_plans, last_device_status, library_path, philox_uint32, ring_normals, sample_batched, scratch_trim,
+    create_plans, debug_fail_alloc, last_device_status, library_path, philox_uint32, ring_normals, sample_batched,
+    scratch_trim,
 )

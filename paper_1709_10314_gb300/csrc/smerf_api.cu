@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <chrono>
 #include <map>
 #include <mutex>
@@ -231,11 +232,30 @@ cudaError_t scratch_alloc(void** p, size_t bytes, int dev, cudaStream_t st)
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return cudaGetLastError();
     cudaMemPool_t pool = cs == cudaStreamCaptureStatusNone ? scratch_pool(dev, true) : nullptr;
-    return pool ? cudaMallocFromPoolAsync(p, bytes, pool, st) : cudaMallocAsync(p, bytes, st);
+    return pool ? smerf::dev_malloc_pool(p, bytes, pool, st) : smerf::dev_malloc_async(p, bytes, st);
 }
 }  // namespace
 
+// allocation-failure injection (smerf_debug_fail_alloc): -1 = off, k >= 0 = the allocation
+// after k more succeeds fails
+static std::atomic<long> g_alloc_countdown(-1);
+
+bool smerf::alloc_fail_now()
+{
+    long v = g_alloc_countdown.load();
+    while (v >= 0) {
+        if (g_alloc_countdown.compare_exchange_weak(v, v - 1)) return v == 0;
+    }
+    return false;
+}
+
 extern "C" {
+
+int smerf_debug_fail_alloc(int k)
+{
+    g_alloc_countdown.store(k < 0 ? -1 : (long)k);
+    return SMERF_OK;
+}
 
 const char* smerf_status_string(int status)
 {
@@ -415,7 +435,7 @@ static int create_plan(const double* kappa, const double* kh_re, const double* k
     if (!pl->segs_host) { delete pl; return SMERF_ENOMEM; }
     memcpy(pl->segs_host, segs.data(), sizeof(Segment) * segs.size());
     int rc = SMERF_OK;
-    if (cudaMalloc(&pl->segs_dev, sizeof(Segment) * segs.size()) != cudaSuccess) rc = SMERF_ENOMEM;
+    if (smerf::dev_malloc((void**)&pl->segs_dev, sizeof(Segment) * segs.size()) != cudaSuccess) rc = SMERF_ENOMEM;
     else if (cudaMemcpy(pl->segs_dev, segs.data(), sizeof(Segment) * segs.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         rc = SMERF_ECUDA;
     if (rc == SMERF_OK) rc = smerf_setup_tables(pl, st, sync);
@@ -644,7 +664,7 @@ int smerf_plan_autotune(smerf_plan* plan, int n_samples, void* stream, int* chos
     int rc = SMERF_OK;
     const size_t sb = (smerf_scratch_bytes(plan, n_samples) + 255) / 256 * 256;
     const size_t tb = smerf_stage_bytes(plan, n_samples);
-    if (cudaMalloc(&out, ob) != cudaSuccess || cudaMalloc(&scratch, sb + tb) != cudaSuccess)
+    if (smerf::dev_malloc((void**)&out, ob) != cudaSuccess || smerf::dev_malloc((void**)&scratch, sb + tb) != cudaSuccess)
         rc = SMERF_ENOMEM;
     if (rc == SMERF_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = SMERF_ECUDA;
     float best = 1e30f;
@@ -688,6 +708,67 @@ int smerf_plan_autotune(smerf_plan* plan, int n_samples, void* stream, int* chos
     if (e1) cudaEventDestroy(e1);
     cudaFree(out);
     cudaFree(scratch);
+    return rc;
+}
+
+int smerf_plan_autotune_anchor(smerf_plan* plan, int n_samples, const int* candidates, int n_cand, void* stream,
+                               int* chosen)
+{
+    if (chosen) *chosen = 0;
+    if (!plan || n_samples < 1 || n_samples > 65535 || n_cand < 1 || n_cand > 16 || !candidates) return SMERF_EINVAL;
+    for (int i = 0; i < n_cand; ++i)
+        if (candidates[i] < 1) return SMERF_EINVAL;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != plan->dev) return SMERF_EINVAL;
+    if (plan->flags & SMERF_ORDER_PAPER) return SMERF_OK;  // Alg. 2's order: no anchors to space
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t ob = (size_t)n_samples * plan->n_theta * plan->n_phi * (plan->recur64 ? 8 : 4);
+    void* out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = SMERF_OK;
+    if (smerf::dev_malloc(&out, ob) != cudaSuccess) rc = SMERF_ENOMEM;
+    if (rc == SMERF_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = SMERF_ECUDA;
+    smerf_plan* best = nullptr;
+    float best_ms = 1e30f;
+    for (int i = 0; rc == SMERF_OK && i < n_cand; ++i) {
+        smerf_plan* cp = nullptr;
+        rc = create_plan(plan->p > 0 ? plan->kappa : nullptr, plan->khat_re, plan->khat_im, plan->complex_spec, plan->p,
+                         plan->A, plan->n_theta, plan->n_phi, plan->flags, candidates[i], &cp);
+        if (rc != SMERF_OK) break;
+        cp->tune = plan->tune;  // the plan's launch configuration, if it fixed one
+        const size_t sb = (smerf_scratch_bytes(cp, n_samples) + 255) / 256 * 256;
+        const size_t tb = smerf_stage_bytes(cp, n_samples);
+        void* scratch = nullptr;
+        if (smerf::dev_malloc(&scratch, sb + tb) != cudaSuccess) rc = SMERF_ENOMEM;
+        float tot = 0.0f;
+        for (int it = 0; rc == SMERF_OK && it < 4; ++it) {
+            if (cudaEventRecord(e0, st) != cudaSuccess) rc = SMERF_ECUDA;
+            if (rc == SMERF_OK)
+                rc = smerf_launch_sample_staged(cp, 1 + it, n_samples, out, scratch,
+                                                tb ? (void*)((unsigned char*)scratch + sb) : nullptr, st, nullptr, nullptr);
+            if (rc == SMERF_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+                rc = SMERF_ECUDA;
+            float ms = 0.0f;
+            if (rc == SMERF_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = SMERF_ECUDA;
+            if (it > 0) tot += ms;  // the first call is a warm-up
+        }
+        cudaFree(scratch);
+        if (rc == SMERF_OK && tot < best_ms) {
+            best_ms = tot;
+            std::swap(best, cp);
+        }
+        if (cp) smerf_plan_destroy(cp);
+    }
+    if (rc == SMERF_OK && best) {
+        // the caller's handle takes the fastest plan's tables; its old tables go with `best`
+        std::swap(*plan, *best);
+        if (chosen) *chosen = plan->H;
+    }
+    if (best) smerf_plan_destroy(best);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
     return rc;
 }
 

@@ -1,13 +1,16 @@
 // smerf_batch.cu -- batched sampling: many requests (plans of different grids, spectra and
-// precisions) in few launches.  Requests of the same kernel shape (recursion and table
-// precision, p, n_phi, anchored or not) form a group that runs as one anchor launch and one
-// segment launch over a device work list; per-request parameters (tables, seed, output,
-// scratch) are read from a descriptor array in device memory.  The work lists and the
-// scratch are built once per batch, so a launch (descriptor copy + kernels) can be captured
-// into a CUDA graph and replayed with new seeds and outputs.
+// precisions) in few launches.  Requests with FP32 recursion run in two persistent phases per
+// table precision: one anchor launch over every request's anchor items, then one launch of
+// persistent CTAs that pull segment items of every shape (p, n_phi, launch configuration) from
+// a device queue, largest first.  Requests with FP64 recursion form groups of one kernel shape
+// that run as one anchor launch and one segment launch each.  Per-request parameters (tables,
+// seed, output, scratch) are read from a descriptor array in device memory.  The work lists and
+// the scratch are built once per batch, so a launch (descriptor copy, queue reset, kernels) can
+// be captured into a CUDA graph and replayed with new seeds and outputs.
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <new>
 #include <tuple>
@@ -32,6 +35,34 @@ int fill_params(int kind, const smerf_plan* pl, uint64_t seed, int n, void* out,
         case kDD: return smerf_fill_params_dd(pl, seed, n, out, scratch, P, batchable, rmax);
         default: return smerf_fill_params_df(pl, seed, n, out, scratch, P, batchable, rmax);
     }
+}
+
+// the FP32-recursion kinds run as two persistent phases
+bool queued(int kind) { return kind == kFF || kind == kFD; }
+
+// A queued kind's work: anchor items, segment items (largest first), the persistent launch's
+// threads, shared memory and CTAs, and the device counter of its queue.
+struct Queue {
+    int kind;
+    int4* d_anc = nullptr;
+    int n_anc = 0;
+    int4* d_seg = nullptr;
+    int n_seg = 0;
+    int nt = 0;
+    size_t smem = 0;
+    int ctas = 0;
+    int* d_head = nullptr;
+};
+
+int launch_queue(const Queue& q, const SampleParams* d, cudaStream_t st)
+{
+    return q.kind == kFF ? smerf_launch_queue_ff(d, q.d_anc, q.n_anc, q.d_seg, q.n_seg, q.d_head, q.nt, q.smem, q.ctas, st)
+                         : smerf_launch_queue_fd(d, q.d_anc, q.n_anc, q.d_seg, q.n_seg, q.d_head, q.nt, q.smem, q.ctas, st);
+}
+
+int queue_ctas(int kind, int nt, size_t smem)
+{
+    return kind == kFF ? smerf_queue_ctas_ff(nt, smem) : smerf_queue_ctas_fd(nt, smem);
 }
 
 int launch_group(int kind, const smerf_plan* rep, const SampleParams* d, const int4* a, int na, const int4* s, int ns,
@@ -63,7 +94,8 @@ struct smerf_batch {
     std::vector<int> counts;
     std::vector<size_t> offs;
     std::vector<int> singles;  // requests whose shape has no batched kernel (launched one by one)
-    std::vector<Group> groups;
+    std::vector<Group> groups;   // kernel shapes (FP64 recursion: launched per group)
+    std::vector<Queue> queues;   // FP32 recursion: two persistent phases per table precision
     void* scratch = nullptr;
     SampleParams* h_descs = nullptr;  // pinned staging
     SampleParams* d_descs = nullptr;
@@ -77,6 +109,11 @@ static void batch_free(smerf_batch* b)
     for (auto& g : b->groups) {
         cudaFree(g.d_anc);
         cudaFree(g.d_seg);
+    }
+    for (auto& q : b->queues) {
+        cudaFree(q.d_anc);
+        cudaFree(q.d_seg);
+        cudaFree(q.d_head);
     }
     cudaFree(b->scratch);
     cudaFree(b->d_descs);
@@ -109,10 +146,10 @@ int smerf_batch_create(const smerf_plan* const* plans, const int* n_samples, int
         total += (smerf_scratch_bytes(plans[i], n_samples[i]) + 255) & ~(size_t)255;
     }
     int rc = SMERF_OK;
-    if (total && cudaMalloc(&b->scratch, total) != cudaSuccess) rc = SMERF_ENOMEM;
+    if (total && smerf::dev_malloc((void**)&b->scratch, total) != cudaSuccess) rc = SMERF_ENOMEM;
     if (rc == SMERF_OK && n_req) {
-        if (cudaMallocHost((void**)&b->h_descs, sizeof(SampleParams) * n_req) != cudaSuccess ||
-            cudaMalloc((void**)&b->d_descs, sizeof(SampleParams) * n_req) != cudaSuccess)
+        if (smerf::host_malloc((void**)&b->h_descs, sizeof(SampleParams) * n_req) != cudaSuccess ||
+            smerf::dev_malloc((void**)&b->d_descs, sizeof(SampleParams) * n_req) != cudaSuccess)
             rc = SMERF_ENOMEM;
     }
     // group by kernel shape; build the work lists
@@ -160,13 +197,72 @@ int smerf_batch_create(const smerf_plan* const* plans, const int* n_samples, int
         Group& gr = b->groups[g];
         gr.n_anc = (int)anc[g].size();
         gr.n_seg = (int)seg[g].size();
-        if (cudaMalloc(&gr.d_anc, sizeof(int4) * gr.n_anc) != cudaSuccess ||
-            cudaMalloc(&gr.d_seg, sizeof(int4) * gr.n_seg) != cudaSuccess) {
+        if (smerf::dev_malloc((void**)&gr.d_anc, sizeof(int4) * gr.n_anc) != cudaSuccess ||
+            smerf::dev_malloc((void**)&gr.d_seg, sizeof(int4) * gr.n_seg) != cudaSuccess) {
             rc = SMERF_ENOMEM;
             break;
         }
         if (cudaMemcpy(gr.d_anc, anc[g].data(), sizeof(int4) * gr.n_anc, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(gr.d_seg, seg[g].data(), sizeof(int4) * gr.n_seg, cudaMemcpyHostToDevice) != cudaSuccess)
+            rc = SMERF_ECUDA;
+    }
+    // the FP32-recursion requests merged into one queue per table precision; each runs with the
+    // queue's build for its size (smerf::queue_build), its descriptor's producer count set to it
+    for (int kind : {(int)kFF, (int)kFD}) {
+        if (rc != SMERF_OK) break;
+        std::vector<int4> qa;
+        std::vector<std::pair<double, int4>> qs;
+        size_t smem = 0;
+        for (size_t g = 0; g < b->groups.size() && rc == SMERF_OK; ++g) {
+            if (b->groups[g].kind != kind) continue;
+            for (const int4& it : anc[g]) qa.push_back(make_int4(it.x, it.y, it.z, it.w | (plans[it.x]->p << 4)));
+            int last = -1;
+            for (const int4& it : seg[g]) {
+                const int i = it.x;
+                if (i == last) continue;  // the request's items are made below, once
+                last = i;
+                const smerf_plan* pl = plans[i];
+                const int units = pl->n_slots / smerf::unit_slots(pl->p);
+                const int bld = smerf::queue_build(units);
+                if (bld < 0) { rc = SMERF_EUNSUPPORTED; break; }
+                const int upt = smerf::queue_upt(bld), rmax = smerf::queue_rmax(bld);
+                b->h_descs[i].np = (((units + upt - 1) / upt + 31) / 32) * 32;
+                const size_t sm = kind == kFF ? smerf_ws_smem_ff(pl, rmax) : smerf_ws_smem_fd(pl, rmax);
+                smem = sm > smem ? sm : smem;
+                const int n = n_samples[i];
+                for (int sgi = 0; sgi < pl->n_segments; ++sgi)
+                    for (int grp = 0; grp < (n + rmax - 1) / rmax; ++grp) {
+                        const smerf::Segment& sg = pl->segs_host[sgi];
+                        const int r = n - grp * rmax < rmax ? n - grp * rmax : rmax;
+                        const double cost = (double)(pl->n_phi / 2) * pl->p * (sg.p1 - sg.p0) * r;
+                        qs.push_back(std::make_pair(cost, make_int4(i, sgi, grp, (pl->p - 1) * smerf::kQueueBuilds + bld)));
+                    }
+            }
+        }
+        if (rc != SMERF_OK || (qa.empty() && qs.empty())) continue;
+        std::stable_sort(qs.begin(), qs.end(), [](const std::pair<double, int4>& x, const std::pair<double, int4>& y) {
+            return x.first > y.first;
+        });
+        Queue q;
+        q.kind = kind;
+        q.n_anc = (int)qa.size();
+        q.n_seg = (int)qs.size();
+        q.nt = smerf::kQueueThreads;
+        q.smem = smem;
+        q.ctas = q.n_seg ? queue_ctas(kind, q.nt, smem) : 0;
+        std::vector<int4> sv;
+        for (auto& x : qs) sv.push_back(x.second);
+        const bool ok = (q.n_seg == 0 || q.ctas > 0) &&
+                        smerf::dev_malloc((void**)&q.d_anc, sizeof(int4) * (q.n_anc ? q.n_anc : 1)) == cudaSuccess &&
+                        smerf::dev_malloc((void**)&q.d_seg, sizeof(int4) * (q.n_seg ? q.n_seg : 1)) == cudaSuccess &&
+                        smerf::dev_malloc((void**)&q.d_head, sizeof(int)) == cudaSuccess;
+        b->queues.push_back(q);
+        if (!ok) {
+            rc = q.n_seg && q.ctas <= 0 ? SMERF_ECUDA : SMERF_ENOMEM;
+            break;
+        }
+        if ((q.n_anc && cudaMemcpy(q.d_anc, qa.data(), sizeof(int4) * q.n_anc, cudaMemcpyHostToDevice) != cudaSuccess) ||
+            (q.n_seg && cudaMemcpy(q.d_seg, sv.data(), sizeof(int4) * q.n_seg, cudaMemcpyHostToDevice) != cudaSuccess))
             rc = SMERF_ECUDA;
     }
     if (rc != SMERF_OK) {
@@ -209,7 +305,12 @@ int smerf_batch_launch(smerf_batch* b, void* stream)
     if (cudaMemcpyAsync(b->d_descs, b->h_descs, sizeof(SampleParams) * b->n_req, cudaMemcpyHostToDevice, st) !=
         cudaSuccess)
         return SMERF_ECUDA;
+    for (const Queue& q : b->queues) {
+        const int rc = launch_queue(q, b->d_descs, st);
+        if (rc != SMERF_OK) return rc;
+    }
     for (const Group& g : b->groups) {
+        if (queued(g.kind)) continue;
         const int rc = launch_group(g.kind, g.rep, b->d_descs, g.d_anc, g.n_anc, g.d_seg, g.n_seg, st);
         if (rc != SMERF_OK) return rc;
     }
@@ -233,6 +334,17 @@ int smerf_batch_info(const smerf_batch* b, int* n_groups, int* n_singles)
     if (n_groups) *n_groups = (int)b->groups.size();
     if (n_singles) *n_singles = (int)b->singles.size();
     return SMERF_OK;
+}
+
+int smerf_batch_launch_count(const smerf_batch* b)
+{
+    if (!b) return SMERF_EINVAL;
+    int n = 0;
+    for (const Queue& q : b->queues) n += (q.n_anc > 0) + (q.n_seg > 0);
+    for (const Group& g : b->groups)
+        if (!queued(g.kind)) n += (g.n_anc > 0) + (g.n_seg > 0);
+    for (int i : b->singles) n += smerf_sample_launches(b->plans[i], b->counts[i]);
+    return n;
 }
 
 int smerf_batch_destroy(smerf_batch* b)

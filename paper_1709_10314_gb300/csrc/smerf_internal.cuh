@@ -126,6 +126,22 @@ __host__ __device__ constexpr int hr_off(int L, int i, int MB = 4)
     return o;
 }
 
+// The batch's persistent segment launch: kQueueThreads threads per CTA, two CTAs per SM; a
+// request runs with np = ceil32(units / upt) <= 256 producer threads (upt the smallest of 1, 2,
+// 4, 8 that allows it), the rest FFT threads, and one realisation per CTA for upt >= 4, two
+// otherwise.  Its shape, shape = (p - 1) * kQueueBuilds + build, selects that build.
+constexpr int kQueueThreads = 384;
+constexpr int kQueueBuilds = 4;  // (upt, rmax): (1,2) (2,2) (4,1) (8,1)
+__host__ __device__ constexpr int queue_upt(int b) { return 1 << b; }
+__host__ __device__ constexpr int queue_rmax(int b) { return b <= 1 ? 2 : 1; }
+// the build of a request with n_units units (-1: more than 8 x 256 units)
+inline int queue_build(int n_units)
+{
+    for (int b = 0; b < kQueueBuilds; ++b)
+        if ((n_units + queue_upt(b) - 1) / queue_upt(b) <= 256) return b;
+    return -1;
+}
+
 // units: the slots whose normals fill whole Philox calls.  p = 1: 2 slots per call;
 // p = 2: 1 slot per call.
 __host__ __device__ constexpr int unit_slots(int M) { return M == 1 ? 2 : 1; }
@@ -200,6 +216,28 @@ template <class C> __device__ __forceinline__ C cmuli(C a) { return cmk<C>(-a.y,
 
 }  // namespace smerf
 
+namespace smerf {
+// Every device or page-locked allocation the library makes goes through these wrappers, so that
+// a test can make one of them fail as if memory were exhausted (smerf_debug_fail_alloc).
+bool alloc_fail_now();  // smerf_api.cu
+inline cudaError_t dev_malloc(void** p, size_t n)
+{
+    return alloc_fail_now() ? cudaErrorMemoryAllocation : cudaMalloc(p, n);
+}
+inline cudaError_t dev_malloc_async(void** p, size_t n, cudaStream_t st)
+{
+    return alloc_fail_now() ? cudaErrorMemoryAllocation : cudaMallocAsync(p, n, st);
+}
+inline cudaError_t dev_malloc_pool(void** p, size_t n, cudaMemPool_t pool, cudaStream_t st)
+{
+    return alloc_fail_now() ? cudaErrorMemoryAllocation : cudaMallocFromPoolAsync(p, n, pool, st);
+}
+inline cudaError_t host_malloc(void** p, size_t n)
+{
+    return alloc_fail_now() ? cudaErrorMemoryAllocation : cudaMallocHost(p, n);
+}
+}  // namespace smerf
+
 // sampling entry points used by smerf_api.cu (the set-up's are in smerf_setup.h)
 int smerf_launch_sample(const smerf_plan* plan, uint64_t seed, int n_samples, void* out,
                         void* scratch, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
@@ -218,6 +256,20 @@ SMERF_DECLARE_GROUP(ff)
 SMERF_DECLARE_GROUP(fd)
 SMERF_DECLARE_GROUP(dd)
 SMERF_DECLARE_GROUP(df)
+// shared memory of the warp-specialised kernel for a request and realisations per CTA
+#define SMERF_DECLARE_GROUP_CONFIG(XX) size_t smerf_ws_smem_##XX(const smerf_plan* pl, int rmax);
+SMERF_DECLARE_GROUP_CONFIG(ff)
+SMERF_DECLARE_GROUP_CONFIG(fd)
+SMERF_DECLARE_GROUP_CONFIG(dd)
+SMERF_DECLARE_GROUP_CONFIG(df)
+// the two persistent phases of a batch for FP32 recursion (FP32 or FP64 tables): one anchor
+// launch, one persistent segment launch of `ctas` CTAs pulling items from a device queue
+#define SMERF_DECLARE_QUEUE(XX)                                                                          \
+    int smerf_launch_queue_##XX(const smerf::SampleParams* d, const int4* anc, int n_anc, const int4* seg, \
+                                int n_seg, int* head, int nt, size_t smem, int ctas, cudaStream_t st);   \
+    int smerf_queue_ctas_##XX(int nt, size_t smem);
+SMERF_DECLARE_QUEUE(ff)
+SMERF_DECLARE_QUEUE(fd)
 
 // launch-configuration candidates of a plan for the autotuner (per precision pair XX):
 // writes up to max_n (upt, rmax, np, nf, minb) tuples of kLaunchInts, returns how many

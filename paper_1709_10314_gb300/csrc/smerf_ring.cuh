@@ -9,7 +9,8 @@
 // e^{2 pi i s / n_phi} for s = j + NT i are pre[j] times the constants e^{2 pi i i / 32}.
 // Later passes load one twiddle e^{2 pi i kk / (Ns R)} per butterfly (the first row of the
 // per-pass table) and form its powers by repeated products, so the tables a CTA reads stay
-// small enough for L1.  Only pass 0's stride-16 stores need a swizzle for conflict-free
+// small enough for L1.  While a ring's FFT runs, the next ring's step rows are prefetched into
+// L2 (cp.async.bulk.prefetch), so the recursion's table loads hit L2.  Only pass 0's stride-16 stores need a swizzle for conflict-free
 // shared memory: its 16-byte chunk q of row r is stored at chunk q ^ (r & 7).
 #pragma once
 
@@ -126,6 +127,19 @@ __device__ __forceinline__ void ring_pass(float2* X, const float2* __restrict__ 
     }
 }
 
+// Asynchronous prefetch of [p, p + bytes) into L2 by the CTA's first 16 threads (p and bytes
+// multiples of 16): the next ring's step rows are fetched while this ring's FFT runs
+__device__ __forceinline__ void ring_l2_prefetch(const void* p, size_t bytes, int tid)
+{
+    constexpr int kParts = 16;
+    const size_t chunk = ((bytes / kParts + 15) / 16) * 16;
+    const size_t off = (size_t)tid * chunk;
+    if (tid < kParts && off < bytes) {
+        const size_t n = bytes - off < chunk ? bytes - off : chunk;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"((const char*)p + off), "r"((unsigned)n) : "memory");
+    }
+}
+
 // One CTA per (segment, realisation r = blockIdx.x); NT threads, thread t owns units
 // u = t + i NT (slots 2u, 2u + 1), i < 8; the states of units i >= 8 - PARK live in shared
 // memory between their steps.
@@ -166,6 +180,8 @@ __global__ void __launch_bounds__(RingPass<LG>::NT, MINB) ring_kernel(SamplePara
     __syncthreads();
 
     const TabT* steps = (const TabT*)(c == 0 ? P.steps[0] : P.steps[1]);
+    const size_t ring_tab_bytes = mp * ROW * sizeof(TabT);  // one ring's step rows, a multiple of 16
+    if (sg.p0 + 1 < sg.p1) ring_l2_prefetch(steps + (size_t)(sg.p0 + 1) * mp * ROW, ring_tab_bytes, tid);
     for (int pos = sg.p0; pos < sg.p1; ++pos) {
         const int ring = c == 0 ? P.k0 - pos : P.k0 + pos;
         const TabT* tb = steps + (size_t)pos * mp * ROW;
@@ -201,6 +217,7 @@ __global__ void __launch_bounds__(RingPass<LG>::NT, MINB) ring_kernel(SamplePara
             }
             reinterpret_cast<float4*>(X)[u] = x;  // the unit's two coefficients
         }
+        if (pos + 1 < sg.p1) ring_l2_prefetch(tb + mp * ROW, ring_tab_bytes, tid);
         __syncthreads();
         if (!(c == 1 && pos == 0)) {  // the start ring is written by the northern chain
             float2* dst = reinterpret_cast<float2*>((float*)P.out + ((size_t)r0 * P.n_theta + ring) * (size_t)P.n_phi);

@@ -1182,6 +1182,62 @@ __global__ void __launch_bounds__(ws_max_threads(MINB), MINB) segment_ws_batched
     ws_body<Real, TabT, M, UPT, RMAX>(P, it.y, it.z);
 }
 
+// ---- uneven batches in two persistent phases
+// Phase 1 runs every group's anchor items in one launch (item: request, block of 128 units,
+// realisation, chain | p << 4).  Phase 2 is one launch of persistent CTAs that take segment
+// items (request, segment, realisation group, shape) from a device queue -- an atomic counter
+// reset before each launch, items ordered largest first -- and run each with the
+// warp-specialised body of its shape, so requests of different grids, spectra and p share one
+// launch.  Phase 2 starts after phase 1 has finished (stream order), so no item waits for
+// another.  A shape is p and the build (units per producer thread, realisations per CTA,
+// queue_build): every shape runs with kQueueThreads threads, two CTAs per SM.
+
+template <class Real, class TabT>
+__global__ void __launch_bounds__(128, SMERF_ANCHOR_MINB) anchor_queue_kernel(const SampleParams* __restrict__ descs,
+                                                                               const int4* __restrict__ items)
+{
+    const int4 it = items[blockIdx.x];
+    const SampleParams P = descs[it.x];
+    NoStage h;
+    const int u = it.y * blockDim.x + threadIdx.x;
+    if ((it.w >> 4) == 1) anchor_body<Real, TabT, 1>(P, u, it.z, it.w & 15, h);
+    else anchor_body<Real, TabT, 2>(P, u, it.z, it.w & 15, h);
+}
+
+template <class Real, class TabT, int SH>
+__device__ __forceinline__ void queue_segment(const SampleParams& P, int seg, int grp)
+{
+    constexpr int M = SH / kQueueBuilds + 1, B = SH % kQueueBuilds;
+    ws_body<Real, TabT, M, queue_upt(B), queue_rmax(B)>(P, seg, grp);
+}
+
+template <class Real, class TabT>
+__global__ void __launch_bounds__(kQueueThreads, 2) segment_queue_kernel(const SampleParams* __restrict__ descs,
+                                                                         const int4* __restrict__ items, int n_items,
+                                                                         int* __restrict__ head)
+{
+    __shared__ int s_k;
+    for (;;) {
+        __syncthreads();  // the previous item's shared buffers and s_k are free again
+        if (threadIdx.x == 0) s_k = atomicAdd(head, 1);
+        __syncthreads();
+        const int k = s_k;
+        if (k >= n_items) return;
+        const int4 it = items[k];
+        const SampleParams P = descs[it.x];
+        switch (it.w) {
+            case 0: queue_segment<Real, TabT, 0>(P, it.y, it.z); break;
+            case 1: queue_segment<Real, TabT, 1>(P, it.y, it.z); break;
+            case 2: queue_segment<Real, TabT, 2>(P, it.y, it.z); break;
+            case 3: queue_segment<Real, TabT, 3>(P, it.y, it.z); break;
+            case 4: queue_segment<Real, TabT, 4>(P, it.y, it.z); break;
+            case 5: queue_segment<Real, TabT, 5>(P, it.y, it.z); break;
+            case 6: queue_segment<Real, TabT, 6>(P, it.y, it.z); break;
+            default: queue_segment<Real, TabT, 7>(P, it.y, it.z); break;
+        }
+    }
+}
+
 }  // namespace smerf
 
 #include "smerf_ring.cuh"
@@ -1601,6 +1657,37 @@ int group_segments(const SegConfig& cfg, const SampleParams* d, const int4* item
     }
 }
 
+// The two persistent phases of a batch (FP32 recursion): anchor launch over anc items, then
+// `ctas` persistent CTAs of nt threads over seg items (head: a device counter, zeroed here).
+template <class Real, class TabT>
+int launch_queue(const SampleParams* d, const int4* anc, int n_anc, const int4* seg, int n_seg, int* head, int nt,
+                 size_t smem, int ctas, cudaStream_t st)
+{
+    if (n_anc > 0) {
+        anchor_queue_kernel<Real, TabT><<<n_anc, 128, 0, st>>>(d, anc);
+        if (cudaGetLastError() != cudaSuccess) return SMERF_ECUDA;
+    }
+    if (n_seg == 0) return SMERF_OK;
+    auto kern = segment_queue_kernel<Real, TabT>;
+    if (set_smem_attr(kern, smem) != cudaSuccess) return SMERF_ECUDA;
+    if (cudaMemsetAsync(head, 0, sizeof(int), st) != cudaSuccess) return SMERF_ECUDA;
+    kern<<<ctas, nt == kQueueThreads ? nt : kQueueThreads, smem, st>>>(d, seg, n_seg, head);
+    return cudaGetLastError() == cudaSuccess ? SMERF_OK : SMERF_ECUDA;
+}
+
+// resident CTAs of the persistent segment launch (nt threads, smem bytes) on this device
+template <class Real, class TabT>
+int queue_ctas(int nt, size_t smem)
+{
+    auto kern = segment_queue_kernel<Real, TabT>;
+    if (set_smem_attr(kern, smem) != cudaSuccess) return -1;
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem) != cudaSuccess) return -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return -1;
+    return per_sm * sms;
+}
+
 template <class Real, class TabT>
 int fill_params_c(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch, SampleParams* P,
                   int* batchable, int* rmax)
@@ -1675,4 +1762,15 @@ int launch_group_m(const smerf_plan* rep, const SampleParams* d, const int4* anc
     int smerf_tune_candidates_##XX(const smerf_plan* pl, int* cand, int max_n)                              \
     {                                                                                                       \
         return smerf::tune_candidates<REAL>(pl, cand, max_n);                                               \
-    }
+    }                                                                                                            \
+    size_t smerf_ws_smem_##XX(const smerf_plan* pl, int rmax) { return smerf::ws_smem<REAL>(pl, rmax); }
+
+// The persistent two-phase batch launch of an FP32-recursion precision pair (its own translation
+// unit, smerf_sample_XX_queue.cu, since it instantiates every shape of both p).
+#define SMERF_QUEUE(REAL, TABT, XX)                                                                       \
+    int smerf_launch_queue_##XX(const smerf::SampleParams* d, const int4* anc, int n_anc, const int4* seg,  \
+                                int n_seg, int* head, int nt, size_t smem, int ctas, cudaStream_t st)      \
+    {                                                                                                     \
+        return smerf::launch_queue<REAL, TABT>(d, anc, n_anc, seg, n_seg, head, nt, smem, ctas, st);      \
+    }                                                                                                     \
+    int smerf_queue_ctas_##XX(int nt, size_t smem) { return smerf::queue_ctas<REAL, TABT>(nt, smem); }

@@ -769,11 +769,11 @@ static int upload_fft_tables(int n_phi, void** tw, void** pre, void** tw2, void*
         }
         if (t2.empty()) t2.assign(2, (R)0);
         void** dst = t == 0 ? tw2 : tw3;
-        if (cudaMalloc(dst, t2.size() * sizeof(R)) != cudaSuccess) return SMERF_ENOMEM;
+        if (smerf::dev_malloc(dst, t2.size() * sizeof(R)) != cudaSuccess) return SMERF_ENOMEM;
         if (cudaMemcpy(*dst, t2.data(), t2.size() * sizeof(R), cudaMemcpyHostToDevice) != cudaSuccess) return SMERF_ECUDA;
     }
-    if (cudaMalloc(tw, t.size() * sizeof(R)) != cudaSuccess) return SMERF_ENOMEM;
-    if (cudaMalloc(pre, p.size() * sizeof(R)) != cudaSuccess) return SMERF_ENOMEM;
+    if (smerf::dev_malloc(tw, t.size() * sizeof(R)) != cudaSuccess) return SMERF_ENOMEM;
+    if (smerf::dev_malloc(pre, p.size() * sizeof(R)) != cudaSuccess) return SMERF_ENOMEM;
     if (cudaMemcpy(*tw, t.data(), t.size() * sizeof(R), cudaMemcpyHostToDevice) != cudaSuccess) return SMERF_ECUDA;
     if (cudaMemcpy(*pre, p.data(), p.size() * sizeof(R), cudaMemcpyHostToDevice) != cudaSuccess) return SMERF_ECUDA;
     return SMERF_OK;
@@ -1065,16 +1065,16 @@ int setup_impl(smerf_plan* pl, cudaStream_t st, bool sync)
 
     pl->table_bytes = 0;
     pl->step_table_bytes = 0;
-    CK(cudaMalloc(&pl->beq, (size_t)tri(M) * mp * es));
+    CK(smerf::dev_malloc((void**)&pl->beq, (size_t)tri(M) * mp * es));
     CK(cudaMemsetAsync(pl->beq, 0, (size_t)tri(M) * mp * es, st));
     pl->table_bytes += (size_t)tri(M) * mp * es;
     for (int c = 0; c < 2; ++c) {
         const int len = pl->chain[c].len;
         const size_t sb = (size_t)(len + 1) * step_row(M) * mp * es;
         const size_t cb = (size_t)(pl->chain[c].n_anchors + 1) * coarse_elems(M) * mp * es;
-        CK(cudaMalloc(&pl->steps[c], sb > 0 ? sb : 16));
+        CK(smerf::dev_malloc((void**)&pl->steps[c], sb > 0 ? sb : 16));
         CK(cudaMemsetAsync(pl->steps[c], 0, sb > 0 ? sb : 16, st));
-        CK(cudaMalloc(&pl->coarse[c], cb > 0 ? cb : 16));
+        CK(smerf::dev_malloc((void**)&pl->coarse[c], cb > 0 ? cb : 16));
         CK(cudaMemsetAsync(pl->coarse[c], 0, cb > 0 ? cb : 16, st));
         pl->table_bytes += sb + cb;
         pl->step_table_bytes += sb;
@@ -1084,7 +1084,7 @@ int setup_impl(smerf_plan* pl, cudaStream_t st, bool sync)
     if (rc != SMERF_OK) goto done;
     if (pl->complex_spec) start_kernel_c<M><<<gm, threads, 0, st>>>(make_spec_c(pl), pl->beq, t64);
     else {
-        CK(cudaMallocAsync((void**)&lqa, (size_t)M * pl->n_modes * sizeof(double), st));
+        CK(smerf::dev_malloc_async((void**)&lqa, (size_t)M * pl->n_modes * sizeof(double), st));
         lq_prefix_kernel<<<1, 1024, 0, st>>>(sp, lqa);
         start_kernel<M><<<gm, threads, 0, st>>>(sp, lqa, pl->beq, t64);
         CK(cudaFreeAsync(lqa, st));
@@ -1101,8 +1101,8 @@ int setup_impl(smerf_plan* pl, cudaStream_t st, bool sync)
         if (len1 + shift > len0) { rc = SMERF_EUNSUPPORTED; goto done; }
         if (len0 > 0) {
             const size_t nb = (size_t)(len0 + 1) * pl->n_modes * M * M * sizeof(double);
-            CK(cudaMallocAsync((void**)&phi, nb, st));
-            CK(cudaMallocAsync((void**)&qv, nb, st));
+            CK(smerf::dev_malloc_async((void**)&phi, nb, st));
+            CK(smerf::dev_malloc_async((void**)&qv, nb, st));
             if (len0 > 65535) { rc = SMERF_EUNSUPPORTED; goto done; }
             dim3 grid(gm, len0);
             if (pl->complex_spec) step_kernel_c<M><<<grid, threads, 0, st>>>(make_spec_c(pl), len0, phi, qv);

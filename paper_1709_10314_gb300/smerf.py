@@ -86,6 +86,8 @@ def _lib():
         L.smerf_batch_sample.restype = ip
         L.smerf_batch_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip)]
         L.smerf_batch_info.restype = ip
+        L.smerf_batch_launch_count.argtypes = [vp]
+        L.smerf_batch_launch_count.restype = ip
         L.smerf_batch_destroy.argtypes = [vp]
         L.smerf_batch_destroy.restype = ip
         L.smerf_plan_info.argtypes = [vp, ctypes.POINTER(_Info)]
@@ -94,6 +96,8 @@ def _lib():
         L.smerf_plan_copy_tables.restype = ip
         L.smerf_plan_autotune.argtypes = [vp, ip, vp, ctypes.POINTER(ip)]
         L.smerf_plan_autotune.restype = ip
+        L.smerf_plan_autotune_anchor.argtypes = [vp, ip, ctypes.POINTER(ip), ip, vp, ctypes.POINTER(ip)]
+        L.smerf_plan_autotune_anchor.restype = ip
         L.smerf_plan_launch_candidates.argtypes = [vp, ctypes.POINTER(ip), ip]
         L.smerf_plan_launch_candidates.restype = ip
         L.smerf_plan_set_launch.argtypes = [vp, ctypes.POINTER(ip)]
@@ -102,6 +106,8 @@ def _lib():
         L.smerf_philox_uint32.restype = ip
         L.smerf_ring_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ip, vp, vp]
         L.smerf_ring_normals.restype = ip
+        L.smerf_debug_fail_alloc.argtypes = [ip]
+        L.smerf_debug_fail_alloc.restype = ip
         L.smerf_status_string.argtypes = [ip]
         L.smerf_status_string.restype = ctypes.c_char_p
         _LIB = L
@@ -196,6 +202,15 @@ class Plan:
         ch = (ctypes.c_int * LAUNCH_INTS)()
         _check("smerf_plan_autotune", _lib().smerf_plan_autotune(self._h, int(n_samples), _stream_ptr(stream), ch))
         return tuple(ch)
+
+    def autotune_anchor(self, n_samples, candidates=(8, 12, 16, 24, 32), stream=None):
+        """smerf_plan_autotune_anchor: rebuild the tables for each anchor spacing, keep the fastest;
+        returns the chosen spacing (0 for a plan in Alg. 2's order)."""
+        cand = (ctypes.c_int * len(candidates))(*[int(v) for v in candidates])
+        ch = ctypes.c_int()
+        _check("smerf_plan_autotune_anchor", _lib().smerf_plan_autotune_anchor(
+            self._h, int(n_samples), cand, len(candidates), _stream_ptr(stream), ctypes.byref(ch)))
+        return ch.value
 
     def launch_candidates(self):
         """smerf_plan_launch_candidates: list of (units/thread, realisations/CTA, producer
@@ -321,6 +336,11 @@ def last_device_status(stream=None):
     return _lib().smerf_last_device_status(_stream_ptr(stream))
 
 
+def debug_fail_alloc(k):
+    """smerf_debug_fail_alloc: make the allocation after k more fail (k < 0: off)."""
+    _check("smerf_debug_fail_alloc", _lib().smerf_debug_fail_alloc(int(k)))
+
+
 def scratch_trim():
     """smerf_scratch_trim: release the idle memory of the per-call scratch pool (current device)."""
     _check("smerf_scratch_trim", _lib().smerf_scratch_trim())
@@ -382,7 +402,7 @@ class Batch:
     def info(self):
         g, s1 = ctypes.c_int(), ctypes.c_int()
         _check("smerf_batch_info", _lib().smerf_batch_info(self._h, ctypes.byref(g), ctypes.byref(s1)))
-        return {"groups": g.value, "singles": s1.value}
+        return {"groups": g.value, "singles": s1.value, "launches": _lib().smerf_batch_launch_count(self._h)}
 
 
 def philox_uint32(key64, ring, ncalls, stream=None):

@@ -9,7 +9,8 @@ of the method's arithmetic).  Each is named by what it is.
   uneven-256                256 requests: n_theta uniform in {128,256,512,1024}, n_phi = 2 n_theta,
                             kappa uniform in [5, 200], p uniform in {1, 2}, 1-8 realisations,
                             FP32 recursion; generator seed 12345, request i draws keys 1000 i + j
-  16384x32768-p1            16384 x 32768, C_l = 1/(l(l+1)+300^2), 4 realisations, FP32 tables
+  16384x32768-p1            16384 x 32768, C_l = 1/(l(l+1)+300^2), 4 realisations, FP32 tables,
+                            anchors every 24 rings (measured best of 16, 24, 32)
   4096x32768-p1             the same spectrum, ring length and realisations on a quarter of the
                             rings (4096): the same kernels at a size for profiling captures
 """
@@ -23,9 +24,9 @@ FIXED = {
     "4096x8192-p1": dict(kappa=[100.0], A=1.0, n_theta=4096, n_phi=8192, n=16, seed=1,
                          recur="fp32", tables="fp64"),
     "16384x32768-p1": dict(kappa=[300.0], A=1.0, n_theta=16384, n_phi=32768, n=4, seed=1,
-                           recur="fp32", tables="fp32"),
+                           recur="fp32", tables="fp32", H=24),
     "4096x32768-p1": dict(kappa=[300.0], A=1.0, n_theta=4096, n_phi=32768, n=4, seed=1,
-                          recur="fp32", tables="fp32"),
+                          recur="fp32", tables="fp32", H=24),
 }
 
 # Segment-kernel launch configurations (units per producer thread, realisations per CTA,

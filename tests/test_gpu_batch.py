@@ -50,6 +50,9 @@ def test_batch_object_reuse_and_groups():
     b = Batch(plans, counts)
     info = b.info()
     assert info["groups"] == 5 and info["singles"] == 0   # plans 0 and 2 share a shape
+    # FP32 recursion with FP32 tables (plans 0, 1, 2, 5) and with FP64 tables (plan 4): an anchor
+    # launch and a persistent segment launch each; FP64 recursion (plan 3): its own two
+    assert info["launches"] == 6
     for seeds in ([1, 2, 3, 4, 5, 6], [100, 200, 300, 400, 500, 600]):
         outs = _outs(plans, counts)
         b.sample(seeds, outs)
@@ -131,3 +134,23 @@ def test_batch_graph_replay_against_oracle():
             ref = oracle.sample(k, 1.0, nt, nphi, sd, n, H=H)
             err = float(np.max(np.abs(o.double().cpu().numpy() - ref))) / float(np.std(ref))
             assert err < (1e-9 if f else 1e-4), (k, nt, nphi, sd, err)
+
+
+def test_uneven_batch_runs_in_two_persistent_launches():
+    """Requests of four grids and both p with FP32 recursion: one anchor launch and one launch of
+    persistent CTAs that pull every shape's segments from the device queue; each request bit
+    for bit what its own smerf_sample call gives."""
+    import torch
+    from paper_1709_10314_gb300 import Batch, Plan
+    specs = [([12.0], 128, 256, 3), ([30.0, 90.0], 256, 512, 2), ([7.0], 64, 128, 5), ([20.0, 50.0], 512, 1024, 1),
+             ([150.0], 1024, 2048, 2), ([40.0, 130.0], 128, 256, 4)]
+    plans = [Plan(k, 1.0, nt, nphi) for (k, nt, nphi, _) in specs]
+    counts = [s[-1] for s in specs]
+    b = Batch(plans, counts)
+    assert b.info()["launches"] == 2 and b.info()["singles"] == 0
+    seeds = [5 * i + 1 for i in range(len(plans))]
+    outs = _outs(plans, counts)
+    b.sample(seeds, outs)
+    torch.cuda.synchronize()
+    for p, sd, n, o in zip(plans, seeds, counts, outs):
+        assert torch.equal(o, p.sample(sd, n))

@@ -71,3 +71,19 @@ def test_batch_with_tuned_and_untuned_plans_of_one_shape():
     torch.cuda.synchronize()
     assert torch.equal(outs[0], a.sample(5, 3))
     assert torch.equal(outs[1], b.sample(6, 5))
+
+
+def test_autotune_anchor_spacing():
+    """smerf_plan_autotune_anchor rebuilds the tables for each candidate spacing, keeps the
+    fastest, and the tuned plan then samples exactly what a plan made with that spacing does."""
+    import torch
+    from paper_1709_10314_gb300 import SMERF_ORDER_PAPER, Plan
+    plan = Plan([20.0, 50.0], 1.0, 128, 256, anchor_spacing=16)
+    h = plan.autotune_anchor(4, candidates=(8, 16, 32))
+    assert h in (8, 16, 32) and plan.info()["anchor_spacing"] == h
+    ref = Plan([20.0, 50.0], 1.0, 128, 256, anchor_spacing=h).sample(9, 4)
+    got = plan.sample(9, 4)
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref)
+    paper = Plan([20.0, 50.0], 1.0, 64, 128, flags=SMERF_ORDER_PAPER)
+    assert paper.autotune_anchor(2, candidates=(8,)) == 0  # Alg. 2's order has no anchors
