@@ -34,6 +34,10 @@ Pins (tests/test_oracle_*.py, run with -m "not gpu"):
   recursion_sample         pinned: equals sample() (the dense factor applied to the same
                            noise) on small grids in both orders, which holds only if the
                            tables, the parents and the noise layout are all right
+  ring_values /            pinned: full rings without offset equal sample(); a ring of n_phi/2
+  sample_rings             points is every second point of the full ring; an offset of s grid
+                           steps is the full ring rolled by s; the field covariance at offset
+                           points equals the direct spherical-harmonic double sum (tiny grids)
 """
 import ctypes
 import math
@@ -50,6 +54,7 @@ __all__ = [
     "sample", "field_std", "mode_variances",
     "conditional_tables", "dft_ring", "fft_ring", "KHat",
     "order_parents", "recursion_tables", "recursion_sample",
+    "ring_values", "sample_rings",
 ]
 
 _lib = None
@@ -470,3 +475,40 @@ def recursion_sample(M, n_phi, order, parents, T, B, seed, n_samples=1, nthreads
     if rc != 0:
         raise ValueError("oracle_recursion_sample: bad arguments")
     return out
+
+
+# ------------------------------------------------ iso-latitude grids (Sec. 1 remark)
+def ring_values(c, n, phi0):
+    """The m-truncated field on one ring at the n points phi_j = phi0 + 2 pi j / n, from its
+    coefficients c[m] = g_m, m = 0..M (M = len(c) - 1): the real field
+        T(phi) = g_0 + 2 sum_{0<m<M} Re(g_m e^{i m phi}) + Re(g_M) cos(M phi),
+    the full ring's convention (prefactor 1, Alg. 2; the Nyquist coefficient's real part) at any
+    phi.  Evaluated directly, O(M n); modes above the ring's own Nyquist alias as the sum says."""
+    c = np.asarray(c, dtype=np.complex128)
+    M = len(c) - 1
+    phi = phi0 + 2.0 * math.pi * np.arange(n) / n
+    m = np.arange(1, M)
+    E = np.exp(1j * np.outer(phi, m))
+    out = np.full(n, c[0].real)
+    out += 2.0 * (E @ c[1:M]).real
+    out += c[M].real * np.cos(M * phi)
+    return out
+
+
+def sample_rings(kappa, A, n_theta, n_phi_ring, phi0_ring, seed, n_samples=1, H=0, K=6, rings=None,
+                 **level_kw):
+    """Realisations on an iso-latitude grid with ring-dependent longitudes: ring k (latitude
+    theta_k = pi (k + 1/2) / n_theta) holds n_phi_ring[k] points starting at phi0_ring[k].  The
+    modes m = 0..max(n_phi_ring)/2, their recursion and noise are those of sample() on the
+    n_theta x max(n_phi_ring) grid; each ring is synthesised at its own points (ring_values).
+    Returns a list over realisations of lists of ring arrays, rings north to south (or in the
+    order of `rings`, a leading subset of the conditioning order)."""
+    n_phi = int(max(n_phi_ring))
+    _, X, order = sample(kappa, A, n_theta, n_phi, seed, n_samples, H=H, K=K, rings=rings,
+                         return_coeffs=True, **level_kw)
+    out_rings = sorted(order) if rings is None else list(rings)
+    pos = {r: i for i, r in enumerate(order)}
+    res = []
+    for j in range(n_samples):
+        res.append([ring_values(X[j, pos[r]], int(n_phi_ring[r]), float(phi0_ring[r])) for r in out_rings])
+    return res
