@@ -496,14 +496,15 @@ def ring_values(c, n, phi0):
 
 
 def sample_rings(kappa, A, n_theta, n_phi_ring, phi0_ring, seed, n_samples=1, H=0, K=6, rings=None,
-                 **level_kw):
+                 n_phi=None, **level_kw):
     """Realisations on an iso-latitude grid with ring-dependent longitudes: ring k (latitude
     theta_k = pi (k + 1/2) / n_theta) holds n_phi_ring[k] points starting at phi0_ring[k].  The
-    modes m = 0..max(n_phi_ring)/2, their recursion and noise are those of sample() on the
-    n_theta x max(n_phi_ring) grid; each ring is synthesised at its own points (ring_values).
-    Returns a list over realisations of lists of ring arrays, rings north to south (or in the
-    order of `rings`, a leading subset of the conditioning order)."""
-    n_phi = int(max(n_phi_ring))
+    modes m = 0..n_phi/2 (n_phi defaults to max(n_phi_ring)), their recursion and noise are those
+    of sample() on the n_theta x n_phi grid; each ring is synthesised at its own points
+    (ring_values).  Returns a list over realisations of lists of ring arrays, rings north to south
+    (or in the order of `rings`, a leading subset of the conditioning order)."""
+    n_phi = int(max(n_phi_ring)) if n_phi is None else int(n_phi)
+    assert max(n_phi_ring) <= n_phi
     _, X, order = sample(kappa, A, n_theta, n_phi, seed, n_samples, H=H, K=K, rings=rings,
                          return_coeffs=True, **level_kw)
     out_rings = sorted(order) if rings is None else list(rings)

@@ -24,7 +24,7 @@ def test_reduced_rings_are_subsamples_and_grid_offsets_are_rolls():
     nt, nphi = 6, 16
     full = oracle.sample([3.0, 8.0], 1.0, nt, nphi, 5, 2, H=0)
     npr = [16, 8, 16, 4, 16, 8]
-    sub = oracle.sample_rings([3.0, 8.0], 1.0, nt, npr, [0.0] * nt, 5, 2, H=0)
+    sub = oracle.sample_rings([3.0, 8.0], 1.0, nt, npr, [0.0] * nt, 5, 2, H=0, n_phi=nphi)
     shift = [0, 3, 5, 1, 15, 2]
     rol = oracle.sample_rings([3.0, 8.0], 1.0, nt, [nphi] * nt, [2 * math.pi * s / nphi for s in shift], 5, 2, H=0)
     tol = 1e-12 * np.std(full)
@@ -83,3 +83,14 @@ def test_offset_ring_covariance_against_spherical_harmonics():
             yr = np.array([_ylm(l, M, t, p) for (t, p) in pts]).real
             Cb += 0.5 * cl * np.outer(yr, yr)
     assert np.allclose(C, Cb, rtol=1e-6, atol=1e-6 * np.abs(Cb).max())
+
+
+def test_modes_beyond_every_ring_alias_onto_them():
+    """A grid whose modes reach past every ring's own Nyquist (no ring holds n_phi points): the
+    rings are still the subsamples of the full n_phi-point rings."""
+    nt, nphi = 5, 32
+    full = oracle.sample([6.0], 1.0, nt, nphi, 9, 1, H=0)
+    npr = [4, 8, 16, 8, 4]
+    sub = oracle.sample_rings([6.0], 1.0, nt, npr, [0.0] * nt, 9, 1, H=0, n_phi=nphi)
+    for k in range(nt):
+        assert np.max(np.abs(sub[0][k] - full[0, k, ::nphi // npr[k]])) <= 1e-12 * np.std(full)
