@@ -112,7 +112,8 @@ int smerf_plan_destroy(smerf_plan* plan);
  *   seed       Philox key of realisation 0; realisation r uses seed + r
  *   n_samples  >= 0 (0 is a no-op)
  *   out        device pointer to n_samples * n_theta * n_phi floats (doubles with
- *              SMERF_RECUR_FP64), 16-byte aligned
+ *              SMERF_RECUR_FP64), 16-byte aligned (n_samples * points_per_sample for a plan
+ *              with ring-dependent longitudes, smerf_plan_set_rings)
  *   stream     cudaStream_t as void*
  *
  * Scratch (the anchor states, 2 * n_samples * (anchors + 1) * 2p * n_phi/2 values) is
@@ -274,9 +275,27 @@ typedef struct smerf_plan_info_t {
     double setup_ms;                       /* wall time of the set-up kernels                   */
     size_t step_table_bytes;               /* the step tables' part of table_bytes (the tables  */
                                            /* the segment kernel reads)                         */
+    size_t points_per_sample;              /* output values of one realisation                  */
 } smerf_plan_info_t;
 
 int smerf_plan_info(const smerf_plan* plan, smerf_plan_info_t* info);
+
+/*
+ * smerf_plan_set_rings -- iso-latitude grid with ring-dependent longitudes (the paper's Sec. 1
+ * remark that the method holds on any iso-latitude grid; HEALPix-like rings).  Ring k keeps its
+ * latitude theta_k and holds n_phi_ring[k] points phi = phi0_ring[k] + 2 pi j / n_phi_ring[k],
+ * j < n_phi_ring[k]; each n_phi_ring[k] a power of two with 4 <= n_phi_ring[k] <= n_phi of the
+ * plan; phi0_ring may be NULL (no offsets).  Host arrays of n_theta values.  The modes
+ * m = 0..n_phi/2, their recursion and noise stay those of the plan; each ring's values are the
+ * m-truncated field evaluated at its points: T(phi) = g_0 + 2 sum_{0<m<n_phi/2} Re(g_m e^{i m phi})
+ * + Re(g_{n_phi/2}) cos(n_phi phi / 2), so modes above the ring's own Nyquist alias onto it.
+ * Output of a sample call: realisation r's rings back to back, ring k at
+ * r * P + sum_{k'<k} n_phi_ring[k'] (P = smerf_plan_info's points_per_sample).  Only plans run by
+ * the warp-specialised kernels (n_phi <= 8192 with FP32 recursion, <= 4096 with FP64) take rings
+ * (else SMERF_EUNSUPPORTED); such plans cannot join a batch.  n_phi_ring = NULL restores the full
+ * grid.  Host only, synchronous; must not run while other calls use the plan.
+ */
+int smerf_plan_set_rings(smerf_plan* plan, const int* n_phi_ring, const double* phi0_ring);
 
 /*
  * smerf_plan_autotune -- time every built launch configuration of the segment kernel that

@@ -41,6 +41,26 @@ void free_plan_memory(smerf_plan* pl)
     cudaFree(pl->tw3);
     cudaFree(pl->segs_dev);
     free(pl->segs_host);
+    cudaFree(pl->rings_n_dev);
+    cudaFree(pl->rings_h_dev);
+    cudaFree(pl->rings_off_dev);
+}
+
+void free_rings(smerf_plan* pl)
+{
+    cudaFree(pl->rings_n_dev);
+    cudaFree(pl->rings_h_dev);
+    cudaFree(pl->rings_off_dev);
+    pl->rings_n_dev = nullptr;
+    pl->rings_h_dev = nullptr;
+    pl->rings_off_dev = nullptr;
+    pl->rings_total = 0;
+}
+
+// output values of one realisation
+size_t plan_points(const smerf_plan* pl)
+{
+    return pl->rings_total ? (size_t)pl->rings_total : (size_t)pl->n_theta * pl->n_phi;
 }
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -406,6 +426,7 @@ static int create_plan(const double* kappa, const double* kh_re, const double* k
     pl->flags = flags;
     pl->recur64 = (flags & SMERF_RECUR_FP64) != 0;
     pl->tab64 = (flags & SMERF_TABLES_FP64) ? true : ((flags & SMERF_TABLES_FP32) ? false : pl->recur64);
+    pl->packed = p == 1 && !pl->recur64 && !pl->tab64 && (n_phi == 16384 || n_phi == 32768);
     int H = anchor_spacing == 0 ? kDefaultAnchor : anchor_spacing;
     if ((flags & SMERF_ORDER_PAPER) || H >= n_theta) H = 0;
     pl->H = H;
@@ -531,7 +552,7 @@ int smerf_sample_host(const smerf_plan* plan, uint64_t seed, int n_samples, void
         return rc;
     }
     cudaGetLastError();  // an unregistered pointer is not an error here
-    const size_t bytes = (size_t)n_samples * plan->n_theta * plan->n_phi * (plan->recur64 ? 8 : 4);
+    const size_t bytes = (size_t)n_samples * plan_points(plan) * (plan->recur64 ? 8 : 4);
     void* dout = nullptr;
     cudaError_t e = scratch_alloc(&dout, bytes, plan->dev, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? SMERF_ENOMEM : SMERF_ECUDA;
@@ -563,6 +584,53 @@ int smerf_plan_info(const smerf_plan* plan, smerf_plan_info_t* info)
     info->step_table_bytes = plan->step_table_bytes;
     info->scratch_bytes_per_sample = smerf_scratch_bytes(plan, 1);
     info->setup_ms = plan->setup_ms;
+    info->points_per_sample = plan_points(plan);
+    return SMERF_OK;
+}
+
+static int tune_candidates(const smerf_plan* plan, int* cand, int max_n);
+
+int smerf_plan_set_rings(smerf_plan* plan, const int* n_phi_ring, const double* phi0_ring)
+{
+    if (!plan) return SMERF_EINVAL;
+    if (!n_phi_ring) {
+        free_rings(plan);
+        return SMERF_OK;
+    }
+    std::vector<int> n(plan->n_theta);
+    std::vector<double> h(plan->n_theta);
+    std::vector<long long> off(plan->n_theta);
+    long long total = 0;
+    for (int k = 0; k < plan->n_theta; ++k) {
+        const int nk = n_phi_ring[k];
+        const double p0 = phi0_ring ? phi0_ring[k] : 0.0;
+        if (!is_pow2(nk) || nk < 4 || nk > plan->n_phi || !isfinite(p0)) return SMERF_EINVAL;
+        n[k] = nk;
+        h[k] = fmod(p0 / SMERF_PI, 2.0);
+        off[k] = total;
+        total += nk;
+    }
+    int cand[smerf::kLaunchInts * 64];
+    if (tune_candidates(plan, cand, 64) == 0) return SMERF_EUNSUPPORTED;  // not a warp-specialised plan
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != plan->dev) return SMERF_EINVAL;
+    free_rings(plan);
+    int rc = SMERF_OK;
+    if (smerf::dev_malloc((void**)&plan->rings_n_dev, sizeof(int) * n.size()) != cudaSuccess ||
+        smerf::dev_malloc((void**)&plan->rings_h_dev, sizeof(double) * h.size()) != cudaSuccess ||
+        smerf::dev_malloc((void**)&plan->rings_off_dev, sizeof(long long) * off.size()) != cudaSuccess)
+        rc = SMERF_ENOMEM;
+    if (rc == SMERF_OK &&
+        (cudaMemcpy(plan->rings_n_dev, n.data(), sizeof(int) * n.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(plan->rings_h_dev, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(plan->rings_off_dev, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice) != cudaSuccess))
+        rc = SMERF_ECUDA;
+    if (rc != SMERF_OK) {
+        free_rings(plan);
+        return rc;
+    }
+    plan->rings_total = total;
     return SMERF_OK;
 }
 
@@ -581,8 +649,8 @@ int smerf_plan_copy_tables(const smerf_plan* plan, int which, int chain, int pos
     } else if (which == 1) {
         if (pos < 1 || pos > plan->chain[chain].len) return SMERF_EINVAL;
         rows = step_elems(M);
-        mode_major = true;
-        base = (const unsigned char*)plan->steps[chain] + (size_t)pos * step_row(M) * mp * es;
+        mode_major = !plan->packed;
+        base = (const unsigned char*)plan->steps[chain] + (size_t)pos * (plan->packed ? rows : step_row(M)) * mp * es;
     } else if (which == 2) {
         if (pos < 1 || pos > plan->chain[chain].n_anchors) return SMERF_EINVAL;
         rows = coarse_elems(M);
@@ -657,7 +725,7 @@ int smerf_plan_autotune(smerf_plan* plan, int n_samples, void* stream, int* chos
         return SMERF_OK;  // no warp-specialised configuration: the built-in choice stays
     }
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t ob = (size_t)n_samples * plan->n_theta * plan->n_phi * (plan->recur64 ? 8 : 4);
+    const size_t ob = (size_t)n_samples * plan_points(plan) * (plan->recur64 ? 8 : 4);
     void* out = nullptr;
     void* scratch = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -761,8 +829,13 @@ int smerf_plan_autotune_anchor(smerf_plan* plan, int n_samples, const int* candi
         if (cp) smerf_plan_destroy(cp);
     }
     if (rc == SMERF_OK && best) {
-        // the caller's handle takes the fastest plan's tables; its old tables go with `best`
+        // the caller's handle takes the fastest plan's tables (keeping its ring layout); its old
+        // tables go with `best`
         std::swap(*plan, *best);
+        std::swap(plan->rings_n_dev, best->rings_n_dev);
+        std::swap(plan->rings_h_dev, best->rings_h_dev);
+        std::swap(plan->rings_off_dev, best->rings_off_dev);
+        std::swap(plan->rings_total, best->rings_total);
         if (chosen) *chosen = plan->H;
     }
     if (best) smerf_plan_destroy(best);

@@ -132,6 +132,8 @@ int smerf_batch_create(const smerf_plan* const* plans, const int* n_samples, int
     if (cudaGetDevice(&dev) != cudaSuccess) return SMERF_ECUDA;
     for (int i = 0; i < n_req; ++i)
         if (!plans[i] || n_samples[i] < 0 || n_samples[i] > 65535 || plans[i]->dev != dev) return SMERF_EINVAL;
+    for (int i = 0; i < n_req; ++i)
+        if (plans[i]->rings_total) return SMERF_EUNSUPPORTED;  // ring-dependent longitudes: single calls only
     smerf_batch* b = new (std::nothrow) smerf_batch;
     if (!b) return SMERF_ENOMEM;
     b->n_req = n_req;

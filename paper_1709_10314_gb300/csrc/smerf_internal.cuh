@@ -44,6 +44,10 @@ struct smerf_plan {
     unsigned flags;
     int H;                 // effective anchor spacing (0 = none)
     bool recur64, tab64;
+    // p = 1 FP32 step tables of plans run by the ring kernel are stored packed: per position
+    // three rows A, C, B of n_modes_pad values (12 bytes per (mode, ring)) instead of one
+    // 16-byte row per mode
+    bool packed;
     smerf::Chain chain[2];
     int n_segments;
     smerf::Segment* segs_host;
@@ -62,6 +66,11 @@ struct smerf_plan {
     size_t step_table_bytes;  // the two step tables' part of table_bytes
     double setup_ms;
     int dev;
+    // ring-dependent longitudes (smerf_plan_set_rings; rings_total = 0: none)
+    int* rings_n_dev;
+    double* rings_h_dev;
+    long long* rings_off_dev;
+    long long rings_total;
     // launch parameters chosen by smerf_plan_autotune (valid = 0: built-in heuristic)
     struct { int valid, upt, rmax, np, nf, minb; float ms; } tune;
 };
@@ -97,6 +106,13 @@ struct SampleParams {
     int pingpong;     // 1: two FFT buffers + right anchors on chip; 0: one buffer, in place
     int np;           // warp-specialised kernel: producer threads
     int lgNc;
+    // iso-latitude grid with ring-dependent longitudes (null: the full n_theta x n_phi grid):
+    // ring k holds ring_n[k] points from phi0 = ring_h[k] pi, at ring_off[k] within a
+    // realisation of ring_total points
+    const int* ring_n;
+    const double* ring_h;
+    const long long* ring_off;
+    long long ring_total;
 };
 
 // High-radix pass plan of the Nc = 2^L point inverse FFT with passes of at most 2^MB points:
@@ -128,12 +144,13 @@ __host__ __device__ constexpr int hr_off(int L, int i, int MB = 4)
 
 // The batch's persistent segment launch: kQueueThreads threads per CTA, two CTAs per SM; a
 // request runs with np = ceil32(units / upt) <= 256 producer threads (upt the smallest of 1, 2,
-// 4, 8 that allows it), the rest FFT threads, and one realisation per CTA for upt >= 4, two
-// otherwise.  Its shape, shape = (p - 1) * kQueueBuilds + build, selects that build.
-constexpr int kQueueThreads = 384;
-constexpr int kQueueBuilds = 4;  // (upt, rmax): (1,2) (2,2) (4,1) (8,1)
+// 4, 8 that allows it), the rest FFT threads, and 4, 2, 2, 1 realisations per CTA for upt = 1,
+// 2, 4, 8.  Its shape, shape = (p - 1) * kQueueBuilds + build, selects that build.
+constexpr int kQueueThreads = 384;   // 320 x 3 and 512 x 2 per SM measured slower
+constexpr int kQueueMinBlocks = 2;
+constexpr int kQueueBuilds = 4;  // (upt, rmax): (1,4) (2,2) (4,2) (8,1)
 __host__ __device__ constexpr int queue_upt(int b) { return 1 << b; }
-__host__ __device__ constexpr int queue_rmax(int b) { return b <= 1 ? 2 : 1; }
+__host__ __device__ constexpr int queue_rmax(int b) { return b == 0 ? 4 : b <= 2 ? 2 : 1; }
 // the build of a request with n_units units (-1: more than 8 x 256 units)
 inline int queue_build(int n_units)
 {

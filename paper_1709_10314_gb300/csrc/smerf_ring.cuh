@@ -143,12 +143,14 @@ __device__ __forceinline__ void ring_l2_prefetch(const void* p, size_t bytes, in
 // One CTA per (segment, realisation r = blockIdx.x); NT threads, thread t owns units
 // u = t + i NT (slots 2u, 2u + 1), i < 8; the states of units i >= 8 - PARK live in shared
 // memory between their steps.
-template <class TabT, int LG, int PARK, int MINB>
+// PACKED: FP32 tables stored as three rows A, C, B per position, mode fastest (smerf_plan.packed)
+template <class TabT, int LG, int PARK, int MINB, bool PACKED>
 __global__ void __launch_bounds__(RingPass<LG>::NT, MINB) ring_kernel(SampleParams P)
 {
     constexpr int Nc = RingPass<LG>::Nc, NT = RingPass<LG>::NT;
     constexpr int U = 8, UP = U - PARK;
-    constexpr int ROW = step_row(1);
+    constexpr int ROW = PACKED ? 3 : step_row(1);  // values per (mode, ring) as stored
+    static_assert(!PACKED || sizeof(TabT) == 4, "packed tables are FP32");
     static_assert(Nc / 2 == U * NT, "8 units of two slots per thread");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint2 rk[10];  // Philox round keys of the CTA's realisation
@@ -190,9 +192,18 @@ __global__ void __launch_bounds__(RingPass<LG>::NT, MINB) ring_kernel(SamplePara
             const int u = tid + i * NT;
             float4 x = i < UP ? xreg[i < UP ? i : 0] : park[(i - UP) * NT + tid];
             if (pos > sg.p0) {
-                float t0[ROW], t1[ROW];
-                load_row<float, TabT, ROW>(tb + (size_t)(2 * u) * ROW, t0);
-                load_row<float, TabT, ROW>(tb + (size_t)(2 * u + 1) * ROW, t1);
+                float t0[4], t1[4];
+                if constexpr (PACKED) {
+                    const float* ta = (const float*)tb;
+                    const float2 a = __ldg(reinterpret_cast<const float2*>(ta + 2 * u));
+                    const float2 cc = __ldg(reinterpret_cast<const float2*>(ta + mp + 2 * u));
+                    const float2 bb = __ldg(reinterpret_cast<const float2*>(ta + 2 * mp + 2 * u));
+                    t0[0] = a.x, t0[1] = cc.x, t0[2] = bb.x;
+                    t1[0] = a.y, t1[1] = cc.y, t1[2] = bb.y;
+                } else {
+                    load_row<float, TabT, 4>(tb + (size_t)(2 * u) * ROW, t0);
+                    load_row<float, TabT, 4>(tb + (size_t)(2 * u + 1) * ROW, t1);
+                }
                 float nr[4];
                 unit_normals_rk<float>(rk, (uint32_t)u, (uint32_t)ring, nr);
                 float4 xr = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -200,11 +211,18 @@ __global__ void __launch_bounds__(RingPass<LG>::NT, MINB) ring_kernel(SamplePara
                 // slot 2u: (x.x Re, x.y Im); slot 2u + 1: (x.z, x.w).  Row: A, C, B.
                 float tn0 = t0[0], tn1 = t0[1], tn2 = t0[2];
                 if (i == 0 && u == 0) {  // slot 0's second chain is the Nyquist mode (own row)
-                    float tn[ROW];
-                    load_row<float, TabT, ROW>(tb + (size_t)Nc * ROW, tn);
-                    tn0 = tn[0];
-                    tn1 = tn[1];
-                    tn2 = tn[2];
+                    if constexpr (PACKED) {
+                        const float* ta = (const float*)tb;
+                        tn0 = ta[Nc];
+                        tn1 = ta[mp + Nc];
+                        tn2 = ta[2 * mp + Nc];
+                    } else {
+                        float tn[4];
+                        load_row<float, TabT, 4>(tb + (size_t)Nc * ROW, tn);
+                        tn0 = tn[0];
+                        tn1 = tn[1];
+                        tn2 = tn[2];
+                    }
                 }
                 // x = A x + C x_right + B xi, accumulated in that order (C x_right = 0 exactly
                 // without a right anchor)

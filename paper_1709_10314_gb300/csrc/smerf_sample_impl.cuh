@@ -1006,6 +1006,105 @@ __host__ __device__ constexpr int ws_lg_hi(int UPT, int M)
     return ((UPT == 1 ? 9 : UPT == 2 ? 10 : UPT == 4 ? 11 : 12) + (M == 1)) < 12 ? ((UPT == 1 ? 9 : UPT == 2 ? 10 : UPT == 4 ? 11 : 12) + (M == 1)) : 12;
 }
 
+// ---- iso-latitude grids with ring-dependent longitudes (the paper's Sec. 1 remark)
+// e^{i pi x} for a real x given in half-turns, reduced to [-1, 1) in FP64 first so that the
+// phase of a large multiple of a small offset keeps full accuracy
+template <class Real> __device__ __forceinline__ cplx<Real> cis_halfturns(double x)
+{
+    x -= 2.0 * floor(0.5 * x + 0.5);
+    Real sn, cs;
+    if constexpr (sizeof(Real) == 4) sincospif((float)x, &sn, &cs);
+    else sincospi(x, &sn, &cs);
+    return cmk<cplx<Real>>(cs, sn);
+}
+
+// Ring `ring` of n = 2 Ncp points from phi0 = h pi: the C2R input X' (slot 0 = (Y_0, Y_Ncp),
+// slot q = Y_q) of the real field T(phi) = sum_{|m| <= M} c_m e^{i m phi} at its points, where
+// c_0 = g_0, c_{+-m} = g_m, conj g_m (0 < m < M) and c_{+-M} = Re g_M / 2 (the Nyquist mode's real
+// part); Y_q = sum over m = q (mod n) of c_m e^{i m phi0} (modes above the ring's own Nyquist
+// alias onto it).  B: the ring's coefficients (slot 0 = (g_0, Re g_M), slot m = g_m) at stride
+// Nc per realisation; W: the folded rings at stride Ncp.
+template <class Real>
+__device__ __forceinline__ void ring_fold(const cplx<Real>* B, cplx<Real>* W, int R, int Nc, int n, double h, int ftid,
+                                          int nf)
+{
+    using C = cplx<Real>;
+    const int Ncp = n / 2, M = Nc;
+    for (int idx = ftid; idx < R * (Ncp + 1); idx += nf) {
+        const int r = idx / (Ncp + 1), q = idx - r * (Ncp + 1);
+        const C* X = B + (size_t)r * Nc;
+        C acc = cmk<C>(0, 0);
+        for (int m = q; m <= M; m += n) {  // m >= 0
+            const C g = m == 0 ? cmk<C>(X[0].x, 0) : (m == M ? cmk<C>((Real)0.5 * X[0].y, 0) : X[m]);
+            acc = cadd(acc, m == 0 ? g : cmul(g, cis_halfturns<Real>(h * m)));
+        }
+        for (int m = q == 0 ? n : n - q; m <= M; m += n) {  // the conjugate terms, -m < 0
+            const C g = m == M ? cmk<C>((Real)0.5 * X[0].y, 0) : X[m];
+            acc = cadd(acc, cconj(cmul(g, cis_halfturns<Real>(h * m))));
+        }
+        C* Y = W + (size_t)r * Ncp;
+        if (q == 0) Y[0].x = acc.x;
+        else if (q == Ncp) Y[0].y = acc.x;
+        else Y[q] = acc;
+    }
+}
+
+// C2R of R rings of n = 2 Ncp points (Ncp = 2^lg >= 2) from their folded input in src (stride
+// Ncp), ping-ponging with dst, last pass to gout: radix-4 Stockham passes (radix 2 last when lg
+// is odd) with the twiddles computed, the packing factors e^{2 pi i s / n} = pre[s pstride] from
+// the plan's table of its full ring.
+template <class C>
+__device__ __forceinline__ void ragged_c2r(C* src, C* dst, int R, int lg, const C* __restrict__ pre, int pstride,
+                                           RingOut<C> gout, int ftid, int nf)
+{
+    using Real = decltype(C::x);
+    const int Nc = 1 << lg;
+    int Ns = 1;
+    bool first = true;
+    while (Ns < Nc) {
+        const int RP = Nc / Ns >= 4 ? 4 : 2, LR = RP == 4 ? 2 : 1;
+        const bool last = Ns * RP == Nc;
+        const int lgnb = lg - LR, nb = 1 << lgnb, total = R << lgnb;
+        for (int b = ftid; b < total; b += nf) {
+            const int r = b >> lgnb, j = b & (nb - 1);
+            const C* S = src + ((size_t)r << lg);
+            C v[4];
+            int kk = 0;
+            if (first) {
+                for (int i = 0; i < RP; ++i) {
+                    const int sidx = j + i * nb;
+                    if (sidx == 0) {
+                        v[i] = cmk<C>(S[0].x + S[0].y, S[0].x - S[0].y);
+                    } else {
+                        const C a = S[sidx], bb = cconj(S[Nc - sidx]);
+                        v[i] = cadd(cadd(a, bb), cmuli(cmul(__ldg(pre + (size_t)sidx * pstride), csub(a, bb))));
+                    }
+                }
+            } else {
+                kk = j & (Ns - 1);
+                for (int i = 0; i < RP; ++i) v[i] = S[j + i * nb];
+                for (int i = 1; i < RP; ++i) v[i] = cmul(v[i], cis_halfturns<Real>(2.0 * i * kk / ((double)Ns * RP)));
+            }
+            if (RP == 4) dft4(v);
+            else dft2(v[0], v[1]);
+            const int idx = ((j - kk) << LR) + kk;
+            if (last) {
+                C* D = gout[r] + idx;
+                for (int a = 0; a < RP; ++a) __stcs(D + a * Ns, v[a]);
+            } else {
+                C* D = dst + ((size_t)r << lg) + idx;
+                for (int a = 0; a < RP; ++a) D[a * Ns] = v[a];
+            }
+        }
+        Ns *= RP;
+        first = false;
+        if (!last) bar_sync(kBarFft, nf);
+        C* t = src;
+        src = dst;
+        dst = t;
+    }
+}
+
 // Warp-specialised segment kernel.  Threads [0, NP) are the producer group: the recursion of
 // ring k (state in registers, units tid, tid + NP, ...) into coefficient buffer B[k & 1].
 // Threads [NP, NP + NF) are the FFT group: the C2R FFT of ring k from B[k & 1] (with W as
@@ -1152,13 +1251,28 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
             const int ring = c == 0 ? P.k0 - pos : P.k0 + pos;
             C* B = bufs + (size_t)(k & 1) * RMAX * Nc;
             if (!(c == 1 && pos == 0)) {  // the start ring is written by the northern chain
-                const RingOut<C> gout{(C*)((Real*)P.out + ((size_t)r0 * P.n_theta + ring) * (size_t)P.n_phi),
-                                      (size_t)P.n_theta * (size_t)(P.n_phi / 2)};
-                if constexpr (sizeof(Real) == 4)
+                RingOut<C> gout{(C*)((Real*)P.out + ((size_t)r0 * P.n_theta + ring) * (size_t)P.n_phi),
+                                (size_t)P.n_theta * (size_t)(P.n_phi / 2)};
+                int n_ring = P.n_phi;
+                double h_ring = 0.0;
+                if (P.ring_n) {  // ring-dependent longitudes: the rings lie back to back
+                    n_ring = P.ring_n[ring];
+                    h_ring = P.ring_h[ring];
+                    gout = RingOut<C>{(C*)((Real*)P.out + (size_t)r0 * P.ring_total + P.ring_off[ring]),
+                                      (size_t)(P.ring_total / 2)};
+                }
+                if (n_ring != P.n_phi || h_ring != 0.0) {
+                    int lg = 0;
+                    while ((2 << lg) < n_ring) ++lg;
+                    ring_fold<Real>(B, W, R, Nc, n_ring, h_ring, ftid, NF);
+                    bar_sync(kBarFft, NF);
+                    ragged_c2r<C>(W, B, R, lg, pre, P.n_phi / n_ring, gout, ftid, NF);
+                } else if constexpr (sizeof(Real) == 4) {
                     hr_c2r<C, ws_lg_lo(UPT, M), ws_lg_hi(UPT, M)>(P.lgNc, B, W, R, twp, (const C*)P.tw2, pre, gout,
                                                                    ftid, NF);
-                else
+                } else {
                     grp_c2r_rt<C>(B, W, R, P.lgNc, twp, pre, gout, ftid, NF);
+                }
             }
             bar_arrive(kBarEmpty + (k & 1), nt);
         }
@@ -1212,17 +1326,18 @@ __device__ __forceinline__ void queue_segment(const SampleParams& P, int seg, in
 }
 
 template <class Real, class TabT>
-__global__ void __launch_bounds__(kQueueThreads, 2) segment_queue_kernel(const SampleParams* __restrict__ descs,
+__global__ void __launch_bounds__(kQueueThreads, kQueueMinBlocks) segment_queue_kernel(const SampleParams* __restrict__ descs,
                                                                          const int4* __restrict__ items, int n_items,
                                                                          int* __restrict__ head)
 {
-    __shared__ int s_k;
-    for (;;) {
-        __syncthreads();  // the previous item's shared buffers and s_k are free again
-        if (threadIdx.x == 0) s_k = atomicAdd(head, 1);
-        __syncthreads();
-        const int k = s_k;
+    // the next item is claimed while the current one runs (s_k[b ^ 1]), hiding the atomic
+    __shared__ int s_k[2];
+    if (threadIdx.x == 0) s_k[0] = atomicAdd(head, 1);
+    __syncthreads();
+    for (int b = 0;; b ^= 1) {
+        const int k = s_k[b];
         if (k >= n_items) return;
+        if (threadIdx.x == 0) s_k[b ^ 1] = atomicAdd(head, 1);
         const int4 it = items[k];
         const SampleParams P = descs[it.x];
         switch (it.w) {
@@ -1235,6 +1350,7 @@ __global__ void __launch_bounds__(kQueueThreads, 2) segment_queue_kernel(const S
             case 6: queue_segment<Real, TabT, 6>(P, it.y, it.z); break;
             default: queue_segment<Real, TabT, 7>(P, it.y, it.z); break;
         }
+        __syncthreads();  // the item's shared buffers are free again and s_k[b ^ 1] is visible
     }
 }
 
@@ -1283,10 +1399,10 @@ auto pick_inplace(int lgNc)
                       : segment_kernel<Real, TabT, M, UPT, 0, PARK>;
 }
 
-template <class TabT, int LG, int PARK, int MINB>
+template <class TabT, int LG, int PARK, int MINB, bool PACKED>
 int launch_ring(const SampleParams& P, int n_segments, size_t smem, cudaStream_t st)
 {
-    auto kern = ring_kernel<TabT, LG, PARK, MINB>;
+    auto kern = ring_kernel<TabT, LG, PARK, MINB, PACKED>;
     if (set_smem_attr(kern, smem) != cudaSuccess) return SMERF_ECUDA;
     dim3 grid(P.n_samples, n_segments);
     kern<<<grid, RingPass<LG>::NT, smem, st>>>(P);
@@ -1322,7 +1438,7 @@ inline bool ring_config(const smerf_plan* pl, SegConfig& cfg)
     const int Nc = pl->n_phi / 2;
     if (!SMERF_RING_KERNEL || sizeof(Real) != 4 || pl->p != 1 || (Nc != 8192 && Nc != 16384)) return false;
     cfg = SegConfig{};
-    cfg.ring = 1;
+    cfg.ring = pl->packed ? 2 : 1;
     cfg.nt = Nc / 16;
     cfg.upt = 8;
     cfg.rmax = 1;
@@ -1488,8 +1604,15 @@ int dispatch_segments(const SampleParams& P, int n_segments, const SegConfig& cf
     }
     if (cfg.ring) {
         if constexpr (sizeof(Real) == 4 && M == 1) {
-            if (P.lgNc == 14) return launch_ring<TabT, 14, 6, 1>(P, n_segments, cfg.smem, st);
-            if (P.lgNc == 13) return launch_ring<TabT, 13, 6, 2>(P, n_segments, cfg.smem, st);
+            if constexpr (sizeof(TabT) == 4) {
+                if (cfg.ring == 2) {
+                    if (P.lgNc == 14) return launch_ring<TabT, 14, 6, 1, true>(P, n_segments, cfg.smem, st);
+                    if (P.lgNc == 13) return launch_ring<TabT, 13, 6, 2, true>(P, n_segments, cfg.smem, st);
+                    return SMERF_EUNSUPPORTED;
+                }
+            }
+            if (P.lgNc == 14) return launch_ring<TabT, 14, 6, 1, false>(P, n_segments, cfg.smem, st);
+            if (P.lgNc == 13) return launch_ring<TabT, 13, 6, 2, false>(P, n_segments, cfg.smem, st);
         }
         return SMERF_EUNSUPPORTED;
     }
@@ -1540,6 +1663,12 @@ int fill_params(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scr
     int lg = 0;
     while ((1 << lg) < P.Nc) ++lg;
     P.lgNc = lg;
+    P.ring_n = pl->rings_total ? pl->rings_n_dev : nullptr;
+    P.ring_h = pl->rings_total ? pl->rings_h_dev : nullptr;
+    P.ring_off = pl->rings_total ? pl->rings_off_dev : nullptr;
+    P.ring_total = pl->rings_total;
+    // ring-dependent longitudes are synthesised by the warp-specialised kernels' FFT group only
+    if (pl->rings_total && !cfg.ws) return SMERF_EUNSUPPORTED;
     return SMERF_OK;
 }
 

@@ -1023,6 +1023,18 @@ static SpecC make_spec_c(const smerf_plan* pl)
         }                                                                         \
     } while (0)
 
+// p = 1 FP32 step rows [position][mode][A, C, B, pad] -> [position][A, C, B][mode]
+__global__ void repack_rows_kernel(const float* __restrict__ rows, float* __restrict__ packed, int mp)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t pos = blockIdx.y;
+    if (m >= mp) return;
+    const float4 r = reinterpret_cast<const float4*>(rows)[pos * mp + m];
+    packed[(pos * 3 + 0) * mp + m] = r.x;
+    packed[(pos * 3 + 1) * mp + m] = r.y;
+    packed[(pos * 3 + 2) * mp + m] = r.z;
+}
+
 template <int M>
 int setup_impl(smerf_plan* pl, cudaStream_t st, bool sync)
 {
@@ -1136,6 +1148,24 @@ int setup_impl(smerf_plan* pl, cudaStream_t st, bool sync)
         CK(cudaFreeAsync(phi, st));
         CK(cudaFreeAsync(qv, st));
         phi = qv = nullptr;
+    }
+    if (M == 1 && pl->packed) {
+        // the ring kernel's packed p = 1 layout: [position][A, C, B][mode]
+        for (int c = 0; c < 2; ++c) {
+            const int len = pl->chain[c].len;
+            const size_t rb = (size_t)(len + 1) * step_row(M) * mp * es;
+            const size_t pb = (size_t)(len + 1) * 3 * mp * es;
+            void* packed = nullptr;
+            CK(smerf::dev_malloc(&packed, pb > 0 ? pb : 16));
+            repack_rows_kernel<<<dim3((unsigned)((mp + 255) / 256), (unsigned)(len + 1)), 256, 0, st>>>(
+                (const float*)pl->steps[c], (float*)packed, (int)mp);
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(st));
+            cudaFree(pl->steps[c]);
+            pl->steps[c] = packed;
+            pl->table_bytes = pl->table_bytes - rb + pb;
+            pl->step_table_bytes = pl->step_table_bytes - rb + pb;
+        }
     }
     if (sync) {
         CK(cudaStreamSynchronize(st));

@@ -31,7 +31,7 @@ class _Info(ctypes.Structure):
                 ("n_anchors", ctypes.c_int * 2), ("n_segments", ctypes.c_int),
                 ("flags", ctypes.c_uint), ("table_bytes", ctypes.c_size_t),
                 ("scratch_bytes_per_sample", ctypes.c_size_t), ("setup_ms", ctypes.c_double),
-                ("step_table_bytes", ctypes.c_size_t)]
+                ("step_table_bytes", ctypes.c_size_t), ("points_per_sample", ctypes.c_size_t)]
 
 
 _LIB = None
@@ -92,6 +92,8 @@ def _lib():
         L.smerf_batch_destroy.restype = ip
         L.smerf_plan_info.argtypes = [vp, ctypes.POINTER(_Info)]
         L.smerf_plan_info.restype = ip
+        L.smerf_plan_set_rings.argtypes = [vp, ctypes.POINTER(ip), dp]
+        L.smerf_plan_set_rings.restype = ip
         L.smerf_plan_copy_tables.argtypes = [vp, ip, ip, ip, dp]
         L.smerf_plan_copy_tables.restype = ip
         L.smerf_plan_autotune.argtypes = [vp, ip, vp, ctypes.POINTER(ip)]
@@ -163,6 +165,24 @@ class Plan:
         self.n_phi = int(n_phi)
         self.flags = int(flags)
         self.fp64 = bool(flags & SMERF_RECUR_FP64)
+        self.ring_points = None
+
+    def set_rings(self, n_phi_ring=None, phi0_ring=None):
+        """smerf_plan_set_rings: ring k holds n_phi_ring[k] points from phi0_ring[k] (None: the
+        full grid again).  sample() then returns [n_samples][sum(n_phi_ring)], rings back to back."""
+        if n_phi_ring is None:
+            _check("smerf_plan_set_rings", _lib().smerf_plan_set_rings(self._h, None, None))
+            self.ring_points = None
+            return
+        n = (ctypes.c_int * self.n_theta)(*[int(v) for v in n_phi_ring])
+        p0 = None if phi0_ring is None else (ctypes.c_double * self.n_theta)(*[float(v) for v in phi0_ring])
+        _check("smerf_plan_set_rings", _lib().smerf_plan_set_rings(self._h, n, p0))
+        self.ring_points = [int(v) for v in n_phi_ring]
+
+    @property
+    def points(self):
+        """Output values of one realisation."""
+        return sum(self.ring_points) if self.ring_points else self.n_theta * self.n_phi
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -187,7 +207,7 @@ class Plan:
                 "anchor_spacing": inf.anchor_spacing, "n_anchors": list(inf.n_anchors),
                 "n_segments": inf.n_segments, "flags": inf.flags, "table_bytes": inf.table_bytes,
                 "scratch_bytes_per_sample": inf.scratch_bytes_per_sample, "setup_ms": inf.setup_ms,
-                "step_table_bytes": inf.step_table_bytes}
+                "step_table_bytes": inf.step_table_bytes, "points_per_sample": inf.points_per_sample}
 
     def launches(self, n_samples):
         """smerf_sample_launches: kernels one sample() call of n_samples launches."""
@@ -258,15 +278,16 @@ class Plan:
             raise ValueError("out must be contiguous")
         if out.device.index != torch.cuda.current_device():
             raise ValueError("out is on %s, the current device is cuda:%d" % (out.device, torch.cuda.current_device()))
-        if int(n_samples) < 0 or out.numel() < int(n_samples) * self.n_theta * self.n_phi:
+        if int(n_samples) < 0 or out.numel() < int(n_samples) * self.points:
             raise ValueError("out holds %d elements; %d realisations need %d" % (
-                out.numel(), int(n_samples), int(n_samples) * self.n_theta * self.n_phi))
+                out.numel(), int(n_samples), int(n_samples) * self.points))
 
     def sample(self, seed, n_samples, out=None, stream=None):
         """Device realisations [n_samples][n_theta][n_phi] (torch tensor on the current device)."""
         import torch
         if out is None:
-            out = torch.empty((n_samples, self.n_theta, self.n_phi), dtype=self.dtype, device="cuda")
+            shape = (n_samples, self.points) if self.ring_points else (n_samples, self.n_theta, self.n_phi)
+            out = torch.empty(shape, dtype=self.dtype, device="cuda")
         self._check_out(out, n_samples)
         _check("smerf_sample", _lib().smerf_sample(self._h, ctypes.c_uint64(seed & (2**64 - 1)), int(n_samples),
                                                     ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
@@ -297,7 +318,8 @@ class Plan:
         """Realisations into host memory (numpy array or pinned torch CPU tensor)."""
         dt = np.float64 if self.fp64 else np.float32
         if out is None:
-            out = np.empty((n_samples, self.n_theta, self.n_phi), dtype=dt)
+            shape = (n_samples, self.points) if self.ring_points else (n_samples, self.n_theta, self.n_phi)
+            out = np.empty(shape, dtype=dt)
         ptr = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
         _check("smerf_sample_host", _lib().smerf_sample_host(self._h, ctypes.c_uint64(seed & (2**64 - 1)),
                                                               int(n_samples), ctypes.c_void_p(ptr),
@@ -327,6 +349,7 @@ def create_plans(specs):
         pl.n_phi = int(d["n_phi"])
         pl.flags = int(d.get("flags", 0))
         pl.fp64 = bool(pl.flags & SMERF_RECUR_FP64)
+        pl.ring_points = None
         plans.append(pl)
     return plans
 

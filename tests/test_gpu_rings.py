@@ -1,0 +1,92 @@
+"""Iso-latitude grids with ring-dependent longitudes (the paper's Sec. 1 remark; HEALPix-like
+rings): each ring's point count and offset set by smerf_plan_set_rings, every ring of every
+realisation against the oracle's synthesis at the same points (oracle.sample_rings)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _healpix_like(n_theta, n_phi):
+    """Rings of 4 * 2^j points growing towards the equator (at most n_phi), every other ring
+    shifted by half a step as HEALPix does."""
+    npr, p0 = [], []
+    for k in range(n_theta):
+        d = min(k, n_theta - 1 - k)  # rings from the nearer pole
+        n = 4
+        while n < n_phi and n < 4 * (d + 1):
+            n *= 2
+        npr.append(n)
+        p0.append(math.pi / n if k % 2 else 0.0)
+    return npr, p0
+
+
+def _rings(out, npr):
+    offs = np.concatenate([[0], np.cumsum(npr)])
+    return [[out[j, offs[k]:offs[k + 1]] for k in range(len(npr))] for j in range(out.shape[0])]
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+@pytest.mark.parametrize("kappa,n_theta,n_phi,H", [([6.0], 16, 64, 4), ([3.0, 8.0], 12, 32, 0)])
+def test_healpix_like_rings_against_oracle(fp64, kappa, n_theta, n_phi, H):
+    import torch
+    from paper_1709_10314_gb300 import SMERF_ORDER_PAPER, SMERF_RECUR_FP64, Plan
+    flags = (SMERF_RECUR_FP64 if fp64 else 0) | (SMERF_ORDER_PAPER if H == 0 else 0)
+    plan = Plan(kappa, 1.0, n_theta, n_phi, flags=flags, anchor_spacing=H)
+    npr, p0 = _healpix_like(n_theta, n_phi)
+    plan.set_rings(npr, p0)
+    assert plan.info()["points_per_sample"] == sum(npr)
+    out = plan.sample(21, 3)
+    torch.cuda.synchronize()
+    assert tuple(out.shape) == (3, sum(npr))
+    got = _rings(out.double().cpu().numpy(), npr)
+    ref = oracle.sample_rings(kappa, 1.0, n_theta, npr, p0, 21, 3, H=H, n_phi=n_phi)
+    std = float(np.std(np.concatenate([np.concatenate(r) for r in ref])))
+    err = max(float(np.max(np.abs(got[j][k] - ref[j][k]))) for j in range(3) for k in range(n_theta)) / std
+    print("rings %s fp64=%s: max|gpu-oracle|/std = %.2e" % (npr, fp64, err))
+    assert err < (1e-9 if fp64 else 1e-4)
+
+
+def test_full_rings_and_reset():
+    """Full rings without offsets reproduce the plain grid bit for bit; offsets only shift the
+    points; set_rings(None) restores the plain grid."""
+    import torch
+    from paper_1709_10314_gb300 import Plan
+    plan = Plan([20.0, 50.0], 1.0, 32, 128, anchor_spacing=8)
+    ref = plan.sample(4, 2)
+    plan.set_rings([128] * 32)
+    full = plan.sample(4, 2)
+    torch.cuda.synchronize()
+    assert torch.equal(full.reshape(ref.shape), ref)
+    shift = [(3 * k) % 128 for k in range(32)]
+    plan.set_rings([128] * 32, [2 * math.pi * s / 128 for s in shift])
+    sh = plan.sample(4, 2).reshape(ref.shape)
+    torch.cuda.synchronize()
+    for k in range(32):
+        d = float((sh[:, k] - torch.roll(ref[:, k], -shift[k], dims=1)).abs().max())
+        assert d <= 1e-4 * float(ref.std())
+    plan.set_rings(None)
+    assert torch.equal(plan.sample(4, 2), ref)
+
+
+def test_ring_layout_rejections():
+    import torch
+    from paper_1709_10314_gb300 import SMERF_TABLES_FP32, Batch, Plan, SmerfError
+    plan = Plan([10.0], 1.0, 8, 32, anchor_spacing=4)
+    for bad in ([12] * 8, [2] * 8, [64] * 8):  # not a power of two, fewer than 4, more than n_phi
+        with pytest.raises(SmerfError) as e:
+            plan.set_rings(bad)
+        assert e.value.status == -1
+    plan.set_rings([32, 16, 8, 4, 4, 8, 16, 32])
+    with pytest.raises(SmerfError) as e:
+        Batch([plan], [1])
+    assert e.value.status == -5
+    big = Plan([300.0], 1.0, 4, 32768, flags=SMERF_TABLES_FP32)  # the ring kernel's size
+    with pytest.raises(SmerfError) as e:
+        big.set_rings([32768, 16384, 16384, 32768])
+    assert e.value.status == -5
+    torch.cuda.synchronize()
