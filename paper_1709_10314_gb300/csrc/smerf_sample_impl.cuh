@@ -1105,6 +1105,21 @@ __device__ __forceinline__ void ragged_c2r(C* src, C* dst, int R, int lg, const 
     }
 }
 
+// A ring whose point count or offset differs from the plan's full ring: fold, then the
+// runtime-size C2R.  Not inlined, so that the warp-specialised bodies (and the batch kernels
+// that hold several of them) keep their register allocation for the full-ring path.
+template <class Real>
+__device__ __noinline__ void ragged_ring(cplx<Real>* B, cplx<Real>* W, int R, int Nc, int n, double h,
+                                         const cplx<Real>* pre, int n_phi, cplx<Real>* gbase, size_t gstride,
+                                         int ftid, int nf)
+{
+    int lg = 0;
+    while ((2 << lg) < n) ++lg;
+    ring_fold<Real>(B, W, R, Nc, n, h, ftid, nf);
+    bar_sync(kBarFft, nf);
+    ragged_c2r<cplx<Real>>(W, B, R, lg, pre, n_phi / n, RingOut<cplx<Real>>{gbase, gstride}, ftid, nf);
+}
+
 // Warp-specialised segment kernel.  Threads [0, NP) are the producer group: the recursion of
 // ring k (state in registers, units tid, tid + NP, ...) into coefficient buffer B[k & 1].
 // Threads [NP, NP + NF) are the FFT group: the C2R FFT of ring k from B[k & 1] (with W as
@@ -1113,7 +1128,8 @@ __device__ __forceinline__ void ragged_c2r(C* src, C* dst, int R, int lg, const 
 //             syncs the two outstanding EMPTY barriers
 //   FFT:      sync FULL[k&1]; FFT; arrive EMPTY[k&1]
 // Every FULL/EMPTY barrier counts NP + NF threads; the FFT passes use a group barrier.
-template <class Real, class TabT, int M, int UPT, int RMAX>
+// RINGS: the request may have ring-dependent longitudes (single-request launches; batches never do)
+template <class Real, class TabT, int M, int UPT, int RMAX, bool RINGS = true>
 __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, int group)
 {
     using C = cplx<Real>;
@@ -1255,18 +1271,14 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
                                 (size_t)P.n_theta * (size_t)(P.n_phi / 2)};
                 int n_ring = P.n_phi;
                 double h_ring = 0.0;
-                if (P.ring_n) {  // ring-dependent longitudes: the rings lie back to back
+                if (RINGS && P.ring_n) {  // ring-dependent longitudes: the rings lie back to back
                     n_ring = P.ring_n[ring];
                     h_ring = P.ring_h[ring];
                     gout = RingOut<C>{(C*)((Real*)P.out + (size_t)r0 * P.ring_total + P.ring_off[ring]),
                                       (size_t)(P.ring_total / 2)};
                 }
-                if (n_ring != P.n_phi || h_ring != 0.0) {
-                    int lg = 0;
-                    while ((2 << lg) < n_ring) ++lg;
-                    ring_fold<Real>(B, W, R, Nc, n_ring, h_ring, ftid, NF);
-                    bar_sync(kBarFft, NF);
-                    ragged_c2r<C>(W, B, R, lg, pre, P.n_phi / n_ring, gout, ftid, NF);
+                if (RINGS && (n_ring != P.n_phi || h_ring != 0.0)) {
+                    ragged_ring<Real>(B, W, R, Nc, n_ring, h_ring, pre, P.n_phi, gout.base, gout.stride, ftid, NF);
                 } else if constexpr (sizeof(Real) == 4) {
                     hr_c2r<C, ws_lg_lo(UPT, M), ws_lg_hi(UPT, M)>(P.lgNc, B, W, R, twp, (const C*)P.tw2, pre, gout,
                                                                    ftid, NF);
@@ -1293,7 +1305,7 @@ __global__ void __launch_bounds__(ws_max_threads(MINB), MINB) segment_ws_batched
 {
     const int4 it = items[blockIdx.x];
     const SampleParams P = descs[it.x];
-    ws_body<Real, TabT, M, UPT, RMAX>(P, it.y, it.z);
+    ws_body<Real, TabT, M, UPT, RMAX, false>(P, it.y, it.z);
 }
 
 // ---- uneven batches in two persistent phases
@@ -1322,7 +1334,7 @@ template <class Real, class TabT, int SH>
 __device__ __forceinline__ void queue_segment(const SampleParams& P, int seg, int grp)
 {
     constexpr int M = SH / kQueueBuilds + 1, B = SH % kQueueBuilds;
-    ws_body<Real, TabT, M, queue_upt(B), queue_rmax(B)>(P, seg, grp);
+    ws_body<Real, TabT, M, queue_upt(B), queue_rmax(B), false>(P, seg, grp);
 }
 
 template <class Real, class TabT>
