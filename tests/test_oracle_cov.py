@@ -64,6 +64,7 @@ CASES = [
     ([10.0], 64, [0, 1, 7, 64]),
     ([20.0, 50.0], 32, [0, 3, 32]),
     ([3.0, 7.0], 8, [0, 2, 4]),
+    ([3.0, 7.0, 15.0], 8, [0, 2, 4]),   # p = 3
 ]
 
 

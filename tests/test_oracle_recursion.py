@@ -32,6 +32,8 @@ CASES = [
     ([4.0], 9, 8, 3),                 # anchored order (anchors, then bridges)
     ([3.0, 8.0], 10, 16, 0),          # p = 2
     ([3.0, 8.0], 12, 16, 4),
+    ([2.0, 5.0, 9.0], 10, 16, 0),     # p = 3
+    ([2.0, 5.0, 9.0], 12, 16, 4),
     (oracle.KHat([complex(0.0, math.sqrt(10.0)), complex(0.0, -math.sqrt(10.0))]), 8, 16, 0),  # Sec. 5
 ]
 

@@ -38,7 +38,8 @@ def _parents(order, n_theta, H):
     return par
 
 
-@pytest.mark.parametrize("kappa,n_theta,H,m", [([4.0], 9, 3, 2), ([3.0, 8.0], 8, 3, 1), ([3.0, 8.0], 8, 0, 3)])
+@pytest.mark.parametrize("kappa,n_theta,H,m", [([4.0], 9, 3, 2), ([3.0, 8.0], 8, 3, 1), ([3.0, 8.0], 8, 0, 3),
+                                                ([2.0, 5.0, 9.0], 8, 3, 1)])
 def test_markov_conditioning(kappa, n_theta, H, m):
     """Conditioning on every earlier ring equals conditioning on the nearest earlier
     neighbours on each side (the Markov property of the M-vector state, Sec. 2);
@@ -118,11 +119,16 @@ def exact_oracle_field_cov(kappa, A, n_theta, n_phi, H=0):
     return C
 
 
-@pytest.mark.parametrize("n_theta,n_phi,spectrum", [(3, 4, "real"), (4, 8, "real"), (4, 8, "sec5")])
+@pytest.mark.parametrize("n_theta,n_phi,spectrum", [(3, 4, "real"), (4, 8, "real"), (4, 8, "sec5"), (4, 8, "p3")])
 def test_field_covariance_tiny_bruteforce(n_theta, n_phi, spectrum):
     # C_l ~ l^-4: the direct sum converges like lmax^-3.  "sec5": the paper's Sec. 5 spectrum
-    # (10 + l^2 (l+1)^2)^-1, complex kappa-hat = +-i sqrt(10)
-    kappa = [2.0, 5.0] if spectrum == "real" else oracle.KHat([complex(0, math.sqrt(10)), complex(0, -math.sqrt(10))])
+    # (10 + l^2 (l+1)^2)^-1, complex kappa-hat = +-i sqrt(10); "p3": three factors, C_l ~ l^-6
+    if spectrum == "real":
+        kappa = [2.0, 5.0]
+    elif spectrum == "p3":
+        kappa = [2.0, 5.0, 9.0]
+    else:
+        kappa = oracle.KHat([complex(0, math.sqrt(10)), complex(0, -math.sqrt(10))])
     A = 1.0
     Cb = truncated_field_cov(kappa, A, n_theta, n_phi, 400)
     Co = exact_oracle_field_cov(kappa, A, n_theta, n_phi)
