@@ -221,9 +221,10 @@ int smerf_batch_destroy(smerf_batch* batch);
 
 /*
  * smerf_sample_noalloc -- smerf_sample without any device allocation.  The paper has no
- * counterpart; this exists for callers that cannot let a library allocate device memory
- * (work captured once into a CUDA graph and replayed, hosts whose device memory is carved
- * out up front, frameworks that own all device memory through their own pool).
+ * counterpart; this exists for callers that cannot let a library allocate device memory:
+ * real-time or embedded hosts whose device memory is carved out once at start-up, and
+ * frameworks that own all device memory through their own pool and forbid other
+ * allocations (a cudaMalloc there can fail, or synchronise the device mid-frame).
  *
  * Same arguments, output and noise as smerf_sample; `out` is still caller-owned device
  * memory.  The anchor-state scratch is a fixed 16 MiB array inside the library's device

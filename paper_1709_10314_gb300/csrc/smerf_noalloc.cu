@@ -2,9 +2,9 @@
 //
 // smerf_sample needs scratch space for the anchor states and takes it from the
 // stream-ordered allocator on every call.  Some callers cannot let a library allocate:
-// code that runs inside a CUDA graph built once and replayed, real-time or embedded hosts
-// whose device memory is carved out up front, or frameworks that own every byte of device
-// memory through their own pool and forbid third-party cudaMalloc calls.  For them,
+// real-time or embedded hosts whose device memory is carved out once at start-up, or
+// frameworks that own every byte of device memory through their own pool and forbid
+// third-party cudaMalloc calls.  For them,
 // smerf_sample_noalloc runs the same anchor and segment kernels with the scratch placed
 // in the fixed array below, which lives in this library's device image: every GPU that
 // loads the library holds these bytes until the process exits.

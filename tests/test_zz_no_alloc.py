@@ -1,6 +1,6 @@
 """smerf_sample_noalloc, the entry point for callers that cannot let the library allocate
-device memory (graphs captured once and replayed, pre-carved device memory, frameworks
-that own every device byte).  Its output must equal smerf_sample's on the same plan and
+device memory (hosts whose device memory is carved out at start-up, frameworks that own
+every device byte through their own pool).  Its output must equal smerf_sample's on the same plan and
 seeds, call after call, since both run the same kernels; only the scratch location
 differs (a fixed 16 MiB device array instead of the stream-ordered allocator).
 
