@@ -551,8 +551,8 @@ def main():
     ap.add_argument("--anchor", type=int, default=0,
                     help="anchor spacing H of the plan (0: the workload's default)")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
-                    choices=["1024x2048-p2", "plain-64x128-p1-fp64", "4096x8192-p1", "16384x32768-p1", "4096x32768-p1",
-                             "uneven-256"])
+                    choices=["1024x2048-p2", "1024x2048-p3", "plain-64x128-p1-fp64", "4096x8192-p1", "16384x32768-p1",
+                             "4096x32768-p1", "uneven-256"])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

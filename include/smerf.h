@@ -42,7 +42,7 @@ typedef struct smerf_plan smerf_plan;
 #define SMERF_EILLCOND (-2)    /* kappa_i^2 closer than 1e-6 relative: partial fractions cancel */
 #define SMERF_ENOMEM (-3)      /* device or host allocation failed                              */
 #define SMERF_ECUDA (-4)       /* a CUDA runtime call or kernel launch failed                    */
-#define SMERF_EUNSUPPORTED (-5) /* valid but not built (e.g. p > 2, n_phi not a power of two)   */
+#define SMERF_EUNSUPPORTED (-5) /* valid but not built (e.g. n_phi not a power of two)          */
 #define SMERF_ESCRATCH (-6)    /* smerf_sample_noalloc: request exceeds its fixed 16 MiB scratch */
 #define SMERF_ETIMEOUT (-7)    /* reserved for a device wait that runs out (none can: see
                                   smerf_last_device_status)                                     */
@@ -60,7 +60,8 @@ typedef struct smerf_plan smerf_plan;
  * computation").  Synchronous: returns after the FP64 set-up kernels finished.
  *
  *   kappa[p]       p distinct values kappa_i > 0 (host pointer, read during the call)
- *   p              number of spectrum factors, 1 <= p <= 2 (state dimension p per real chain)
+ *   p              number of spectrum factors, 1 <= p <= 3 (state dimension p per real chain;
+ *                  p = 3 is built for n_phi <= 8192, or <= 4096 with SMERF_RECUR_FP64)
  *   A              amplitude > 0
  *   n_theta        rings, 2 <= n_theta <= 65536
  *   n_phi          longitudes, a power of two, 8 <= n_phi <= 32768

@@ -186,8 +186,11 @@ int smerf_launch_sample_staged(const smerf_plan* pl, uint64_t seed, int n, void*
     sh.coarse[1] = sm.dst[1];
     sh.beq = sm.dst[2];
     sh.tab64 = false;
-    return pl->p == 1 ? smerf_launch_sample_staged_p1(&sh, sm, job, seed, n, out, scratch, st, ev0, ev1)
-                      : smerf_launch_sample_staged_p2(&sh, sm, job, seed, n, out, scratch, st, ev0, ev1);
+    switch (pl->p) {
+        case 1: return smerf_launch_sample_staged_p1(&sh, sm, job, seed, n, out, scratch, st, ev0, ev1);
+        case 2: return smerf_launch_sample_staged_p2(&sh, sm, job, seed, n, out, scratch, st, ev0, ev1);
+        default: return smerf_launch_sample_staged_p3(&sh, sm, job, seed, n, out, scratch, st, ev0, ev1);
+    }
 }
 
 int smerf_launch_sample(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch, cudaStream_t st,
@@ -405,6 +408,9 @@ static int create_plan(const double* kappa, const double* kh_re, const double* k
 {
     if (p > kMaxP) return SMERF_EUNSUPPORTED;
     if (!is_pow2(n_phi) || n_phi < 8 || n_phi > 32768) return SMERF_EUNSUPPORTED;
+    // p = 3 runs on the warp-specialised kernels, whose ring buffers and right-anchor states must
+    // fit in one SM's shared memory: rings up to 4096 complex points in FP32, 2048 in FP64
+    if (p == 3 && n_phi > ((flags & SMERF_RECUR_FP64) ? 4096 : 8192)) return SMERF_EUNSUPPORTED;
 
     smerf_plan* pl = new (std::nothrow) smerf_plan;
     if (!pl) return SMERF_ENOMEM;

@@ -2,11 +2,12 @@
 // precisions) in few launches.  Requests with FP32 recursion run in two persistent phases per
 // table precision: one anchor launch over every request's anchor items, then one launch of
 // persistent CTAs that pull segment items of every shape (p, n_phi, launch configuration) from
-// a device queue, largest first.  Requests with FP64 recursion form groups of one kernel shape
-// that run as one anchor launch and one segment launch each.  Per-request parameters (tables,
-// seed, output, scratch) are read from a descriptor array in device memory.  The work lists and
-// the scratch are built once per batch, so a launch (descriptor copy, queue reset, kernels) can
-// be captured into a CUDA graph and replayed with new seeds and outputs.
+// a device queue, largest first.  Requests with FP64 recursion or p = 3 form groups of one
+// kernel shape that run as one anchor launch and one segment launch each.  Per-request
+// parameters (tables, seed, output, scratch) are read from a descriptor array in device
+// memory.  The work lists and the scratch are built once per batch, so a launch (descriptor
+// copy, queue reset, kernels) can be captured into a CUDA graph and replayed with new seeds and
+// outputs.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -37,8 +38,10 @@ int fill_params(int kind, const smerf_plan* pl, uint64_t seed, int n, void* out,
     }
 }
 
-// the FP32-recursion kinds run as two persistent phases
-bool queued(int kind) { return kind == kFF || kind == kFD; }
+// FP32-recursion groups with p <= 2 run as two persistent phases (p = 3, whose units hold 12
+// state values, keeps a launch pair per group so that the persistent kernel's registers stay
+// sized for p <= 2)
+bool queued(int kind, int p) { return (kind == kFF || kind == kFD) && p <= 2; }
 
 // A queued kind's work: anchor items, segment items (largest first), the persistent launch's
 // threads, shared memory and CTAs, and the device counter of its queue.
@@ -216,7 +219,7 @@ int smerf_batch_create(const smerf_plan* const* plans, const int* n_samples, int
         std::vector<std::pair<double, int4>> qs;
         size_t smem = 0;
         for (size_t g = 0; g < b->groups.size() && rc == SMERF_OK; ++g) {
-            if (b->groups[g].kind != kind) continue;
+            if (b->groups[g].kind != kind || !queued(kind, b->groups[g].rep->p)) continue;
             for (const int4& it : anc[g]) qa.push_back(make_int4(it.x, it.y, it.z, it.w | (plans[it.x]->p << 4)));
             int last = -1;
             for (const int4& it : seg[g]) {
@@ -312,7 +315,7 @@ int smerf_batch_launch(smerf_batch* b, void* stream)
         if (rc != SMERF_OK) return rc;
     }
     for (const Group& g : b->groups) {
-        if (queued(g.kind)) continue;
+        if (queued(g.kind, g.rep->p)) continue;
         const int rc = launch_group(g.kind, g.rep, b->d_descs, g.d_anc, g.n_anc, g.d_seg, g.n_seg, st);
         if (rc != SMERF_OK) return rc;
     }
@@ -344,7 +347,7 @@ int smerf_batch_launch_count(const smerf_batch* b)
     int n = 0;
     for (const Queue& q : b->queues) n += (q.n_anc > 0) + (q.n_seg > 0);
     for (const Group& g : b->groups)
-        if (!queued(g.kind)) n += (g.n_anc > 0) + (g.n_seg > 0);
+        if (!queued(g.kind, g.rep->p)) n += (g.n_anc > 0) + (g.n_seg > 0);
     for (int i : b->singles) n += smerf_sample_launches(b->plans[i], b->counts[i]);
     return n;
 }

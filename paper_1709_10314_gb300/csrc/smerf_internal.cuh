@@ -14,7 +14,7 @@
 
 namespace smerf {
 
-constexpr int kMaxP = 2;             // spectrum factors supported by the kernels
+constexpr int kMaxP = 3;             // spectrum factors supported by the kernels
 constexpr int kDefaultAnchor = 16;   // default anchor spacing H
 
 // ------------------------------------------------------------------ plan
@@ -159,9 +159,12 @@ inline int queue_build(int n_units)
     return -1;
 }
 
-// units: the slots whose normals fill whole Philox calls.  p = 1: 2 slots per call;
-// p = 2: 1 slot per call.
-__host__ __device__ constexpr int unit_slots(int M) { return M == 1 ? 2 : 1; }
+// units: the fewest slots whose 2p normals each fill whole Philox calls (4 normals per call).
+// p = 1: 2 slots per call; p = 2: 1 slot per call; p = 3: 2 slots per 3 calls.  A unit holds
+// unit_vals(p) state values and draws the normals of calls [unit_calls u, unit_calls (u + 1)).
+__host__ __device__ constexpr int unit_slots(int M) { return M == 2 ? 1 : 2; }
+__host__ __device__ constexpr int unit_vals(int M) { return 2 * M * unit_slots(M); }
+__host__ __device__ constexpr int unit_calls(int M) { return unit_vals(M) / 4; }
 
 // ----------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11.
@@ -317,14 +320,15 @@ struct StageSmall {
     float* dst[3];
     unsigned end[3];  // cumulative element counts of coarse[0], coarse[1], beq
 };
-// the staged call for p = 1, 2 (smerf_sample_ff_p1.cu, smerf_sample_ff_p2.cu): plan `sh` reads
-// the FP32 copies S.dst and J.dst
+// the staged call for p = 1, 2, 3 (smerf_sample_ff_pM.cu): plan `sh` reads the FP32 copies
+// S.dst and J.dst
 #define SMERF_DECLARE_STAGED(M)                                                                     \
     int smerf_launch_sample_staged_p##M(const smerf_plan* sh, const StageSmall& S, const StageJob& J,      \
                                         uint64_t seed, int n, void* out, void* scratch, cudaStream_t st,    \
                                         cudaEvent_t ev0, cudaEvent_t ev1);
 SMERF_DECLARE_STAGED(1)
 SMERF_DECLARE_STAGED(2)
+SMERF_DECLARE_STAGED(3)
 
 // dynamic shared-memory attribute bookkeeping (smerf_api.cu)
 int smerf_smem_attr_done(const void* kern, int dev, size_t smem, bool record);

@@ -14,7 +14,8 @@
 //
 // Slots: slot s in [1, n_phi/2) is mode m = s (Re and Im chains); slot 0 holds the real
 // chain of m = 0 and the Re chain of the Nyquist mode m = n_phi/2.  A "unit" is the set
-// of slots whose 2p normals fill one Philox call (p = 1: two slots, p = 2: one slot).
+// of slots whose 2p normals fill whole Philox calls (p = 1: two slots per call, p = 2: one slot
+// per call, p = 3: two slots per three calls); it holds unit_vals(p) state values.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -46,14 +47,18 @@ __host__ __device__ constexpr int ws_max_threads(int minb) { return minb == 1 ? 
 
 template <int M> constexpr int kG = unit_slots(M);
 
-// the 4 normals of Philox call `call` of ring `ring` for realisation key `key64`
-template <class Real>
-__device__ __forceinline__ void unit_normals(uint64_t key64, uint32_t call, uint32_t ring, Real (&n)[4])
+// the 4 NC normals of unit u of ring `ring` for realisation key `key64`: Philox calls
+// [NC u, NC (u + 1)), four normals each
+template <class Real, int NC = 1>
+__device__ __forceinline__ void unit_normals(uint64_t key64, uint32_t u, uint32_t ring, Real (&n)[4 * NC])
 {
     const PhiloxKey key{(uint32_t)key64, (uint32_t)(key64 >> 32)};
-    const uint4 w = philox4x32_10(make_uint4(call, ring, 0u, 0u), key);
-    box_muller(w.x, w.y, n[0], n[1]);
-    box_muller(w.z, w.w, n[2], n[3]);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        const uint4 w = philox4x32_10(make_uint4(u * NC + j, ring, 0u, 0u), key);
+        box_muller(w.x, w.y, n[4 * j], n[4 * j + 1]);
+        box_muller(w.z, w.w, n[4 * j + 2], n[4 * j + 3]);
+    }
 }
 
 template <class Real, class TabT>
@@ -74,8 +79,8 @@ __device__ __forceinline__ float tabcvt<float, double>(double v)
     return __uint_as_float((t & 0x7FFFFFFFu) | (hi & 0x80000000u));
 }
 
-// anchor scratch offset: [c][r][j][slot][f], f = part * M + q (a unit's 2p x unit_slots
-// values, four in both built cases, are contiguous)
+// anchor scratch offset: [c][r][j][slot][f], f = part * M + q (a unit's unit_vals(M) values
+// are contiguous: 16 bytes for p = 1, 2 and 48 for p = 3 in FP32)
 template <int M>
 __device__ __forceinline__ size_t aoff(const SampleParams& P, int c, int r, int j, int f, int slot)
 {
@@ -95,6 +100,41 @@ template <> struct Vec4<double> {
     static __device__ __forceinline__ void st(double* p, const double (&v)[4]) { reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]); reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]); }
 };
 
+// a unit's NV state values (NV a multiple of 4; 16-byte aligned) as NV / 4 Vec4 accesses
+template <class Real, int NV> struct VecN {
+    static_assert(NV % 4 == 0, "whole Vec4 groups");
+    using Q = Real[4];
+    static __device__ __forceinline__ void ld(const Real* p, Real (&v)[NV])
+    {
+#pragma unroll
+        for (int k = 0; k < NV; k += 4) Vec4<Real>::ld(p + k, *reinterpret_cast<Q*>(&v[k]));
+    }
+    static __device__ __forceinline__ void ldg(const Real* p, Real (&v)[NV])
+    {
+#pragma unroll
+        for (int k = 0; k < NV; k += 4) Vec4<Real>::ldg(p + k, *reinterpret_cast<Q*>(&v[k]));
+    }
+    static __device__ __forceinline__ void st(Real* p, const Real (&v)[NV])
+    {
+#pragma unroll
+        for (int k = 0; k < NV; k += 4) Vec4<Real>::st(p + k, *reinterpret_cast<const Q*>(&v[k]));
+    }
+};
+
+// a unit's coefficients g_m into the ring buffer (slot 0's imaginary part carries the Nyquist
+// chain): p = 1 as one vector store of (Re, Im, Re, Im), else one complex value per slot
+template <class C, class Real, int M>
+__device__ __forceinline__ void put_unit(C* ring, int u, const Real (&x)[unit_vals(M)])
+{
+    constexpr int G = unit_slots(M);
+    if constexpr (M == 1) {
+        Vec4<Real>::st(reinterpret_cast<Real*>(ring + 2 * u), x);
+    } else {
+#pragma unroll
+        for (int g = 0; g < G; ++g) ring[G * u + g] = cmk<C>(x[g * 2 * M], x[g * 2 * M + M]);
+    }
+}
+
 // one step-table row (step_row(M) values, 16-byte aligned) converted to the recursion precision
 template <class Real, class TabT, int ROW>
 __device__ __forceinline__ void load_row(const TabT* p, Real (&t)[ROW])
@@ -110,7 +150,7 @@ __device__ __forceinline__ void load_row(const TabT* p, Real (&t)[ROW])
 
 // ------------------------------------------------------------------ anchors
 // anchors whose table values and normals are fetched ahead of the one being stepped
-__host__ __device__ constexpr int anchor_ahead(int M) { return M == 1 ? 4 : 2; }
+__host__ __device__ constexpr int anchor_ahead(int M) { return M == 1 ? 4 : M == 2 ? 2 : 1; }
 
 // Work an anchor thread carries out beside its anchors: prologue() before the first anchor,
 // step(j, d) at the end of anchor j's step (d = (j - 1) mod anchor_ahead(M)).  NoStage: none.
@@ -234,10 +274,11 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
     const size_t mp = P.n_modes_pad;
     const uint64_t key = P.seed + (uint64_t)r;
     Real* anc = (Real*)P.anc;
+    constexpr int NU = unit_vals(M), NC = unit_calls(M);
     Real x[G][2][M];
-    Real nr[4];
+    Real nr[NU];
     // start ring: x = B_eq xi (x basis); the southern chain keeps S x
-    unit_normals<Real>(key, (uint32_t)u, (uint32_t)P.k0, nr);
+    unit_normals<Real, NC>(key, (uint32_t)u, (uint32_t)P.k0, nr);
     const TabT* beq = (const TabT*)P.beq;
 #pragma unroll
     for (int g = 0; g < G; ++g)
@@ -255,14 +296,14 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
             }
         }
     {
-        Real v[4];
+        Real v[NU];
 #pragma unroll
         for (int g = 0; g < G; ++g)
 #pragma unroll
             for (int part = 0; part < 2; ++part)
 #pragma unroll
                 for (int q = 0; q < M; ++q) v[g * 2 * M + part * M + q] = x[g][part][q];
-        Vec4<Real>::st(anc + aoff<M>(P, c, r, 0, 0, G * u), v);
+        VecN<Real, NU>::st(anc + aoff<M>(P, c, r, 0, 0, G * u), v);
     }
     // anchors: x_j = Phi x_{j-1} + chol(S) xi.  The table values and normals of the next AD
     // anchors are fetched ahead of the matrix-vector products (they do not depend on the
@@ -273,13 +314,13 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
     const int na = c == 0 ? P.n_anchors[0] : P.n_anchors[1];
     constexpr int AD = anchor_ahead(M);  // anchors prefetched ahead (the loads come from L2 or HBM)
     Real tq[AD][G][2][Ec];
-    Real nq[AD][4];
+    Real nq[AD][NU];
     const int k0 = P.k0, H = P.H, Ncm = P.Nc;  // copies: the lambda must not take P's address
     // table values of anchor j, converted; both chains of a slot share its mode's values except
     // slot 0, whose second chain is the Nyquist mode
-    auto fetch = [=](int j, Real (&t)[G][2][Ec], Real (&xi)[4]) {
+    auto fetch = [=](int j, Real (&t)[G][2][Ec], Real (&xi)[NU]) {
         const int ring = c == 0 ? k0 - j * H : k0 + j * H;
-        unit_normals<Real>(key, (uint32_t)u, (uint32_t)ring, xi);
+        unit_normals<Real, NC>(key, (uint32_t)u, (uint32_t)ring, xi);
         const TabT* tb = cs + (size_t)j * Ec * mp;
 #pragma unroll
         for (int g = 0; g < G; ++g) {
@@ -323,14 +364,14 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
 #pragma unroll
                     for (int q = 0; q < M; ++q) x[g][part][q] = xn[q];
                 }
-            Real v[4];
+            Real v[NU];
 #pragma unroll
             for (int g = 0; g < G; ++g)
 #pragma unroll
                 for (int part = 0; part < 2; ++part)
 #pragma unroll
                     for (int q = 0; q < M; ++q) v[g * 2 * M + part * M + q] = x[g][part][q];
-            Vec4<Real>::st(anc + aoff<M>(P, c, r, j, 0, G * u), v);
+            VecN<Real, NU>::st(anc + aoff<M>(P, c, r, j, 0, G * u), v);
             if (j + AD <= na) fetch(j + AD, tq[d], nq[d]);
             hook.step(j, d);
         }
@@ -667,37 +708,43 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const uint2* rk)
 // The normals of one Philox call for NB realisations at once (round keys rk[0..NB)): the NB
 // generator chains are independent and run interleaved; the first round's products, which
 // depend on the counter only, are shared.
-template <class Real, int NB>
-__device__ __forceinline__ void unit_normals_multi(const uint2 (*rk)[10], uint32_t call, uint32_t ring, Real (&n)[NB][4])
+template <class Real, int NB, int NC = 1>
+__device__ __forceinline__ void unit_normals_multi(const uint2 (*rk)[10], uint32_t u, uint32_t ring, Real (&n)[NB][4 * NC])
 {
     const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
-    uint4 c[NB];
 #pragma unroll
-    for (int b = 0; b < NB; ++b) c[b] = make_uint4(call, ring, 0u, 0u);
+    for (int j = 0; j < NC; ++j) {  // the unit's Philox calls NC u + j
+        uint4 c[NB];
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
+        for (int b = 0; b < NB; ++b) c[b] = make_uint4(u * NC + j, ring, 0u, 0u);
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const uint2 k = rk[b][r];
+                const uint64_t p0 = (uint64_t)M0 * c[b].x;
+                const uint64_t p1 = (uint64_t)M1 * c[b].z;
+                c[b] = make_uint4((uint32_t)(p1 >> 32) ^ c[b].y ^ k.x, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c[b].w ^ k.y,
+                                  (uint32_t)p0);
+            }
+        }
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-            const uint2 k = rk[b][r];
-            const uint64_t p0 = (uint64_t)M0 * c[b].x;
-            const uint64_t p1 = (uint64_t)M1 * c[b].z;
-            c[b] = make_uint4((uint32_t)(p1 >> 32) ^ c[b].y ^ k.x, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c[b].w ^ k.y,
-                              (uint32_t)p0);
+            box_muller(c[b].x, c[b].y, n[b][4 * j], n[b][4 * j + 1]);
+            box_muller(c[b].z, c[b].w, n[b][4 * j + 2], n[b][4 * j + 3]);
         }
-    }
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        box_muller(c[b].x, c[b].y, n[b][0], n[b][1]);
-        box_muller(c[b].z, c[b].w, n[b][2], n[b][3]);
     }
 }
 
-template <class Real>
-__device__ __forceinline__ void unit_normals_rk(const uint2* rk, uint32_t call, uint32_t ring, Real (&n)[4])
+template <class Real, int NC = 1>
+__device__ __forceinline__ void unit_normals_rk(const uint2* rk, uint32_t u, uint32_t ring, Real (&n)[4 * NC])
 {
-    const uint4 w = philox_rk(make_uint4(call, ring, 0u, 0u), rk);
-    box_muller(w.x, w.y, n[0], n[1]);
-    box_muller(w.z, w.w, n[2], n[3]);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        const uint4 w = philox_rk(make_uint4(u * NC + j, ring, 0u, 0u), rk);
+        box_muller(w.x, w.y, n[4 * j], n[4 * j + 1]);
+        box_muller(w.z, w.w, n[4 * j + 2], n[4 * j + 3]);
+    }
 }
 
 // In-place segment kernel, for rings too long for the warp-specialised kernel's three
@@ -715,7 +762,7 @@ __global__ void __launch_bounds__(1024, 1) segment_kernel(SampleParams P)
     constexpr int ROW = step_row(M);
     constexpr int EPT = UPT * G;          // complex FFT points per thread
     constexpr int UP = UPT - PARK;        // units whose state stays in registers during the FFT
-    static_assert(2 * M * G == 4, "a unit holds four state values");
+    constexpr int NU = unit_vals(M), NC = unit_calls(M);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint2 rk[10];              // Philox round keys of the CTA's realisation
 
@@ -729,7 +776,7 @@ __global__ void __launch_bounds__(1024, 1) segment_kernel(SampleParams P)
     const Real* anc = (const Real*)P.anc;
     const bool has_right = sg.right >= 0;
 
-    // shared memory: the ring buffer, then the parked states [PARK][nt][4]
+    // shared memory: the ring buffer, then the parked states [PARK][nt][NU]
     C* buf0 = reinterpret_cast<C*>(smem_raw);
     Real* park = reinterpret_cast<Real*>(buf0 + Nc);
     const C* twp = (const C*)P.tw;
@@ -741,19 +788,21 @@ __global__ void __launch_bounds__(1024, 1) segment_kernel(SampleParams P)
     // right-anchor states are read from the scratch ([slot][2M])
     const Real* xrg = anc + aoff<M>(P, c, r0, has_right ? sg.right : 0, 0, 0);
 
-    // states: units i < UP in registers, the others in the park area ([PARK][nt][4]) between
+    // states: units i < UP in registers, the others in the park area ([PARK][nt][NU]) between
     // their steps
-    Real xreg[UP > 0 ? UP : 1][4];
+    Real xreg[UP > 0 ? UP : 1][NU];
 #pragma unroll
     for (int i = 0; i < UPT; ++i) {
         const int u = tid + i * nt;
-        Real v[4] = {0, 0, 0, 0};
-        if (u < n_units) Vec4<Real>::ldg(anc + aoff<M>(P, c, r0, sg.left, 0, G * u), v);
+        Real v[NU];
+#pragma unroll
+        for (int k = 0; k < NU; ++k) v[k] = 0;
+        if (u < n_units) VecN<Real, NU>::ldg(anc + aoff<M>(P, c, r0, sg.left, 0, G * u), v);
         if (i < UP) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) xreg[i < UP ? i : 0][k] = v[k];
+            for (int k = 0; k < NU; ++k) xreg[i < UP ? i : 0][k] = v[k];
         } else {
-            Vec4<Real>::st(park + ((size_t)(i - UP) * nt + tid) * 4, v);
+            VecN<Real, NU>::st(park + ((size_t)(i - UP) * nt + tid) * NU, v);
         }
     }
     __syncthreads();
@@ -766,22 +815,22 @@ __global__ void __launch_bounds__(1024, 1) segment_kernel(SampleParams P)
         for (int i = 0; i < UPT; ++i) {
             const int u = tid + i * nt;
             if (u >= n_units) continue;
-            Real x[4];
-            Real* pk = park + ((size_t)(i - UP) * nt + tid) * 4;
+            Real x[NU];
+            Real* pk = park + ((size_t)(i - UP) * nt + tid) * NU;
             if (i < UP) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) x[k] = xreg[i < UP ? i : 0][k];
+                for (int k = 0; k < NU; ++k) x[k] = xreg[i < UP ? i : 0][k];
             } else {
-                Vec4<Real>::ld(pk, x);
+                VecN<Real, NU>::ld(pk, x);
             }
             if (pos > sg.p0) {
                 Real ta[G][ROW];
 #pragma unroll
                 for (int g = 0; g < G; ++g) load_row<Real, TabT, ROW>(tb + (size_t)(G * u + g) * ROW, ta[g]);
-                Real nr[4];
-                unit_normals_rk<Real>(rk, (uint32_t)u, (uint32_t)ring, nr);
-                Real xr[4];
-                if (has_right) Vec4<Real>::ldg(xrg + (size_t)G * u * 2 * M, xr);
+                Real nr[NU];
+                unit_normals_rk<Real, NC>(rk, (uint32_t)u, (uint32_t)ring, nr);
+                Real xr[NU];
+                if (has_right) VecN<Real, NU>::ldg(xrg + (size_t)G * u * 2 * M, xr);
 #pragma unroll
                 for (int g = 0; g < G; ++g)
 #pragma unroll
@@ -802,14 +851,13 @@ __global__ void __launch_bounds__(1024, 1) segment_kernel(SampleParams P)
                     }
                 if (i < UP) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) xreg[i < UP ? i : 0][k] = x[k];
+                    for (int k = 0; k < NU; ++k) xreg[i < UP ? i : 0][k] = x[k];
                 } else {
-                    Vec4<Real>::st(pk, x);
+                    VecN<Real, NU>::st(pk, x);
                 }
             }
             // the unit's coefficients of this ring (slot 0's imaginary part = Nyquist)
-            if constexpr (G == 2) Vec4<Real>::st(reinterpret_cast<Real*>(buf0 + 2 * u), x);
-            else buf0[u] = cmk<C>(x[0], x[M]);
+            put_unit<C, Real, M>(buf0, u, x);
         }
         __syncthreads();
         if (!(c == 1 && pos == 0)) {  // the start ring is written by the northern chain
@@ -1000,10 +1048,15 @@ __device__ __forceinline__ void hr_c2r(int lgNc, C* b0, C* b1, int R, const C* t
 
 // log2 Nc range the warp-specialised kernel with UPT units per producer thread meets: the
 // launch configurations use UPT only while 16 UPT < units <= 512 UPT (units = Nc / unit_slots)
-__host__ __device__ constexpr int ws_lg_lo(int UPT, int M) { return UPT == 1 ? 2 : (UPT == 2 ? 6 : UPT == 4 ? 7 : 8) + (M == 1); }
+__host__ __device__ constexpr int ws_lg_lo(int UPT, int M)
+{
+    return UPT == 1 ? 2 : (UPT == 2 ? 6 : UPT == 4 ? 7 : 8) + (unit_slots(M) == 2);
+}
 __host__ __device__ constexpr int ws_lg_hi(int UPT, int M)
 {
-    return ((UPT == 1 ? 9 : UPT == 2 ? 10 : UPT == 4 ? 11 : 12) + (M == 1)) < 12 ? ((UPT == 1 ? 9 : UPT == 2 ? 10 : UPT == 4 ? 11 : 12) + (M == 1)) : 12;
+    return ((UPT == 1 ? 9 : UPT == 2 ? 10 : UPT == 4 ? 11 : 12) + (unit_slots(M) == 2)) < 12
+               ? ((UPT == 1 ? 9 : UPT == 2 ? 10 : UPT == 4 ? 11 : 12) + (unit_slots(M) == 2))
+               : 12;
 }
 
 // ---- iso-latitude grids with ring-dependent longitudes (the paper's Sec. 1 remark)
@@ -1136,7 +1189,7 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
     constexpr int G = kG<M>;
     constexpr int ROW = step_row(M);
     constexpr int RB = RMAX < SMERF_RB ? RMAX : SMERF_RB;  // realisations whose noise is drawn together
-    static_assert(2 * M * G == 4, "a unit holds four state values");
+    constexpr int NU = unit_vals(M), NC = unit_calls(M);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint2 rk[RMAX][10];
 
@@ -1176,17 +1229,17 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
 
     if (tid < NP) {
         // ------------------------------------------------ producer group
-        Real x[UPT][RMAX][4];
+        Real x[UPT][RMAX][NU];
 #pragma unroll
         for (int i = 0; i < UPT; ++i) {
             const int u = tid + i * NP;
 #pragma unroll
             for (int r = 0; r < RMAX; ++r) {
                 if (u < n_units && r < R) {
-                    Vec4<Real>::ldg(anc + aoff<M>(P, c, r0 + r, sg.left, 0, G * u), x[i][r]);
+                    VecN<Real, NU>::ldg(anc + aoff<M>(P, c, r0 + r, sg.left, 0, G * u), x[i][r]);
                 } else {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) x[i][r][k] = 0;
+                    for (int k = 0; k < NU; ++k) x[i][r][k] = 0;
                 }
             }
         }
@@ -1210,14 +1263,14 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
                     for (int rb = 0; rb < RMAX; rb += RB) {
                         if (rb >= R) continue;
                         // normals of realisations rb .. rb + RB - 1 (those past R are not used)
-                        Real nrb[RB][4];
-                        unit_normals_multi<Real, RB>(rk + rb, (uint32_t)u, (uint32_t)ring, nrb);
+                        Real nrb[RB][NU];
+                        unit_normals_multi<Real, RB, NC>(rk + rb, (uint32_t)u, (uint32_t)ring, nrb);
 #pragma unroll
                     for (int r = rb; r < rb + RB; ++r) {
                         if (r >= R) continue;
                         const Real* nr = nrb[r - rb];
-                        Real xr[4];
-                        if (has_right) Vec4<Real>::ld(xRs + ((size_t)r * Nc + G * u) * 2 * M, xr);
+                        Real xr[NU];
+                        if (has_right) VecN<Real, NU>::ld(xRs + ((size_t)r * Nc + G * u) * 2 * M, xr);
 #pragma unroll
                         for (int g = 0; g < G; ++g)
 #pragma unroll
@@ -1247,12 +1300,7 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
 #pragma unroll
                 for (int r = 0; r < RMAX; ++r) {
                     if (r >= R) continue;
-                    if constexpr (G == 2) {
-                        // p = 1: the unit's two slots (Re, Im, Re, Im) in one vector store
-                        Vec4<Real>::st(reinterpret_cast<Real*>(B + (size_t)r * Nc + 2 * u), x[i][r]);
-                    } else {
-                        B[(size_t)r * Nc + u] = cmk<C>(x[i][r][0], x[i][r][M]);
-                    }
+                    put_unit<C, Real, M>(B + (size_t)r * Nc, u, x[i][r]);
                 }
             }
             __threadfence_block();
@@ -1460,9 +1508,9 @@ inline bool ring_config(const smerf_plan* pl, SegConfig& cfg)
     return true;
 }
 
-template <class Real> constexpr int ws_rmax_cap(int upt)
+template <class Real> constexpr int ws_rmax_cap(int upt, int M)
 {
-    return sizeof(Real) == 8 ? 1 : (upt <= 2 ? 4 : (upt == 4 ? 2 : 1));
+    return sizeof(Real) == 8 || M == 3 ? 1 : (upt <= 2 ? 4 : (upt == 4 ? 2 : 1));
 }
 
 template <class Real>
@@ -1473,8 +1521,11 @@ inline size_t ws_smem(const smerf_plan* pl, int rmax)
 }
 
 // (units per thread, realisations per CTA, CTAs per SM) with a built warp-specialised kernel
-template <class Real> inline bool ws_built(int upt, int rmax, int minb = 1)
+// for state size M (p = 3, whose units hold 12 state values: one realisation per CTA, one
+// CTA per SM)
+template <class Real> inline bool ws_built(int upt, int rmax, int minb, int M)
 {
+    if (M == 3) return minb == 1 && rmax == 1 && (upt == 1 || upt == 2 || upt == 4 || upt == 8);
     if (minb == 2) return sizeof(Real) == 4 && ((upt == 4 && (rmax == 1 || rmax == 2)) || (upt == 8 && rmax == 1));
     if (minb != 1) return false;
     if (sizeof(Real) == 8) return rmax == 1 && (upt == 1 || upt == 2 || upt == 4 || upt == 8);
@@ -1499,7 +1550,7 @@ inline int tune_candidates(const smerf_plan* pl, int* cand, int max_n)
             if (np > 512 || (upt > 1 && (n_units + upt / 2 - 1) / (upt / 2) <= 32)) continue;
             for (int k = 0; k < 3; ++k) {
                 const int rmax = rm[k];
-                if (!ws_built<Real>(upt, rmax, minb) || ws_smem<Real>(pl, rmax) > 226 * 1024) continue;
+                if (!ws_built<Real>(upt, rmax, minb, pl->p) || ws_smem<Real>(pl, rmax) > 226 * 1024) continue;
                 const int div[3] = {2, 1, 4};
                 for (int d = 0; d < 3; ++d) {
                     int nf = ((np / div[d] + 31) / 32) * 32;
@@ -1527,7 +1578,7 @@ inline SegConfig seg_config(const smerf_plan* pl)
     const int M = pl->p;
     const int n_units = pl->n_slots / unit_slots(M);
     const int Nc = pl->n_phi / 2;
-    if (pl->tune.valid && ws_built<Real>(pl->tune.upt, pl->tune.rmax, pl->tune.minb) &&
+    if (pl->tune.valid && ws_built<Real>(pl->tune.upt, pl->tune.rmax, pl->tune.minb, M) &&
         ws_smem<Real>(pl, pl->tune.rmax) <= 226 * 1024 &&
         (n_units + pl->tune.upt - 1) / pl->tune.upt <= pl->tune.np &&
         pl->tune.np + pl->tune.nf <= ws_max_threads(pl->tune.minb)) {
@@ -1547,7 +1598,7 @@ inline SegConfig seg_config(const smerf_plan* pl)
     while (upt < 8 && !fits(upt)) upt *= 2;
     if (fits(upt)) {
         const int np = np_of(upt), nf = nf_of(np);
-        for (int rmax = ws_rmax_cap<Real>(upt); rmax >= 1; rmax /= 2) {
+        for (int rmax = ws_rmax_cap<Real>(upt, M); rmax >= 1; rmax /= 2) {
             const size_t smem = (size_t)3 * rmax * Nc * 2 * sizeof(Real) +
                                 (pl->H > 0 ? (size_t)rmax * Nc * 2 * M * sizeof(Real) : 0);
             if (smem <= kMaxSmem) {
@@ -1575,7 +1626,7 @@ inline SegConfig seg_config(const smerf_plan* pl)
     cfg.nt = nt;
     cfg.rmax = 1;
     // park all but two units' states during the FFT if shared memory allows, else half, else none
-    const size_t ring = (size_t)Nc * 2 * sizeof(Real), per_unit = (size_t)nt * 4 * sizeof(Real);
+    const size_t ring = (size_t)Nc * 2 * sizeof(Real), per_unit = (size_t)nt * unit_vals(M) * sizeof(Real);
     cfg.park = ring + (upt - 2) * per_unit <= kMaxSmem ? upt - 2 : ring + (upt / 2) * per_unit <= kMaxSmem ? upt / 2 : 0;
     cfg.smem = ring + cfg.park * per_unit;
     return cfg;
@@ -1585,7 +1636,8 @@ template <class Real, class TabT, int M>
 int dispatch_segments(const SampleParams& P, int n_segments, const SegConfig& cfg, cudaStream_t st)
 {
     if (cfg.ws) {
-        if constexpr (sizeof(Real) == 8) {
+        if constexpr (sizeof(Real) == 8 || M == 3) {
+            if (cfg.rmax != 1 || cfg.minb != 1) return SMERF_EUNSUPPORTED;
             switch (cfg.upt) {
                 case 1: return launch_ws<Real, TabT, M, 1, 1>(P, n_segments, cfg.nt, cfg.smem, st);
                 case 2: return launch_ws<Real, TabT, M, 2, 1>(P, n_segments, cfg.nt, cfg.smem, st);
@@ -1628,13 +1680,17 @@ int dispatch_segments(const SampleParams& P, int n_segments, const SegConfig& cf
         }
         return SMERF_EUNSUPPORTED;
     }
-    switch (cfg.upt * 16 + cfg.park) {
-        case 4 * 16 + 2: return launch_inplace<Real, TabT, M, 4, 2>(P, n_segments, cfg.nt, cfg.smem, st);
-        case 4 * 16 + 0: return launch_inplace<Real, TabT, M, 4, 0>(P, n_segments, cfg.nt, cfg.smem, st);
-        case 8 * 16 + 6: return launch_inplace<Real, TabT, M, 8, 6>(P, n_segments, cfg.nt, cfg.smem, st);
-        case 8 * 16 + 4: return launch_inplace<Real, TabT, M, 8, 4>(P, n_segments, cfg.nt, cfg.smem, st);
-        case 8 * 16 + 0: return launch_inplace<Real, TabT, M, 8, 0>(P, n_segments, cfg.nt, cfg.smem, st);
-        default: return SMERF_EUNSUPPORTED;
+    if constexpr (M == 3) {
+        return SMERF_EUNSUPPORTED;  // p = 3 runs on the warp-specialised kernels only
+    } else {
+        switch (cfg.upt * 16 + cfg.park) {
+            case 4 * 16 + 2: return launch_inplace<Real, TabT, M, 4, 2>(P, n_segments, cfg.nt, cfg.smem, st);
+            case 4 * 16 + 0: return launch_inplace<Real, TabT, M, 4, 0>(P, n_segments, cfg.nt, cfg.smem, st);
+            case 8 * 16 + 6: return launch_inplace<Real, TabT, M, 8, 6>(P, n_segments, cfg.nt, cfg.smem, st);
+            case 8 * 16 + 4: return launch_inplace<Real, TabT, M, 8, 4>(P, n_segments, cfg.nt, cfg.smem, st);
+            case 8 * 16 + 0: return launch_inplace<Real, TabT, M, 8, 0>(P, n_segments, cfg.nt, cfg.smem, st);
+            default: return SMERF_EUNSUPPORTED;
+        }
     }
 }
 
@@ -1679,8 +1735,10 @@ int fill_params(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scr
     P.ring_h = pl->rings_total ? pl->rings_h_dev : nullptr;
     P.ring_off = pl->rings_total ? pl->rings_off_dev : nullptr;
     P.ring_total = pl->rings_total;
-    // ring-dependent longitudes are synthesised by the warp-specialised kernels' FFT group only
-    if (pl->rings_total && !cfg.ws) return SMERF_EUNSUPPORTED;
+    // ring-dependent longitudes are synthesised by the warp-specialised kernels' FFT group only,
+    // and p = 3 is built for those kernels only (rings up to 4096 complex points in FP32, 2048
+    // in FP64)
+    if ((pl->rings_total || pl->p == 3) && !cfg.ws) return SMERF_EUNSUPPORTED;
     return SMERF_OK;
 }
 
@@ -1769,7 +1827,8 @@ int launch_ws_batched(const SampleParams* d, const int4* items, int n_items, int
 template <class Real, class TabT, int M>
 int group_segments(const SegConfig& cfg, const SampleParams* d, const int4* items, int n_items, cudaStream_t st)
 {
-    if constexpr (sizeof(Real) == 8) {
+    if constexpr (sizeof(Real) == 8 || M == 3) {
+        if (cfg.rmax != 1 || cfg.minb != 1) return SMERF_EUNSUPPORTED;
         switch (cfg.upt) {
             case 1: return launch_ws_batched<Real, TabT, M, 1, 1>(d, items, n_items, cfg.nt, cfg.smem, st);
             case 2: return launch_ws_batched<Real, TabT, M, 2, 1>(d, items, n_items, cfg.nt, cfg.smem, st);
@@ -1878,15 +1937,20 @@ int launch_group_m(const smerf_plan* rep, const SampleParams* d, const int4* anc
                                       cudaEvent_t);                                                         \
     int smerf_launch_sample_##XX##_p2(const smerf_plan*, uint64_t, int, void*, void*, cudaStream_t, cudaEvent_t, \
                                       cudaEvent_t);                                                         \
+    int smerf_launch_sample_##XX##_p3(const smerf_plan*, uint64_t, int, void*, void*, cudaStream_t, cudaEvent_t, \
+                                      cudaEvent_t);                                                         \
     int smerf_launch_group_##XX##_p1(const smerf_plan*, const smerf::SampleParams*, const int4*, int,       \
                                      const int4*, int, cudaStream_t);                                       \
     int smerf_launch_group_##XX##_p2(const smerf_plan*, const smerf::SampleParams*, const int4*, int,       \
                                      const int4*, int, cudaStream_t);                                       \
+    int smerf_launch_group_##XX##_p3(const smerf_plan*, const smerf::SampleParams*, const int4*, int,       \
+                                     const int4*, int, cudaStream_t);                                       \
     int smerf_launch_sample_##XX(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch,      \
                                  cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1)                         \
     {                                                                                                       \
-        return pl->p == 1 ? smerf_launch_sample_##XX##_p1(pl, seed, n, out, scratch, st, ev0, ev1)          \
-                          : smerf_launch_sample_##XX##_p2(pl, seed, n, out, scratch, st, ev0, ev1);         \
+        return pl->p == 1   ? smerf_launch_sample_##XX##_p1(pl, seed, n, out, scratch, st, ev0, ev1)        \
+               : pl->p == 2 ? smerf_launch_sample_##XX##_p2(pl, seed, n, out, scratch, st, ev0, ev1)        \
+                            : smerf_launch_sample_##XX##_p3(pl, seed, n, out, scratch, st, ev0, ev1);       \
     }                                                                                                       \
     int smerf_fill_params_##XX(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scratch,        \
                                smerf::SampleParams* P, int* batchable, int* rmax)                           \
@@ -1897,8 +1961,9 @@ int launch_group_m(const smerf_plan* rep, const SampleParams* d, const int4* anc
                                 const int4* anc_items, int n_anc, const int4* seg_items, int n_seg,         \
                                 cudaStream_t st)                                                            \
     {                                                                                                       \
-        return rep->p == 1 ? smerf_launch_group_##XX##_p1(rep, d_descs, anc_items, n_anc, seg_items, n_seg, st) \
-                           : smerf_launch_group_##XX##_p2(rep, d_descs, anc_items, n_anc, seg_items, n_seg, st); \
+        return rep->p == 1   ? smerf_launch_group_##XX##_p1(rep, d_descs, anc_items, n_anc, seg_items, n_seg, st) \
+               : rep->p == 2 ? smerf_launch_group_##XX##_p2(rep, d_descs, anc_items, n_anc, seg_items, n_seg, st) \
+                             : smerf_launch_group_##XX##_p3(rep, d_descs, anc_items, n_anc, seg_items, n_seg, st); \
     }                                                                                                       \
     int smerf_tune_candidates_##XX(const smerf_plan* pl, int* cand, int max_n)                              \
     {                                                                                                       \

@@ -127,7 +127,28 @@ template <int M> __device__ inline Mat<M> mT(const Mat<M>& x) { Mat<M> r; for (i
 template <int M> __device__ inline Mat<M> madd(const Mat<M>& x, const Mat<M>& y) { Mat<M> r; for (int i = 0; i < M; ++i) for (int j = 0; j < M; ++j) r.a[i][j] = x.a[i][j] + y.a[i][j]; return r; }
 template <int M> __device__ inline Mat<M> msym(const Mat<M>& x) { Mat<M> r; for (int i = 0; i < M; ++i) for (int j = 0; j < M; ++j) r.a[i][j] = 0.5 * (x.a[i][j] + x.a[j][i]); return r; }
 
-// inverse of a general M x M matrix (M <= 2)
+// inverse of a 3 x 3 matrix by its adjugate (cofactors, the transposed minors) over the
+// determinant; T is a real or complex matrix type, S its scalar
+template <class T, class S> __device__ inline T inv3(const T& x)
+{
+    const auto& a = x.a;
+    T r;
+    r.a[0][0] = a[1][1] * a[2][2] - a[1][2] * a[2][1];
+    r.a[0][1] = a[0][2] * a[2][1] - a[0][1] * a[2][2];
+    r.a[0][2] = a[0][1] * a[1][2] - a[0][2] * a[1][1];
+    r.a[1][0] = a[1][2] * a[2][0] - a[1][0] * a[2][2];
+    r.a[1][1] = a[0][0] * a[2][2] - a[0][2] * a[2][0];
+    r.a[1][2] = a[0][2] * a[1][0] - a[0][0] * a[1][2];
+    r.a[2][0] = a[1][0] * a[2][1] - a[1][1] * a[2][0];
+    r.a[2][1] = a[0][1] * a[2][0] - a[0][0] * a[2][1];
+    r.a[2][2] = a[0][0] * a[1][1] - a[0][1] * a[1][0];
+    const S d = a[0][0] * r.a[0][0] + a[0][1] * r.a[1][0] + a[0][2] * r.a[2][0];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) r.a[i][j] = r.a[i][j] / d;
+    return r;
+}
+
+// inverse of a general M x M matrix (M <= 3)
 template <int M> __device__ inline Mat<M> minv(const Mat<M>& x);
 template <> __device__ inline Mat<1> minv<1>(const Mat<1>& x) { Mat<1> r; r.a[0][0] = 1.0 / x.a[0][0]; return r; }
 template <> __device__ inline Mat<2> minv<2>(const Mat<2>& x)
@@ -138,6 +159,7 @@ template <> __device__ inline Mat<2> minv<2>(const Mat<2>& x)
     r.a[1][0] = -x.a[1][0] / d; r.a[1][1] = x.a[0][0] / d;
     return r;
 }
+template <> __device__ inline Mat<3> minv<3>(const Mat<3>& x) { return inv3<Mat<3>, double>(x); }
 
 // lower Cholesky factor of a symmetric positive semi-definite matrix (0 where it degenerates)
 template <int M> __device__ inline Mat<M> mchol(const Mat<M>& x)
@@ -816,6 +838,7 @@ template <> __device__ inline MatC<2> cminv<2>(const MatC<2>& x)
     r.a[1][0] = -x.a[1][0] / d; r.a[1][1] = x.a[0][0] / d;
     return r;
 }
+template <> __device__ inline MatC<3> cminv<3>(const MatC<3>& x) { return inv3<MatC<3>, cdbl>(x); }
 
 // 2F1(-l, l+1; 1+mu; x) with kappa-hat = k2 complex, as S * 1e250^E (terms two per division)
 __device__ void hyp_scaled_c(cdbl k2, int mu, double x, cdbl& S, int& E)
@@ -1118,6 +1141,7 @@ int setup_impl(smerf_plan* pl, cudaStream_t st, bool sync)
             if (len0 > 65535) { rc = SMERF_EUNSUPPORTED; goto done; }
             dim3 grid(gm, len0);
             if (pl->complex_spec) step_kernel_c<M><<<grid, threads, 0, st>>>(make_spec_c(pl), len0, phi, qv);
+            else if (M == 3) step_kernel<M><<<grid, threads, 0, st>>>(sp, 0, len0, phi, qv);  // per-mode series
             else {
                 // the recurrence in m, but for a first step whose equatorward ring (x > 1/2) would
                 // amplify rounding errors by more than 1e3 over the orders: that one by the
@@ -1188,6 +1212,7 @@ int smerf_setup_tables(smerf_plan* pl, cudaStream_t st, bool sync)
     switch (pl->p) {
         case 1: return setup_impl<1>(pl, st, sync);
         case 2: return setup_impl<2>(pl, st, sync);
+        case 3: return setup_impl<3>(pl, st, sync);
         default: return SMERF_EUNSUPPORTED;
     }
 }

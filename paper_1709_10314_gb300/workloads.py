@@ -4,6 +4,8 @@ of the method's arithmetic).  Each is named by what it is.
   plain-64x128-p1-fp64      64 x 128, C_l = 1/(l(l+1)+10^2), 1 realisation, FP64 recursion
   1024x2048-p2              1024 x 2048, C_l = 1/((l(l+1)+20^2)(l(l+1)+50^2)), 64 realisations,
                             FP64 tables, FP32 recursion + FFT (the throughput workload)
+  1024x2048-p3              1024 x 2048, C_l = 1/((l(l+1)+20^2)(l(l+1)+50^2)(l(l+1)+120^2)),
+                            64 realisations, FP64 tables, FP32 recursion + FFT (three factors)
   4096x8192-p1              4096 x 8192, C_l = 1/(l(l+1)+100^2), 16 realisations (precision sweep:
                             recursion FP64/FP32 x tables FP64/FP32)
   uneven-256                256 requests: n_theta uniform in {128,256,512,1024}, n_phi = 2 n_theta,
@@ -20,6 +22,8 @@ FIXED = {
     "plain-64x128-p1-fp64": dict(kappa=[10.0], A=1.0, n_theta=64, n_phi=128, n=1, seed=1,
                                  recur="fp64", tables="fp64", order="paper"),
     "1024x2048-p2": dict(kappa=[20.0, 50.0], A=1.0, n_theta=1024, n_phi=2048, n=64, seed=1,
+                         recur="fp32", tables="fp64"),
+    "1024x2048-p3": dict(kappa=[20.0, 50.0, 120.0], A=1.0, n_theta=1024, n_phi=2048, n=64, seed=1,
                          recur="fp32", tables="fp64"),
     "4096x8192-p1": dict(kappa=[100.0], A=1.0, n_theta=4096, n_phi=8192, n=16, seed=1,
                          recur="fp32", tables="fp64"),

@@ -54,7 +54,9 @@ def _create(lib, kappa, p, A, nt, nphi, flags=0, H=0):
     (([1.0], 1, 1.0, 16, 31), -1),              # odd n_phi
     (([3.0, 3.0000000001], 2, 1.0, 16, 32), -2),  # near-equal kappa: partial fractions cancel
     (([1.0], 1, 1.0, 16, 48), -5),              # n_phi not a power of two
-    (([1.0, 2.0, 3.0], 3, 1.0, 16, 32), -5),    # p = 3 not built
+    (([1.0, 2.0, 3.0, 4.0], 4, 1.0, 16, 32), -1),  # p > 3
+    (([2.0, 5.0, 5.0000000001], 3, 1.0, 16, 32), -2),  # p = 3 with near-equal kappa
+    (([2.0, 5.0, 9.0], 3, 1.0, 16, 16384), -5),  # p = 3 rings longer than 4096 complex points
 ])
 def test_validation_without_gpu(lib, args, code):
     rc, h = _create(lib, *args)

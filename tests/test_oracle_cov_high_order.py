@@ -44,6 +44,12 @@ PINS = [
     # 24 x 16384, p = 1, anchors every 8 rings: start ring, anchors, first bridge rings
     ([300.0], 24, 3000, [12, 4, 20, 11, 10], 4, dict(c_turn_diag=4.0), 2e-5),
     ([300.0], 24, 8192, [12, 4, 20, 11, 10], 4, dict(c_turn_diag=4.0), 2e-5),
+    # p = 3 parity grids (tests/test_gpu_p3.py): 6 x 4096 with anchors every 2 rings (start
+    # ring, an anchor, a bridge ring) and 4 x 8192 in Alg. 2's order (K = 4, c_turn_diag = 8)
+    ([4.0, 9.0, 20.0], 6, 700, [3, 1, 2], 4, dict(c_turn_diag=8.0), 3e-6),
+    ([4.0, 9.0, 20.0], 6, 2048, [3, 1, 2], 4, dict(c_turn_diag=8.0), 3e-6),
+    ([4.0, 9.0, 20.0], 4, 1500, [2, 1], 4, dict(c_turn_diag=8.0), 3e-6),
+    ([4.0, 9.0, 20.0], 4, 4096, [2, 1], 4, dict(c_turn_diag=8.0), 3e-6),
 ]
 
 
