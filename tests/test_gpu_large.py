@@ -46,7 +46,11 @@ def test_precision_sweep_4096x8192(recur, tables):
     err = float(np.max(np.abs(got - ref))) / std
     SWEEP[(recur, tables)] = out[0].double().cpu().numpy() if recur == "fp64" and tables == "fp64" else out[0].cpu()
     print("precision sweep 4096x8192 recur=%s tables=%s: start ring max|gpu-oracle|/std = %.3e" % (recur, tables, err))
-    assert err < (1e-6 if recur == "fp64" and tables == "fp64" else 1e-4)
+    # FP64 throughout: the oracle's own accuracy at K = 4, c_turn_diag = 16 (pinned to 2e-8 of
+    # the diagonal scale; measured 1.2e-8); FP64 recursion on FP32 tables: the tables' rounding
+    # (measured 1.1e-7); FP32 recursion: 1e-4 of the field std
+    bound = {("fp64", "fp64"): 5e-8, ("fp64", "fp32"): 1e-6}.get((recur, tables), 1e-4)
+    assert err < bound
     if ("fp64", "fp64") in SWEEP and recur != "fp64":
         ref64 = SWEEP[("fp64", "fp64")]
         e = float(np.max(np.abs(out[0].double().cpu().numpy() - ref64))) / float(np.std(ref64))
