@@ -295,8 +295,10 @@ def run_gb300(args, rank, world, local_rank):
         sfu_ops = sum(n * p.n_theta * (p.n_phi // 2) * sfu_ops_per_item(p.info()["p"]) for p, n in zip(plans, counts))
         out_bytes = points * 4
         workload = ("uneven batch: 256 requests, n_theta in {128,256,512,1024}, n_phi=2 n_theta, kappa in [5,200], "
-                    "p in {1,2}, 1-8 realisations, FP32 recursion, FP%s tables, one CUDA-graph replay per step"
-                    % ("64" if args.tables == "fp64" else "32"))
+                    "p in {1,2}, 1-8 realisations, FP32 recursion, FP%s tables, one CUDA-graph replay per step%s"
+                    % ("64" if args.tables == "fp64" else "32",
+                       ", one persistent launch" if args.single_launch else ", anchor launch + persistent launch"))
+        batch.set_single_launch(args.single_launch)
         dtype = "f32"
         anchor = 16  # the plans' default anchor spacing
         setup_ms = plans[0].info()["setup_ms"]  # the wall time of the one call that made them all
@@ -313,7 +315,7 @@ def run_gb300(args, rank, world, local_rank):
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=s_cap, capture_error_mode="relaxed"):
             batch.launch(stream=s_cap)
-        launches = batch.info()["launches"]  # one anchor launch + one persistent segment launch
+        launches = batch.info()["launches"]  # anchor launch + persistent launch, or one persistent launch
 
         def step(i, ev0=None, ev1=None):
             torch.cuda.synchronize()
@@ -548,6 +550,8 @@ def main():
     ap.add_argument("--launch", default=None,
                     help="fix the segment-kernel launch configuration: units/thread,realisations/CTA,"
                          "producer threads,FFT threads (one of the plan's candidates)")
+    ap.add_argument("--single-launch", action="store_true",
+                    help="uneven batch: anchors and segments in one persistent launch")
     ap.add_argument("--anchor", type=int, default=0,
                     help="anchor spacing H of the plan (0: the workload's default)")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,

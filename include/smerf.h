@@ -44,8 +44,8 @@ typedef struct smerf_plan smerf_plan;
 #define SMERF_ECUDA (-4)       /* a CUDA runtime call or kernel launch failed                    */
 #define SMERF_EUNSUPPORTED (-5) /* valid but not built (e.g. n_phi not a power of two)          */
 #define SMERF_ESCRATCH (-6)    /* smerf_sample_noalloc: request exceeds its fixed 16 MiB scratch */
-#define SMERF_ETIMEOUT (-7)    /* reserved for a device wait that runs out (none can: see
-                                  smerf_last_device_status)                                     */
+#define SMERF_ETIMEOUT (-7)    /* a device wait ran out (the persistent batch launch's wait for
+                                  a request's anchors: smerf_batch_status)                      */
 
 /* plan flags */
 #define SMERF_RECUR_FP64 0x1u    /* recursion, FFT and output in FP64 (default FP32, float out)   */
@@ -134,10 +134,11 @@ int smerf_sample_timed(const smerf_plan* plan, uint64_t seed, int n_samples, voi
 /*
  * smerf_last_device_status -- synchronises `stream` (cudaStream_t as void*, NULL = legacy
  * default stream) and reports how the work queued on it ended: SMERF_OK, or SMERF_ECUDA if a
- * kernel or copy on it failed (a non-sticky CUDA error is cleared).  The sampling kernels keep
- * no device error word: none waits on a flag or on another CTA (the producer/FFT hand-off
- * uses the CTA's own named barriers, the table staging cp.async groups, both complete by
- * construction), so no wait can run out and SMERF_ETIMEOUT is never returned.
+ * kernel or copy on it failed (a non-sticky CUDA error is cleared).  The single-request
+ * kernels keep no device error word: none waits on a flag or on another CTA (the
+ * producer/FFT hand-off uses the CTA's own named barriers, the table staging cp.async
+ * groups, both complete by construction).  The one device wait of the library, in the
+ * persistent batch launch, reports through smerf_batch_status.
  */
 int smerf_last_device_status(void* stream);
 
@@ -191,13 +192,19 @@ int smerf_sample_batched(const smerf_plan* const* plans, const uint64_t* seeds,
  * smerf_batch_set: stores seeds[i] and outputs outs[i] (16-byte aligned; device memory, or
  *   page-locked host memory that the GPU addresses with the same pointer, such as
  *   cudaHostAlloc memory or pinned torch tensors, which the kernels then write over the
- *   CPU-GPU link) in the batch's pinned staging memory.  Host-only; the previous launch's copy of the staging
- *   memory must have completed (synchronise its stream first).
+ *   CPU-GPU link) in the batch's pinned staging memory.  Host-only; the previous launch's
+ *   copy of the staging memory must have completed (synchronise its stream first).
  * smerf_batch_launch: copies the staging memory to the device and launches the batch on
- *   `stream` (asynchronous): for FP32 recursion, one anchor launch over all requests' anchor
- *   items, a reset of the work queue, and one launch of persistent CTAs that take the segment
- *   items of every shape from that queue (Alg. 2's two steps, the anchors before the segments
- *   by stream order); for FP64 recursion, an anchor and a segment launch per kernel shape.  Capturable into a CUDA graph: a replay re-reads the staging
+ *   `stream` (asynchronous).  FP32 recursion with p <= 2, by default: one launch over every
+ *   request's anchor items (Alg. 2's first step: start ring and anchors), a reset of the work
+ *   queue, and one launch of persistent CTAs that take the segment items of every shape (the
+ *   rings between anchors) from that queue; stream order puts the anchors first.  With
+ *   smerf_batch_set_single_launch(batch, 1): a reset of the queue and one launch of persistent
+ *   CTAs that take every anchor item and then every segment item from it; a segment item
+ *   first waits, on the device, until every anchor item of its request has finished.  That
+ *   wait is bounded (about one second): when it runs out the item is skipped and the launch
+ *   records it, which smerf_batch_status reports.  FP64 recursion or p = 3: an anchor and a
+ *   segment launch per kernel shape.  Capturable into a CUDA graph: a replay re-reads the staging
  *   memory, so smerf_batch_set between replays changes seeds and outputs.  Requests whose
  *   shape has no batched kernel (n_phi = 32768 in FP32) are launched individually, with their
  *   seed and output passed by value; a batch that holds such requests returns
@@ -206,9 +213,20 @@ int smerf_sample_batched(const smerf_plan* const* plans, const uint64_t* seeds,
  * smerf_batch_sample: smerf_batch_set + smerf_batch_launch.
  * smerf_batch_info: number of kernel shapes among the batched requests (groups) and of
  *   individually launched requests.
+ * smerf_batch_set_single_launch: 1 selects the one-launch form of the FP32-recursion work
+ *   above, 0 (the default) the two-launch form, for the following launches.  Both give the
+ *   same fields; the two-launch form is the faster of the two on GB300 (its persistent kernel
+ *   carries no anchor code).  SMERF_EINVAL for other values.
  * smerf_batch_launch_count: kernels one smerf_batch_launch starts (requests with FP32
- *   recursion: one anchor launch and one persistent segment launch per table precision, every
- *   shape together; FP64 recursion: two per shape; plus the individually launched requests').
+ *   recursion and p <= 2: two per table precision, or one with the single-launch form, every
+ *   shape together; FP64 recursion or p = 3: two per shape; plus the individually launched
+ *   requests').
+ * smerf_batch_status: synchronises `stream` and reports how the batch's last persistent
+ *   launches ended: SMERF_OK, SMERF_ETIMEOUT if a segment item's wait for its anchors ran out
+ *   (its rings were not written), or SMERF_ECUDA.
+ * smerf_debug_batch_fail_waits: test hook; the batch's next single launch starts its anchor
+ *   counters one below zero, so that no segment item's wait can be met and smerf_batch_status
+ *   then returns SMERF_ETIMEOUT.  The launch after that is normal again.
  * smerf_batch_destroy: frees the batch; synchronise its streams first.  NULL is accepted.
  */
 typedef struct smerf_batch smerf_batch;
@@ -218,6 +236,9 @@ int smerf_batch_launch(smerf_batch* batch, void* stream);
 int smerf_batch_sample(smerf_batch* batch, const uint64_t* seeds, void* const* outs, void* stream);
 int smerf_batch_info(const smerf_batch* batch, int* n_groups, int* n_singles);
 int smerf_batch_launch_count(const smerf_batch* batch);
+int smerf_batch_status(const smerf_batch* batch, void* stream);
+int smerf_batch_set_single_launch(smerf_batch* batch, int single);
+int smerf_debug_batch_fail_waits(smerf_batch* batch);
 int smerf_batch_destroy(smerf_batch* batch);
 
 /*

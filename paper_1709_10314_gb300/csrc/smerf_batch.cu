@@ -38,34 +38,37 @@ int fill_params(int kind, const smerf_plan* pl, uint64_t seed, int n, void* out,
     }
 }
 
-// FP32-recursion groups with p <= 2 run as two persistent phases (p = 3, whose units hold 12
+// FP32-recursion groups with p <= 2 run in the persistent launch (p = 3, whose units hold 12
 // state values, keeps a launch pair per group so that the persistent kernel's registers stay
 // sized for p <= 2)
 bool queued(int kind, int p) { return (kind == kFF || kind == kFD) && p <= 2; }
 
-// A queued kind's work: anchor items, segment items (largest first), the persistent launch's
-// threads, shared memory and CTAs, and the device counter of its queue.
+// A queued kind's work: its items (every anchor item, then every segment item, each list
+// largest request first), the persistent launch's shared memory and CTAs, and its control
+// words (queue head, status, one anchor counter per request of the batch).
 struct Queue {
     int kind;
-    int4* d_anc = nullptr;
+    int4* d_items = nullptr;   // anchor items (blocks of kQueueThreads units), then segment items
+    int n_items = 0;
     int n_anc = 0;
-    int4* d_seg = nullptr;
-    int n_seg = 0;
-    int nt = 0;
+    int4* d_anc128 = nullptr;  // the anchor items in blocks of 128 units (the anchor launch)
+    int n_anc128 = 0;
     size_t smem = 0;
     int ctas = 0;
-    int* d_head = nullptr;
+    int* d_ctl = nullptr;
 };
 
-int launch_queue(const Queue& q, const SampleParams* d, cudaStream_t st)
+int launch_queue(const Queue& q, const SampleParams* d, int n_req, int single, int fail_waits, cudaStream_t st)
 {
-    return q.kind == kFF ? smerf_launch_queue_ff(d, q.d_anc, q.n_anc, q.d_seg, q.n_seg, q.d_head, q.nt, q.smem, q.ctas, st)
-                         : smerf_launch_queue_fd(d, q.d_anc, q.n_anc, q.d_seg, q.n_seg, q.d_head, q.nt, q.smem, q.ctas, st);
+    return q.kind == kFF ? smerf_launch_queue_ff(d, q.d_items, q.n_items, q.n_anc, q.d_anc128, q.n_anc128, q.d_ctl,
+                                                 n_req, single, fail_waits, q.smem, q.ctas, st)
+                         : smerf_launch_queue_fd(d, q.d_items, q.n_items, q.n_anc, q.d_anc128, q.n_anc128, q.d_ctl,
+                                                 n_req, single, fail_waits, q.smem, q.ctas, st);
 }
 
-int queue_ctas(int kind, int nt, size_t smem)
+int queue_ctas(int kind, size_t smem)
 {
-    return kind == kFF ? smerf_queue_ctas_ff(nt, smem) : smerf_queue_ctas_fd(nt, smem);
+    return kind == kFF ? smerf_queue_ctas_ff(smem) : smerf_queue_ctas_fd(smem);
 }
 
 int launch_group(int kind, const smerf_plan* rep, const SampleParams* d, const int4* a, int na, const int4* s, int ns,
@@ -98,7 +101,9 @@ struct smerf_batch {
     std::vector<size_t> offs;
     std::vector<int> singles;  // requests whose shape has no batched kernel (launched one by one)
     std::vector<Group> groups;   // kernel shapes (FP64 recursion: launched per group)
-    std::vector<Queue> queues;   // FP32 recursion: two persistent phases per table precision
+    std::vector<Queue> queues;   // FP32 recursion: the persistent work per table precision
+    int single = 0;              // 1: one persistent launch per queue; 0: anchor launch + persistent launch
+    int fail_waits = 0;          // test hook: the next single launch's anchor waits cannot be met
     void* scratch = nullptr;
     SampleParams* h_descs = nullptr;  // pinned staging
     SampleParams* d_descs = nullptr;
@@ -114,9 +119,9 @@ static void batch_free(smerf_batch* b)
         cudaFree(g.d_seg);
     }
     for (auto& q : b->queues) {
-        cudaFree(q.d_anc);
-        cudaFree(q.d_seg);
-        cudaFree(q.d_head);
+        cudaFree(q.d_items);
+        cudaFree(q.d_anc128);
+        cudaFree(q.d_ctl);
     }
     cudaFree(b->scratch);
     cudaFree(b->d_descs);
@@ -215,12 +220,10 @@ int smerf_batch_create(const smerf_plan* const* plans, const int* n_samples, int
     // queue's build for its size (smerf::queue_build), its descriptor's producer count set to it
     for (int kind : {(int)kFF, (int)kFD}) {
         if (rc != SMERF_OK) break;
-        std::vector<int4> qa;
-        std::vector<std::pair<double, int4>> qs;
+        std::vector<std::pair<double, int4>> qa, qa128, qs;  // (request cost or item cost, item)
         size_t smem = 0;
         for (size_t g = 0; g < b->groups.size() && rc == SMERF_OK; ++g) {
             if (b->groups[g].kind != kind || !queued(kind, b->groups[g].rep->p)) continue;
-            for (const int4& it : anc[g]) qa.push_back(make_int4(it.x, it.y, it.z, it.w | (plans[it.x]->p << 4)));
             int last = -1;
             for (const int4& it : seg[g]) {
                 const int i = it.x;
@@ -235,39 +238,59 @@ int smerf_batch_create(const smerf_plan* const* plans, const int* n_samples, int
                 const size_t sm = kind == kFF ? smerf_ws_smem_ff(pl, rmax) : smerf_ws_smem_fd(pl, rmax);
                 smem = sm > smem ? sm : smem;
                 const int n = n_samples[i];
+                double total = 0.0;
                 for (int sgi = 0; sgi < pl->n_segments; ++sgi)
                     for (int grp = 0; grp < (n + rmax - 1) / rmax; ++grp) {
                         const smerf::Segment& sg = pl->segs_host[sgi];
                         const int r = n - grp * rmax < rmax ? n - grp * rmax : rmax;
                         const double cost = (double)(pl->n_phi / 2) * pl->p * (sg.p1 - sg.p0) * r;
+                        total += cost;
                         qs.push_back(std::make_pair(cost, make_int4(i, sgi, grp, (pl->p - 1) * smerf::kQueueBuilds + bld)));
                     }
+                // the request's anchor items (smerf::queue_anchor_items of them): both chains, every
+                // realisation, blocks of kQueueThreads units
+                const int nb = (units + smerf::kQueueThreads - 1) / smerf::kQueueThreads;
+                for (int c = 0; c < 2; ++c)
+                    for (int r = 0; r < n; ++r)
+                        for (int ub = 0; ub < nb; ++ub)
+                            qa.push_back(std::make_pair(total, make_int4(i, ub, r, -1 - ((pl->p << 4) | c))));
+                // the same in blocks of 128 units, for the anchor launch of the two-launch form
+                const int nb128 = (units + 127) / 128;
+                for (int c = 0; c < 2; ++c)
+                    for (int r = 0; r < n; ++r)
+                        for (int ub = 0; ub < nb128; ++ub)
+                            qa128.push_back(std::make_pair(total, make_int4(i, ub, r, (pl->p << 4) | c)));
             }
         }
         if (rc != SMERF_OK || (qa.empty() && qs.empty())) continue;
-        std::stable_sort(qs.begin(), qs.end(), [](const std::pair<double, int4>& x, const std::pair<double, int4>& y) {
-            return x.first > y.first;
-        });
+        auto larger = [](const std::pair<double, int4>& x, const std::pair<double, int4>& y) { return x.first > y.first; };
+        std::stable_sort(qa.begin(), qa.end(), larger);
+        std::stable_sort(qa128.begin(), qa128.end(), larger);
+        std::stable_sort(qs.begin(), qs.end(), larger);
+        std::vector<int4> anc128;
+        for (auto& x : qa128) anc128.push_back(x.second);
+        std::vector<int4> items;
+        for (auto& x : qa) items.push_back(x.second);
+        for (auto& x : qs) items.push_back(x.second);
         Queue q;
         q.kind = kind;
         q.n_anc = (int)qa.size();
-        q.n_seg = (int)qs.size();
-        q.nt = smerf::kQueueThreads;
+        q.n_items = (int)items.size();
+        q.n_anc128 = (int)anc128.size();
         q.smem = smem;
-        q.ctas = q.n_seg ? queue_ctas(kind, q.nt, smem) : 0;
-        std::vector<int4> sv;
-        for (auto& x : qs) sv.push_back(x.second);
-        const bool ok = (q.n_seg == 0 || q.ctas > 0) &&
-                        smerf::dev_malloc((void**)&q.d_anc, sizeof(int4) * (q.n_anc ? q.n_anc : 1)) == cudaSuccess &&
-                        smerf::dev_malloc((void**)&q.d_seg, sizeof(int4) * (q.n_seg ? q.n_seg : 1)) == cudaSuccess &&
-                        smerf::dev_malloc((void**)&q.d_head, sizeof(int)) == cudaSuccess;
+        q.ctas = queue_ctas(kind, smem);
+        const bool ok = q.ctas > 0 &&
+                        smerf::dev_malloc((void**)&q.d_items, sizeof(int4) * q.n_items) == cudaSuccess &&
+                        smerf::dev_malloc((void**)&q.d_anc128, sizeof(int4) * (q.n_anc128 ? q.n_anc128 : 1)) == cudaSuccess &&
+                        smerf::dev_malloc((void**)&q.d_ctl, sizeof(int) * (2 + n_req)) == cudaSuccess;
         b->queues.push_back(q);
         if (!ok) {
-            rc = q.n_seg && q.ctas <= 0 ? SMERF_ECUDA : SMERF_ENOMEM;
+            rc = q.ctas <= 0 ? SMERF_ECUDA : SMERF_ENOMEM;
             break;
         }
-        if ((q.n_anc && cudaMemcpy(q.d_anc, qa.data(), sizeof(int4) * q.n_anc, cudaMemcpyHostToDevice) != cudaSuccess) ||
-            (q.n_seg && cudaMemcpy(q.d_seg, sv.data(), sizeof(int4) * q.n_seg, cudaMemcpyHostToDevice) != cudaSuccess))
+        if (cudaMemcpy(q.d_items, items.data(), sizeof(int4) * q.n_items, cudaMemcpyHostToDevice) != cudaSuccess ||
+            (q.n_anc128 && cudaMemcpy(q.d_anc128, anc128.data(), sizeof(int4) * q.n_anc128, cudaMemcpyHostToDevice) !=
+                               cudaSuccess))
             rc = SMERF_ECUDA;
     }
     if (rc != SMERF_OK) {
@@ -310,8 +333,10 @@ int smerf_batch_launch(smerf_batch* b, void* stream)
     if (cudaMemcpyAsync(b->d_descs, b->h_descs, sizeof(SampleParams) * b->n_req, cudaMemcpyHostToDevice, st) !=
         cudaSuccess)
         return SMERF_ECUDA;
+    const int fail = b->single && b->fail_waits;
+    if (b->single) b->fail_waits = 0;
     for (const Queue& q : b->queues) {
-        const int rc = launch_queue(q, b->d_descs, st);
+        const int rc = launch_queue(q, b->d_descs, b->n_req, b->single, fail, st);
         if (rc != SMERF_OK) return rc;
     }
     for (const Group& g : b->groups) {
@@ -345,11 +370,41 @@ int smerf_batch_launch_count(const smerf_batch* b)
 {
     if (!b) return SMERF_EINVAL;
     int n = 0;
-    for (const Queue& q : b->queues) n += (q.n_anc > 0) + (q.n_seg > 0);
+    for (const Queue& q : b->queues)
+        n += b->single ? q.n_items > 0 : (q.n_anc128 > 0) + (q.n_items > q.n_anc);
     for (const Group& g : b->groups)
         if (!queued(g.kind, g.rep->p)) n += (g.n_anc > 0) + (g.n_seg > 0);
     for (int i : b->singles) n += smerf_sample_launches(b->plans[i], b->counts[i]);
     return n;
+}
+
+int smerf_batch_status(const smerf_batch* b, void* stream)
+{
+    if (!b) return SMERF_EINVAL;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return SMERF_ECUDA;
+    }
+    for (const Queue& q : b->queues) {
+        int status = 0;
+        if (cudaMemcpy(&status, q.d_ctl + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SMERF_ECUDA;
+        if (status != 0) return SMERF_ETIMEOUT;
+    }
+    return SMERF_OK;
+}
+
+int smerf_batch_set_single_launch(smerf_batch* b, int single)
+{
+    if (!b || (single != 0 && single != 1)) return SMERF_EINVAL;
+    b->single = single;
+    return SMERF_OK;
+}
+
+int smerf_debug_batch_fail_waits(smerf_batch* b)
+{
+    if (!b) return SMERF_EINVAL;
+    b->fail_waits = 1;
+    return SMERF_OK;
 }
 
 int smerf_batch_destroy(smerf_batch* b)

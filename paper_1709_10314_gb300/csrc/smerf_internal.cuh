@@ -142,7 +142,7 @@ __host__ __device__ constexpr int hr_off(int L, int i, int MB = 4)
     return o;
 }
 
-// The batch's persistent segment launch: kQueueThreads threads per CTA, two CTAs per SM; a
+// The batch's persistent launch: kQueueThreads threads per CTA, two CTAs per SM; a
 // request runs with np = ceil32(units / upt) <= 256 producer threads (upt the smallest of 1, 2,
 // 4, 8 that allows it), the rest FFT threads, and 4, 2, 2, 1 realisations per CTA for upt = 1,
 // 2, 4, 8.  Its shape, shape = (p - 1) * kQueueBuilds + build, selects that build.
@@ -282,12 +282,15 @@ SMERF_DECLARE_GROUP_CONFIG(ff)
 SMERF_DECLARE_GROUP_CONFIG(fd)
 SMERF_DECLARE_GROUP_CONFIG(dd)
 SMERF_DECLARE_GROUP_CONFIG(df)
-// the two persistent phases of a batch for FP32 recursion (FP32 or FP64 tables): one anchor
-// launch, one persistent segment launch of `ctas` CTAs pulling items from a device queue
+// the persistent work of a batch for FP32 recursion (FP32 or FP64 tables): `ctas` CTAs pulling
+// anchor items, then segment items, from a device queue in one launch (single), or an anchor
+// launch over anc128 and a persistent launch over the segment items; ctl = head, status, anchor
+// counters
 #define SMERF_DECLARE_QUEUE(XX)                                                                          \
-    int smerf_launch_queue_##XX(const smerf::SampleParams* d, const int4* anc, int n_anc, const int4* seg, \
-                                int n_seg, int* head, int nt, size_t smem, int ctas, cudaStream_t st);   \
-    int smerf_queue_ctas_##XX(int nt, size_t smem);
+    int smerf_launch_queue_##XX(const smerf::SampleParams* d, const int4* items, int n_items, int n_anc,  \
+                                const int4* anc128, int n_anc128, int* ctl, int n_req, int single,         \
+                                int fail_waits, size_t smem, int ctas, cudaStream_t st);                   \
+    int smerf_queue_ctas_##XX(size_t smem);
 SMERF_DECLARE_QUEUE(ff)
 SMERF_DECLARE_QUEUE(fd)
 

@@ -91,11 +91,13 @@ __device__ __forceinline__ size_t aoff(const SampleParams& P, int c, int r, int 
 template <class Real> struct Vec4;
 template <> struct Vec4<float> {
     static __device__ __forceinline__ void ld(const float* p, float (&v)[4]) { const float4 a = *reinterpret_cast<const float4*>(p); v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; }
+    static __device__ __forceinline__ void ldcg(const float* p, float (&v)[4]) { const float4 a = __ldcg(reinterpret_cast<const float4*>(p)); v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; }
     static __device__ __forceinline__ void ldg(const float* p, float (&v)[4]) { const float4 a = __ldg(reinterpret_cast<const float4*>(p)); v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; }
     static __device__ __forceinline__ void st(float* p, const float (&v)[4]) { *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]); }
 };
 template <> struct Vec4<double> {
     static __device__ __forceinline__ void ld(const double* p, double (&v)[4]) { const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1]; v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; }
+    static __device__ __forceinline__ void ldcg(const double* p, double (&v)[4]) { const double2 a = __ldcg(reinterpret_cast<const double2*>(p)), b = __ldcg(reinterpret_cast<const double2*>(p) + 1); v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; }
     static __device__ __forceinline__ void ldg(const double* p, double (&v)[4]) { const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1); v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; }
     static __device__ __forceinline__ void st(double* p, const double (&v)[4]) { reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]); reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]); }
 };
@@ -113,6 +115,18 @@ template <class Real, int NV> struct VecN {
     {
 #pragma unroll
         for (int k = 0; k < NV; k += 4) Vec4<Real>::ldg(p + k, *reinterpret_cast<Q*>(&v[k]));
+    }
+    static __device__ __forceinline__ void ldcg(const Real* p, Real (&v)[NV])
+    {
+#pragma unroll
+        for (int k = 0; k < NV; k += 4) Vec4<Real>::ldcg(p + k, *reinterpret_cast<Q*>(&v[k]));
+    }
+    // anchor states: through the read-only path when an earlier launch wrote them, through L2
+    // only (CG) when the same launch did (the persistent batch kernel)
+    template <bool CG> static __device__ __forceinline__ void ld_anchor(const Real* p, Real (&v)[NV])
+    {
+        if constexpr (CG) ldcg(p, v);
+        else ldg(p, v);
     }
     static __device__ __forceinline__ void st(Real* p, const Real (&v)[NV])
     {
@@ -1181,8 +1195,9 @@ __device__ __noinline__ void ragged_ring(cplx<Real>* B, cplx<Real>* W, int R, in
 //             syncs the two outstanding EMPTY barriers
 //   FFT:      sync FULL[k&1]; FFT; arrive EMPTY[k&1]
 // Every FULL/EMPTY barrier counts NP + NF threads; the FFT passes use a group barrier.
-// RINGS: the request may have ring-dependent longitudes (single-request launches; batches never do)
-template <class Real, class TabT, int M, int UPT, int RMAX, bool RINGS = true>
+// RINGS: the request may have ring-dependent longitudes (single-request launches; batches never do).
+// CG: the anchor states were written by the same launch (read through L2, not the read-only path).
+template <class Real, class TabT, int M, int UPT, int RMAX, bool RINGS = true, bool CG = false>
 __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, int group)
 {
     using C = cplx<Real>;
@@ -1221,7 +1236,7 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
         for (int idx = 4 * tid; idx < R * per; idx += 4 * nt) {
             const int r = idx / per, rest = idx - r * per;
             Real v[4];
-            Vec4<Real>::ldg(anc + aoff<M>(P, c, r0 + r, sg.right, 0, 0) + rest, v);
+            VecN<Real, 4>::template ld_anchor<CG>(anc + aoff<M>(P, c, r0 + r, sg.right, 0, 0) + rest, v);
             Vec4<Real>::st(xRs + idx, v);
         }
     }
@@ -1236,7 +1251,7 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
 #pragma unroll
             for (int r = 0; r < RMAX; ++r) {
                 if (u < n_units && r < R) {
-                    VecN<Real, NU>::ldg(anc + aoff<M>(P, c, r0 + r, sg.left, 0, G * u), x[i][r]);
+                    VecN<Real, NU>::template ld_anchor<CG>(anc + aoff<M>(P, c, r0 + r, sg.left, 0, G * u), x[i][r]);
                 } else {
 #pragma unroll
                     for (int k = 0; k < NU; ++k) x[i][r][k] = 0;
@@ -1356,16 +1371,131 @@ __global__ void __launch_bounds__(ws_max_threads(MINB), MINB) segment_ws_batched
     ws_body<Real, TabT, M, UPT, RMAX, false>(P, it.y, it.z);
 }
 
-// ---- uneven batches in two persistent phases
-// Phase 1 runs every group's anchor items in one launch (item: request, block of 128 units,
-// realisation, chain | p << 4).  Phase 2 is one launch of persistent CTAs that take segment
-// items (request, segment, realisation group, shape) from a device queue -- an atomic counter
-// reset before each launch, items ordered largest first -- and run each with the
-// warp-specialised body of its shape, so requests of different grids, spectra and p share one
-// launch.  Phase 2 starts after phase 1 has finished (stream order), so no item waits for
-// another.  A shape is p and the build (units per producer thread, realisations per CTA,
-// queue_build): every shape runs with kQueueThreads threads, two CTAs per SM.
+// ---- uneven batches: one persistent launch, or an anchor launch and a persistent launch
+// Persistent CTAs (kQueueThreads threads, two per SM, as many as are resident) take items from
+// a device queue -- an atomic counter reset before each launch.  The queue holds every
+// request's anchor items first (request, block of kQueueThreads units, realisation, and
+// w = -1 - (p << 4 | chain)), then the segment items (request, segment, realisation group,
+// shape w >= 0), each list largest request first.  An anchor item walks its units' start
+// states and anchors (anchor_body) and then adds one to its request's counter of finished
+// anchor items; a segment item first waits until that counter shows all of its request's
+// anchor items, then runs the warp-specialised body of its shape (p and the build: units per
+// producer thread, realisations per CTA, queue_build), so requests of different grids, spectra
+// and p share the launch and the anchors of later requests overlap the segments of earlier
+// ones.  Every anchor item is claimed before any segment item and runs without waiting, so a
+// waiting CTA only waits for items that resident CTAs are running; the wait is still bounded
+// (about a second, kQueueWaitNs), after which it records SMERF_ETIMEOUT's cause in the
+// launch's status word, skips the item, and makes every later wait give up at once.
+//
+// ctl[0]: queue head; ctl[1]: status (0, or 1 once a wait ran out); ctl[2 + i]: finished
+// anchor items of request i.
 
+constexpr unsigned long long kQueueWaitNs = 1000000000ull;  // a wait's limit in wall time
+constexpr unsigned kQueueWaitPolls = 1u << 22;              // and in polls
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ int ld_acquire(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// anchor items of a request: both chains, every realisation, blocks of kQueueThreads units
+__host__ __device__ inline int queue_anchor_items(int n_samples, int n_units)
+{
+    return 2 * n_samples * ((n_units + kQueueThreads - 1) / kQueueThreads);
+}
+
+// one thread: wait until *done >= need (bounded); false if the wait ran out or another did
+__device__ inline bool wait_anchors(const int* done, int need, int* status)
+{
+    unsigned long long t0 = 0;
+    for (unsigned i = 0; i < kQueueWaitPolls; ++i) {
+        if (ld_acquire(done) >= need) return true;
+        if (ld_acquire(status) != 0) return false;
+        const unsigned long long t = global_ns();
+        if (i == 0) t0 = t;
+        else if (t - t0 > kQueueWaitNs) break;
+        __nanosleep(128);
+    }
+    atomicCAS(status, 0, 1);
+    return false;
+}
+
+// an anchor item of the persistent launch (called out of line: its registers stay apart from
+// the segment bodies')
+template <class Real, class TabT>
+__device__ __noinline__ void queue_anchor(const SampleParams* __restrict__ desc, int code, int ub, int r)
+{
+    const SampleParams P = *desc;
+    NoStage h;
+    const int u = ub * kQueueThreads + threadIdx.x;
+    if ((code >> 4) == 1) anchor_body<Real, TabT, 1>(P, u, r, code & 15, h);
+    else anchor_body<Real, TabT, 2>(P, u, r, code & 15, h);
+}
+
+template <class Real, class TabT, int SH>
+__device__ __forceinline__ void queue_segment(const SampleParams& P, int seg, int grp)
+{
+    constexpr int M = SH / kQueueBuilds + 1, B = SH % kQueueBuilds;
+    ws_body<Real, TabT, M, queue_upt(B), queue_rmax(B), false, true>(P, seg, grp);
+}
+
+template <class Real, class TabT>
+__global__ void __launch_bounds__(kQueueThreads, kQueueMinBlocks) queue_kernel(const SampleParams* __restrict__ descs,
+                                                                 const int4* __restrict__ items, int n_items,
+                                                                 int* __restrict__ ctl)
+{
+    // the next item is claimed while the current one runs (s_k[b ^ 1]), hiding the atomic
+    __shared__ int s_k[2];
+    __shared__ int s_go;
+    if (threadIdx.x == 0) s_k[0] = atomicAdd(ctl, 1);
+    __syncthreads();
+    for (int b = 0;; b ^= 1) {
+        const int k = s_k[b];
+        if (k >= n_items) return;
+        if (threadIdx.x == 0) s_k[b ^ 1] = atomicAdd(ctl, 1);
+        const int4 it = items[k];
+        if (it.w < 0) {
+            queue_anchor<Real, TabT>(descs + it.x, -1 - it.w, it.y, it.z);
+            __syncthreads();  // every anchor state of the item is written
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(ctl + 2 + it.x, 1);
+            }
+        } else {
+            const SampleParams P = descs[it.x];
+            if (threadIdx.x == 0)
+                s_go = wait_anchors(ctl + 2 + it.x, queue_anchor_items(P.n_samples, P.n_units), ctl + 1);
+            __syncthreads();
+            if (s_go) {
+                switch (it.w) {
+                    case 0: queue_segment<Real, TabT, 0>(P, it.y, it.z); break;
+                    case 1: queue_segment<Real, TabT, 1>(P, it.y, it.z); break;
+                    case 2: queue_segment<Real, TabT, 2>(P, it.y, it.z); break;
+                    case 3: queue_segment<Real, TabT, 3>(P, it.y, it.z); break;
+                    case 4: queue_segment<Real, TabT, 4>(P, it.y, it.z); break;
+                    case 5: queue_segment<Real, TabT, 5>(P, it.y, it.z); break;
+                    case 6: queue_segment<Real, TabT, 6>(P, it.y, it.z); break;
+                    default: queue_segment<Real, TabT, 7>(P, it.y, it.z); break;
+                }
+            }
+        }
+        __syncthreads();  // the item's shared buffers and s_go are free again, s_k[b ^ 1] is visible
+    }
+}
+
+// The same work in two launches (the default; measured faster, since the persistent kernel then
+// carries no anchor code and keeps the register allocation of the segment bodies): every
+// anchor item in one launch of 128-thread blocks (item: request, block of 128 units,
+// realisation, p << 4 | chain), then the persistent CTAs over the segment items alone, which
+// need no wait: stream order puts every anchor before them.
 template <class Real, class TabT>
 __global__ void __launch_bounds__(128, SMERF_ANCHOR_MINB) anchor_queue_kernel(const SampleParams* __restrict__ descs,
                                                                                const int4* __restrict__ items)
@@ -1379,10 +1509,10 @@ __global__ void __launch_bounds__(128, SMERF_ANCHOR_MINB) anchor_queue_kernel(co
 }
 
 template <class Real, class TabT, int SH>
-__device__ __forceinline__ void queue_segment(const SampleParams& P, int seg, int grp)
+__device__ __forceinline__ void queue_segment_after(const SampleParams& P, int seg, int grp)
 {
     constexpr int M = SH / kQueueBuilds + 1, B = SH % kQueueBuilds;
-    ws_body<Real, TabT, M, queue_upt(B), queue_rmax(B), false>(P, seg, grp);
+    ws_body<Real, TabT, M, queue_upt(B), queue_rmax(B), false, false>(P, seg, grp);
 }
 
 template <class Real, class TabT>
@@ -1390,8 +1520,7 @@ __global__ void __launch_bounds__(kQueueThreads, kQueueMinBlocks) segment_queue_
                                                                          const int4* __restrict__ items, int n_items,
                                                                          int* __restrict__ head)
 {
-    // the next item is claimed while the current one runs (s_k[b ^ 1]), hiding the atomic
-    __shared__ int s_k[2];
+    __shared__ int s_k[2];  // the next item is claimed while the current one runs
     if (threadIdx.x == 0) s_k[0] = atomicAdd(head, 1);
     __syncthreads();
     for (int b = 0;; b ^= 1) {
@@ -1401,14 +1530,14 @@ __global__ void __launch_bounds__(kQueueThreads, kQueueMinBlocks) segment_queue_
         const int4 it = items[k];
         const SampleParams P = descs[it.x];
         switch (it.w) {
-            case 0: queue_segment<Real, TabT, 0>(P, it.y, it.z); break;
-            case 1: queue_segment<Real, TabT, 1>(P, it.y, it.z); break;
-            case 2: queue_segment<Real, TabT, 2>(P, it.y, it.z); break;
-            case 3: queue_segment<Real, TabT, 3>(P, it.y, it.z); break;
-            case 4: queue_segment<Real, TabT, 4>(P, it.y, it.z); break;
-            case 5: queue_segment<Real, TabT, 5>(P, it.y, it.z); break;
-            case 6: queue_segment<Real, TabT, 6>(P, it.y, it.z); break;
-            default: queue_segment<Real, TabT, 7>(P, it.y, it.z); break;
+            case 0: queue_segment_after<Real, TabT, 0>(P, it.y, it.z); break;
+            case 1: queue_segment_after<Real, TabT, 1>(P, it.y, it.z); break;
+            case 2: queue_segment_after<Real, TabT, 2>(P, it.y, it.z); break;
+            case 3: queue_segment_after<Real, TabT, 3>(P, it.y, it.z); break;
+            case 4: queue_segment_after<Real, TabT, 4>(P, it.y, it.z); break;
+            case 5: queue_segment_after<Real, TabT, 5>(P, it.y, it.z); break;
+            case 6: queue_segment_after<Real, TabT, 6>(P, it.y, it.z); break;
+            default: queue_segment_after<Real, TabT, 7>(P, it.y, it.z); break;
         }
         __syncthreads();  // the item's shared buffers are free again and s_k[b ^ 1] is visible
     }
@@ -1857,35 +1986,54 @@ int group_segments(const SegConfig& cfg, const SampleParams* d, const int4* item
     }
 }
 
-// The two persistent phases of a batch (FP32 recursion): anchor launch over anc items, then
-// `ctas` persistent CTAs of nt threads over seg items (head: a device counter, zeroed here).
+// A batch's persistent work (FP32 recursion).  One launch (single): `ctas` CTAs of queue_kernel
+// over the n_items items (the anchor items first); ctl holds 2 + n_req integers (head, status,
+// per-request anchor counters), set here before the launch; fail_waits (a test hook) starts the
+// anchor counters at -1 instead of 0, so that no segment item's wait can be met: the waits run
+// out and the status word records it.  Two launches (otherwise): anchor_queue_kernel over the
+// n_anc128 items of anc128, then `ctas` CTAs of segment_queue_kernel over the segment items
+// (items + n_anc, n_items - n_anc of them), ctl[0] their queue head.
 template <class Real, class TabT>
-int launch_queue(const SampleParams* d, const int4* anc, int n_anc, const int4* seg, int n_seg, int* head, int nt,
-                 size_t smem, int ctas, cudaStream_t st)
+int launch_queue(const SampleParams* d, const int4* items, int n_items, int n_anc, const int4* anc128, int n_anc128,
+                 int* ctl, int n_req, int single, int fail_waits, size_t smem, int ctas, cudaStream_t st)
 {
-    if (n_anc > 0) {
-        anchor_queue_kernel<Real, TabT><<<n_anc, 128, 0, st>>>(d, anc);
+    if (n_items == 0) return SMERF_OK;
+    if (single) {
+        auto kern = queue_kernel<Real, TabT>;
+        if (set_smem_attr(kern, smem) != cudaSuccess) return SMERF_ECUDA;
+        if (cudaMemsetAsync(ctl, 0, sizeof(int) * 2, st) != cudaSuccess) return SMERF_ECUDA;
+        if (n_req > 0 && cudaMemsetAsync(ctl + 2, fail_waits ? 0xFF : 0, sizeof(int) * n_req, st) != cudaSuccess)
+            return SMERF_ECUDA;
+        kern<<<ctas, kQueueThreads, smem, st>>>(d, items, n_items, ctl);
+        return cudaGetLastError() == cudaSuccess ? SMERF_OK : SMERF_ECUDA;
+    }
+    if (n_anc128 > 0) {
+        anchor_queue_kernel<Real, TabT><<<n_anc128, 128, 0, st>>>(d, anc128);
         if (cudaGetLastError() != cudaSuccess) return SMERF_ECUDA;
     }
-    if (n_seg == 0) return SMERF_OK;
+    if (n_items == n_anc) return SMERF_OK;
     auto kern = segment_queue_kernel<Real, TabT>;
     if (set_smem_attr(kern, smem) != cudaSuccess) return SMERF_ECUDA;
-    if (cudaMemsetAsync(head, 0, sizeof(int), st) != cudaSuccess) return SMERF_ECUDA;
-    kern<<<ctas, nt == kQueueThreads ? nt : kQueueThreads, smem, st>>>(d, seg, n_seg, head);
+    if (cudaMemsetAsync(ctl, 0, sizeof(int) * 2, st) != cudaSuccess) return SMERF_ECUDA;
+    kern<<<ctas, kQueueThreads, smem, st>>>(d, items + n_anc, n_items - n_anc, ctl);
     return cudaGetLastError() == cudaSuccess ? SMERF_OK : SMERF_ECUDA;
 }
 
-// resident CTAs of the persistent segment launch (nt threads, smem bytes) on this device
+// resident CTAs of the persistent launch (kQueueThreads threads, smem bytes) on this device:
+// the smaller of the two persistent kernels' counts, so that either mode may use it
 template <class Real, class TabT>
-int queue_ctas(int nt, size_t smem)
+int queue_ctas(size_t smem)
 {
-    auto kern = segment_queue_kernel<Real, TabT>;
-    if (set_smem_attr(kern, smem) != cudaSuccess) return -1;
-    int per_sm = 0, dev = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem) != cudaSuccess) return -1;
+    auto k1 = queue_kernel<Real, TabT>;
+    auto k2 = segment_queue_kernel<Real, TabT>;
+    if (set_smem_attr(k1, smem) != cudaSuccess || set_smem_attr(k2, smem) != cudaSuccess) return -1;
+    int per1 = 0, per2 = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k1, kQueueThreads, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k2, kQueueThreads, smem) != cudaSuccess)
+        return -1;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return -1;
-    return per_sm * sms;
+    return (per1 < per2 ? per1 : per2) * sms;
 }
 
 template <class Real, class TabT>
@@ -1971,12 +2119,14 @@ int launch_group_m(const smerf_plan* rep, const SampleParams* d, const int4* anc
     }                                                                                                            \
     size_t smerf_ws_smem_##XX(const smerf_plan* pl, int rmax) { return smerf::ws_smem<REAL>(pl, rmax); }
 
-// The persistent two-phase batch launch of an FP32-recursion precision pair (its own translation
-// unit, smerf_sample_XX_queue.cu, since it instantiates every shape of both p).
+// The persistent batch launch of an FP32-recursion precision pair (its own translation unit,
+// smerf_sample_XX_queue.cu, since it instantiates every shape of p = 1 and 2).
 #define SMERF_QUEUE(REAL, TABT, XX)                                                                       \
-    int smerf_launch_queue_##XX(const smerf::SampleParams* d, const int4* anc, int n_anc, const int4* seg,  \
-                                int n_seg, int* head, int nt, size_t smem, int ctas, cudaStream_t st)      \
+    int smerf_launch_queue_##XX(const smerf::SampleParams* d, const int4* items, int n_items, int n_anc,   \
+                                const int4* anc128, int n_anc128, int* ctl, int n_req, int single,          \
+                                int fail_waits, size_t smem, int ctas, cudaStream_t st)                     \
     {                                                                                                     \
-        return smerf::launch_queue<REAL, TABT>(d, anc, n_anc, seg, n_seg, head, nt, smem, ctas, st);      \
+        return smerf::launch_queue<REAL, TABT>(d, items, n_items, n_anc, anc128, n_anc128, ctl, n_req,      \
+                                               single, fail_waits, smem, ctas, st);                         \
     }                                                                                                     \
-    int smerf_queue_ctas_##XX(int nt, size_t smem) { return smerf::queue_ctas<REAL, TABT>(nt, smem); }
+    int smerf_queue_ctas_##XX(size_t smem) { return smerf::queue_ctas<REAL, TABT>(smem); }

@@ -88,6 +88,12 @@ def _lib():
         L.smerf_batch_info.restype = ip
         L.smerf_batch_launch_count.argtypes = [vp]
         L.smerf_batch_launch_count.restype = ip
+        L.smerf_batch_status.argtypes = [vp, vp]
+        L.smerf_batch_status.restype = ip
+        L.smerf_batch_set_single_launch.argtypes = [vp, ip]
+        L.smerf_batch_set_single_launch.restype = ip
+        L.smerf_debug_batch_fail_waits.argtypes = [vp]
+        L.smerf_debug_batch_fail_waits.restype = ip
         L.smerf_batch_destroy.argtypes = [vp]
         L.smerf_batch_destroy.restype = ip
         L.smerf_plan_info.argtypes = [vp, ctypes.POINTER(_Info)]
@@ -421,6 +427,21 @@ class Batch:
         S, O = self._arrays(seeds, outs)
         _check("smerf_batch_sample", _lib().smerf_batch_sample(self._h, S, O, _stream_ptr(stream)))
         return outs
+
+    def set_single_launch(self, single):
+        """smerf_batch_set_single_launch: True runs the FP32-recursion work of the following launches
+        as one persistent launch (anchor items, then segment items), False (the default) as an
+        anchor launch and a persistent launch."""
+        _check("smerf_batch_set_single_launch", _lib().smerf_batch_set_single_launch(self._h, 1 if single else 0))
+
+    def status(self, stream=None):
+        """smerf_batch_status: synchronises the stream; SMERF_OK (0), or SMERF_ETIMEOUT (-7) when a
+        segment item's wait for its request's anchors ran out in the last launch."""
+        return _lib().smerf_batch_status(self._h, _stream_ptr(stream))
+
+    def debug_fail_waits(self):
+        """smerf_debug_batch_fail_waits: the next launch's anchor waits cannot be met (test hook)."""
+        _check("smerf_debug_batch_fail_waits", _lib().smerf_debug_batch_fail_waits(self._h))
 
     def info(self):
         g, s1 = ctypes.c_int(), ctypes.c_int()

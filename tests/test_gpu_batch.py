@@ -51,8 +51,12 @@ def test_batch_object_reuse_and_groups():
     info = b.info()
     assert info["groups"] == 5 and info["singles"] == 0   # plans 0 and 2 share a shape
     # FP32 recursion with FP32 tables (plans 0, 1, 2, 5) and with FP64 tables (plan 4): an anchor
-    # launch and a persistent segment launch each; FP64 recursion (plan 3): its own two
+    # launch and a persistent launch each (one persistent launch each in the single-launch
+    # form); FP64 recursion (plan 3): an anchor and a segment launch
     assert info["launches"] == 6
+    b.set_single_launch(True)
+    assert b.info()["launches"] == 4
+    b.set_single_launch(False)
     for seeds in ([1, 2, 3, 4, 5, 6], [100, 200, 300, 400, 500, 600]):
         outs = _outs(plans, counts)
         b.sample(seeds, outs)
@@ -136,10 +140,12 @@ def test_batch_graph_replay_against_oracle():
             assert err < (1e-9 if f else 1e-4), (k, nt, nphi, sd, err)
 
 
-def test_uneven_batch_runs_in_two_persistent_launches():
-    """Requests of four grids and both p with FP32 recursion: one anchor launch and one launch of
-    persistent CTAs that pull every shape's segments from the device queue; each request bit
-    for bit what its own smerf_sample call gives."""
+@pytest.mark.parametrize("single", [False, True])
+def test_uneven_batch_persistent_launches(single):
+    """Requests of four grids and both p with FP32 recursion: an anchor launch and one launch of
+    persistent CTAs that pull every shape's segments from the device queue, or (single) one
+    launch of persistent CTAs that pull every request's anchor items and then every segment;
+    each request bit for bit what its own smerf_sample call gives, launch after launch."""
     import torch
     from paper_1709_10314_gb300 import Batch, Plan
     specs = [([12.0], 128, 256, 3), ([30.0, 90.0], 256, 512, 2), ([7.0], 64, 128, 5), ([20.0, 50.0], 512, 1024, 1),
@@ -147,10 +153,40 @@ def test_uneven_batch_runs_in_two_persistent_launches():
     plans = [Plan(k, 1.0, nt, nphi) for (k, nt, nphi, _) in specs]
     counts = [s[-1] for s in specs]
     b = Batch(plans, counts)
-    assert b.info()["launches"] == 2 and b.info()["singles"] == 0
-    seeds = [5 * i + 1 for i in range(len(plans))]
+    b.set_single_launch(single)
+    assert b.info()["launches"] == (1 if single else 2) and b.info()["singles"] == 0
+    for rep in range(3):
+        seeds = [5 * i + 1 + 1000 * rep for i in range(len(plans))]
+        outs = _outs(plans, counts)
+        b.sample(seeds, outs)
+        assert b.status() == 0
+        for p, sd, n, o in zip(plans, seeds, counts, outs):
+            assert torch.equal(o, p.sample(sd, n))
+
+
+def test_anchor_wait_that_runs_out_is_reported_and_the_batch_recovers():
+    """The persistent launch's one device wait (a segment item waiting for its request's anchor
+    items) is bounded: with the anchor counters started one below zero (the test hook) no wait
+    can be met, the first runs out after about a second, the others give up at once, and
+    smerf_batch_status reports SMERF_ETIMEOUT with the context still usable.  The next launch
+    is normal and exact."""
+    import time
+    import torch
+    from paper_1709_10314_gb300 import Batch, Plan
+    plans = [Plan([12.0], 1.0, 64, 128), Plan([30.0, 90.0], 1.0, 128, 256)]
+    counts = [2, 3]
+    b = Batch(plans, counts)
+    b.set_single_launch(True)
     outs = _outs(plans, counts)
-    b.sample(seeds, outs)
-    torch.cuda.synchronize()
-    for p, sd, n, o in zip(plans, seeds, counts, outs):
+    for o in outs:
+        o.fill_(float("nan"))
+    b.debug_fail_waits()
+    t0 = time.perf_counter()
+    b.sample([1, 2], outs)
+    assert b.status() == -7
+    assert time.perf_counter() - t0 < 30.0
+    assert all(bool(torch.isnan(o).all()) for o in outs)   # no segment ran: no ring written
+    b.sample([1, 2], outs)
+    assert b.status() == 0
+    for p, sd, n, o in zip(plans, [1, 2], counts, outs):
         assert torch.equal(o, p.sample(sd, n))

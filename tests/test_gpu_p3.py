@@ -109,7 +109,7 @@ def test_every_candidate_gives_the_same_field(flags_name):
 
 def test_batch_with_p3_requests_equals_single_calls():
     """p = 3 requests run in a batch as one anchor and one segment launch per kernel shape,
-    beside the persistent phases of the p = 1, 2 requests."""
+    beside the anchor and persistent launches of the p = 1, 2 requests."""
     import torch
     from paper_1709_10314_gb300 import Batch, SMERF_RECUR_FP64
     plans = [_plan(24, 512, 5), _plan(17, 256, 4), _plan(24, 512, 5, kappa=(6.0,)),
@@ -123,8 +123,8 @@ def test_batch_with_p3_requests_equals_single_calls():
     torch.cuda.synchronize()
     for p, n, s, o in zip(plans, counts, seeds, outs):
         assert torch.equal(o, p.sample(s, n))
-    # two persistent phases (p = 1, 2), a launch pair for each p = 3 shape: 24 x 512 and
-    # 17 x 256 in FP32, 16 x 128 in FP64
+    # an anchor and a persistent launch (p = 1, 2), a launch pair for each p = 3 shape: 24 x 512
+    # and 17 x 256 in FP32, 16 x 128 in FP64
     assert b.info()["launches"] == 2 + 2 * 3
 
 
