@@ -324,12 +324,16 @@ int smerf_plan_set_rings(smerf_plan* plan, const int* n_phi_ring, const double* 
  * smerf_plan_autotune -- time every built launch configuration of the segment kernel that
  * fits this plan on n_samples realisations and keep the fastest for later calls.  A launch
  * configuration is SMERF_LAUNCH_INTS integers: (units per producer thread, realisations per
- * CTA, producer threads, FFT threads, CTAs per SM the kernel is built for).  Launch
- * parameters only: the output of later calls is unchanged.  Synchronous; allocates a
- * temporary output; must not run while other calls use the plan.  chosen (may be NULL)
- * receives the chosen configuration, all 0 when the plan's shape has no tunable kernel.
+ * CTA, producer threads, FFT threads, CTAs per SM the kernel is built for, FFT radix plan).
+ * The radix plan is 16 (the ring's C2R FFT in Stockham passes of up to 16 points, a
+ * fixed-size plan per ring length: 1024 points as 16, 8, 8) or 4 (radix-4 passes for any
+ * length); FP64 recursion offers 4 only.  The first five integers change launch parameters
+ * only; the radix plan changes the FFT's rounding (FP32: ~1e-7 of the field std), so configurations
+ * with the same radix plan give identical output.  Synchronous; allocates a temporary output;
+ * must not run while other calls use the plan.  chosen (may be NULL) receives the chosen
+ * configuration, all 0 when the plan's shape has no tunable kernel.
  */
-#define SMERF_LAUNCH_INTS 5
+#define SMERF_LAUNCH_INTS 6
 int smerf_plan_autotune(smerf_plan* plan, int n_samples, void* stream, int* chosen);
 
 /*
@@ -358,8 +362,8 @@ int smerf_plan_launch_candidates(const smerf_plan* plan, int* cand, int max_n);
 /*
  * smerf_plan_set_launch -- fix the segment-kernel launch configuration (SMERF_LAUNCH_INTS
  * integers) to one of the candidates (e.g. a choice smerf_plan_autotune made in an earlier
- * process), or with config == NULL return to the built-in choice.  SMERF_EINVAL if config is
- * not a candidate.  Host only; the output of later calls is unchanged.
+ * process), or with config == NULL return to the built-in choice (radix plan 16 in FP32).
+ * SMERF_EINVAL if config is not a candidate.  Host only.
  */
 int smerf_plan_set_launch(smerf_plan* plan, const int* config);
 

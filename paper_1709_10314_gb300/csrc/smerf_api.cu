@@ -595,6 +595,7 @@ int smerf_plan_info(const smerf_plan* plan, smerf_plan_info_t* info)
 }
 
 static int tune_candidates(const smerf_plan* plan, int* cand, int max_n);
+constexpr int kMaxCand = 128;  // launch candidates a plan can have (the tuner's buffers)
 
 int smerf_plan_set_rings(smerf_plan* plan, const int* n_phi_ring, const double* phi0_ring)
 {
@@ -616,8 +617,8 @@ int smerf_plan_set_rings(smerf_plan* plan, const int* n_phi_ring, const double* 
         off[k] = total;
         total += nk;
     }
-    int cand[smerf::kLaunchInts * 64];
-    if (tune_candidates(plan, cand, 64) == 0) return SMERF_EUNSUPPORTED;  // not a warp-specialised plan
+    int cand[smerf::kLaunchInts * kMaxCand];
+    if (tune_candidates(plan, cand, kMaxCand) == 0) return SMERF_EUNSUPPORTED;  // not a warp-specialised plan
     int dev = -1;
     cudaGetDevice(&dev);
     if (dev != plan->dev) return SMERF_EINVAL;
@@ -684,11 +685,23 @@ static int tune_candidates(const smerf_plan* plan, int* cand, int max_n)
 int smerf_plan_launch_candidates(const smerf_plan* plan, int* cand, int max_n)
 {
     if (!plan || max_n < 0 || (max_n > 0 && !cand)) return SMERF_EINVAL;
-    int tmp[smerf::kLaunchInts * 64];
-    const int n = tune_candidates(plan, tmp, 64);
+    int tmp[smerf::kLaunchInts * kMaxCand];
+    const int n = tune_candidates(plan, tmp, kMaxCand);
     for (int i = 0; i < n && i < max_n; ++i)
         for (int k = 0; k < smerf::kLaunchInts; ++k) cand[smerf::kLaunchInts * i + k] = tmp[smerf::kLaunchInts * i + k];
     return n;
+}
+
+// a plan's fixed launch configuration from kLaunchInts integers (a candidate)
+static void set_tune(smerf_plan* plan, const int* c)
+{
+    plan->tune.valid = 1;
+    plan->tune.upt = c[0];
+    plan->tune.rmax = c[1];
+    plan->tune.np = c[2];
+    plan->tune.nf = c[3];
+    plan->tune.minb = c[4];
+    plan->tune.radix = c[5];
 }
 
 int smerf_plan_set_launch(smerf_plan* plan, const int* config)
@@ -698,17 +711,14 @@ int smerf_plan_set_launch(smerf_plan* plan, const int* config)
         plan->tune.valid = 0;
         return SMERF_OK;
     }
-    int cand[smerf::kLaunchInts * 64];
-    const int n = tune_candidates(plan, cand, 64);
+    int cand[smerf::kLaunchInts * kMaxCand];
+    const int n = tune_candidates(plan, cand, kMaxCand);
     for (int i = 0; i < n; ++i) {
         const int* c = cand + smerf::kLaunchInts * i;
-        if (c[0] == config[0] && c[1] == config[1] && c[2] == config[2] && c[3] == config[3] && c[4] == config[4]) {
-            plan->tune.valid = 1;
-            plan->tune.upt = config[0];
-            plan->tune.rmax = config[1];
-            plan->tune.np = config[2];
-            plan->tune.nf = config[3];
-            plan->tune.minb = config[4];
+        bool same = true;
+        for (int k = 0; k < smerf::kLaunchInts; ++k) same = same && c[k] == config[k];
+        if (same) {
+            set_tune(plan, c);
             plan->tune.ms = 0.0f;
             return SMERF_OK;
         }
@@ -722,8 +732,8 @@ int smerf_plan_autotune(smerf_plan* plan, int n_samples, void* stream, int* chos
     int dev = -1;
     cudaGetDevice(&dev);
     if (dev != plan->dev) return SMERF_EINVAL;
-    int cand[smerf::kLaunchInts * 64];
-    const int nc = tune_candidates(plan, cand, 64);
+    int cand[smerf::kLaunchInts * kMaxCand];
+    const int nc = tune_candidates(plan, cand, kMaxCand);
     plan->tune.valid = 0;
     if (nc == 0) {
         if (chosen)
@@ -744,13 +754,7 @@ int smerf_plan_autotune(smerf_plan* plan, int n_samples, void* stream, int* chos
     float best = 1e30f;
     int bi = -1;
     for (int i = 0; rc == SMERF_OK && i < nc; ++i) {
-        plan->tune.valid = 1;
-        const int* ci = cand + smerf::kLaunchInts * i;
-        plan->tune.upt = ci[0];
-        plan->tune.rmax = ci[1];
-        plan->tune.np = ci[2];
-        plan->tune.nf = ci[3];
-        plan->tune.minb = ci[4];
+        set_tune(plan, cand + smerf::kLaunchInts * i);
         float tot = 0.0f;
         for (int it = 0; rc == SMERF_OK && it < 4; ++it) {
             rc = smerf_launch_sample_staged(plan, 1 + it, n_samples, out, scratch,
@@ -767,13 +771,8 @@ int smerf_plan_autotune(smerf_plan* plan, int n_samples, void* stream, int* chos
     }
     plan->tune.valid = 0;
     if (rc == SMERF_OK && bi >= 0) {
-        plan->tune.valid = 1;
         const int* cb = cand + smerf::kLaunchInts * bi;
-        plan->tune.upt = cb[0];
-        plan->tune.rmax = cb[1];
-        plan->tune.np = cb[2];
-        plan->tune.nf = cb[3];
-        plan->tune.minb = cb[4];
+        set_tune(plan, cb);
         plan->tune.ms = best / 3.0f;
         if (chosen)
             for (int k = 0; k < smerf::kLaunchInts; ++k) chosen[k] = cb[k];

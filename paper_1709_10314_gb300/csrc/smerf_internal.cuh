@@ -72,7 +72,7 @@ struct smerf_plan {
     long long* rings_off_dev;
     long long rings_total;
     // launch parameters chosen by smerf_plan_autotune (valid = 0: built-in heuristic)
-    struct { int valid, upt, rmax, np, nf, minb; float ms; } tune;
+    struct { int valid, upt, rmax, np, nf, minb, radix; float ms; } tune;
 };
 
 namespace smerf {
@@ -106,6 +106,7 @@ struct SampleParams {
     int pingpong;     // 1: two FFT buffers + right anchors on chip; 0: one buffer, in place
     int np;           // warp-specialised kernel: producer threads
     int lgNc;
+    int fft_r4;       // warp-specialised kernel, FP32: 1 = radix-4 FFT passes, 0 = the high-radix plan
     // iso-latitude grid with ring-dependent longitudes (null: the full n_theta x n_phi grid):
     // ring k holds ring_n[k] points from phi0 = ring_h[k] pi, at ring_off[k] within a
     // realisation of ring_total points

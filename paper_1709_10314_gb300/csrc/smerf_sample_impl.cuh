@@ -43,7 +43,9 @@ namespace smerf {
 constexpr int kWsMaxThreads = SMERF_WS_MAXT;
 // Thread limit of the warp-specialised kernels built for MINB resident CTAs per SM: one CTA
 // gets 65536 / SMERF_WS_MAXT registers per thread, two get 64 (512 threads each).
-__host__ __device__ constexpr int ws_max_threads(int minb) { return minb == 1 ? kWsMaxThreads : 512; }
+// p = 3 (12 state values and two 24-value table rows per unit) is built for at most 512 threads
+// (128 registers) with one CTA per SM.
+__host__ __device__ constexpr int ws_max_threads(int minb, int M = 1) { return minb == 1 && M != 3 ? kWsMaxThreads : 512; }
 
 template <int M> constexpr int kG = unit_slots(M);
 
@@ -1342,9 +1344,10 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
                 }
                 if (RINGS && (n_ring != P.n_phi || h_ring != 0.0)) {
                     ragged_ring<Real>(B, W, R, Nc, n_ring, h_ring, pre, P.n_phi, gout.base, gout.stride, ftid, NF);
-                } else if constexpr (sizeof(Real) == 4) {
-                    hr_c2r<C, ws_lg_lo(UPT, M), ws_lg_hi(UPT, M)>(P.lgNc, B, W, R, twp, (const C*)P.tw2, pre, gout,
-                                                                   ftid, NF);
+                } else if (sizeof(Real) == 4 && !P.fft_r4) {
+                    if constexpr (sizeof(Real) == 4)
+                        hr_c2r<C, ws_lg_lo(UPT, M), ws_lg_hi(UPT, M)>(P.lgNc, B, W, R, twp, (const C*)P.tw2, pre, gout,
+                                                                       ftid, NF);
                 } else {
                     grp_c2r_rt<C>(B, W, R, P.lgNc, twp, pre, gout, ftid, NF);
                 }
@@ -1355,7 +1358,7 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
 }
 
 template <class Real, class TabT, int M, int UPT, int RMAX, int MINB>
-__global__ void __launch_bounds__(ws_max_threads(MINB), MINB) segment_ws_kernel(SampleParams P)
+__global__ void __launch_bounds__(ws_max_threads(MINB, M), MINB) segment_ws_kernel(SampleParams P)
 {
     ws_body<Real, TabT, M, UPT, RMAX>(P, blockIdx.y, blockIdx.x);
 }
@@ -1363,7 +1366,7 @@ __global__ void __launch_bounds__(ws_max_threads(MINB), MINB) segment_ws_kernel(
 // batched: item = (request, segment, realisation group); all requests of a launch share the
 // kernel shape (precision, p, n_phi, anchors or not) and hence the launch configuration
 template <class Real, class TabT, int M, int UPT, int RMAX, int MINB>
-__global__ void __launch_bounds__(ws_max_threads(MINB), MINB) segment_ws_batched_kernel(const SampleParams* __restrict__ descs,
+__global__ void __launch_bounds__(ws_max_threads(MINB, M), MINB) segment_ws_batched_kernel(const SampleParams* __restrict__ descs,
                                                                  const int4* __restrict__ items)
 {
     const int4 it = items[blockIdx.x];
@@ -1613,7 +1616,7 @@ int launch_inplace(const SampleParams& P, int n_segments, int nt, size_t smem, c
 // upt (<= 512), FFT threads np/2, rmax realisations per CTA (as many as registers and shared
 // memory allow).  Otherwise the in-place kernel (one FFT buffer, anchors read from the
 // scratch, one realisation per CTA, up to 1024 threads).
-struct SegConfig { int ws, upt, nt, np, rmax, park, minb; size_t smem; int ring; };
+struct SegConfig { int ws, upt, nt, np, rmax, park, minb; size_t smem; int ring; int radix; };
 
 // Long rings with p = 1 in FP32 (Nc = 8192 or 16384): the ring kernel (smerf_ring.cuh), NT =
 // Nc / 16 threads, 8 units per thread of which 6 are parked in shared memory; at Nc = 8192 two
@@ -1664,8 +1667,9 @@ template <class Real> inline bool ws_built(int upt, int rmax, int minb, int M)
 
 // Every warp-specialised configuration that fits the plan, as kLaunchInts integers (units per
 // producer thread, realisations per CTA, producer threads np = units / upt (<= 512, multiple
-// of 32), FFT threads nf in {np/2, np, np/4}, CTAs per SM the kernel is built for; np + nf
-// within that build's thread limit).
+// of 32), FFT threads nf in {np/2, np, np/4}, CTAs per SM the kernel is built for, FFT radix
+// plan; np + nf within that build's thread limit).  Radix plan 16 (the fixed high-radix plan)
+// where the build has one for this ring length (FP32), and 4 (radix-4 passes) always.
 template <class Real>
 inline int tune_candidates(const smerf_plan* pl, int* cand, int max_n)
 {
@@ -1684,16 +1688,24 @@ inline int tune_candidates(const smerf_plan* pl, int* cand, int max_n)
                 for (int d = 0; d < 3; ++d) {
                     int nf = ((np / div[d] + 31) / 32) * 32;
                     if (nf < 32) nf = 32;
-                    if (np + nf > ws_max_threads(minb)) continue;
-                    if (n < max_n) {
-                        int* c = cand + kLaunchInts * n;
-                        c[0] = upt;
-                        c[1] = rmax;
-                        c[2] = np;
-                        c[3] = nf;
-                        c[4] = minb;
+                    if (np + nf > ws_max_threads(minb, pl->p)) continue;
+                    int lg = 0;
+                    while ((2 << lg) < pl->n_phi) ++lg;
+                    const int lo = ws_lg_lo(upt, pl->p), hi = ws_lg_hi(upt, pl->p);
+                    const bool hr = sizeof(Real) == 4 && lg >= lo && lg <= hi;
+                    for (int radix : {16, 4}) {
+                        if (radix == 16 && !hr) continue;
+                        if (n < max_n) {
+                            int* c = cand + kLaunchInts * n;
+                            c[0] = upt;
+                            c[1] = rmax;
+                            c[2] = np;
+                            c[3] = nf;
+                            c[4] = minb;
+                            c[5] = radix;
+                        }
+                        ++n;
                     }
-                    ++n;
                 }
             }
         }
@@ -1710,7 +1722,7 @@ inline SegConfig seg_config(const smerf_plan* pl)
     if (pl->tune.valid && ws_built<Real>(pl->tune.upt, pl->tune.rmax, pl->tune.minb, M) &&
         ws_smem<Real>(pl, pl->tune.rmax) <= 226 * 1024 &&
         (n_units + pl->tune.upt - 1) / pl->tune.upt <= pl->tune.np &&
-        pl->tune.np + pl->tune.nf <= ws_max_threads(pl->tune.minb)) {
+        pl->tune.np + pl->tune.nf <= ws_max_threads(pl->tune.minb, M)) {
         cfg.ws = 1;
         cfg.upt = pl->tune.upt;
         cfg.rmax = pl->tune.rmax;
@@ -1718,11 +1730,12 @@ inline SegConfig seg_config(const smerf_plan* pl)
         cfg.np = pl->tune.np;
         cfg.nt = pl->tune.np + pl->tune.nf;
         cfg.smem = ws_smem<Real>(pl, cfg.rmax);
+        cfg.radix = pl->tune.radix;
         return cfg;
     }
     auto np_of = [&](int u) { return (((n_units + u - 1) / u + 31) / 32) * 32; };
     auto nf_of = [](int np) { return np / 2 > 32 ? ((np / 2 + 31) / 32) * 32 : 32; };
-    auto fits = [&](int u) { return np_of(u) <= 512 && np_of(u) + nf_of(np_of(u)) <= kWsMaxThreads; };
+    auto fits = [&](int u) { return np_of(u) <= 512 && np_of(u) + nf_of(np_of(u)) <= ws_max_threads(1, M); };
     int upt = 1;
     while (upt < 8 && !fits(upt)) upt *= 2;
     if (fits(upt)) {
@@ -1738,6 +1751,7 @@ inline SegConfig seg_config(const smerf_plan* pl)
                 cfg.rmax = rmax;
                 cfg.minb = 1;
                 cfg.smem = smem;
+                cfg.radix = sizeof(Real) == 4 ? 16 : 4;
                 return cfg;
             }
         }
@@ -1857,6 +1871,7 @@ int fill_params(const smerf_plan* pl, uint64_t seed, int n, void* out, void* scr
     if (pl->n_segments > 65535) return SMERF_EUNSUPPORTED;
     P.pingpong = cfg.ws;
     P.np = cfg.np;
+    P.fft_r4 = cfg.ws && cfg.radix == 4;
     int lg = 0;
     while ((1 << lg) < P.Nc) ++lg;
     P.lgNc = lg;

@@ -35,7 +35,7 @@ class _Info(ctypes.Structure):
 
 
 _LIB = None
-LAUNCH_INTS = 5  # SMERF_LAUNCH_INTS
+LAUNCH_INTS = 6  # SMERF_LAUNCH_INTS
 
 
 def library_path():
@@ -240,12 +240,13 @@ class Plan:
 
     def launch_candidates(self):
         """smerf_plan_launch_candidates: list of (units/thread, realisations/CTA, producer
-        threads, FFT threads, CTAs per SM)."""
-        buf = (ctypes.c_int * (LAUNCH_INTS * 64))()
-        n = _lib().smerf_plan_launch_candidates(self._h, buf, 64)
+        threads, FFT threads, CTAs per SM, FFT radix plan 16 or 4)."""
+        cap = 128
+        buf = (ctypes.c_int * (LAUNCH_INTS * cap))()
+        n = _lib().smerf_plan_launch_candidates(self._h, buf, cap)
         if n < 0:
             _check("smerf_plan_launch_candidates", n)
-        return [tuple(buf[LAUNCH_INTS * i:LAUNCH_INTS * i + LAUNCH_INTS]) for i in range(n)]
+        return [tuple(buf[LAUNCH_INTS * i:LAUNCH_INTS * i + LAUNCH_INTS]) for i in range(min(n, cap))]
 
     def set_launch(self, config):
         """smerf_plan_set_launch: fix a launch configuration (None: built-in choice)."""

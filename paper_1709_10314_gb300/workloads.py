@@ -34,14 +34,16 @@ FIXED = {
 }
 
 # Segment-kernel launch configurations (units per producer thread, realisations per CTA,
-# producer threads, FFT threads, CTAs per SM) that smerf_plan_autotune chose on a GB300, per
-# (workload, recursion precision, table precision); bench.py uses them unless asked to re-tune.
+# producer threads, FFT threads, CTAs per SM, FFT radix plan) that smerf_plan_autotune chose on
+# a GB300, per (workload, recursion precision, table precision); bench.py uses them unless asked
+# to re-tune.
 TUNED_LAUNCH = {
-    ("1024x2048-p2", "fp32", "fp64"): (4, 1, 256, 64, 2),
-    ("1024x2048-p2", "fp32", "fp32"): (4, 1, 256, 64, 2),
-    ("1024x2048-p2", "fp64", "fp64"): (4, 1, 256, 128, 1),
-    ("4096x8192-p1", "fp32", "fp64"): (4, 1, 512, 256, 1),
-    ("plain-64x128-p1-fp64", "fp64", "fp64"): (1, 1, 32, 32, 1),
+    ("1024x2048-p2", "fp32", "fp64"): (4, 1, 256, 64, 2, 16),
+    ("1024x2048-p2", "fp32", "fp32"): (4, 1, 256, 64, 2, 16),
+    ("1024x2048-p2", "fp64", "fp64"): (4, 1, 256, 128, 1, 4),
+    ("1024x2048-p3", "fp32", "fp64"): (2, 1, 256, 128, 1, 16),
+    ("4096x8192-p1", "fp32", "fp64"): (4, 1, 512, 256, 1, 16),
+    ("plain-64x128-p1-fp64", "fp64", "fp64"): (1, 1, 32, 32, 1, 4),
 }
 
 

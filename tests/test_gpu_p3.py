@@ -2,8 +2,9 @@
 chain, Eqs. (trans_matrix), (innov_matrix), (state_space)).  The CUDA path through the C ABI
 against the oracle on the same seeded inputs, element by element: FP64 recursion within 1e-10
 of the field std on small grids in both orders, FP32 recursion within 1e-4; the launch
-candidates (one to eight units per producer thread) bit for bit against the built-in choice;
-batches holding p = 3 requests against single calls."""
+candidates (one to eight units per producer thread) with the built-in FFT radix plan bit for bit
+against the built-in choice, the other radix plan to rounding; batches holding p = 3 requests
+against single calls."""
 import numpy as np
 import pytest
 
@@ -88,7 +89,10 @@ def test_fp32_long_rings_every_candidate(n_theta, n_phi, H, n):
         plan.set_launch(cfg)
         got = plan.sample(13, n)
         torch.cuda.synchronize()
-        assert torch.equal(got, ref_gpu), cfg
+        if cfg[5] == 16:   # the built-in radix plan
+            assert torch.equal(got, ref_gpu), cfg
+        else:
+            assert rel_err(got.cpu().numpy(), ref, float(np.std(ref))) < 1e-4, cfg
     plan.set_launch(None)
 
 
@@ -101,9 +105,14 @@ def test_every_candidate_gives_the_same_field(flags_name):
     torch.cuda.synchronize()
     cands = plan.launch_candidates()
     assert len(cands) >= 2 and all(c[1] == 1 and c[4] == 1 for c in cands)
+    default_radix = 4 if flags_name == "fp64" else 16
     for cfg in cands:
         plan.set_launch(cfg)
-        assert torch.equal(plan.sample(4, 3), ref), cfg
+        got = plan.sample(4, 3)
+        if cfg[5] == default_radix:
+            assert torch.equal(got, ref), cfg
+        else:
+            assert float((got.double() - ref.double()).abs().max() / ref.double().std()) < 1e-5, cfg
     plan.set_launch(None)
 
 

@@ -27,8 +27,8 @@ from gpu_util import oracle_field, rel_err
 pytestmark = pytest.mark.gpu
 
 KAPPA2 = (20.0, 50.0)
-C2_LAUNCH = {("fp32", "fp64"): (4, 1, 256, 64, 2), ("fp32", "fp32"): (4, 1, 256, 64, 2),
-             ("fp64", "fp64"): (4, 1, 256, 128, 1)}
+C2_LAUNCH = {("fp32", "fp64"): (4, 1, 256, 64, 2, 16), ("fp32", "fp32"): (4, 1, 256, 64, 2, 16),
+             ("fp64", "fp64"): (4, 1, 256, 128, 1, 4)}
 
 
 def _plan(kappa, nt, nphi, recur, tables, H, launch=None):

@@ -1,8 +1,9 @@
 """Launch-configuration autotuning: every candidate configuration of the segment kernel
 (units per producer thread, realisations per CTA, producer and FFT threads, CTAs per SM the
-kernel is built for) produces the same
-field as the built-in choice, the autotuner picks one of the candidates, a fixed choice can be
-set and cleared, and a batch mixing a tuned and an untuned plan of one shape is still exact."""
+kernel is built for, FFT radix plan) with the same radix plan produces the same field bit for
+bit, the built-in choice among them; the two radix plans agree to FP32 rounding; the autotuner
+picks one of the candidates, a fixed choice can be set and cleared, and a batch mixing a tuned
+and an untuned plan of one shape is still exact."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -24,13 +25,21 @@ def test_every_candidate_gives_the_same_field(flags_name):
         assert len(cands) >= 1
         ref = plan.sample(7, 5)   # 5 realisations: a ragged last group for 2 and 4 per CTA
         torch.cuda.synchronize()
+        by_radix = {}
         for cfg in cands:
-            upt, rmax, n_prod, n_fft, per_sm = cfg
+            upt, rmax, n_prod, n_fft, per_sm, radix = cfg
             assert n_prod % 32 == 0 and n_fft % 32 == 0 and n_prod + n_fft <= (768 if per_sm == 1 else 512)
+            assert radix in (16, 4) and (radix == 4 or flags_name != "fp64")
             plan.set_launch(cfg)
             got = plan.sample(7, 5)
             torch.cuda.synchronize()
-            assert torch.equal(got, ref), (flags_name, kappa, n_phi, cfg)
+            first = by_radix.setdefault(radix, got)
+            assert torch.equal(got, first), (flags_name, kappa, n_phi, cfg)
+        # the built-in choice: the high-radix plan where there is one (FP32), else radix 4
+        assert torch.equal(ref, by_radix[16] if 16 in by_radix else by_radix[4])
+        if len(by_radix) == 2:
+            d = (by_radix[16].double() - by_radix[4].double()).abs().max() / ref.double().std()
+            assert float(d) < 1e-5, float(d)
         plan.set_launch(None)
         assert torch.equal(plan.sample(7, 5), ref)
 
@@ -41,19 +50,27 @@ def test_autotune_picks_a_candidate():
     ref = plan.sample(3, 4)
     chosen = plan.autotune(8)
     assert chosen in plan.launch_candidates()
+    got = plan.sample(3, 4)
     torch.cuda.synchronize()
-    assert torch.equal(plan.sample(3, 4), ref)
+    if chosen[5] == 16:   # the built-in radix plan: the same field bit for bit
+        assert torch.equal(got, ref)
+    else:
+        assert float((got.double() - ref.double()).abs().max() / ref.double().std()) < 1e-5
 
 
 def test_set_launch_rejects_non_candidates():
     from paper_1709_10314_gb300 import SmerfError
     plan = _plan()
     with pytest.raises(SmerfError):
-        plan.set_launch((3, 1, 96, 64, 1))
+        plan.set_launch((3, 1, 96, 64, 1, 16))
     with pytest.raises(SmerfError):
-        plan.set_launch((1, 4, 32, 800, 1))
+        plan.set_launch((1, 4, 32, 800, 1, 16))
     with pytest.raises(SmerfError):
-        plan.set_launch((2, 4, 512, 128, 2))   # not built for two CTAs per SM
+        plan.set_launch((2, 4, 512, 128, 2, 16))   # not built for two CTAs per SM
+    with pytest.raises(SmerfError):
+        plan.set_launch((2, 4, 256, 128, 1, 8))    # no radix-8 plan
+    with pytest.raises(ValueError):
+        plan.set_launch((2, 4, 256, 128, 1))       # six integers
 
 
 def test_batch_with_tuned_and_untuned_plans_of_one_shape():
