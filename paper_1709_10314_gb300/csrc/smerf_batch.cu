@@ -207,6 +207,7 @@ int smerf_batch_create(const smerf_plan* const* plans, const int* n_samples, int
         Group& gr = b->groups[g];
         gr.n_anc = (int)anc[g].size();
         gr.n_seg = (int)seg[g].size();
+        if (queued(gr.kind, gr.rep->p)) continue;  // its items go to the persistent queue below
         if (smerf::dev_malloc((void**)&gr.d_anc, sizeof(int4) * gr.n_anc) != cudaSuccess ||
             smerf::dev_malloc((void**)&gr.d_seg, sizeof(int4) * gr.n_seg) != cudaSuccess) {
             rc = SMERF_ENOMEM;
