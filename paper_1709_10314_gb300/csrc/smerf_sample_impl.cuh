@@ -37,6 +37,10 @@
 #ifndef SMERF_RB
 #define SMERF_RB 1
 #endif
+// Thread limit of the p = 3 warp-specialised kernels (one CTA per SM)
+#ifndef SMERF_P3_MAXT
+#define SMERF_P3_MAXT 512
+#endif
 
 namespace smerf {
 
@@ -45,7 +49,7 @@ constexpr int kWsMaxThreads = SMERF_WS_MAXT;
 // gets 65536 / SMERF_WS_MAXT registers per thread, two get 64 (512 threads each).
 // p = 3 (12 state values and two 24-value table rows per unit) is built for at most 512 threads
 // (128 registers) with one CTA per SM.
-__host__ __device__ constexpr int ws_max_threads(int minb, int M = 1) { return minb == 1 && M != 3 ? kWsMaxThreads : 512; }
+__host__ __device__ constexpr int ws_max_threads(int minb, int M = 1) { return minb == 1 && M != 3 ? kWsMaxThreads : SMERF_P3_MAXT; }
 
 template <int M> constexpr int kG = unit_slots(M);
 
@@ -1273,6 +1277,40 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
                 for (int i = 0; i < UPT; ++i) {
                     const int u = tid + i * NP;
                     if (u >= n_units) continue;
+                    if constexpr (M == 3) {
+                        // p = 3 (one realisation per CTA): the unit's normals first, then one
+                        // 24-value table row at a time, so that two rows are never live together
+                        static_assert(RMAX == 1, "p = 3 builds hold one realisation per CTA");
+                        Real nr[NU];
+                        unit_normals_multi<Real, 1, NC>(rk, (uint32_t)u, (uint32_t)ring, *reinterpret_cast<Real(*)[1][NU]>(nr));
+#pragma unroll
+                        for (int g = 0; g < G; ++g) {
+                            Real tg[ROW];
+                            load_row<Real, TabT, ROW>(tb + (size_t)(G * u + g) * ROW, tg);
+#pragma unroll
+                            for (int part = 0; part < 2; ++part) {
+                                Real(&xs)[M] = *reinterpret_cast<Real(*)[M]>(&x[i][0][g * 2 * M + part * M]);
+                                const Real* xi = nr + g * 2 * M + part * M;
+                                Real xr[M];
+                                if (has_right) {
+#pragma unroll
+                                    for (int q = 0; q < M; ++q) xr[q] = xRs[(size_t)(G * u + g) * 2 * M + part * M + q];
+                                }
+                                if (g == 0 && part == 1 && u == 0) {
+                                    // slot 0, second part: the Nyquist chain (mode Nc, own table row)
+                                    Real tn[ROW];
+                                    load_row<Real, TabT, ROW>(tb + (size_t)Nc * ROW, tn);
+                                    if (has_right) step_state<Real, M, true>(tn, xs, xi, xr);
+                                    else step_state<Real, M, false>(tn, xs, xi, nullptr);
+                                } else if (has_right) {
+                                    step_state<Real, M, true>(tg, xs, xi, xr);
+                                } else {
+                                    step_state<Real, M, false>(tg, xs, xi, nullptr);
+                                }
+                            }
+                        }
+                        continue;
+                    }
                     Real ta[G][ROW];
 #pragma unroll
                     for (int g = 0; g < G; ++g) load_row<Real, TabT, ROW>(tb + (size_t)(G * u + g) * ROW, ta[g]);

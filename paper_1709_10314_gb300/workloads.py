@@ -41,7 +41,7 @@ TUNED_LAUNCH = {
     ("1024x2048-p2", "fp32", "fp64"): (4, 1, 256, 64, 2, 16),
     ("1024x2048-p2", "fp32", "fp32"): (4, 1, 256, 64, 2, 16),
     ("1024x2048-p2", "fp64", "fp64"): (4, 1, 256, 128, 1, 4),
-    ("1024x2048-p3", "fp32", "fp64"): (2, 1, 256, 128, 1, 16),
+    ("1024x2048-p3", "fp32", "fp64"): (4, 1, 128, 32, 1, 16),
     ("4096x8192-p1", "fp32", "fp64"): (4, 1, 512, 256, 1, 16),
     ("plain-64x128-p1-fp64", "fp64", "fp64"): (1, 1, 32, 32, 1, 4),
 }
