@@ -56,21 +56,24 @@ def test_batch_object_reuse_and_groups():
     assert info["launches"] == 6
     b.set_single_launch(True)
     assert b.info()["launches"] == 4
-    b.set_single_launch(False)
-    for seeds in ([1, 2, 3, 4, 5, 6], [100, 200, 300, 400, 500, 600]):
+    for single, seeds in ((False, [1, 2, 3, 4, 5, 6]), (True, [100, 200, 300, 400, 500, 600])):
+        b.set_single_launch(single)
         outs = _outs(plans, counts)
         b.sample(seeds, outs)
+        assert b.status() == 0
         torch.cuda.synchronize()
         for p, s, n, o in zip(plans, seeds, counts, outs):
             assert torch.equal(o, p.sample(s, n))
 
 
-def test_batch_cuda_graph_replay():
+@pytest.mark.parametrize("single", [False, True])
+def test_batch_cuda_graph_replay(single):
     import torch
     from paper_1709_10314_gb300 import Batch
     plans = _plans()[:3]
     counts = [4, 2, 3]
     b = Batch(plans, counts)
+    b.set_single_launch(single)
     outs = _outs(plans, counts)
     b.set([1, 2, 3], outs)
     s = torch.cuda.Stream()
@@ -85,6 +88,7 @@ def test_batch_cuda_graph_replay():
         b.set(seeds, outs)
         g.replay()
         torch.cuda.synchronize()
+        assert b.status() == 0
         for p, sd, n, o in zip(plans, seeds, counts, outs):
             assert torch.equal(o, p.sample(sd, n))
 

@@ -31,7 +31,8 @@ def _rings(out, npr):
 
 
 @pytest.mark.parametrize("fp64", [False, True])
-@pytest.mark.parametrize("kappa,n_theta,n_phi,H", [([6.0], 16, 64, 4), ([3.0, 8.0], 12, 32, 0)])
+@pytest.mark.parametrize("kappa,n_theta,n_phi,H", [([6.0], 16, 64, 4), ([3.0, 8.0], 12, 32, 0),
+                                                 ([2.0, 5.0, 9.0], 14, 64, 3)])
 def test_healpix_like_rings_against_oracle(fp64, kappa, n_theta, n_phi, H):
     import torch
     from paper_1709_10314_gb300 import SMERF_ORDER_PAPER, SMERF_RECUR_FP64, Plan
