@@ -10,8 +10,11 @@
 // Later passes load one twiddle e^{2 pi i kk / (Ns R)} per butterfly (the first row of the
 // per-pass table) and form its powers by repeated products, so the tables a CTA reads stay
 // small enough for L1.  While a ring's FFT runs, the next ring's step rows are prefetched into
-// L2 (cp.async.bulk.prefetch), so the recursion's table loads hit L2.  Only pass 0's stride-16 stores need a swizzle for conflict-free
-// shared memory: its 16-byte chunk q of row r is stored at chunk q ^ (r & 7).
+// L2 (cp.async.bulk.prefetch), so the recursion's table loads hit L2.  Only pass 0's stride-16
+// stores need a swizzle for conflict-free shared memory: its 16-byte chunk q of row r is stored
+// at chunk q ^ (r & 7).  In the 16384-point
+// ring's two radix-8 passes a thread takes two neighbouring butterflies, so that its shared
+// accesses, twiddle loads and the last pass's stores to HBM are 16-byte vector accesses.
 #pragma once
 
 namespace smerf {
@@ -97,6 +100,40 @@ __device__ __forceinline__ void ring_pass(float2* X, const float2* __restrict__ 
 {
     using PP = typename RingPass<LG>::template P<PI>;
     constexpr int R = PP::R, Ns = PP::Ns, NB = PP::NB, KB = PP::KB, NT = RingPass<LG>::NT;
+    if constexpr (LG == 14 && KB == 2 && PI >= 2) {
+        // the radix-8 passes of the 16384-point ring: butterflies j = 2 tid and 2 tid + 1, whose
+        // points, twiddles and outputs are adjacent, so that every shared, twiddle and output
+        // access is one 16-byte vector access for both (j < NB = 2 NT; Ns >= 256, so both share
+        // one block of Ns and their outputs are neighbours)
+        static_assert(2 * NT == NB && Ns >= 64 && Ns % 2 == 0, "two neighbouring butterflies per thread");
+        float2 v[2][R];
+        const int j = 2 * tid;
+        const int kk = j & (Ns - 1);
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const float4 w = reinterpret_cast<const float4*>(X)[(j + i * NB) >> 1];
+            v[0][i] = make_float2(w.x, w.y);
+            v[1][i] = make_float2(w.z, w.w);
+        }
+        const float4 t = __ldg(reinterpret_cast<const float4*>(tw2 + PP::TW + kk));
+        ring_twiddle<R>(v[0], make_float2(t.x, t.y));
+        dft<float2, R>(v[0]);
+        ring_twiddle<R>(v[1], make_float2(t.z, t.w));
+        dft<float2, R>(v[1]);
+        if constexpr (!PP::LAST) __syncthreads();  // every read of this pass before any write
+        const int idx = (j - kk) * R + kk;
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+            const float4 w = make_float4(v[0][a].x, v[0][a].y, v[1][a].x, v[1][a].y);
+            if constexpr (PP::LAST) __stcs(reinterpret_cast<float4*>(gout + idx + a * Ns), w);
+            else reinterpret_cast<float4*>(X)[(idx + a * Ns) >> 1] = w;
+        }
+        if constexpr (!PP::LAST) {
+            __syncthreads();
+            ring_pass<LG, PI + 1>(X, tw2, gout, tid);
+        }
+        return;
+    }
     float2 v[KB][R];
 #pragma unroll
     for (int q = 0; q < KB; ++q) {
