@@ -24,7 +24,8 @@ Pins (tests/test_oracle_*.py, run with -m "not gpu"):
   ring_normals             pinned: KS test against the normal CDF, moment checks
   legendre_row             pinned: scipy.special.lpmv, closed forms for small l
   cov_m                    pinned: closed-form Green's function (Eq. (Jmatrix_efficient))
-                           evaluated independently with mpmath, at grid points
+                           evaluated independently with mpmath, at grid points (one, two and
+                           three spectrum factors; orders up to 16384 at the GPU tests' levels)
   sample / chol            pinned: brute-force Gaussian conditioning (Markov property),
                            sample covariance vs the m-truncated analytic covariance,
                            tiny-grid brute force over (l, m) spherical-harmonic sums,
@@ -32,8 +33,8 @@ Pins (tests/test_oracle_*.py, run with -m "not gpu"):
   dft_ring                 pinned: numpy.fft.irfft (library routine)
   fft_ring                 pinned: numpy.fft.irfft and dft_ring
   recursion_sample         pinned: equals sample() (the dense factor applied to the same
-                           noise) on small grids in both orders, which holds only if the
-                           tables, the parents and the noise layout are all right
+                           noise) on small grids in both orders and for p = 1, 2, 3, which
+                           holds only if the tables, the parents and the noise layout are all right
   ring_values /            pinned: full rings without offset equal sample(); a ring of n_phi/2
   sample_rings             points is every second point of the full ring; an offset of s grid
                            steps is the full ring rolled by s; the field covariance at offset
