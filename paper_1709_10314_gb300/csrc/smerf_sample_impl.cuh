@@ -999,6 +999,41 @@ __device__ __forceinline__ void hr_pass(const C* __restrict__ src, C* __restrict
     constexpr int LGNB = LGNC - LR, nb = 1 << LGNB;
     const C* twp = tw2 + hr_off(LGNC, PASS);
     const int total = R << LGNB;
+    if constexpr (LAST && !FIRST && sizeof(C) == 8 && RP <= 8) {
+        // FP32 last pass of radix up to 8 (two radix-16 butterflies would not fit the register
+        // budget: 4096-point rings measured 12 % slower): a thread takes butterflies j and j + 1
+        // (j even), whose swizzled inputs share one 16-byte pair (hr_swz(j + 1) = hr_swz(j) ^ 1)
+        // and whose twiddles and outputs are neighbours (Ns >= 2): 16-byte shared loads,
+        // twiddle loads and streaming HBM stores
+        static_assert(Ns >= 2 && nb >= 2, "neighbouring butterflies share a block");
+        for (int b = 2 * ftid; b < total; b += 2 * nf) {
+            const int r = b >> LGNB, j = b & (nb - 1);
+            const C* S = src + (r << LGNC);
+            const int kk = j & (Ns - 1);
+            C v0[RP], v1[RP];
+#pragma unroll
+            for (int i = 0; i < RP; ++i) {
+                const int f = hr_swz(j + i * nb);
+                const float4 w = reinterpret_cast<const float4*>(S)[f >> 1];
+                const C lo = cmk<C>(w.x, w.y), hi = cmk<C>(w.z, w.w);
+                v0[i] = (f & 1) ? hi : lo;
+                v1[i] = (f & 1) ? lo : hi;
+            }
+#pragma unroll
+            for (int i = 1; i < RP; ++i) {
+                const float4 t = __ldg(reinterpret_cast<const float4*>(twp + (i - 1) * Ns + kk));
+                v0[i] = cmul(v0[i], cmk<C>(t.x, t.y));
+                v1[i] = cmul(v1[i], cmk<C>(t.z, t.w));
+            }
+            dft<C, RP>(v0);
+            dft<C, RP>(v1);
+            C* D = gout[r] + ((j - kk) << LR) + kk;
+#pragma unroll
+            for (int a = 0; a < RP; ++a)
+                __stcs(reinterpret_cast<float4*>(D + a * Ns), make_float4(v0[a].x, v0[a].y, v1[a].x, v1[a].y));
+        }
+        return;
+    }
     for (int b = ftid; b < total; b += nf) {
         const int r = b >> LGNB, j = b & (nb - 1);
         const C* S = src + (r << LGNC);
