@@ -999,7 +999,7 @@ __device__ __forceinline__ void hr_pass(const C* __restrict__ src, C* __restrict
     constexpr int LGNB = LGNC - LR, nb = 1 << LGNB;
     const C* twp = tw2 + hr_off(LGNC, PASS);
     const int total = R << LGNB;
-    if constexpr (LAST && !FIRST && sizeof(C) == 8 && RP <= 8) {
+    if constexpr (!FIRST && sizeof(C) == 8 && RP <= 8) {
         // FP32 last pass of radix up to 8 (two radix-16 butterflies would not fit the register
         // budget: 4096-point rings measured 12 % slower): a thread takes butterflies j and j + 1
         // (j even), whose swizzled inputs share one 16-byte pair (hr_swz(j + 1) = hr_swz(j) ^ 1)
@@ -1027,10 +1027,22 @@ __device__ __forceinline__ void hr_pass(const C* __restrict__ src, C* __restrict
             }
             dft<C, RP>(v0);
             dft<C, RP>(v1);
-            C* D = gout[r] + ((j - kk) << LR) + kk;
+            const int idx = ((j - kk) << LR) + kk;
+            if constexpr (LAST) {
+                C* D = gout[r] + idx;
 #pragma unroll
-            for (int a = 0; a < RP; ++a)
-                __stcs(reinterpret_cast<float4*>(D + a * Ns), make_float4(v0[a].x, v0[a].y, v1[a].x, v1[a].y));
+                for (int a = 0; a < RP; ++a)
+                    __stcs(reinterpret_cast<float4*>(D + a * Ns), make_float4(v0[a].x, v0[a].y, v1[a].x, v1[a].y));
+            } else {
+                // hr_swz(idx + a Ns + 1) = hr_swz(idx + a Ns) ^ 1 (idx + a Ns even)
+                float4* D = reinterpret_cast<float4*>(dst + (r << LGNC));
+#pragma unroll
+                for (int a = 0; a < RP; ++a) {
+                    const int f = hr_swz(idx + a * Ns);
+                    D[f >> 1] = (f & 1) ? make_float4(v1[a].x, v1[a].y, v0[a].x, v0[a].y)
+                                        : make_float4(v0[a].x, v0[a].y, v1[a].x, v1[a].y);
+                }
+            }
         }
         return;
     }
