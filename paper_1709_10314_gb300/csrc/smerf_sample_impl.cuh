@@ -987,7 +987,9 @@ __device__ __forceinline__ void grp_c2r_rt(C* buf0, C* buf1, int R, int lgNc, co
 // e ^ ((e >> 4) & 15), so that the strided stores of the early passes and the unit-stride
 // loads of the next pass are both free of bank conflicts (hr_swz).  The coefficient buffer
 // the producer fills (first pass input) is in natural order; the last pass writes HBM.
-template <class C, int LGNC, int PASS>
+// PAIR: FP32 passes of radix up to 8 take two neighbouring butterflies per thread (below); the
+// persistent batch kernel, whose register budget is tighter, keeps one
+template <class C, int LGNC, int PASS, bool PAIR = true>
 __device__ __forceinline__ void hr_pass(const C* __restrict__ src, C* __restrict__ dst, int R,
                                         const C* __restrict__ tw2, const C* __restrict__ pre, RingOut<C> gout,
                                         int ftid, int nf)
@@ -999,7 +1001,7 @@ __device__ __forceinline__ void hr_pass(const C* __restrict__ src, C* __restrict
     constexpr int LGNB = LGNC - LR, nb = 1 << LGNB;
     const C* twp = tw2 + hr_off(LGNC, PASS);
     const int total = R << LGNB;
-    if constexpr (!FIRST && sizeof(C) == 8 && RP <= 8) {
+    if constexpr (PAIR && !FIRST && sizeof(C) == 8 && RP <= 8) {
         // FP32 last pass of radix up to 8 (two radix-16 butterflies would not fit the register
         // budget: 4096-point rings measured 12 % slower): a thread takes butterflies j and j + 1
         // (j even), whose swizzled inputs share one 16-byte pair (hr_swz(j + 1) = hr_swz(j) ^ 1)
@@ -1086,28 +1088,28 @@ __device__ __forceinline__ void hr_pass(const C* __restrict__ src, C* __restrict
     }
 }
 
-template <class C, int LGNC, int PASS = 0>
+template <class C, int LGNC, int PASS = 0, bool PAIR = true>
 __device__ __forceinline__ void hr_c2r_fixed(C* src, C* dst, int R, const C* tw2, const C* pre, RingOut<C> gout,
                                              int ftid, int nf)
 {
-    hr_pass<C, LGNC, PASS>(src, dst, R, tw2, pre, gout, ftid, nf);
+    hr_pass<C, LGNC, PASS, PAIR>(src, dst, R, tw2, pre, gout, ftid, nf);
     if constexpr (PASS + 1 < hr_passes(LGNC)) {
         bar_sync(kBarFft, nf);
-        hr_c2r_fixed<C, LGNC, PASS + 1>(dst, src, R, tw2, pre, gout, ftid, nf);
+        hr_c2r_fixed<C, LGNC, PASS + 1, PAIR>(dst, src, R, tw2, pre, gout, ftid, nf);
     }
 }
 
 // high-radix fixed-size FFTs for log2 Nc in [LO, HI], the runtime-size radix-4 one otherwise
-template <class C, int LO, int HI>
+template <class C, int LO, int HI, bool PAIR = true>
 __device__ __forceinline__ void hr_c2r(int lgNc, C* b0, C* b1, int R, const C* twp, const C* tw2, const C* pre,
                                        RingOut<C> gout, int ftid, int nf)
 {
     if constexpr (LO <= HI) {
         if (lgNc == LO) {
-            hr_c2r_fixed<C, LO>(b0, b1, R, tw2, pre, gout, ftid, nf);
+            hr_c2r_fixed<C, LO, 0, PAIR>(b0, b1, R, tw2, pre, gout, ftid, nf);
             return;
         }
-        hr_c2r<C, LO + 1, HI>(lgNc, b0, b1, R, twp, tw2, pre, gout, ftid, nf);
+        hr_c2r<C, LO + 1, HI, PAIR>(lgNc, b0, b1, R, twp, tw2, pre, gout, ftid, nf);
     } else {
         grp_c2r_rt<C>(b0, b1, R, lgNc, twp, pre, gout, ftid, nf);
     }
@@ -1250,7 +1252,8 @@ __device__ __noinline__ void ragged_ring(cplx<Real>* B, cplx<Real>* W, int R, in
 // Every FULL/EMPTY barrier counts NP + NF threads; the FFT passes use a group barrier.
 // RINGS: the request may have ring-dependent longitudes (single-request launches; batches never do).
 // CG: the anchor states were written by the same launch (read through L2, not the read-only path).
-template <class Real, class TabT, int M, int UPT, int RMAX, bool RINGS = true, bool CG = false>
+// PAIR: see hr_pass (false in the persistent batch kernels).
+template <class Real, class TabT, int M, int UPT, int RMAX, bool RINGS = true, bool CG = false, bool PAIR = true>
 __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, int group)
 {
     using C = cplx<Real>;
@@ -1431,7 +1434,7 @@ __device__ __forceinline__ void ws_body(const SampleParams& P, int seg_index, in
                     ragged_ring<Real>(B, W, R, Nc, n_ring, h_ring, pre, P.n_phi, gout.base, gout.stride, ftid, NF);
                 } else if (sizeof(Real) == 4 && !P.fft_r4) {
                     if constexpr (sizeof(Real) == 4)
-                        hr_c2r<C, ws_lg_lo(UPT, M), ws_lg_hi(UPT, M)>(P.lgNc, B, W, R, twp, (const C*)P.tw2, pre, gout,
+                        hr_c2r<C, ws_lg_lo(UPT, M), ws_lg_hi(UPT, M), PAIR>(P.lgNc, B, W, R, twp, (const C*)P.tw2, pre, gout,
                                                                        ftid, NF);
                 } else {
                     grp_c2r_rt<C>(B, W, R, P.lgNc, twp, pre, gout, ftid, NF);
@@ -1532,7 +1535,7 @@ template <class Real, class TabT, int SH>
 __device__ __forceinline__ void queue_segment(const SampleParams& P, int seg, int grp)
 {
     constexpr int M = SH / kQueueBuilds + 1, B = SH % kQueueBuilds;
-    ws_body<Real, TabT, M, queue_upt(B), queue_rmax(B), false, true>(P, seg, grp);
+    ws_body<Real, TabT, M, queue_upt(B), queue_rmax(B), false, true, false>(P, seg, grp);
 }
 
 template <class Real, class TabT>
@@ -1600,7 +1603,7 @@ template <class Real, class TabT, int SH>
 __device__ __forceinline__ void queue_segment_after(const SampleParams& P, int seg, int grp)
 {
     constexpr int M = SH / kQueueBuilds + 1, B = SH % kQueueBuilds;
-    ws_body<Real, TabT, M, queue_upt(B), queue_rmax(B), false, false>(P, seg, grp);
+    ws_body<Real, TabT, M, queue_upt(B), queue_rmax(B), false, false, false>(P, seg, grp);
 }
 
 template <class Real, class TabT>
