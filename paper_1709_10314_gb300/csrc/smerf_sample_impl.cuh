@@ -171,6 +171,9 @@ __device__ __forceinline__ void load_row(const TabT* p, Real (&t)[ROW])
 // ------------------------------------------------------------------ anchors
 // anchors whose table values and normals are fetched ahead of the one being stepped
 __host__ __device__ constexpr int anchor_ahead(int M) { return M == 1 ? 4 : M == 2 ? 2 : 1; }
+// resident 128-thread blocks per SM the anchor kernels are built for: FP64 and p = 3 (whose
+// fetched-ahead tables are 60 values) with the registers of four, FP32 p <= 2 seven
+__host__ __device__ constexpr int anchor_minb(int real_bytes, int M) { return real_bytes == 8 || M == 3 ? 4 : SMERF_ANCHOR_MINB; }
 
 // Work an anchor thread carries out beside its anchors: prologue() before the first anchor,
 // step(j, d) at the end of anchor j's step (d = (j - 1) mod anchor_ahead(M)).  NoStage: none.
@@ -401,7 +404,7 @@ __device__ __forceinline__ void anchor_body(const SampleParams& P, int u, int r,
 
 // one thread per (chain c, realisation r, unit u)
 template <class Real, class TabT, int M>
-__global__ void __launch_bounds__(128, sizeof(Real) == 8 ? 4 : SMERF_ANCHOR_MINB) anchor_kernel(SampleParams P)
+__global__ void __launch_bounds__(128, anchor_minb(sizeof(Real), M)) anchor_kernel(SampleParams P)
 {
     NoStage h;
     anchor_body<Real, TabT, M>(P, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, blockIdx.z, h);
@@ -410,7 +413,7 @@ __global__ void __launch_bounds__(128, sizeof(Real) == 8 ? 4 : SMERF_ANCHOR_MINB
 // anchor_kernel that also converts the plan's FP64 step tables to FP32 (StageCarrier); its
 // anchors read the coarse and start tables already staged as FP32
 template <class Real, class TabT, int M>
-__global__ void __launch_bounds__(128, SMERF_ANCHOR_MINB) anchor_stage_kernel(SampleParams P, StageJob J)
+__global__ void __launch_bounds__(128, anchor_minb(4, M)) anchor_stage_kernel(SampleParams P, StageJob J)
 {
     static_assert(sizeof(Real) == 4 && sizeof(TabT) == 4, "staging converts FP64 tables for FP32 recursion");
     __shared__ __align__(16) double slots[kStageSlots * 128 * kStageGroup];  // [slot][thread][group]
@@ -427,7 +430,7 @@ __global__ void __launch_bounds__(128, SMERF_ANCHOR_MINB) anchor_stage_kernel(Sa
 
 // batched: item = (request, block of 128 units, realisation, chain)
 template <class Real, class TabT, int M>
-__global__ void __launch_bounds__(128, sizeof(Real) == 8 ? 4 : SMERF_ANCHOR_MINB) anchor_batched_kernel(const SampleParams* __restrict__ descs,
+__global__ void __launch_bounds__(128, anchor_minb(sizeof(Real), M)) anchor_batched_kernel(const SampleParams* __restrict__ descs,
                                                              const int4* __restrict__ items)
 {
     const int4 it = items[blockIdx.x];
