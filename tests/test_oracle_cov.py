@@ -122,6 +122,8 @@ KHAT_CASES = [
     # the spectrum of the paper's Sec. 5 example, C_l = (10 + l^2 (l+1)^2)^-1: kappa-hat = +-i sqrt(10)
     ([complex(0.0, math.sqrt(10.0)), complex(0.0, -math.sqrt(10.0))], 16, [0, 1, 5, 16]),
     ([complex(40.0, 300.0), complex(40.0, -300.0)], 32, [0, 7, 32]),
+    # p = 3: the Sec. 5 pair and one real factor (kappa-hat = 25)
+    ([complex(0.0, math.sqrt(10.0)), complex(0.0, -math.sqrt(10.0)), complex(25.0, 0.0)], 16, [0, 3, 16]),
 ]
 
 

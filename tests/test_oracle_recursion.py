@@ -35,6 +35,7 @@ CASES = [
     ([2.0, 5.0, 9.0], 10, 16, 0),     # p = 3
     ([2.0, 5.0, 9.0], 12, 16, 4),
     (oracle.KHat([complex(0.0, math.sqrt(10.0)), complex(0.0, -math.sqrt(10.0))]), 8, 16, 0),  # Sec. 5
+    (oracle.KHat([complex(0.0, math.sqrt(10.0)), complex(0.0, -math.sqrt(10.0)), 25.0]), 9, 16, 3),  # pair + real
 ]
 
 
