@@ -85,13 +85,15 @@ int smerf_plan_create_ex(const double* kappa, int p, double A, int n_theta, int 
  * directly (Eq. (Cl): C_l = A / prod_i (l(l+1) + kappa-hat_i)), which may be complex as in the
  * paper's Sec. 5 example C_l = (10 + l^2 (l+1)^2)^-1, kappa-hat = +-i sqrt(10).
  *   khat_re, khat_im  host arrays of p doubles: real and imaginary parts of kappa-hat_i.
- *                     Either all real and > 0 (the same plan as smerf_plan_create_ex with
- *                     kappa_i = sqrt(kappa-hat_i)), or p = 2 and one complex-conjugate pair
- *                     (a + ib, a - ib), b != 0, for which C_l > 0 at every l.
+ *                     All real and > 0: the same plan as smerf_plan_create_ex with
+ *                     kappa_i = sqrt(kappa-hat_i).  Otherwise every non-real value is directly
+ *                     followed by its conjugate (a + ib, a - ib), b != 0, and the real values
+ *                     are > 0 (p = 2: one pair; p = 3: one pair and one real value, either
+ *                     order), so that C_l > 0 at every l.
  * The set-up runs the same construction in complex arithmetic (l_i, 2F1, the solution
  * matrices, the partial-fraction weights and Gamma factors complex); the tables are real.
  * Other arguments, ownership and errors as for smerf_plan_create_ex (SMERF_EINVAL for other
- * complex patterns, SMERF_EILLCOND when |b| < 5e-7 |kappa-hat|).
+ * complex patterns, SMERF_EILLCOND when two kappa-hat_i lie closer than 1e-6 of the larger).
  */
 int smerf_plan_create_khat(const double* khat_re, const double* khat_im, int p, double A, int n_theta, int n_phi,
                            unsigned flags, int anchor_spacing, smerf_plan** out_plan);

@@ -396,9 +396,23 @@ int smerf_plan_create_khat(const double* khat_re, const double* khat_im, int p, 
         }
         return smerf_plan_create_ex(kappa, p, A, n_theta, n_phi, flags, anchor_spacing, out_plan);
     }
-    // complex kappa-hat: exactly one conjugate pair (p = 2), so that C_l is real and positive
-    if (p != 2 || khat_re[0] != khat_re[1] || khat_im[0] != -khat_im[1]) return SMERF_EINVAL;
-    if (fabs(2.0 * khat_im[0]) < 1e-6 * hypot(khat_re[0], khat_im[0])) return SMERF_EILLCOND;
+    // complex kappa-hat: every non-real value directly followed by its conjugate, the real values
+    // positive, so that C_l = A / prod_i (l(l+1) + kappa-hat_i) is real and positive for every l
+    for (int i = 0; i < p; ++i) {
+        if (khat_im[i] == 0.0) {
+            if (!(khat_re[i] > 0.0)) return SMERF_EINVAL;
+            continue;
+        }
+        if (i + 1 >= p || khat_re[i + 1] != khat_re[i] || khat_im[i + 1] != -khat_im[i]) return SMERF_EINVAL;
+        ++i;
+    }
+    // distinct values (the partial fractions of Eq. (C_ell_efficient) divide by their differences)
+    for (int i = 0; i < p; ++i)
+        for (int j = i + 1; j < p; ++j) {
+            const double d = hypot(khat_re[i] - khat_re[j], khat_im[i] - khat_im[j]);
+            const double s = fmax(hypot(khat_re[i], khat_im[i]), hypot(khat_re[j], khat_im[j]));
+            if (d < 1e-6 * s) return SMERF_EILLCOND;
+        }
     return create_plan(nullptr, khat_re, khat_im, 1, p, A, n_theta, n_phi, flags, anchor_spacing, out_plan);
 }
 

@@ -145,7 +145,8 @@ class Plan:
 
     def __init__(self, kappa=None, A=1.0, n_theta=64, n_phi=128, flags=0, anchor_spacing=0, khat=None):
         """Spectrum C_l = A / prod_i (l(l+1) + kappa-hat_i): real `kappa` (kappa-hat_i =
-        kappa_i^2), or `khat` given directly (real values, or one complex-conjugate pair)."""
+        kappa_i^2), or `khat` given directly (positive real values and adjacent complex-conjugate
+        pairs, e.g. [a + ib, a - ib] or [a + ib, a - ib, c])."""
         L = _lib()
         h = ctypes.c_void_p()
         dp = ctypes.POINTER(ctypes.c_double)

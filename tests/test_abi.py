@@ -97,3 +97,6 @@ def test_khat_validation_without_gpu(lib):
     assert call([1.0, 2.0], [2.0, -2.0], 2) == -1     # real parts differ
     assert call([1.0, 1.0], [1e-9, -1e-9], 2) == -2   # nearly a double root: ill-conditioned
     assert call([-1.0], [0.0], 1) == -1               # real kappa-hat must be > 0
+    assert call([0.0, 0.0, -4.0], [3.0, -3.0, 0.0], 3) == -1   # p = 3: pair and a real value <= 0
+    assert call([0.0, 0.0, 1.0], [3.0, -3.0, 2.0], 3) == -1    # p = 3: pair and an unpaired complex value
+    assert call([5.0, 0.0, 0.0], [0.0, 3.0, 2.0], 3) == -1     # p = 3: real value, then no conjugate pair

@@ -1,5 +1,6 @@
 """Spectra given by kappa-hat, including a complex-conjugate pair (Eq. (Cl); the paper's
-Sec. 5 example C_l = (10 + l^2 (l+1)^2)^-1 has kappa-hat = +-i sqrt(10)): the CUDA path
+Sec. 5 example C_l = (10 + l^2 (l+1)^2)^-1 has kappa-hat = +-i sqrt(10)) alone or beside a real
+factor (p = 3): the CUDA path
 through smerf_plan_create_khat against the oracle on the same seeded noise.  FP64 recursion
 within 1e-10 of the field std, FP32 within 1e-4."""
 import math
@@ -14,6 +15,7 @@ pytestmark = pytest.mark.gpu
 
 SEC5 = (complex(0.0, math.sqrt(10.0)), complex(0.0, -math.sqrt(10.0)))
 PAIR = (complex(40.0, 300.0), complex(40.0, -300.0))
+SEC5_REAL = SEC5 + (complex(25.0, 0.0),)   # p = 3: the Sec. 5 pair and one real factor
 
 
 def _plan(khat, n_theta, n_phi, H, flags=0):
@@ -28,6 +30,8 @@ def _plan(khat, n_theta, n_phi, H, flags=0):
     (SEC5, 32, 64, 4, 3, 9),      # anchored, ragged segments
     (SEC5, 33, 64, 8, 1, 1),      # odd n_theta: start on the equator ring
     (PAIR, 24, 64, 5, 2, 3),
+    (SEC5_REAL, 16, 32, 0, 2, 7),   # p = 3, Alg. 2's order
+    (SEC5_REAL, 21, 64, 4, 3, 8),   # p = 3, anchored, odd n_theta
 ])
 def test_fp64_complex_kappa_hat(khat, n_theta, n_phi, H, n, seed):
     import torch
@@ -50,6 +54,23 @@ def test_fp32_sec5_spectrum_64x128():
     kh = oracle.KHat(SEC5)
     ref = oracle_field(kh, 1.0, 64, 128, 1, 4, 16)
     assert rel_err(got, ref, oracle_std(kh, 1.0, 64, 128)) < 1e-4
+
+
+def test_fp32_pair_and_real_factor():
+    """p = 3 with a complex-conjugate pair and a real factor, FP32 recursion, within 1e-4;
+    the real factor first or last gives the same field (the set-up's partial fractions only
+    change order: FP64 within 1e-10)."""
+    import torch
+    from paper_1709_10314_gb300 import SMERF_RECUR_FP64
+    plan = _plan(SEC5_REAL, 24, 128, 6)
+    got = plan.sample(2, 3).cpu().numpy()
+    torch.cuda.synchronize()
+    kh = oracle.KHat(SEC5_REAL)
+    ref = oracle_field(kh, 1.0, 24, 128, 2, 3, 6)
+    assert rel_err(got, ref, oracle_std(kh, 1.0, 24, 128)) < 1e-4
+    a = _plan(SEC5_REAL, 16, 32, 4, SMERF_RECUR_FP64).sample(3, 2).cpu().numpy()
+    b = _plan((SEC5_REAL[2],) + SEC5, 16, 32, 4, SMERF_RECUR_FP64).sample(3, 2).cpu().numpy()
+    assert rel_err(a, b, float(np.std(b))) < 1e-10
 
 
 def test_real_kappa_hat_is_the_kappa_plan():
