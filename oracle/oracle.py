@@ -239,11 +239,17 @@ def cov_modes(ms, kappa, A, theta, K=6, **level_kw):
 
 
 # ------------------------------------------------------------ grid, order
-def ring_theta(n_theta):
+def ring_theta(n_theta, theta=None):
     """Cell-centred equiangular rings theta_k = pi (k + 1/2) / n_theta, k = 0..n_theta-1
     (north to south).  The paper's grid (Sec. 4) is garbled in print; this is the
-    symmetric reading with no pole rings."""
-    return math.pi * (np.arange(n_theta) + 0.5) / n_theta
+    symmetric reading with no pole rings.  `theta` (n_theta colatitudes, increasing in
+    (0, pi) and symmetric about the equator) replaces them on other iso-latitude grids
+    (Sec. 1 remark: the method needs only rings of constant latitude), e.g. HEALPix."""
+    if theta is None:
+        return math.pi * (np.arange(n_theta) + 0.5) / n_theta
+    th = np.asarray(theta, dtype=np.float64)
+    assert th.shape == (n_theta,)
+    return th
 
 
 def chain_layout(n_theta, H):
@@ -279,14 +285,14 @@ def conditioning_order(n_theta, H):
 
 
 # --------------------------------------------------------------- factor
-def joint_factors(kappa, A, n_theta, n_phi, H=0, K=6, rings=None, modes=None, **level_kw):
+def joint_factors(kappa, A, n_theta, n_phi, H=0, K=6, rings=None, modes=None, theta=None, **level_kw):
     """Dense lower Cholesky factors of every mode's joint state covariance in
     conditioning order (Cholesky = sequential Gaussian conditioning,
     Eqs. (trans_matrix), (innov_matrix), (state_initial)).  `rings` restricts to a
     leading subset of that order, whose factor is the leading block of the full one.
     Returns (order, [Sigma_m], [L_m]) for m in `modes` (default 0..n_phi/2)."""
     order = conditioning_order(n_theta, H) if rings is None else list(rings)
-    th = ring_theta(n_theta)[order]
+    th = ring_theta(n_theta, theta)[order]
     ms = list(range(n_phi // 2 + 1)) if modes is None else list(modes)
     S = cov_modes(ms, kappa, A, th, K=K, **level_kw)
     Ls = [np.linalg.cholesky(S[i]) for i in range(len(ms))]
@@ -334,7 +340,7 @@ def dft_ring(N, re, im):
 
 # --------------------------------------------------------------- sample
 def sample(kappa, A, n_theta, n_phi, seed, n_samples=1, H=0, K=6, rings=None,
-           factors=None, return_coeffs=False, **level_kw):
+           factors=None, return_coeffs=False, theta=None, **level_kw):
     """Realisations j = 0..n_samples-1 with Philox key seed + j.
 
     Returns float64 [n_samples][n_rings][n_phi]: every ring north to south (default),
@@ -348,7 +354,7 @@ def sample(kappa, A, n_theta, n_phi, seed, n_samples=1, H=0, K=6, rings=None,
         order = list(rings)
         assert order == order_full[:len(order)], "rings must be a leading subset of the order"
     if factors is None:
-        factors = joint_factors(kappa, A, n_theta, n_phi, H, K, rings=order, **level_kw)[2]
+        factors = joint_factors(kappa, A, n_theta, n_phi, H, K, rings=order, theta=theta, **level_kw)[2]
     n = len(order)
     out_rings = sorted(order) if rings is None else order
     pos = {r: i for i, r in enumerate(order)}
@@ -384,12 +390,12 @@ def sample(kappa, A, n_theta, n_phi, seed, n_samples=1, H=0, K=6, rings=None,
     return res
 
 
-def mode_variances(kappa, A, n_theta, n_phi, K=6, rings=None, **level_kw):
+def mode_variances(kappa, A, n_theta, n_phi, K=6, rings=None, theta=None, **level_kw):
     """J^m_00(z_k, z_k) = E|g_m(z_k)|^2 for m = 0..n_phi/2 at the given rings
     (Lemma 2.1).  Returns [n_phi/2+1][n_rings]."""
     M = _spec(kappa)[1]
     idx = list(range(n_theta)) if rings is None else list(rings)
-    th = ring_theta(n_theta)[idx]
+    th = ring_theta(n_theta, theta)[idx]
     ms = list(range(n_phi // 2 + 1))
     out = np.zeros((len(ms), len(idx)))
     for i, t in enumerate(th):
@@ -398,11 +404,11 @@ def mode_variances(kappa, A, n_theta, n_phi, K=6, rings=None, **level_kw):
     return out
 
 
-def field_std(kappa, A, n_theta, n_phi, K=6, rings=None):
+def field_std(kappa, A, n_theta, n_phi, K=6, rings=None, theta=None):
     """Root of the ring-mean pointwise variance of the discrete field:
     mean_k [J^0_00 + 2 sum_{0<m<n_phi/2} J^m_00 + J^{n_phi/2}_00 / 2], the variance of
     the m-truncated field with the real-DFT convention (Lemma 2.1)."""
-    V = mode_variances(kappa, A, n_theta, n_phi, K, rings)
+    V = mode_variances(kappa, A, n_theta, n_phi, K, rings, theta=theta)
     Hm = n_phi // 2
     w = np.full(Hm + 1, 2.0)
     w[0] = 1.0
@@ -429,7 +435,7 @@ def order_parents(order):
     return par
 
 
-def recursion_tables(kappa, A, n_theta, n_phi, H=0, K=6, rings=None, modes=None, **level_kw):
+def recursion_tables(kappa, A, n_theta, n_phi, H=0, K=6, rings=None, modes=None, theta=None, **level_kw):
     """Tables of Alg. 2's recursion for every mode and every position of the conditioning
     order (or of its leading subset `rings`), from the oracle's joint covariance: the
     transition onto each parent by Gaussian conditioning (Eq. (trans_matrix)) and, as the
@@ -438,7 +444,7 @@ def recursion_tables(kappa, A, n_theta, n_phi, H=0, K=6, rings=None, modes=None,
     Returns (order, parents, T [n_modes][n_pos][2][M][M], B [n_modes][n_pos][M][M]) for the
     modes `modes` (default 0..n_phi/2)."""
     M = _spec(kappa)[1]
-    order, S, L = joint_factors(kappa, A, n_theta, n_phi, H, K, rings=rings, modes=modes, **level_kw)
+    order, S, L = joint_factors(kappa, A, n_theta, n_phi, H, K, rings=rings, modes=modes, theta=theta, **level_kw)
     par = order_parents(order)
     n = len(order)
     T = np.zeros((len(S), n, 2, M, M))
@@ -497,9 +503,10 @@ def ring_values(c, n, phi0):
 
 
 def sample_rings(kappa, A, n_theta, n_phi_ring, phi0_ring, seed, n_samples=1, H=0, K=6, rings=None,
-                 n_phi=None, **level_kw):
-    """Realisations on an iso-latitude grid with ring-dependent longitudes: ring k (latitude
-    theta_k = pi (k + 1/2) / n_theta) holds n_phi_ring[k] points starting at phi0_ring[k].  The
+                 n_phi=None, theta=None, **level_kw):
+    """Realisations on an iso-latitude grid with ring-dependent longitudes: ring k (colatitude
+    theta_k = pi (k + 1/2) / n_theta, or theta[k]) holds n_phi_ring[k] points starting at
+    phi0_ring[k] (any even count: ring_values evaluates the field at each point).  The
     modes m = 0..n_phi/2 (n_phi defaults to max(n_phi_ring)), their recursion and noise are those
     of sample() on the n_theta x n_phi grid; each ring is synthesised at its own points
     (ring_values).  Returns a list over realisations of lists of ring arrays, rings north to south
@@ -507,7 +514,7 @@ def sample_rings(kappa, A, n_theta, n_phi_ring, phi0_ring, seed, n_samples=1, H=
     n_phi = int(max(n_phi_ring)) if n_phi is None else int(n_phi)
     assert max(n_phi_ring) <= n_phi
     _, X, order = sample(kappa, A, n_theta, n_phi, seed, n_samples, H=H, K=K, rings=rings,
-                         return_coeffs=True, **level_kw)
+                         return_coeffs=True, theta=theta, **level_kw)
     out_rings = sorted(order) if rings is None else list(rings)
     pos = {r: i for i, r in enumerate(order)}
     res = []
