@@ -98,6 +98,21 @@ int smerf_plan_create_ex(const double* kappa, int p, double A, int n_theta, int 
 int smerf_plan_create_khat(const double* khat_re, const double* khat_im, int p, double A, int n_theta, int n_phi,
                            unsigned flags, int anchor_spacing, smerf_plan** out_plan);
 
+/*
+ * smerf_plan_create_theta -- smerf_plan_create_ex on an iso-latitude grid whose rings sit at
+ * the given colatitudes instead of the equiangular theta_k = pi (k + 1/2) / n_theta (the paper's
+ * Sec. 1 remark: the method needs only rings of constant latitude; e.g. HEALPix, whose ring
+ * point counts and offsets smerf_plan_set_rings then sets).
+ *   theta[n_theta]  host array (read during the call): ring colatitudes in radians, strictly
+ *                   increasing inside (0, pi) and symmetric about the equator,
+ *                   |theta[k] + theta[n_theta - 1 - k] - pi| <= 1e-12 pi (the southern chain's
+ *                   steps are the northern ones mirrored, Alg. 1).
+ * Every other argument, the ownership and the errors as for smerf_plan_create_ex (SMERF_EINVAL
+ * for colatitudes that break these rules).
+ */
+int smerf_plan_create_theta(const double* kappa, int p, double A, int n_theta, const double* theta, int n_phi,
+                            unsigned flags, int anchor_spacing, smerf_plan** out_plan);
+
 /* smerf_plan_create -- smerf_plan_create_ex with the default anchor spacing. */
 int smerf_plan_create(const double* kappa, int p, double A, int n_theta, int n_phi,
                       unsigned flags, smerf_plan** out_plan);
@@ -307,10 +322,12 @@ int smerf_plan_info(const smerf_plan* plan, smerf_plan_info_t* info);
 
 /*
  * smerf_plan_set_rings -- iso-latitude grid with ring-dependent longitudes (the paper's Sec. 1
- * remark that the method holds on any iso-latitude grid; HEALPix-like rings).  Ring k keeps its
- * latitude theta_k and holds n_phi_ring[k] points phi = phi0_ring[k] + 2 pi j / n_phi_ring[k],
- * j < n_phi_ring[k]; each n_phi_ring[k] a power of two with 4 <= n_phi_ring[k] <= n_phi of the
- * plan; phi0_ring may be NULL (no offsets).  Host arrays of n_theta values.  The modes
+ * remark that the method holds on any iso-latitude grid; HEALPix rings with the colatitudes of
+ * smerf_plan_create_theta).  Ring k keeps its colatitude theta_k and holds n_phi_ring[k] points
+ * phi = phi0_ring[k] + 2 pi j / n_phi_ring[k], j < n_phi_ring[k]; each n_phi_ring[k] even with
+ * 4 <= n_phi_ring[k] <= n_phi of the plan (a power of two takes a radix-4 FFT, other counts a
+ * direct synthesis, O(n_phi_ring[k]^2) per ring); phi0_ring may be NULL (no offsets).  Host
+ * arrays of n_theta values.  The modes
  * m = 0..n_phi/2, their recursion and noise stay those of the plan; each ring's values are the
  * m-truncated field evaluated at its points: T(phi) = g_0 + 2 sum_{0<m<n_phi/2} Re(g_m e^{i m phi})
  * + Re(g_{n_phi/2}) cos(n_phi phi / 2), so modes above the ring's own Nyquist alias onto it.

@@ -44,6 +44,8 @@ void free_plan_memory(smerf_plan* pl)
     cudaFree(pl->rings_n_dev);
     cudaFree(pl->rings_h_dev);
     cudaFree(pl->rings_off_dev);
+    free(pl->theta_host);
+    cudaFree(pl->theta_dev);
 }
 
 void free_rings(smerf_plan* pl)
@@ -309,7 +311,7 @@ static int check_grid(int p, double A, int n_theta, int n_phi, unsigned flags, i
 
 static int create_plan(const double* kappa, const double* kh_re, const double* kh_im, int complex_spec, int p,
                        double A, int n_theta, int n_phi, unsigned flags, int anchor_spacing, smerf_plan** out_plan,
-                       cudaStream_t st = 0, bool sync = true);
+                       cudaStream_t st = 0, bool sync = true, const double* theta = nullptr);
 
 // smerf_plan_create_ex with the set-up ordered on `st` (sync: wait for it)
 static int create_ex_on(const double* kappa, int p, double A, int n_theta, int n_phi, unsigned flags,
@@ -418,7 +420,7 @@ int smerf_plan_create_khat(const double* khat_re, const double* khat_im, int p, 
 
 static int create_plan(const double* kappa, const double* kh_re, const double* kh_im, int complex_spec, int p,
                        double A, int n_theta, int n_phi, unsigned flags, int anchor_spacing, smerf_plan** out_plan,
-                       cudaStream_t st, bool sync)
+                       cudaStream_t st, bool sync, const double* theta)
 {
     if (p > kMaxP) return SMERF_EUNSUPPORTED;
     if (!is_pow2(n_phi) || n_phi < 8 || n_phi > 32768) return SMERF_EUNSUPPORTED;
@@ -479,6 +481,15 @@ static int create_plan(const double* kappa, const double* kh_re, const double* k
     if (smerf::dev_malloc((void**)&pl->segs_dev, sizeof(Segment) * segs.size()) != cudaSuccess) rc = SMERF_ENOMEM;
     else if (cudaMemcpy(pl->segs_dev, segs.data(), sizeof(Segment) * segs.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         rc = SMERF_ECUDA;
+    if (rc == SMERF_OK && theta) {  // the grid's own ring colatitudes
+        const size_t tb = sizeof(double) * (size_t)n_theta;
+        pl->theta_host = (double*)malloc(tb);
+        if (!pl->theta_host || smerf::dev_malloc((void**)&pl->theta_dev, tb) != cudaSuccess) rc = SMERF_ENOMEM;
+        else {
+            memcpy(pl->theta_host, theta, tb);
+            if (cudaMemcpy(pl->theta_dev, theta, tb, cudaMemcpyHostToDevice) != cudaSuccess) rc = SMERF_ECUDA;
+        }
+    }
     if (rc == SMERF_OK) rc = smerf_setup_tables(pl, st, sync);
     if (rc != SMERF_OK) {
         free_plan_memory(pl);
@@ -487,6 +498,33 @@ static int create_plan(const double* kappa, const double* kh_re, const double* k
     }
     *out_plan = pl;
     return SMERF_OK;
+}
+
+int smerf_plan_create_theta(const double* kappa, int p, double A, int n_theta, const double* theta, int n_phi,
+                            unsigned flags, int anchor_spacing, smerf_plan** out_plan)
+{
+    if (!out_plan) return SMERF_EINVAL;
+    *out_plan = nullptr;
+    if (!kappa || !theta) return SMERF_EINVAL;
+    int rc = check_grid(p, A, n_theta, n_phi, flags, anchor_spacing);
+    if (rc != SMERF_OK) return rc;
+    // increasing colatitudes inside (0, pi), symmetric about the equator (the southern chain's
+    // steps are the northern ones mirrored, Alg. 1)
+    for (int k = 0; k < n_theta; ++k) {
+        if (!isfinite(theta[k]) || !(theta[k] > 0.0) || !(theta[k] < SMERF_PI)) return SMERF_EINVAL;
+        if (k > 0 && !(theta[k] > theta[k - 1])) return SMERF_EINVAL;
+        if (fabs(theta[k] + theta[n_theta - 1 - k] - SMERF_PI) > 1e-12 * SMERF_PI) return SMERF_EINVAL;
+    }
+    for (int i = 0; i < p; ++i)
+        if (!(kappa[i] > 0.0) || !isfinite(kappa[i])) return SMERF_EINVAL;
+    for (int i = 0; i < p; ++i)
+        for (int j = i + 1; j < p; ++j) {
+            const double a = kappa[i] * kappa[i], b = kappa[j] * kappa[j];
+            if (fabs(a - b) < 1e-6 * fmax(a, b)) return SMERF_EILLCOND;
+        }
+    double kr[kMaxP + 1] = {0}, ki[kMaxP + 1] = {0};
+    for (int i = 0; i < p && i <= kMaxP; ++i) kr[i] = kappa[i] * kappa[i];
+    return create_plan(kappa, kr, ki, 0, p, A, n_theta, n_phi, flags, anchor_spacing, out_plan, 0, true, theta);
 }
 
 int smerf_plan_create(const double* kappa, int p, double A, int n_theta, int n_phi, unsigned flags,
@@ -625,7 +663,7 @@ int smerf_plan_set_rings(smerf_plan* plan, const int* n_phi_ring, const double* 
     for (int k = 0; k < plan->n_theta; ++k) {
         const int nk = n_phi_ring[k];
         const double p0 = phi0_ring ? phi0_ring[k] : 0.0;
-        if (!is_pow2(nk) || nk < 4 || nk > plan->n_phi || !isfinite(p0)) return SMERF_EINVAL;
+        if ((nk & 1) || nk < 4 || nk > plan->n_phi || !isfinite(p0)) return SMERF_EINVAL;
         n[k] = nk;
         h[k] = fmod(p0 / SMERF_PI, 2.0);
         off[k] = total;
@@ -821,7 +859,7 @@ int smerf_plan_autotune_anchor(smerf_plan* plan, int n_samples, const int* candi
     for (int i = 0; rc == SMERF_OK && i < n_cand; ++i) {
         smerf_plan* cp = nullptr;
         rc = create_plan(plan->p > 0 ? plan->kappa : nullptr, plan->khat_re, plan->khat_im, plan->complex_spec, plan->p,
-                         plan->A, plan->n_theta, plan->n_phi, plan->flags, candidates[i], &cp);
+                         plan->A, plan->n_theta, plan->n_phi, plan->flags, candidates[i], &cp, 0, true, plan->theta_host);
         if (rc != SMERF_OK) break;
         cp->tune = plan->tune;  // the plan's launch configuration, if it fixed one
         const size_t sb = (smerf_scratch_bytes(cp, n_samples) + 255) / 256 * 256;

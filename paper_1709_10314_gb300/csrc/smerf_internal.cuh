@@ -40,6 +40,10 @@ struct smerf_plan {
     int complex_spec;              // some kappa-hat_i is complex (a conjugate pair)
     double A;
     int n_theta, n_phi, n_modes, n_modes_pad, n_slots;
+    // ring colatitudes of an iso-latitude grid other than the equiangular one (host and device
+    // copies, symmetric about the equator; null: theta_k = pi (k + 1/2) / n_theta)
+    double* theta_host;
+    double* theta_dev;
     int k0;
     unsigned flags;
     int H;                 // effective anchor spacing (0 = none)

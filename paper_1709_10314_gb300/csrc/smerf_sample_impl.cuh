@@ -1230,18 +1230,43 @@ __device__ __forceinline__ void ragged_c2r(C* src, C* dst, int R, int lg, const 
     }
 }
 
+// Rings of an even point count n that is not a power of two (HEALPix polar caps): the real
+// synthesis T_j = Y_0 + (-1)^j Y_{n/2} + 2 sum_{0<q<n/2} Re(Y_q e^{2 pi i q j / n}) of the folded
+// input directly, O(n^2) per ring, each phase reduced exactly (cis_halfturns of (q j mod n)).
+template <class Real>
+__device__ __forceinline__ void ring_direct(const cplx<Real>* W, int R, int n, cplx<Real>* gbase, size_t gstride,
+                                            int ftid, int nf)
+{
+    using C = cplx<Real>;
+    const int Ncp = n / 2;
+    for (int idx = ftid; idx < R * n; idx += nf) {
+        const int r = idx / n, j = idx - r * n;
+        const C* Y = W + (size_t)r * Ncp;
+        Real t = Y[0].x + ((j & 1) ? -Y[0].y : Y[0].y);
+        for (int q = 1; q < Ncp; ++q) {
+            const C e = cis_halfturns<Real>(2.0 * (double)(((long long)q * j) % n) / (double)n);
+            t += (Real)2 * (Y[q].x * e.x - Y[q].y * e.y);
+        }
+        reinterpret_cast<Real*>(gbase + (size_t)r * gstride)[j] = t;
+    }
+}
+
 // A ring whose point count or offset differs from the plan's full ring: fold, then the
-// runtime-size C2R.  Not inlined, so that the warp-specialised bodies (and the batch kernels
-// that hold several of them) keep their register allocation for the full-ring path.
+// runtime-size C2R (n a power of two) or the direct synthesis (other even n).  Not inlined, so
+// that the warp-specialised bodies keep their register allocation for the full-ring path.
 template <class Real>
 __device__ __noinline__ void ragged_ring(cplx<Real>* B, cplx<Real>* W, int R, int Nc, int n, double h,
                                          const cplx<Real>* pre, int n_phi, cplx<Real>* gbase, size_t gstride,
                                          int ftid, int nf)
 {
-    int lg = 0;
-    while ((2 << lg) < n) ++lg;
     ring_fold<Real>(B, W, R, Nc, n, h, ftid, nf);
     bar_sync(kBarFft, nf);
+    if (n & (n - 1)) {
+        ring_direct<Real>(W, R, n, gbase, gstride, ftid, nf);
+        return;
+    }
+    int lg = 0;
+    while ((2 << lg) < n) ++lg;
     ragged_c2r<cplx<Real>>(W, B, R, lg, pre, n_phi / n, RingOut<cplx<Real>>{gbase, gstride}, ftid, nf);
 }
 

@@ -52,7 +52,14 @@ struct Spec {
     double A;
     double kmax;
     int n_theta, k0, n_modes, n_modes_pad;
+    const double* theta;  // device: ring colatitudes (null: equiangular, pi (k + 1/2) / n_theta)
 };
+
+// colatitude of ring k (the plan's table, or the equiangular grid)
+__device__ __host__ inline double ring_colat(const double* theta, int n_theta, int k)
+{
+    return theta ? theta[k] : SMERF_PI * ((double)k + 0.5) / (double)n_theta;
+}
 
 // 2F1(-l, l+1; 1+mu; x) for kappa^2 = k2 (a positive series) as S * 1e250^E.  Terms are
 // taken two at a time with one division: r0 = a0/d0 and r1 = a1/d1 from 1/(d0 d1).
@@ -104,7 +111,7 @@ __device__ inline double hyp_rel(double k2, int mu, double x, double sref_inv, i
 __device__ __host__ inline double chain_theta(const Spec& sp, int c, int pos)
 {
     const int k = (c == 0) ? sp.k0 - pos : sp.n_theta - 1 - sp.k0 - pos;
-    return SMERF_PI * ((double)k + 0.5) / (double)sp.n_theta;
+    return ring_colat(sp.theta, sp.n_theta, k);
 }
 
 // ---------------------------------------------------------------- small matrices
@@ -640,7 +647,7 @@ __global__ void start_kernel(Spec sp, const double* lqa, void* beq, bool tab64)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= sp.n_modes) return;
-    const double th0 = SMERF_PI * ((double)sp.k0 + 0.5) / (double)sp.n_theta;
+    const double th0 = ring_colat(sp.theta, sp.n_theta, sp.k0);
     const double t0 = tan(0.5 * th0);
     const double sx = sin(0.5 * th0), cx = cos(0.5 * th0);
     const double x0 = sx * sx, xb0 = cx * cx;
@@ -813,6 +820,7 @@ struct SpecC {
     cdbl k2[kMaxP], b[kMaxP], lG0[kMaxP];  // kappa-hat_i, b_i, log(Gamma(1+l_i) Gamma(-l_i))
     double A, kmax;
     int n_theta, k0, n_modes, n_modes_pad;
+    const double* theta;  // device: ring colatitudes (null: equiangular)
 };
 
 template <int M> struct MatC { cdbl a[M][M]; };
@@ -906,8 +914,8 @@ __global__ void step_kernel_c(SpecC sp, int len, double* phi, double* qout)
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int pos = blockIdx.y + 1;
     if (m >= sp.n_modes || pos > len) return;
-    const double th1 = SMERF_PI * ((double)(sp.k0 - pos + 1) + 0.5) / (double)sp.n_theta;
-    const double th2 = SMERF_PI * ((double)(sp.k0 - pos) + 0.5) / (double)sp.n_theta;
+    const double th1 = ring_colat(sp.theta, sp.n_theta, sp.k0 - pos + 1);
+    const double th2 = ring_colat(sp.theta, sp.n_theta, sp.k0 - pos);
     const double t1 = tan(0.5 * th1), t2 = tan(0.5 * th2);
     const double u1 = log(t1), u2 = log(t2);
     const double s1 = sin(0.5 * th1), s2 = sin(0.5 * th2);
@@ -970,7 +978,7 @@ __global__ void start_kernel_c(SpecC sp, void* beq, bool tab64)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= sp.n_modes) return;
-    const double th0 = SMERF_PI * ((double)sp.k0 + 0.5) / (double)sp.n_theta;
+    const double th0 = ring_colat(sp.theta, sp.n_theta, sp.k0);
     const double t0 = tan(0.5 * th0);
     const double sx = sin(0.5 * th0), cx = cos(0.5 * th0);
     const double x0 = sx * sx, xb0 = cx * cx;
@@ -1032,6 +1040,7 @@ static SpecC make_spec_c(const smerf_plan* pl)
     sc.k0 = pl->k0;
     sc.n_modes = pl->n_modes;
     sc.n_modes_pad = pl->n_modes_pad;
+    sc.theta = pl->theta_dev;
     return sc;
 }
 
@@ -1087,6 +1096,7 @@ int setup_impl(smerf_plan* pl, cudaStream_t st, bool sync)
     sp.k0 = pl->k0;
     sp.n_modes = pl->n_modes;
     sp.n_modes_pad = pl->n_modes_pad;
+    sp.theta = pl->theta_dev;
 
     const bool t64 = pl->tab64;
     const size_t es = t64 ? 8 : 4;
@@ -1146,7 +1156,7 @@ int setup_impl(smerf_plan* pl, cudaStream_t st, bool sync)
                 // the recurrence in m, but for a first step whose equatorward ring (x > 1/2) would
                 // amplify rounding errors by more than 1e3 over the orders: that one by the
                 // per-mode series
-                const double th = chain_theta(sp, 0, 0), x1 = sin(0.5 * th) * sin(0.5 * th);
+                const double th = ring_colat(pl->theta_host, pl->n_theta, pl->k0), x1 = sin(0.5 * th) * sin(0.5 * th);
                 const bool first_series = x1 > 0.5 && (double)(pl->n_modes - 1) * log(x1 / (1.0 - x1)) > log(1e3);
                 const int first = first_series ? 2 : 1;
                 if (first_series) step_kernel<M><<<dim3(gm, 1), threads, 0, st>>>(sp, 0, 1, phi, qv);

@@ -54,6 +54,8 @@ def _lib():
                                            ctypes.POINTER(vp)]
         L.smerf_plan_create_ex.restype = ip
         L.smerf_plan_create_khat.argtypes = [dp, dp, ip, ctypes.c_double, ip, ip, ctypes.c_uint, ip, ctypes.POINTER(vp)]
+        L.smerf_plan_create_theta.argtypes = [dp, ip, ctypes.c_double, ip, dp, ip, ctypes.c_uint, ip, ctypes.POINTER(vp)]
+        L.smerf_plan_create_theta.restype = ip
         L.smerf_plan_create_khat.restype = ip
         L.smerf_plan_destroy.argtypes = [vp]
         L.smerf_plan_destroy.restype = ip
@@ -143,10 +145,11 @@ class _PlanSpec(ctypes.Structure):
 class Plan:
     """A sampling plan (device-resident conditional-covariance tables)."""
 
-    def __init__(self, kappa=None, A=1.0, n_theta=64, n_phi=128, flags=0, anchor_spacing=0, khat=None):
+    def __init__(self, kappa=None, A=1.0, n_theta=64, n_phi=128, flags=0, anchor_spacing=0, khat=None, theta=None):
         """Spectrum C_l = A / prod_i (l(l+1) + kappa-hat_i): real `kappa` (kappa-hat_i =
         kappa_i^2), or `khat` given directly (positive real values and adjacent complex-conjugate
-        pairs, e.g. [a + ib, a - ib] or [a + ib, a - ib, c])."""
+        pairs, e.g. [a + ib, a - ib] or [a + ib, a - ib, c]).  `theta` (with `kappa`): the ring
+        colatitudes of another iso-latitude grid (smerf_plan_create_theta), e.g. HEALPix."""
         L = _lib()
         h = ctypes.c_void_p()
         dp = ctypes.POINTER(ctypes.c_double)
@@ -159,6 +162,15 @@ class Plan:
                                             int(n_theta), int(n_phi), int(flags), int(anchor_spacing),
                                             ctypes.byref(h)))
             k = np.asarray(kh)
+        elif theta is not None:
+            k = np.ascontiguousarray(np.atleast_1d(kappa), dtype=np.float64)
+            th = np.ascontiguousarray(theta, dtype=np.float64)
+            if th.shape != (int(n_theta),):
+                raise ValueError("theta must hold n_theta colatitudes")
+            _check("smerf_plan_create_theta",
+                   L.smerf_plan_create_theta(k.ctypes.data_as(dp), len(k), float(A), int(n_theta),
+                                             th.ctypes.data_as(dp), int(n_phi), int(flags), int(anchor_spacing),
+                                             ctypes.byref(h)))
         else:
             k = np.ascontiguousarray(np.atleast_1d(kappa), dtype=np.float64)
             _check("smerf_plan_create_ex",

@@ -78,7 +78,7 @@ def test_ring_layout_rejections():
     import torch
     from paper_1709_10314_gb300 import SMERF_TABLES_FP32, Batch, Plan, SmerfError
     plan = Plan([10.0], 1.0, 8, 32, anchor_spacing=4)
-    for bad in ([12] * 8, [2] * 8, [64] * 8):  # not a power of two, fewer than 4, more than n_phi
+    for bad in ([13] * 8, [2] * 8, [64] * 8):  # odd, fewer than 4, more than n_phi
         with pytest.raises(SmerfError) as e:
             plan.set_rings(bad)
         assert e.value.status == -1
@@ -91,3 +91,57 @@ def test_ring_layout_rejections():
         big.set_rings([32768, 16384, 16384, 32768])
     assert e.value.status == -5
     torch.cuda.synchronize()
+
+
+def _healpix(nside):
+    """HEALPix rings (colatitudes, point counts, first-pixel longitudes), the pixelisation's
+    published formulae (Gorski et al. 2005), as in the oracle's own HEALPix tests."""
+    from test_oracle_healpix import healpix_rings
+    return healpix_rings(nside)
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+@pytest.mark.parametrize("nside,n_phi,kappa,H", [(3, 16, [3.0, 7.0], 0), (4, 16, [6.0], 4),
+                                                 (6, 32, [5.0, 12.0], 5), (3, 16, [2.0, 5.0, 9.0], 3)])
+def test_healpix_grid_against_oracle(fp64, nside, n_phi, kappa, H):
+    """Full HEALPix grids: rings at the HEALPix colatitudes (smerf_plan_create_theta) with 4i
+    points in the polar caps and 4 nside in the belt, half-pixel offsets as HEALPix places them
+    (smerf_plan_set_rings; 12-, 20- and 24-point rings take the direct synthesis), every ring of
+    every realisation against the oracle at the same points."""
+    import torch
+    from paper_1709_10314_gb300 import SMERF_ORDER_PAPER, SMERF_RECUR_FP64, Plan
+    th, npr, p0 = _healpix(nside)
+    nt = len(th)
+    flags = (SMERF_RECUR_FP64 if fp64 else 0) | (SMERF_ORDER_PAPER if H == 0 else 0)
+    plan = Plan(kappa, 1.0, nt, n_phi, flags=flags, anchor_spacing=H, theta=list(th))
+    plan.set_rings(npr, p0)
+    assert plan.info()["points_per_sample"] == 12 * nside * nside
+    out = plan.sample(31, 2)
+    torch.cuda.synchronize()
+    got = _rings(out.double().cpu().numpy(), npr)
+    ref = oracle.sample_rings(kappa, 1.0, nt, npr, p0, 31, 2, H=H, n_phi=n_phi, theta=th)
+    std = float(np.std(np.concatenate([np.concatenate(r) for r in ref])))
+    err = max(float(np.max(np.abs(got[j][k] - ref[j][k]))) for j in range(2) for k in range(nt)) / std
+    print("HEALPix nside %d p=%d fp64=%s: max|gpu-oracle|/std = %.2e" % (nside, len(kappa), fp64, err))
+    assert err < (1e-9 if fp64 else 1e-4)
+
+
+def test_colatitudes_given_explicitly_are_the_default_grid():
+    """The equiangular colatitudes passed to smerf_plan_create_theta build the same tables as the
+    default plan: the same field bit for bit."""
+    import torch
+    from paper_1709_10314_gb300 import Plan
+    th = oracle.ring_theta(24)
+    a = Plan([20.0, 50.0], 1.0, 24, 64, anchor_spacing=6).sample(5, 3)
+    b = Plan([20.0, 50.0], 1.0, 24, 64, anchor_spacing=6, theta=list(th)).sample(5, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_colatitude_rejections():
+    from paper_1709_10314_gb300 import Plan, SmerfError
+    th = list(oracle.ring_theta(8))
+    for bad in (th[::-1], [t * 0.9 for t in th], th[:-1] + [math.pi], [0.0] + th[1:]):
+        with pytest.raises(SmerfError) as e:
+            Plan([10.0], 1.0, 8, 32, theta=bad)
+        assert e.value.status == -1
