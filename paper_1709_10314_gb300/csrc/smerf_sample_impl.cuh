@@ -1143,6 +1143,16 @@ template <class Real> __device__ __forceinline__ cplx<Real> cis_halfturns(double
     return cmk<cplx<Real>>(cs, sn);
 }
 
+// e^{2 pi i a / n} for integers 0 <= a < n: the fraction 2a / n in the recursion precision (exact
+// for a power-of-two n, within half an ulp otherwise), then sincospi
+template <class Real> __device__ __forceinline__ cplx<Real> ring_phase(int a, int n)
+{
+    Real sn, cs;
+    if constexpr (sizeof(Real) == 4) sincospif(2.0f * (float)a / (float)n, &sn, &cs);
+    else sincospi(2.0 * (double)a / (double)n, &sn, &cs);
+    return cmk<cplx<Real>>(cs, sn);
+}
+
 // Ring `ring` of n = 2 Ncp points from phi0 = h pi: the C2R input X' (slot 0 = (Y_0, Y_Ncp),
 // slot q = Y_q) of the real field T(phi) = sum_{|m| <= M} c_m e^{i m phi} at its points, where
 // c_0 = g_0, c_{+-m} = g_m, conj g_m (0 < m < M) and c_{+-M} = Re g_M / 2 (the Nyquist mode's real
@@ -1155,17 +1165,25 @@ __device__ __forceinline__ void ring_fold(const cplx<Real>* B, cplx<Real>* W, in
 {
     using C = cplx<Real>;
     const int Ncp = n / 2, M = Nc;
+    // e^{i m phi0} along m = m0 + k n: exact (FP64-reduced) every 16 terms, products by
+    // e^{i n phi0} between, so that rounding grows over at most 16 products
+    const C step = cis_halfturns<Real>(h * n);
     for (int idx = ftid; idx < R * (Ncp + 1); idx += nf) {
         const int r = idx / (Ncp + 1), q = idx - r * (Ncp + 1);
         const C* X = B + (size_t)r * Nc;
         C acc = cmk<C>(0, 0);
-        for (int m = q; m <= M; m += n) {  // m >= 0
+        C e = cmk<C>(1, 0);
+        int k = 0;
+        for (int m = q; m <= M; m += n, ++k) {  // m >= 0
+            e = (k & 15) == 0 ? cis_halfturns<Real>(h * m) : cmul(e, step);
             const C g = m == 0 ? cmk<C>(X[0].x, 0) : (m == M ? cmk<C>((Real)0.5 * X[0].y, 0) : X[m]);
-            acc = cadd(acc, m == 0 ? g : cmul(g, cis_halfturns<Real>(h * m)));
+            acc = cadd(acc, m == 0 ? g : cmul(g, e));
         }
-        for (int m = q == 0 ? n : n - q; m <= M; m += n) {  // the conjugate terms, -m < 0
+        k = 0;
+        for (int m = q == 0 ? n : n - q; m <= M; m += n, ++k) {  // the conjugate terms, -m < 0
+            e = (k & 15) == 0 ? cis_halfturns<Real>(h * m) : cmul(e, step);
             const C g = m == M ? cmk<C>((Real)0.5 * X[0].y, 0) : X[m];
-            acc = cadd(acc, cconj(cmul(g, cis_halfturns<Real>(h * m))));
+            acc = cadd(acc, cconj(cmul(g, e)));
         }
         C* Y = W + (size_t)r * Ncp;
         if (q == 0) Y[0].x = acc.x;
@@ -1208,7 +1226,7 @@ __device__ __forceinline__ void ragged_c2r(C* src, C* dst, int R, int lg, const 
             } else {
                 kk = j & (Ns - 1);
                 for (int i = 0; i < RP; ++i) v[i] = S[j + i * nb];
-                for (int i = 1; i < RP; ++i) v[i] = cmul(v[i], cis_halfturns<Real>(2.0 * i * kk / ((double)Ns * RP)));
+                for (int i = 1; i < RP; ++i) v[i] = cmul(v[i], ring_phase<Real>(i * kk, Ns * RP));
             }
             if (RP == 4) dft4(v);
             else dft2(v[0], v[1]);
@@ -1232,7 +1250,8 @@ __device__ __forceinline__ void ragged_c2r(C* src, C* dst, int R, int lg, const 
 
 // Rings of an even point count n that is not a power of two (HEALPix polar caps): the real
 // synthesis T_j = Y_0 + (-1)^j Y_{n/2} + 2 sum_{0<q<n/2} Re(Y_q e^{2 pi i q j / n}) of the folded
-// input directly, O(n^2) per ring, each phase reduced exactly (cis_halfturns of (q j mod n)).
+// input directly, O(n^2) per ring; the phases e^{2 pi i q j / n} exact (integer reduction of
+// q j mod n) every 16 terms and products by e^{2 pi i j / n} between.
 template <class Real>
 __device__ __forceinline__ void ring_direct(const cplx<Real>* W, int R, int n, cplx<Real>* gbase, size_t gstride,
                                             int ftid, int nf)
@@ -1243,9 +1262,12 @@ __device__ __forceinline__ void ring_direct(const cplx<Real>* W, int R, int n, c
         const int r = idx / n, j = idx - r * n;
         const C* Y = W + (size_t)r * Ncp;
         Real t = Y[0].x + ((j & 1) ? -Y[0].y : Y[0].y);
+        const C w = ring_phase<Real>(j, n);
+        C e = w;
         for (int q = 1; q < Ncp; ++q) {
-            const C e = cis_halfturns<Real>(2.0 * (double)(((long long)q * j) % n) / (double)n);
+            if ((q & 15) == 0) e = ring_phase<Real>((int)(((long long)q * j) % n), n);
             t += (Real)2 * (Y[q].x * e.x - Y[q].y * e.y);
+            e = cmul(e, w);
         }
         reinterpret_cast<Real*>(gbase + (size_t)r * gstride)[j] = t;
     }
