@@ -100,3 +100,27 @@ def test_khat_validation_without_gpu(lib):
     assert call([0.0, 0.0, -4.0], [3.0, -3.0, 0.0], 3) == -1   # p = 3: pair and a real value <= 0
     assert call([0.0, 0.0, 1.0], [3.0, -3.0, 2.0], 3) == -1    # p = 3: pair and an unpaired complex value
     assert call([5.0, 0.0, 0.0], [0.0, 3.0, 2.0], 3) == -1     # p = 3: real value, then no conjugate pair
+
+
+def test_colatitude_validation_without_gpu(lib):
+    """smerf_plan_create_theta rejects colatitudes that are not increasing inside (0, pi) and
+    symmetric about the equator before it touches a GPU."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.smerf_plan_create_theta.restype = ctypes.c_int
+    out = ctypes.c_void_p()
+    n = 8
+    good = [np.pi * (k + 0.5) / n for k in range(n)]
+
+    def call(theta, kappa=(10.0,), nt=n):
+        k = np.ascontiguousarray(kappa, dtype=np.float64)
+        t = np.ascontiguousarray(theta, dtype=np.float64)
+        return lib.smerf_plan_create_theta(k.ctypes.data_as(dp), len(kappa), ctypes.c_double(1.0), nt,
+                                           t.ctypes.data_as(dp), 32, ctypes.c_uint(0), 0, ctypes.byref(out))
+    assert call(good[::-1]) == -1                          # decreasing
+    assert call([t * 0.9 for t in good]) == -1             # not symmetric about the equator
+    assert call([0.0] + good[1:-1] + [np.pi]) == -1        # pole rings
+    assert call(good[:4] + good[3:7]) == -1                # a repeated colatitude
+    assert call(good[:-1] + [float("nan")]) == -1          # not finite
+    assert call(good, kappa=(-1.0,)) == -1                 # kappa <= 0
+    assert call(good, kappa=(3.0, 3.0000000001)) == -2     # near-equal kappa
+    assert not out.value
