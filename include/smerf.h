@@ -223,7 +223,8 @@ int smerf_sample_batched(const smerf_plan* const* plans, const uint64_t* seeds,
  *   records it, which smerf_batch_status reports.  FP64 recursion or p = 3: an anchor and a
  *   segment launch per kernel shape.  Capturable into a CUDA graph: a replay re-reads the staging
  *   memory, so smerf_batch_set between replays changes seeds and outputs.  Requests whose
- *   shape has no batched kernel (n_phi = 32768 in FP32) are launched individually, with their
+ *   shape has no batched kernel (n_phi = 32768 in FP32), and requests whose plan has
+ *   ring-dependent longitudes (smerf_plan_set_rings), are launched individually, with their
  *   seed and output passed by value; a batch that holds such requests returns
  *   SMERF_EUNSUPPORTED when `stream` is capturing (a replay could not see later seeds and
  *   outputs) and launches normally otherwise.
@@ -334,8 +335,10 @@ int smerf_plan_info(const smerf_plan* plan, smerf_plan_info_t* info);
  * Output of a sample call: realisation r's rings back to back, ring k at
  * r * P + sum_{k'<k} n_phi_ring[k'] (P = smerf_plan_info's points_per_sample).  Only plans run by
  * the warp-specialised kernels (n_phi <= 8192 with FP32 recursion, <= 4096 with FP64) take rings
- * (else SMERF_EUNSUPPORTED); such plans cannot join a batch.  n_phi_ring = NULL restores the full
- * grid.  Host only, synchronous; must not run while other calls use the plan.
+ * (else SMERF_EUNSUPPORTED); in a batch such a plan's request is launched individually.
+ * n_phi_ring = NULL restores the full grid.  Host only, synchronous; must not run while other
+ * calls use the plan, nor while a batch made with the plan exists (a batch takes each plan's
+ * ring layout when it is created).
  */
 int smerf_plan_set_rings(smerf_plan* plan, const int* n_phi_ring, const double* phi0_ring);
 

@@ -140,8 +140,6 @@ int smerf_batch_create(const smerf_plan* const* plans, const int* n_samples, int
     if (cudaGetDevice(&dev) != cudaSuccess) return SMERF_ECUDA;
     for (int i = 0; i < n_req; ++i)
         if (!plans[i] || n_samples[i] < 0 || n_samples[i] > 65535 || plans[i]->dev != dev) return SMERF_EINVAL;
-    for (int i = 0; i < n_req; ++i)
-        if (plans[i]->rings_total) return SMERF_EUNSUPPORTED;  // ring-dependent longitudes: single calls only
     smerf_batch* b = new (std::nothrow) smerf_batch;
     if (!b) return SMERF_ENOMEM;
     b->n_req = n_req;
@@ -174,7 +172,9 @@ int smerf_batch_create(const smerf_plan* const* plans, const int* n_samples, int
         const int kind = kind_of(pl);
         rc = fill_params(kind, pl, 0, n, nullptr, (char*)b->scratch + b->offs[i], &b->h_descs[i], &batchable, &rmax);
         if (rc != SMERF_OK || n == 0) continue;
-        if (!batchable) {
+        // ring-dependent longitudes: the batched kernels write whole equiangular rings only, so
+        // such a request is launched as a single call would launch it
+        if (!batchable || pl->rings_total) {
             b->singles.push_back(i);
             continue;
         }

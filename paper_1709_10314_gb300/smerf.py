@@ -389,7 +389,41 @@ def scratch_trim():
     _check("smerf_scratch_trim", _lib().smerf_scratch_trim())
 
 
+def _batch_needs(plans, n_samples):
+    """(dtype, elements) that each request's output must hold."""
+    return [(p.dtype, int(n) * p.points) for p, n in zip(plans, n_samples)]
+
+
+def _check_batch_outs(needs, outs):
+    """The C ABI cannot see a buffer's length.  Request i's output: a tensor of its plan's dtype,
+    dense, with room for its realisations (needs[i] = (dtype, elements)), on the current CUDA
+    device or in page-locked host memory (which the kernels write over the CPU-GPU link); else
+    ValueError."""
+    import torch
+    if len(outs) != len(needs):
+        raise ValueError("%d outputs for %d requests" % (len(outs), len(needs)))
+    cur = None
+    for i, ((dt, need), o) in enumerate(zip(needs, outs)):
+        if not isinstance(o, torch.Tensor):
+            raise ValueError("output %d is not a tensor" % i)
+        if o.is_cuda:
+            cur = torch.cuda.current_device() if cur is None else cur
+            if o.device.index != cur:
+                raise ValueError("output %d is on %s, the current device is cuda:%d" % (i, o.device, cur))
+        elif not o.is_pinned():
+            raise ValueError("output %d is in pageable host memory; use a CUDA or pinned tensor" % i)
+        if o.dtype != dt:
+            raise ValueError("output %d has dtype %s; its plan writes %s" % (i, o.dtype, dt))
+        if not o.is_contiguous():
+            raise ValueError("output %d must be contiguous" % i)
+        if o.numel() < need:
+            raise ValueError("output %d holds %d elements; its realisations need %d" % (i, o.numel(), need))
+
+
 def sample_batched(plans, seeds, n_samples, outs, stream=None):
+    if len(n_samples) != len(plans) or len(seeds) != len(plans) or min([int(v) for v in n_samples] + [0]) < 0:
+        raise ValueError("one seed and one count >= 0 per plan")
+    _check_batch_outs(_batch_needs(plans, n_samples), outs)
     n = len(plans)
     P = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
     S = (ctypes.c_uint64 * n)(*[s & (2**64 - 1) for s in seeds])
@@ -407,11 +441,14 @@ class Batch:
         n = len(plans)
         self._plans = list(plans)  # keep the plans alive
         self.n_samples = [int(v) for v in n_samples]
+        if len(self.n_samples) != n:
+            raise ValueError("%d counts for %d plans" % (len(self.n_samples), n))
         P = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
         N = (ctypes.c_int * n)(*self.n_samples)
         h = ctypes.c_void_p()
         _check("smerf_batch_create", L.smerf_batch_create(P, N, n, ctypes.byref(h)))
         self._h = h
+        self._needs = _batch_needs(plans, self.n_samples)  # the ring layouts the batch was made with
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -425,6 +462,9 @@ class Batch:
             pass
 
     def _arrays(self, seeds, outs):
+        if len(seeds) != len(self._plans):
+            raise ValueError("%d seeds for %d requests" % (len(seeds), len(self._plans)))
+        _check_batch_outs(self._needs, outs)
         n = len(self._plans)
         S = (ctypes.c_uint64 * n)(*[s & (2**64 - 1) for s in seeds])
         O = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])

@@ -124,3 +124,30 @@ def test_colatitude_validation_without_gpu(lib):
     assert call(good, kappa=(-1.0,)) == -1                 # kappa <= 0
     assert call(good, kappa=(3.0, 3.0000000001)) == -2     # near-equal kappa
     assert not out.value
+
+
+def test_batch_output_checks_without_gpu():
+    """The binding checks each batch output against its request before any call: count, tensor,
+    pinned or device memory, dtype, contiguity, length."""
+    import torch
+    from paper_1709_10314_gb300.smerf import _check_batch_outs
+    needs = [(torch.float32, 12), (torch.float64, 6)]
+    ok = [torch.zeros(12), torch.zeros(6, dtype=torch.float64)]
+    for outs in (ok[:1],                                            # one output short of the requests
+                 [ok[0], np.zeros(6)],                              # not a tensor
+                 ok,                                                # pageable host memory
+                 ):
+        with pytest.raises(ValueError):
+            _check_batch_outs(needs, outs)
+    # the remaining checks come after the memory check; on a host without a GPU no tensor is
+    # pinned, so they are reached with the memory check's answer fixed by a stand-in
+    class Pinned(torch.Tensor):
+        def is_pinned(self, *a, **k):
+            return True
+    pin = [o.as_subclass(Pinned) for o in ok]
+    _check_batch_outs(needs, pin)
+    for bad in ([pin[0], pin[1].float().as_subclass(Pinned)],       # dtype
+                [pin[0], torch.zeros(5, dtype=torch.float64).as_subclass(Pinned)],  # too short
+                [torch.zeros(12, 2)[:, 0].as_subclass(Pinned), pin[1]]):           # not contiguous
+        with pytest.raises(ValueError):
+            _check_batch_outs(needs, bad)

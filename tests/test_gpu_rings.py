@@ -76,21 +76,52 @@ def test_full_rings_and_reset():
 
 def test_ring_layout_rejections():
     import torch
-    from paper_1709_10314_gb300 import SMERF_TABLES_FP32, Batch, Plan, SmerfError
+    from paper_1709_10314_gb300 import SMERF_TABLES_FP32, Plan, SmerfError
     plan = Plan([10.0], 1.0, 8, 32, anchor_spacing=4)
     for bad in ([13] * 8, [2] * 8, [64] * 8):  # odd, fewer than 4, more than n_phi
         with pytest.raises(SmerfError) as e:
             plan.set_rings(bad)
         assert e.value.status == -1
-    plan.set_rings([32, 16, 8, 4, 4, 8, 16, 32])
-    with pytest.raises(SmerfError) as e:
-        Batch([plan], [1])
-    assert e.value.status == -5
     big = Plan([300.0], 1.0, 4, 32768, flags=SMERF_TABLES_FP32)  # the ring kernel's size
     with pytest.raises(SmerfError) as e:
         big.set_rings([32768, 16384, 16384, 32768])
     assert e.value.status == -5
     torch.cuda.synchronize()
+
+
+def test_ring_plans_in_a_batch():
+    """A batch launches the requests of ring-dependent plans individually, beside its batched
+    groups; every request's output equals the single call's, bit for bit, in both launch forms."""
+    import torch
+    from paper_1709_10314_gb300 import SMERF_RECUR_FP64, Batch, Plan, sample_batched
+    a = Plan([6.0], 1.0, 16, 64, anchor_spacing=4)
+    b = Plan([3.0, 8.0], 1.0, 12, 32, flags=SMERF_RECUR_FP64, anchor_spacing=4)
+    c = Plan([10.0], 1.0, 32, 64, anchor_spacing=8)  # plain grid: batched
+    for pl, (nt, nphi) in ((a, (16, 64)), (b, (12, 32))):
+        npr, p0 = _healpix_like(nt, nphi)
+        pl.set_rings(npr, p0)
+    plans, counts, seeds = [a, b, c], [3, 2, 2], [7, 8, 9]
+    ref = [p.sample(s, n) for p, s, n in zip(plans, seeds, counts)]
+    bt = Batch(plans, counts)
+    assert bt.info()["singles"] == 2 and bt.info()["groups"] == 1
+    for single in (False, True):
+        bt.set_single_launch(single)
+        outs = [torch.full_like(r, float("nan")) for r in ref]
+        bt.sample(seeds, outs)
+        assert bt.status() == 0
+        torch.cuda.synchronize()
+        for o, r in zip(outs, ref):
+            assert torch.equal(o, r)
+    outs = [torch.full_like(r, float("nan")) for r in ref]
+    sample_batched(plans, seeds, counts, outs)
+    torch.cuda.synchronize()
+    for o, r in zip(outs, ref):
+        assert torch.equal(o, r)
+    # the C ABI cannot see a buffer's length: the binding checks it against the ring layout
+    short = [o[:, :-1].contiguous() if i == 0 else o for i, o in enumerate(outs)]
+    with pytest.raises(ValueError):
+        bt.sample(seeds, short)
+    bt.close()
 
 
 def _healpix(nside):
