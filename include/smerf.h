@@ -104,9 +104,14 @@ int smerf_plan_create_khat(const double* khat_re, const double* khat_im, int p, 
  * Sec. 1 remark: the method needs only rings of constant latitude; e.g. HEALPix, whose ring
  * point counts and offsets smerf_plan_set_rings then sets).
  *   theta[n_theta]  host array (read during the call): ring colatitudes in radians, strictly
- *                   increasing inside (0, pi) and symmetric about the equator,
- *                   |theta[k] + theta[n_theta - 1 - k] - pi| <= 1e-12 pi (the southern chain's
- *                   steps are the northern ones mirrored, Alg. 1).
+ *                   increasing inside (0, pi).  They need not cover the sphere nor be symmetric
+ *                   about the equator (a band of latitudes serves).  On a symmetric grid,
+ *                   |theta[k] + theta[n_theta - 1 - k] - pi| <= 1e-12 pi for every k, both chains
+ *                   start at ring n_theta / 2 and the southern chain's steps are the northern
+ *                   ones mirrored (Alg. 1); on any other grid they start at the ring nearest the
+ *                   equator (the southern one of two at the same distance) and the set-up
+ *                   computes the southern chain's steps on their own (Alg. 2 starts at the
+ *                   equator; a chain may then hold no ring).
  * Every other argument, the ownership and the errors as for smerf_plan_create_ex (SMERF_EINVAL
  * for colatitudes that break these rules).
  */

@@ -30,6 +30,9 @@ Pins (tests/test_oracle_*.py, run with -m "not gpu"):
                            sample covariance vs the m-truncated analytic covariance,
                            tiny-grid brute force over (l, m) spherical-harmonic sums,
                            Im(g_0) and Im(g_{n_phi/2}) invariants
+  start_ring               pinned: the equator ring (or the first south of it) on symmetric
+                           grids, the ring nearest the equator on bands; the recursion from it
+                           equals the dense factor on northern, southern and straddling bands
   dft_ring                 pinned: numpy.fft.irfft (library routine)
   fft_ring                 pinned: numpy.fft.irfft and dft_ring
   recursion_sample         pinned: equals sample() (the dense factor applied to the same
@@ -50,7 +53,7 @@ from . import build as _build
 
 __all__ = [
     "lib", "philox4x32_10", "raw_uint32", "ring_normals", "Cl", "legendre_row",
-    "cov_partial", "cov_m", "default_levels", "ring_theta", "chain_layout",
+    "cov_partial", "cov_m", "default_levels", "ring_theta", "start_ring", "chain_layout",
     "conditioning_order", "normal_index", "joint_factor", "joint_factors", "cov_modes",
     "sample", "field_std", "mode_variances",
     "conditional_tables", "dft_ring", "fft_ring", "KHat",
@@ -243,8 +246,8 @@ def ring_theta(n_theta, theta=None):
     """Cell-centred equiangular rings theta_k = pi (k + 1/2) / n_theta, k = 0..n_theta-1
     (north to south).  The paper's grid (Sec. 4) is garbled in print; this is the
     symmetric reading with no pole rings.  `theta` (n_theta colatitudes, increasing in
-    (0, pi) and symmetric about the equator) replaces them on other iso-latitude grids
-    (Sec. 1 remark: the method needs only rings of constant latitude), e.g. HEALPix."""
+    (0, pi)) replaces them on other iso-latitude grids (Sec. 1 remark: the method needs
+    only rings of constant latitude), e.g. HEALPix, or a band of latitudes."""
     if theta is None:
         return math.pi * (np.arange(n_theta) + 0.5) / n_theta
     th = np.asarray(theta, dtype=np.float64)
@@ -252,14 +255,28 @@ def ring_theta(n_theta, theta=None):
     return th
 
 
-def chain_layout(n_theta, H):
-    """Start ring and the two chains.  k0 = n_theta // 2 (the equator ring for odd
-    n_theta, the first ring south of it for even n_theta); the northern chain visits
+def start_ring(n_theta, theta=None):
+    """Alg. 2 builds outward from the equator.  On a grid symmetric about it (the default
+    grid; given colatitudes with theta_k + theta_{n_theta-1-k} = pi within 1e-12 pi) the
+    start ring is n_theta // 2: the equator ring for odd n_theta, the first ring south of
+    it for even n_theta.  On any other grid it is the ring nearest the equator, the
+    southern one of two at the same distance."""
+    if theta is None:
+        return n_theta // 2
+    th = np.asarray(theta, dtype=np.float64)
+    if all(abs(th[k] + th[n_theta - 1 - k] - math.pi) <= 1e-12 * math.pi for k in range(n_theta)):
+        return n_theta // 2
+    d = [abs(t - math.pi / 2) for t in th]
+    return max(k for k in range(n_theta) if d[k] == min(d))
+
+
+def chain_layout(n_theta, H, theta=None):
+    """Start ring k0 (start_ring) and the two chains: the northern chain visits
     k0-1, ..., 0 and the southern chain k0+1, ..., n_theta-1 (Alg. 2 builds outward
     from the equator).  Anchors sit every H rings along each chain (H <= 0 or
     H >= n_theta: none, which is exactly Alg. 2's order).
     Returns (k0, [north rings], [south rings], [north anchor flags], [south anchor flags])."""
-    k0 = n_theta // 2
+    k0 = start_ring(n_theta, theta)
     north = [k0 - i for i in range(1, k0 + 1)]
     south = [k0 + i for i in range(1, n_theta - k0)]
     use = 0 < H < n_theta
@@ -269,13 +286,13 @@ def chain_layout(n_theta, H):
     return k0, north, south, flags(north), flags(south)
 
 
-def conditioning_order(n_theta, H):
+def conditioning_order(n_theta, H, theta=None):
     """Rings in the order the sampler conditions on them: the start ring, the northern
     anchors outward, the southern anchors outward, then every other northern ring
     outward, then every other southern ring outward.  Each ring's conditional law given
     all earlier rings equals its law given its nearest earlier neighbours (Markov
     property of the state, Sec. 2), which is what the sampler uses."""
-    k0, north, south, fn, fs = chain_layout(n_theta, H)
+    k0, north, south, fn, fs = chain_layout(n_theta, H, theta)
     order = [k0]
     order += [r for r, f in zip(north, fn) if f]
     order += [r for r, f in zip(south, fs) if f]
@@ -291,7 +308,7 @@ def joint_factors(kappa, A, n_theta, n_phi, H=0, K=6, rings=None, modes=None, th
     Eqs. (trans_matrix), (innov_matrix), (state_initial)).  `rings` restricts to a
     leading subset of that order, whose factor is the leading block of the full one.
     Returns (order, [Sigma_m], [L_m]) for m in `modes` (default 0..n_phi/2)."""
-    order = conditioning_order(n_theta, H) if rings is None else list(rings)
+    order = conditioning_order(n_theta, H, theta) if rings is None else list(rings)
     th = ring_theta(n_theta, theta)[order]
     ms = list(range(n_phi // 2 + 1)) if modes is None else list(modes)
     S = cov_modes(ms, kappa, A, th, K=K, **level_kw)
@@ -347,7 +364,7 @@ def sample(kappa, A, n_theta, n_phi, seed, n_samples=1, H=0, K=6, rings=None,
     or the rings of `rings` (a leading subset of the conditioning order) in that order."""
     M = _spec(kappa)[1]
     Hm = n_phi // 2
-    order_full = conditioning_order(n_theta, H)
+    order_full = conditioning_order(n_theta, H, theta)
     if rings is None:
         order = order_full
     else:

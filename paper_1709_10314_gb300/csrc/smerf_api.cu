@@ -444,7 +444,7 @@ static int create_plan(const double* kappa, const double* kh_re, const double* k
     pl->n_slots = n_phi / 2;
     pl->n_modes = n_phi / 2 + 1;
     pl->n_modes_pad = ((pl->n_modes + 31) / 32) * 32;
-    pl->k0 = n_theta / 2;
+    pl->k0 = smerf_start_ring(theta, n_theta);
     pl->flags = flags;
     pl->recur64 = (flags & SMERF_RECUR_FP64) != 0;
     pl->tab64 = (flags & SMERF_TABLES_FP64) ? true : ((flags & SMERF_TABLES_FP32) ? false : pl->recur64);
@@ -481,13 +481,21 @@ static int create_plan(const double* kappa, const double* kh_re, const double* k
     if (smerf::dev_malloc((void**)&pl->segs_dev, sizeof(Segment) * segs.size()) != cudaSuccess) rc = SMERF_ENOMEM;
     else if (cudaMemcpy(pl->segs_dev, segs.data(), sizeof(Segment) * segs.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         rc = SMERF_ECUDA;
-    if (rc == SMERF_OK && theta) {  // the grid's own ring colatitudes
+    if (rc == SMERF_OK && theta) {
+        // the grid's own ring colatitudes; on the device followed by those of the mirrored grid,
+        // pi - theta_{n_theta-1-j}, whose northern chain is the southern chain of a grid that is
+        // not symmetric about the equator (the set-up computes its steps there)
         const size_t tb = sizeof(double) * (size_t)n_theta;
         pl->theta_host = (double*)malloc(tb);
-        if (!pl->theta_host || smerf::dev_malloc((void**)&pl->theta_dev, tb) != cudaSuccess) rc = SMERF_ENOMEM;
+        std::vector<double> both(2 * (size_t)n_theta);
+        for (int j = 0; j < n_theta; ++j) {
+            both[j] = theta[j];
+            both[n_theta + j] = SMERF_PI - theta[n_theta - 1 - j];
+        }
+        if (!pl->theta_host || smerf::dev_malloc((void**)&pl->theta_dev, 2 * tb) != cudaSuccess) rc = SMERF_ENOMEM;
         else {
             memcpy(pl->theta_host, theta, tb);
-            if (cudaMemcpy(pl->theta_dev, theta, tb, cudaMemcpyHostToDevice) != cudaSuccess) rc = SMERF_ECUDA;
+            if (cudaMemcpy(pl->theta_dev, both.data(), 2 * tb, cudaMemcpyHostToDevice) != cudaSuccess) rc = SMERF_ECUDA;
         }
     }
     if (rc == SMERF_OK) rc = smerf_setup_tables(pl, st, sync);
@@ -508,12 +516,11 @@ int smerf_plan_create_theta(const double* kappa, int p, double A, int n_theta, c
     if (!kappa || !theta) return SMERF_EINVAL;
     int rc = check_grid(p, A, n_theta, n_phi, flags, anchor_spacing);
     if (rc != SMERF_OK) return rc;
-    // increasing colatitudes inside (0, pi), symmetric about the equator (the southern chain's
-    // steps are the northern ones mirrored, Alg. 1)
+    // increasing colatitudes inside (0, pi); any such set of rings (the Markov property along the
+    // colatitude holds on every iso-latitude grid, Sec. 2)
     for (int k = 0; k < n_theta; ++k) {
         if (!isfinite(theta[k]) || !(theta[k] > 0.0) || !(theta[k] < SMERF_PI)) return SMERF_EINVAL;
         if (k > 0 && !(theta[k] > theta[k - 1])) return SMERF_EINVAL;
-        if (fabs(theta[k] + theta[n_theta - 1 - k] - SMERF_PI) > 1e-12 * SMERF_PI) return SMERF_EINVAL;
     }
     for (int i = 0; i < p; ++i)
         if (!(kappa[i] > 0.0) || !isfinite(kappa[i])) return SMERF_EINVAL;

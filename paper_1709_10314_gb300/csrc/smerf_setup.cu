@@ -3,8 +3,8 @@
 //
 // Everything lives in the "northern frame": a chain runs from its start angle toward the
 // north pole (theta decreasing).  The southern chain is the mirror image z -> -z of the
-// northern problem (Sec. 4: "negative values follow by symmetry"); its tables act on the
-// mirrored state S x, S = diag((-1)^q).
+// northern problem (Sec. 4 obtains the southern rings from the mirror symmetry); its tables act
+// on the mirrored state S x, S = diag((-1)^q).
 //
 // Notation (Sec. 3).  kappa-hat_i = kappa_i^2 = -l_i (l_i + 1).  For integer order mu,
 //   P^mu_l(z)  = (Q_mu / mu!) t^mu F_mu(x),   P^mu_l(-z) = (Q_mu / mu!) t^-mu F_mu(1-x),
@@ -1137,51 +1137,70 @@ int setup_impl(smerf_plan* pl, cudaStream_t st, bool sync)
     }
     CK(cudaGetLastError());
     {
-        // Step transitions and covariances of the northern chain.  The southern chain's steps are
-        // their mirror images (z -> -z): in the northern frame its step pos is the northern step
-        // pos + shift, shift = 1 for even n_theta (start ring south of the equator) and 0 for
-        // odd n_theta, so one computation serves both chains.
+        // Step transitions and covariances of the northern chain.  On a grid symmetric about the
+        // equator the southern chain's steps are their mirror images (z -> -z): in the northern
+        // frame its step pos is the northern step pos + shift, shift = 1 for even n_theta (start
+        // ring south of the equator) and 0 for odd n_theta, so one computation serves both
+        // chains.  On any other grid a second pass computes them as the northern chain of the
+        // mirrored grid theta'_j = pi - theta_{n_theta-1-j} (stored after the grid's own
+        // colatitudes) from its start ring n_theta - 1 - k0, whose ring k0' - pos is the southern
+        // chain's ring k0 + pos.
         const int len0 = pl->chain[0].len, len1 = pl->chain[1].len;
+        const bool sym = smerf_grid_symmetric(pl->theta_host, pl->n_theta);
         const int shift = (pl->n_theta % 2 == 0) ? 1 : 0;
-        if (len1 + shift > len0) { rc = SMERF_EUNSUPPORTED; goto done; }
-        if (len0 > 0) {
-            const size_t nb = (size_t)(len0 + 1) * pl->n_modes * M * M * sizeof(double);
-            CK(smerf::dev_malloc_async((void**)&phi, nb, st));
-            CK(smerf::dev_malloc_async((void**)&qv, nb, st));
-            if (len0 > 65535) { rc = SMERF_EUNSUPPORTED; goto done; }
-            dim3 grid(gm, len0);
-            if (pl->complex_spec) step_kernel_c<M><<<grid, threads, 0, st>>>(make_spec_c(pl), len0, phi, qv);
-            else if (M == 3) step_kernel<M><<<grid, threads, 0, st>>>(sp, 0, len0, phi, qv);  // per-mode series
-            else {
-                // the recurrence in m, but for a first step whose equatorward ring (x > 1/2) would
-                // amplify rounding errors by more than 1e3 over the orders: that one by the
-                // per-mode series
-                const double th = ring_colat(pl->theta_host, pl->n_theta, pl->k0), x1 = sin(0.5 * th) * sin(0.5 * th);
-                const bool first_series = x1 > 0.5 && (double)(pl->n_modes - 1) * log(x1 / (1.0 - x1)) > log(1e3);
-                const int first = first_series ? 2 : 1;
-                if (first_series) step_kernel<M><<<dim3(gm, 1), threads, 0, st>>>(sp, 0, 1, phi, qv);
-                if (len0 >= first) {
-                    const int n = len0 - first + 1;
-                    if (M == 1) step_kernel_rec<<<(n + kRecWarps - 1) / kRecWarps, 32 * kRecWarps, 0, st>>>(sp, first, len0, phi, qv);
-                    else step_kernel_rec2<<<n, 32, 0, st>>>(sp, first, len0, phi, qv);
-                }
+        if (sym && len1 + shift > len0) { rc = SMERF_EUNSUPPORTED; goto done; }
+        for (int pass = 0; pass < (sym ? 1 : 2); ++pass) {
+            const int len = pass == 0 ? len0 : len1;
+            Spec s = sp;
+            SpecC sc = pl->complex_spec ? make_spec_c(pl) : SpecC();
+            // colatitude of the pass's start ring in its own frame
+            double th = ring_colat(pl->theta_host, pl->n_theta, pl->k0);
+            if (pass == 1) {
+                s.theta = sc.theta = pl->theta_dev + pl->n_theta;
+                s.k0 = sc.k0 = pl->n_theta - 1 - pl->k0;
+                th = SMERF_PI - th;
             }
-            CK(cudaGetLastError());
+            if (len > 0) {
+                const size_t nb = (size_t)(len + 1) * pl->n_modes * M * M * sizeof(double);
+                CK(smerf::dev_malloc_async((void**)&phi, nb, st));
+                CK(smerf::dev_malloc_async((void**)&qv, nb, st));
+                if (len > 65535) { rc = SMERF_EUNSUPPORTED; goto done; }
+                dim3 grid(gm, len);
+                if (pl->complex_spec) step_kernel_c<M><<<grid, threads, 0, st>>>(sc, len, phi, qv);
+                else if (M == 3) step_kernel<M><<<grid, threads, 0, st>>>(s, 0, len, phi, qv);  // per-mode series
+                else {
+                    // the recurrence in m, but for a first step whose equatorward ring (x > 1/2)
+                    // would amplify rounding errors by more than 1e3 over the orders: that one by
+                    // the per-mode series (the start ring is the ring nearest the equator, so no
+                    // later step starts south of it)
+                    const double x1 = sin(0.5 * th) * sin(0.5 * th);
+                    const bool first_series = x1 > 0.5 && (double)(pl->n_modes - 1) * log(x1 / (1.0 - x1)) > log(1e3);
+                    const int first = first_series ? 2 : 1;
+                    if (first_series) step_kernel<M><<<dim3(gm, 1), threads, 0, st>>>(s, 0, 1, phi, qv);
+                    if (len >= first) {
+                        const int n = len - first + 1;
+                        if (M == 1) step_kernel_rec<<<(n + kRecWarps - 1) / kRecWarps, 32 * kRecWarps, 0, st>>>(s, first, len, phi, qv);
+                        else step_kernel_rec2<<<n, 32, 0, st>>>(s, first, len, phi, qv);
+                    }
+                }
+                CK(cudaGetLastError());
+            }
+            // the chains whose tables this pass's steps give: both (symmetric grid), or one
+            for (int c = sym ? 0 : pass; c < (sym ? 2 : pass + 1); ++c) {
+                const int lc = pl->chain[c].len;
+                if (lc == 0) continue;
+                const size_t off = (sym && c == 1) ? (size_t)shift * pl->n_modes * M * M : 0;
+                const int H = pl->H;
+                const int nseg = H > 0 ? (lc / H + 1) : 1;
+                dim3 grid(gm, nseg);
+                segment_tables_kernel<M><<<grid, threads, 0, st>>>(sp, c, lc, H, phi + off, qv + off, pl->steps[c],
+                                                             pl->coarse[c], t64);
+                CK(cudaGetLastError());
+            }
+            if (phi) CK(cudaFreeAsync(phi, st));
+            if (qv) CK(cudaFreeAsync(qv, st));
+            phi = qv = nullptr;
         }
-        for (int c = 0; c < 2; ++c) {
-            const int len = pl->chain[c].len;
-            if (len == 0) continue;
-            const size_t off = c == 0 ? 0 : (size_t)shift * pl->n_modes * M * M;
-            const int H = pl->H;
-            const int nseg = H > 0 ? (len / H + 1) : 1;
-            dim3 grid(gm, nseg);
-            segment_tables_kernel<M><<<grid, threads, 0, st>>>(sp, c, len, H, phi + off, qv + off, pl->steps[c],
-                                                         pl->coarse[c], t64);
-            CK(cudaGetLastError());
-        }
-        CK(cudaFreeAsync(phi, st));
-        CK(cudaFreeAsync(qv, st));
-        phi = qv = nullptr;
     }
     if (M == 1 && pl->packed) {
         // the ring kernel's packed p = 1 layout: [position][A, C, B][mode]
@@ -1216,6 +1235,23 @@ done:
 }
 
 }  // namespace
+
+bool smerf_grid_symmetric(const double* theta, int n_theta)
+{
+    if (!theta) return true;
+    for (int k = 0; k < n_theta; ++k)
+        if (fabs(theta[k] + theta[n_theta - 1 - k] - SMERF_PI) > 1e-12 * SMERF_PI) return false;
+    return true;
+}
+
+int smerf_start_ring(const double* theta, int n_theta)
+{
+    if (smerf_grid_symmetric(theta, n_theta)) return n_theta / 2;
+    int k0 = 0;
+    for (int k = 1; k < n_theta; ++k)
+        if (fabs(theta[k] - 0.5 * SMERF_PI) <= fabs(theta[k0] - 0.5 * SMERF_PI)) k0 = k;
+    return k0;
+}
 
 int smerf_setup_tables(smerf_plan* pl, cudaStream_t st, bool sync)
 {

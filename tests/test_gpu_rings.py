@@ -169,10 +169,44 @@ def test_colatitudes_given_explicitly_are_the_default_grid():
     assert torch.equal(a, b)
 
 
+def _band(lo, hi, n, seed):
+    """n increasing colatitudes from lo to hi with uneven steps."""
+    w = 1.0 + 0.6 * np.random.default_rng(seed).random(n - 1)
+    return list(lo + (hi - lo) * np.concatenate([[0.0], np.cumsum(w) / w.sum()]))
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+@pytest.mark.parametrize("kappa,theta,n_phi,H", [
+    ([6.0], _band(0.2, 1.4, 12, 1), 32, 4),               # northern band: the southern chain is empty
+    ([3.0, 8.0], _band(0.4, 2.9, 15, 2), 64, 0),          # straddling the equator, Alg. 2's order
+    ([2.0, 5.0, 9.0], _band(1.9, 2.9, 10, 3), 32, 3),     # southern band: the northern chain is empty
+    ([20.0], _band(0.3, 1.5, 9, 4) + _band(1.7, 2.0, 4, 5), 256, 3),      # start ring north of the
+    ([20.0, 45.0], _band(0.3, 1.5, 9, 4) + _band(1.7, 2.0, 4, 5), 256, 0),  # equator, many modes
+    ([20.0, 45.0], _band(1.0, 1.45, 5, 6) + _band(1.62, 2.8, 9, 7), 256, 4),  # ... south of it
+])
+def test_band_grid_against_oracle(fp64, kappa, theta, n_phi, H):
+    """Grids that are not symmetric about the equator (a band of latitudes, or rings placed
+    unevenly about the equator; the Sec. 1 remark that any iso-latitude grid serves): the chains
+    start at the ring nearest the equator and the southern chain's steps are computed on their
+    own; every ring of every realisation against the oracle on the same colatitudes."""
+    import torch
+    from paper_1709_10314_gb300 import SMERF_ORDER_PAPER, SMERF_RECUR_FP64, Plan
+    nt = len(theta)
+    flags = (SMERF_RECUR_FP64 if fp64 else 0) | (SMERF_ORDER_PAPER if H == 0 else 0)
+    plan = Plan(kappa, 1.0, nt, n_phi, flags=flags, anchor_spacing=H, theta=theta)
+    out = plan.sample(17, 2)
+    torch.cuda.synchronize()
+    ref = oracle.sample(kappa, 1.0, nt, n_phi, 17, 2, H=H, theta=theta)
+    err = float(np.max(np.abs(out.double().cpu().numpy() - ref))) / float(np.std(ref))
+    print("band k0=%d p=%d fp64=%s: max|gpu-oracle|/std = %.2e" % (
+        oracle.start_ring(nt, theta), len(kappa), fp64, err))
+    assert err < (1e-9 if fp64 else 1e-4)
+
+
 def test_colatitude_rejections():
     from paper_1709_10314_gb300 import Plan, SmerfError
     th = list(oracle.ring_theta(8))
-    for bad in (th[::-1], [t * 0.9 for t in th], th[:-1] + [math.pi], [0.0] + th[1:]):
+    for bad in (th[::-1], th[:-1] + [math.pi], [0.0] + th[1:], th[:4] + th[3:7]):
         with pytest.raises(SmerfError) as e:
             Plan([10.0], 1.0, 8, 32, theta=bad)
         assert e.value.status == -1

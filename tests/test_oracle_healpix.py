@@ -50,13 +50,16 @@ def test_healpix_ring_layout():
     assert np.all(np.diff(th) > 0)
 
 
-def test_healpix_covariance_against_spherical_harmonics():
+@pytest.mark.parametrize("n_rings", [11, 7])
+def test_healpix_covariance_against_spherical_harmonics(n_rings):
     """The covariance of the oracle's field at the HEALPix pixel centres (Nside = 3, modes up to
     the grid's n_phi / 2 = 6, the rings of 4 and 8 points aliasing the modes above their own
     Nyquist) against the direct double sum over (l, m) of C_l Y_lm Y_lm* (|m| < 6) plus the
-    Nyquist mode's real part."""
+    Nyquist mode's real part; on all 11 rings, and on the 7 northern ones (a grid that is not
+    symmetric about the equator)."""
     kappa = [2.0, 5.0]
     th, npr, phi0 = healpix_rings(3)
+    th, npr, phi0 = th[:n_rings], npr[:n_rings], phi0[:n_rings]
     nt, nphi = len(th), 12
     M = nphi // 2
     pts = [(th[k], phi0[k] + 2 * math.pi * j / npr[k]) for k in range(nt) for j in range(npr[k])]
@@ -113,3 +116,40 @@ def test_healpix_samples_are_the_factor_on_the_noise(H):
         for k in range(nt):
             ref = oracle.ring_values(X[j, pos[k]], npr[k], phi0[k])
             assert np.allclose(got[j][k], ref, rtol=0, atol=1e-14)
+
+
+def test_start_ring():
+    """Alg. 2 starts at the equator: n_theta // 2 on a symmetric grid, else the ring nearest it
+    (the southern one of two at the same distance)."""
+    assert oracle.start_ring(9) == 4 and oracle.start_ring(10) == 5
+    th, _, _ = healpix_rings(3)
+    assert oracle.start_ring(11, th) == 5
+    assert oracle.start_ring(4, [0.2, 0.5, 0.9, 1.3]) == 3            # a northern band: its last ring
+    assert oracle.start_ring(3, [2.0, 2.5, 3.0]) == 0                 # a southern band: its first ring
+    assert oracle.start_ring(4, [0.3, 1.5, 1.7, 2.0]) == 1            # straddling, nearer the north
+    h = math.pi / 2
+    assert oracle.start_ring(4, [0.3, h - 0.1, h + 0.1, 2.0]) == 2    # a tie: the southern ring
+    k0, north, south, _, _ = oracle.chain_layout(4, 0, [0.2, 0.5, 0.9, 1.3])
+    assert (k0, north, south) == (3, [2, 1, 0], [])
+
+
+BANDS = [
+    ([4.0], [0.25, 0.4, 0.6, 0.75, 0.95, 1.1, 1.3], 8, 0),              # northern band: one chain
+    ([3.0, 8.0], [0.25, 0.4, 0.6, 0.75, 0.95, 1.1, 1.3], 16, 3),
+    ([2.0, 5.0, 9.0], [0.5, 0.8, 1.2, 1.5, 1.75, 2.1, 2.3, 2.6], 16, 3),  # straddling, uneven steps
+    ([3.0, 8.0], [1.9, 2.1, 2.2, 2.5, 2.8], 16, 0),                     # southern band
+]
+
+
+@pytest.mark.parametrize("kappa,theta,n_phi,H", BANDS)
+def test_band_recursion_equals_dense_factor(kappa, theta, n_phi, H):
+    """On grids that are not symmetric about the equator the recursion from the start ring
+    nearest the equator, with tables from Gaussian conditioning, reproduces the dense factor on
+    the same noise: the order keeps the Markov property (Sec. 2) wherever the chains start."""
+    nt = len(theta)
+    order, par, T, B = oracle.recursion_tables(kappa, 1.0, nt, n_phi, H=H, theta=theta)
+    assert order[0] == oracle.start_ring(nt, theta)
+    got = oracle.recursion_sample(len(kappa), n_phi, order, par, T, B, seed=5, n_samples=2, use_fft=True)
+    ref = oracle.sample(kappa, 1.0, nt, n_phi, seed=5, n_samples=2, H=H, theta=theta)
+    got = got[:, np.argsort(order)]
+    assert np.max(np.abs(got - ref)) <= 1e-10 * np.std(ref)
