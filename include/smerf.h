@@ -118,6 +118,17 @@ int smerf_plan_create_khat(const double* khat_re, const double* khat_im, int p, 
 int smerf_plan_create_theta(const double* kappa, int p, double A, int n_theta, const double* theta, int n_phi,
                             unsigned flags, int anchor_spacing, smerf_plan** out_plan);
 
+/*
+ * smerf_plan_create_khat_theta -- smerf_plan_create_khat (the spectrum by its kappa-hat values,
+ * complex-conjugate pairs allowed) at the ring colatitudes theta[n_theta] of
+ * smerf_plan_create_theta, with the same rules for them.  theta = NULL is SMERF_EINVAL (use
+ * smerf_plan_create_khat for the equiangular grid).  Every other argument, the ownership and the
+ * errors as for smerf_plan_create_khat.
+ */
+int smerf_plan_create_khat_theta(const double* khat_re, const double* khat_im, int p, double A, int n_theta,
+                                 const double* theta, int n_phi, unsigned flags, int anchor_spacing,
+                                 smerf_plan** out_plan);
+
 /* smerf_plan_create -- smerf_plan_create_ex with the default anchor spacing. */
 int smerf_plan_create(const double* kappa, int p, double A, int n_theta, int n_phi,
                       unsigned flags, smerf_plan** out_plan);

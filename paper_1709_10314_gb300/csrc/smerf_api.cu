@@ -313,6 +313,17 @@ static int create_plan(const double* kappa, const double* kh_re, const double* k
                        double A, int n_theta, int n_phi, unsigned flags, int anchor_spacing, smerf_plan** out_plan,
                        cudaStream_t st = 0, bool sync = true, const double* theta = nullptr);
 
+// ring colatitudes of an iso-latitude grid: finite, strictly increasing inside (0, pi) (any such
+// set of rings: the Markov property along the colatitude holds on every iso-latitude grid, Sec. 2)
+static int check_colatitudes(const double* theta, int n_theta)
+{
+    for (int k = 0; k < n_theta; ++k) {
+        if (!isfinite(theta[k]) || !(theta[k] > 0.0) || !(theta[k] < SMERF_PI)) return SMERF_EINVAL;
+        if (k > 0 && !(theta[k] > theta[k - 1])) return SMERF_EINVAL;
+    }
+    return SMERF_OK;
+}
+
 // smerf_plan_create_ex with the set-up ordered on `st` (sync: wait for it)
 static int create_ex_on(const double* kappa, int p, double A, int n_theta, int n_phi, unsigned flags,
                         int anchor_spacing, smerf_plan** out_plan, cudaStream_t st, bool sync)
@@ -375,14 +386,16 @@ int smerf_plan_create_many(const smerf_plan_spec* specs, int n, smerf_plan** out
     return rc;
 }
 
-int smerf_plan_create_khat(const double* khat_re, const double* khat_im, int p, double A, int n_theta, int n_phi,
-                           unsigned flags, int anchor_spacing, smerf_plan** out_plan)
+// smerf_plan_create_khat on the equiangular grid (theta = NULL) or at the given colatitudes
+static int create_khat(const double* khat_re, const double* khat_im, int p, double A, int n_theta,
+                       const double* theta, int n_phi, unsigned flags, int anchor_spacing, smerf_plan** out_plan)
 {
     if (!out_plan) return SMERF_EINVAL;
     *out_plan = nullptr;
     if (!khat_re || !khat_im) return SMERF_EINVAL;
     int rc = check_grid(p, A, n_theta, n_phi, flags, anchor_spacing);
     if (rc != SMERF_OK) return rc;
+    if (theta && check_colatitudes(theta, n_theta) != SMERF_OK) return SMERF_EINVAL;
     if (p > kMaxP) return SMERF_EUNSUPPORTED;
     int complex_spec = 0;
     for (int i = 0; i < p; ++i) {
@@ -396,7 +409,8 @@ int smerf_plan_create_khat(const double* khat_re, const double* khat_im, int p, 
             if (!(khat_re[i] > 0.0)) return SMERF_EINVAL;
             kappa[i] = sqrt(khat_re[i]);
         }
-        return smerf_plan_create_ex(kappa, p, A, n_theta, n_phi, flags, anchor_spacing, out_plan);
+        return theta ? smerf_plan_create_theta(kappa, p, A, n_theta, theta, n_phi, flags, anchor_spacing, out_plan)
+                     : smerf_plan_create_ex(kappa, p, A, n_theta, n_phi, flags, anchor_spacing, out_plan);
     }
     // complex kappa-hat: every non-real value directly followed by its conjugate, the real values
     // positive, so that C_l = A / prod_i (l(l+1) + kappa-hat_i) is real and positive for every l
@@ -415,7 +429,24 @@ int smerf_plan_create_khat(const double* khat_re, const double* khat_im, int p, 
             const double s = fmax(hypot(khat_re[i], khat_im[i]), hypot(khat_re[j], khat_im[j]));
             if (d < 1e-6 * s) return SMERF_EILLCOND;
         }
-    return create_plan(nullptr, khat_re, khat_im, 1, p, A, n_theta, n_phi, flags, anchor_spacing, out_plan);
+    return create_plan(nullptr, khat_re, khat_im, 1, p, A, n_theta, n_phi, flags, anchor_spacing, out_plan, 0, true,
+                       theta);
+}
+
+int smerf_plan_create_khat(const double* khat_re, const double* khat_im, int p, double A, int n_theta, int n_phi,
+                           unsigned flags, int anchor_spacing, smerf_plan** out_plan)
+{
+    return create_khat(khat_re, khat_im, p, A, n_theta, nullptr, n_phi, flags, anchor_spacing, out_plan);
+}
+
+int smerf_plan_create_khat_theta(const double* khat_re, const double* khat_im, int p, double A, int n_theta,
+                                 const double* theta, int n_phi, unsigned flags, int anchor_spacing,
+                                 smerf_plan** out_plan)
+{
+    if (!out_plan) return SMERF_EINVAL;
+    *out_plan = nullptr;
+    if (!theta) return SMERF_EINVAL;
+    return create_khat(khat_re, khat_im, p, A, n_theta, theta, n_phi, flags, anchor_spacing, out_plan);
 }
 
 static int create_plan(const double* kappa, const double* kh_re, const double* kh_im, int complex_spec, int p,
@@ -516,12 +547,7 @@ int smerf_plan_create_theta(const double* kappa, int p, double A, int n_theta, c
     if (!kappa || !theta) return SMERF_EINVAL;
     int rc = check_grid(p, A, n_theta, n_phi, flags, anchor_spacing);
     if (rc != SMERF_OK) return rc;
-    // increasing colatitudes inside (0, pi); any such set of rings (the Markov property along the
-    // colatitude holds on every iso-latitude grid, Sec. 2)
-    for (int k = 0; k < n_theta; ++k) {
-        if (!isfinite(theta[k]) || !(theta[k] > 0.0) || !(theta[k] < SMERF_PI)) return SMERF_EINVAL;
-        if (k > 0 && !(theta[k] > theta[k - 1])) return SMERF_EINVAL;
-    }
+    if (check_colatitudes(theta, n_theta) != SMERF_OK) return SMERF_EINVAL;
     for (int i = 0; i < p; ++i)
         if (!(kappa[i] > 0.0) || !isfinite(kappa[i])) return SMERF_EINVAL;
     for (int i = 0; i < p; ++i)

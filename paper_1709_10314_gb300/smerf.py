@@ -57,6 +57,9 @@ def _lib():
         L.smerf_plan_create_theta.argtypes = [dp, ip, ctypes.c_double, ip, dp, ip, ctypes.c_uint, ip, ctypes.POINTER(vp)]
         L.smerf_plan_create_theta.restype = ip
         L.smerf_plan_create_khat.restype = ip
+        L.smerf_plan_create_khat_theta.argtypes = [dp, dp, ip, ctypes.c_double, ip, dp, ip, ctypes.c_uint, ip,
+                                                   ctypes.POINTER(vp)]
+        L.smerf_plan_create_khat_theta.restype = ip
         L.smerf_plan_destroy.argtypes = [vp]
         L.smerf_plan_destroy.restype = ip
         L.smerf_sample.argtypes = [vp, ctypes.c_uint64, ip, vp, vp]
@@ -148,25 +151,36 @@ class Plan:
     def __init__(self, kappa=None, A=1.0, n_theta=64, n_phi=128, flags=0, anchor_spacing=0, khat=None, theta=None):
         """Spectrum C_l = A / prod_i (l(l+1) + kappa-hat_i): real `kappa` (kappa-hat_i =
         kappa_i^2), or `khat` given directly (positive real values and adjacent complex-conjugate
-        pairs, e.g. [a + ib, a - ib] or [a + ib, a - ib, c]).  `theta` (with `kappa`): the ring
-        colatitudes of another iso-latitude grid (smerf_plan_create_theta), e.g. HEALPix."""
+        pairs, e.g. [a + ib, a - ib] or [a + ib, a - ib, c]).  `theta`: the ring colatitudes of
+        another iso-latitude grid (smerf_plan_create_theta, smerf_plan_create_khat_theta), e.g.
+        HEALPix or a band of latitudes."""
         L = _lib()
         h = ctypes.c_void_p()
         dp = ctypes.POINTER(ctypes.c_double)
+        if (kappa is None) == (khat is None):
+            raise ValueError("give the spectrum as kappa or as khat")
+        th = None
+        if theta is not None:
+            th = np.ascontiguousarray(theta, dtype=np.float64)
+            if th.shape != (int(n_theta),):
+                raise ValueError("theta must hold n_theta colatitudes")
         if khat is not None:
             kh = [complex(v) for v in np.atleast_1d(khat)]
             re = np.ascontiguousarray([v.real for v in kh], dtype=np.float64)
             im = np.ascontiguousarray([v.imag for v in kh], dtype=np.float64)
-            _check("smerf_plan_create_khat",
-                   L.smerf_plan_create_khat(re.ctypes.data_as(dp), im.ctypes.data_as(dp), len(kh), float(A),
-                                            int(n_theta), int(n_phi), int(flags), int(anchor_spacing),
-                                            ctypes.byref(h)))
+            if th is None:
+                _check("smerf_plan_create_khat",
+                       L.smerf_plan_create_khat(re.ctypes.data_as(dp), im.ctypes.data_as(dp), len(kh), float(A),
+                                                int(n_theta), int(n_phi), int(flags), int(anchor_spacing),
+                                                ctypes.byref(h)))
+            else:
+                _check("smerf_plan_create_khat_theta",
+                       L.smerf_plan_create_khat_theta(re.ctypes.data_as(dp), im.ctypes.data_as(dp), len(kh),
+                                                      float(A), int(n_theta), th.ctypes.data_as(dp), int(n_phi),
+                                                      int(flags), int(anchor_spacing), ctypes.byref(h)))
             k = np.asarray(kh)
-        elif theta is not None:
+        elif th is not None:
             k = np.ascontiguousarray(np.atleast_1d(kappa), dtype=np.float64)
-            th = np.ascontiguousarray(theta, dtype=np.float64)
-            if th.shape != (int(n_theta),):
-                raise ValueError("theta must hold n_theta colatitudes")
             _check("smerf_plan_create_theta",
                    L.smerf_plan_create_theta(k.ctypes.data_as(dp), len(k), float(A), int(n_theta),
                                              th.ctypes.data_as(dp), int(n_phi), int(flags), int(anchor_spacing),

@@ -150,3 +150,45 @@ def test_batch_output_checks_without_gpu():
                 [torch.zeros(12, 2)[:, 0].as_subclass(Pinned), pin[1]]):           # not contiguous
         with pytest.raises(ValueError):
             _check_batch_outs(needs, bad)
+
+
+def test_khat_colatitude_validation_without_gpu(lib):
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.smerf_plan_create_khat_theta.restype = ctypes.c_int
+    out = ctypes.c_void_p()
+    good = [np.pi * (k + 0.5) / 8 for k in range(8)]
+
+    def call(re, im, theta):
+        r = np.ascontiguousarray(re, dtype=np.float64)
+        i = np.ascontiguousarray(im, dtype=np.float64)
+        t = None if theta is None else np.ascontiguousarray(theta, dtype=np.float64)
+        return lib.smerf_plan_create_khat_theta(r.ctypes.data_as(dp), i.ctypes.data_as(dp), len(re),
+                                                ctypes.c_double(1.0), 8, None if t is None else t.ctypes.data_as(dp),
+                                                32, ctypes.c_uint(0), 0, ctypes.byref(out))
+    assert call([0.0, 0.0], [3.0, -3.0], None) == -1               # no colatitudes
+    assert call([0.0, 0.0], [3.0, -3.0], good[::-1]) == -1         # decreasing
+    assert call([0.0, 0.0], [3.0, -3.0], good[:-1] + [np.pi]) == -1  # a pole ring
+    assert call([4.0], [0.0], good[:-1] + [np.pi]) == -1           # real kappa-hat: the same rules
+    assert call([0.0, 0.0], [3.0, 2.0], good) == -1                # not a conjugate pair
+    assert not out.value
+
+
+def test_plan_spectrum_arguments_without_gpu(lib):
+    from paper_1709_10314_gb300 import Plan
+    with pytest.raises(ValueError):
+        Plan(A=1.0, n_theta=8, n_phi=32)                             # no spectrum
+    with pytest.raises(ValueError):
+        Plan([3.0], 1.0, 8, 32, khat=[9.0])                          # two spectra
+    with pytest.raises(ValueError):
+        Plan([3.0], 1.0, 8, 32, theta=[0.5, 1.0, 1.5])               # not n_theta colatitudes
+
+
+def test_plan_colatitudes_through_the_binding_without_gpu(lib):
+    """The binding's calls of the two colatitude entry points marshal their arguments; the
+    library rejects the colatitudes before it touches a GPU."""
+    from paper_1709_10314_gb300 import Plan, SmerfError
+    bad = [0.5, 0.4, 1.0, 1.5]                                        # not increasing
+    for kw in (dict(kappa=[3.0]), dict(khat=[complex(0, 3), complex(0, -3)]), dict(khat=[9.0])):
+        with pytest.raises(SmerfError) as e:
+            Plan(A=1.0, n_theta=4, n_phi=32, theta=bad, **kw)
+        assert e.value.status == -1

@@ -86,3 +86,39 @@ def test_rejects_other_complex_patterns():
     for bad in ([complex(1, 2), complex(1, 3)], [complex(1, 2), complex(2, -2)], [complex(0, 1)]):
         with pytest.raises(SmerfError):
             Plan(A=1.0, n_theta=16, n_phi=32, khat=bad)
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+@pytest.mark.parametrize("khat,grid,n_phi,H", [
+    (SEC5, "healpix3", 16, 3),      # the Sec. 5 spectrum at the Nside 3 HEALPix colatitudes
+    (PAIR, "band", 64, 0),          # a pair on a band that straddles the equator unevenly
+    (SEC5_REAL, "band", 32, 4),     # p = 3: the pair and a real factor
+])
+def test_complex_kappa_hat_at_given_colatitudes(fp64, khat, grid, n_phi, H):
+    """smerf_plan_create_khat_theta: complex kappa-hat on the rings of another iso-latitude grid
+    (the set-up's complex construction at the given colatitudes) against the oracle."""
+    import torch
+    from paper_1709_10314_gb300 import SMERF_ORDER_PAPER, SMERF_RECUR_FP64, Plan
+    if grid == "healpix3":
+        from test_oracle_healpix import healpix_rings
+        theta = list(healpix_rings(3)[0])
+    else:
+        theta = [0.35, 0.6, 0.8, 1.05, 1.3, 1.62, 1.8, 2.05, 2.4, 2.6, 2.9]
+    nt = len(theta)
+    flags = (SMERF_RECUR_FP64 if fp64 else 0) | (SMERF_ORDER_PAPER if H == 0 else 0)
+    plan = Plan(A=1.0, n_theta=nt, n_phi=n_phi, flags=flags, anchor_spacing=H, khat=list(khat), theta=theta)
+    got = plan.sample(6, 2).double().cpu().numpy()
+    torch.cuda.synchronize()
+    ref = oracle.sample(oracle.KHat(khat), 1.0, nt, n_phi, 6, 2, H=H, theta=theta)
+    err = rel_err(got, ref, float(np.std(ref)))
+    print("khat at colatitudes %s p=%d fp64=%s: %.2e" % (grid, len(khat), fp64, err))
+    assert err < (1e-9 if fp64 else 1e-4)
+
+
+def test_real_kappa_hat_at_given_colatitudes_is_the_kappa_plan():
+    import torch
+    from paper_1709_10314_gb300 import Plan
+    theta = [0.3, 0.55, 0.9, 1.2, 1.45, 1.7, 2.0]
+    a = Plan(A=1.0, n_theta=7, n_phi=32, anchor_spacing=3, khat=[400.0, 2500.0], theta=theta)
+    b = Plan([20.0, 50.0], 1.0, 7, 32, anchor_spacing=3, theta=theta)
+    assert torch.equal(a.sample(4, 2), b.sample(4, 2))
