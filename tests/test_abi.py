@@ -192,3 +192,53 @@ def test_plan_colatitudes_through_the_binding_without_gpu(lib):
         with pytest.raises(SmerfError) as e:
             Plan(A=1.0, n_theta=4, n_phi=32, theta=bad, **kw)
         assert e.value.status == -1
+
+
+def test_null_handles_and_empty_calls_without_gpu(lib):
+    """Every entry point that takes a plan or a batch answers SMERF_EINVAL for a NULL handle, and
+    the empty calls are no-ops, before any CUDA call."""
+    V = ctypes.c_void_p
+    null = V()
+    for fn, args in [
+        ("smerf_sample", (null, ctypes.c_uint64(0), 1, null, null)),
+        ("smerf_sample_timed", (null, ctypes.c_uint64(0), 1, null, null, null, null)),
+        ("smerf_sample_host", (null, ctypes.c_uint64(0), 1, null, null)),
+        ("smerf_sample_noalloc", (null, ctypes.c_uint64(0), 1, null, null)),
+        ("smerf_sample_batched", (null, null, null, null, 1, null)),
+        ("smerf_plan_info", (null, null)),
+        ("smerf_plan_set_rings", (null, null, null)),
+        ("smerf_plan_autotune", (null, 1, null, null)),
+        ("smerf_plan_set_launch", (null, null)),
+        ("smerf_plan_launch_candidates", (null, null, 0)),
+        ("smerf_plan_copy_tables", (null, 0, 0, 0, null)),
+        ("smerf_plan_create_many", (null, 1, null)),
+        ("smerf_batch_create", (null, null, 1, ctypes.byref(V()))),
+        ("smerf_batch_create", (null, null, 0, null)),
+        ("smerf_batch_set", (null, null, null)),
+        ("smerf_batch_launch", (null, null)),
+        ("smerf_batch_sample", (null, null, null, null)),
+        ("smerf_batch_info", (null, null, null)),
+        ("smerf_batch_launch_count", (null,)),
+        ("smerf_batch_status", (null, null)),
+        ("smerf_batch_set_single_launch", (null, 0)),
+        ("smerf_debug_batch_fail_waits", (null,)),
+        ("smerf_philox_uint32", (ctypes.c_uint64(0), 0, ctypes.c_int64(-1), null, null)),
+        ("smerf_ring_normals", (ctypes.c_uint64(0), 0, ctypes.c_int64(-1), 0, null, null)),
+    ]:
+        f = getattr(lib, fn)
+        f.restype = ctypes.c_int
+        assert f(*args) == -1, fn
+    chosen = ctypes.c_int(7)
+    cand = (ctypes.c_int * 1)(8)
+    lib.smerf_plan_autotune_anchor.restype = ctypes.c_int
+    assert lib.smerf_plan_autotune_anchor(null, 1, cand, 1, null, ctypes.byref(chosen)) == -1 and chosen.value == 0
+    for fn, args in [
+        ("smerf_sample_batched", (null, null, null, null, 0, null)),   # no requests
+        ("smerf_plan_create_many", (null, 0, null)),                   # no plans
+        ("smerf_batch_destroy", (null,)),
+        ("smerf_philox_uint32", (ctypes.c_uint64(0), 0, ctypes.c_int64(0), null, null)),
+        ("smerf_ring_normals", (ctypes.c_uint64(0), 0, ctypes.c_int64(0), 0, null, null)),
+    ]:
+        f = getattr(lib, fn)
+        f.restype = ctypes.c_int
+        assert f(*args) == 0, fn
