@@ -12,6 +12,9 @@
  * sampled ring by ring outward from the equator (Eqs. (state_space), (state_initial),
  * Alg. 2) and synthesised per ring by a real inverse DFT with prefactor 1:
  *     T(theta_k, phi_j) = g_0 + 2 sum_{0<m<n_phi/2} Re(g_m e^{i m phi_j}) + Re(g_{n_phi/2}) (-1)^j.
+ * Other iso-latitude grids: rings at given colatitudes (smerf_plan_create_theta,
+ * smerf_plan_create_khat_theta; HEALPix rings, latitude bands) and ring-dependent longitudes
+ * (smerf_plan_set_rings).
  *
  * Conventions shared by every entry point
  *  - All calls return an int status (SMERF_OK or a negative SMERF_E* code); none aborts,
