@@ -103,8 +103,8 @@ def test_khat_validation_without_gpu(lib):
 
 
 def test_colatitude_validation_without_gpu(lib):
-    """smerf_plan_create_theta rejects colatitudes that are not increasing inside (0, pi) and
-    symmetric about the equator before it touches a GPU."""
+    """smerf_plan_create_theta rejects colatitudes that are not finite and strictly increasing
+    inside (0, pi), and bad spectra, before it touches a GPU."""
     dp = ctypes.POINTER(ctypes.c_double)
     lib.smerf_plan_create_theta.restype = ctypes.c_int
     out = ctypes.c_void_p()
