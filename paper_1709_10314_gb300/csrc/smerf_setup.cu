@@ -1016,8 +1016,7 @@ __global__ void start_kernel_c(SpecC sp, void* beq, bool tab64)
 // host: the complex spectrum's constants
 static SpecC make_spec_c(const smerf_plan* pl)
 {
-    SpecC sc;
-    memset(&sc, 0, sizeof(sc));
+    SpecC sc = SpecC();  // value-initialised: every member zero
     const int M = pl->p;
     sc.A = pl->A;
     sc.kmax = 0.0;
