@@ -354,6 +354,9 @@ class Plan:
         if out is None:
             shape = (n_samples, self.points) if self.ring_points else (n_samples, self.n_theta, self.n_phi)
             out = np.empty(shape, dtype=dt)
+        if int(n_samples) < 0:
+            raise ValueError("n_samples must be >= 0")
+        _check_host_out(out, dt, self.dtype, int(n_samples) * self.points)
         ptr = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
         _check("smerf_sample_host", _lib().smerf_sample_host(self._h, ctypes.c_uint64(seed & (2**64 - 1)),
                                                               int(n_samples), ctypes.c_void_p(ptr),
@@ -401,6 +404,31 @@ def debug_fail_alloc(k):
 def scratch_trim():
     """smerf_scratch_trim: release the idle memory of the per-call scratch pool (current device)."""
     _check("smerf_scratch_trim", _lib().smerf_scratch_trim())
+
+
+def _check_host_out(out, np_dtype, torch_dtype, need):
+    """The C ABI cannot see a buffer's length: a host output is a writeable C-contiguous numpy
+    array of np_dtype, or a contiguous CPU torch tensor of torch_dtype, holding at least `need`
+    elements; else ValueError."""
+    import torch
+    if isinstance(out, np.ndarray):
+        if out.dtype != np_dtype:
+            raise ValueError("out has dtype %s; this plan writes %s" % (out.dtype, np.dtype(np_dtype)))
+        if not out.flags["C_CONTIGUOUS"] or not out.flags["WRITEABLE"]:
+            raise ValueError("out must be a writeable C-contiguous array")
+        n = out.size
+    elif isinstance(out, torch.Tensor):
+        if out.is_cuda:
+            raise ValueError("out is a CUDA tensor; sample() writes device memory")
+        if out.dtype != torch_dtype:
+            raise ValueError("out has dtype %s; this plan writes %s" % (out.dtype, torch_dtype))
+        if not out.is_contiguous():
+            raise ValueError("out must be contiguous")
+        n = out.numel()
+    else:
+        raise ValueError("out must be a numpy array or a CPU torch tensor")
+    if n < need:
+        raise ValueError("out holds %d elements; the realisations need %d" % (n, need))
 
 
 def _batch_needs(plans, n_samples):

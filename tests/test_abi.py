@@ -242,3 +242,18 @@ def test_null_handles_and_empty_calls_without_gpu(lib):
         f = getattr(lib, fn)
         f.restype = ctypes.c_int
         assert f(*args) == 0, fn
+
+
+def test_host_output_checks_without_gpu():
+    """sample_host's buffer check: dtype, layout, writeability, memory kind and length."""
+    import torch
+    from paper_1709_10314_gb300.smerf import _check_host_out
+    f32 = (np.float32, torch.float32, 12)
+    _check_host_out(np.zeros(12, dtype=np.float32), *f32)
+    _check_host_out(torch.zeros(3, 4), *f32)
+    ro = np.zeros(12, dtype=np.float32)
+    ro.flags.writeable = False
+    for bad in (np.zeros(12), np.zeros(11, dtype=np.float32), np.zeros((12, 2), dtype=np.float32)[:, 0], ro,
+                torch.zeros(12, dtype=torch.float64), torch.zeros(11), torch.zeros(12, 2)[:, 0], [0.0] * 12):
+        with pytest.raises(ValueError):
+            _check_host_out(bad, *f32)
