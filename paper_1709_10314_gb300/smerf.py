@@ -207,6 +207,8 @@ class Plan:
             _check("smerf_plan_set_rings", _lib().smerf_plan_set_rings(self._h, None, None))
             self.ring_points = None
             return
+        if len(n_phi_ring) != self.n_theta or (phi0_ring is not None and len(phi0_ring) != self.n_theta):
+            raise ValueError("one point count (and one offset) per ring: %d rings" % self.n_theta)
         n = (ctypes.c_int * self.n_theta)(*[int(v) for v in n_phi_ring])
         p0 = None if phi0_ring is None else (ctypes.c_double * self.n_theta)(*[float(v) for v in phi0_ring])
         _check("smerf_plan_set_rings", _lib().smerf_plan_set_rings(self._h, n, p0))

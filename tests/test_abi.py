@@ -257,3 +257,16 @@ def test_host_output_checks_without_gpu():
                 torch.zeros(12, dtype=torch.float64), torch.zeros(11), torch.zeros(12, 2)[:, 0], [0.0] * 12):
         with pytest.raises(ValueError):
             _check_host_out(bad, *f32)
+
+
+def test_ring_layout_lengths_without_gpu():
+    """set_rings takes one point count (and one offset) per ring; other lengths are refused before
+    the library is called."""
+    from paper_1709_10314_gb300 import Plan
+    pl = Plan.__new__(Plan)  # no device tables: the check comes first
+    pl.n_theta = 4
+    pl.ring_points = None
+    for args in (([8, 8, 8],), ([8] * 5,), ([8] * 4, [0.0] * 3)):
+        with pytest.raises(ValueError):
+            pl.set_rings(*args)
+    assert pl.ring_points is None
